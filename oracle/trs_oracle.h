@@ -1,0 +1,131 @@
+/*
+ * trs_oracle.h -- plain FP64 CPU oracle for the CPR-FPF preconditioned FGMRES
+ * solve of one Newton-step block Jacobian of a thermal reservoir model
+ * (Liu & Chen, arXiv 1812.03952).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two are written
+ * independently from the paper and from the readings listed with each
+ * function in trs_oracle.c.
+ *
+ * Matrices are general block CSR ("BSR"): n block rows, b x b blocks stored
+ * row-major, rp[n+1] (int64) row pointers, col[nnzb] (int32) sorted column
+ * indices, val[nnzb*b*b].  Vectors hold n*b doubles, block by block.
+ *
+ * Return codes: 0 = success, 1 = not converged, -1 = invalid input,
+ * -2 = singular block / matrix, -3 = coarsening stalled, -4 = out of memory,
+ * -5 = too many colours.
+ */
+#ifndef TRS_ORACLE_H
+#define TRS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- synthetic Jacobian assembly (TPFA stencil + Peaceman-type wells) ---- */
+int64_t orc_assembly_nnzb(int nx, int ny, int nz, int nw, int64_t np,
+                          const int32_t *perf_well, const int32_t *perf_cell);
+int orc_assemble(int nx, int ny, int nz, int b, const double *k, double kvkh, double c_t,
+                 const double *M, const double *acc, int nw, int64_t np,
+                 const int32_t *perf_well, const int32_t *perf_cell, const double *wi,
+                 const double *lam, int64_t *rp, int32_t *col, double *val);
+
+/* ---- block sparse kernels ---- */
+void orc_bsr_spmv(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                  const double *x, double *y, double alpha, double beta);
+void orc_bsr_spmv_t(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                    const double *x, double *y, double alpha, double beta);
+int orc_bsr_transpose(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                      int64_t *rpT, int32_t *colT, double *valT);
+int orc_pattern_symmetric(int64_t n, const int64_t *rp, const int32_t *col);
+
+/* ---- decoupling ---- */
+int orc_gj_inverse(int b, const double *D, double *inv);
+int orc_decouple(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                 double *vt, double *dinv);
+void orc_pressure_matrix(int64_t n, int b, const int64_t *rp, const int32_t *col,
+                         const double *vt, double *ap);
+
+/* ---- aggregation AMG on a scalar CSR matrix ---- */
+int64_t orc_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                     double theta, int64_t *srp, int32_t *scol);
+int orc_mis2(int64_t n, const int64_t *srp, const int32_t *scol, uint32_t seed, int8_t *state);
+int64_t orc_aggregate(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                      const int64_t *srp, const int32_t *scol, const int8_t *state, int32_t *agg);
+int64_t orc_galerkin_nnz(int64_t n, const int64_t *rp, const int32_t *col, const int32_t *agg,
+                         int64_t n_agg);
+void orc_galerkin(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                  const int32_t *agg, int64_t n_agg, int64_t *crp, int32_t *ccol, double *cval);
+double orc_gershgorin(int64_t n, const int64_t *rp, const int32_t *col, const double *val);
+void orc_chebyshev(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                   double lam_max, int degree, const double *r, double *e, int zero_init);
+
+void *orc_amg_setup(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                    double theta, int coarse_max, int max_levels, int cheb_degree, uint32_t seed,
+                    int *status);
+int orc_amg_levels(const void *h);
+int64_t orc_amg_level_n(const void *h, int l);
+int64_t orc_amg_level_nnz(const void *h, int l);
+void orc_amg_level_copy(const void *h, int l, int64_t *rp, int32_t *col, double *val);
+void orc_amg_level_agg(const void *h, int l, int32_t *agg);
+double orc_amg_level_lambda(const void *h, int l);
+void orc_amg_vcycle(const void *h, const double *r, double *e);
+void orc_amg_free(void *h);
+
+/* ---- dense LU with partial pivoting ---- */
+int orc_dense_lu(int64_t n, double *a, int32_t *piv);
+void orc_dense_lu_solve(int64_t n, const double *lu, const int32_t *piv, double *x);
+
+/* ---- multicolouring and block ILU(0) ---- */
+int orc_colour_jp(int64_t n, const int64_t *rp, const int32_t *col, uint32_t seed, int32_t *colour);
+void *orc_bilu0_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *vt,
+                      const int32_t *colour, int *status);
+void orc_bilu0_solve(const void *h, const double *r, double *y);
+void orc_bilu0_factors(const void *h, double *F);
+void orc_bilu0_free(void *h);
+
+/* ---- CPR-FPF preconditioner and FGMRES ---- */
+typedef struct {
+  double theta;      /* AMG strength threshold */
+  int coarse_max;    /* stop coarsening at n <= coarse_max */
+  int max_levels;
+  int cheb_degree;
+  uint32_t seed;
+} orc_cpr_opts;
+
+void *orc_cpr_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                    const orc_cpr_opts *opts, int *status);
+void orc_cpr_apply(const void *h, const double *v, double *z);
+int orc_cpr_info(const void *h, int *n_levels, int *n_colours);
+const void *orc_cpr_amg(const void *h);
+void orc_cpr_colours(const void *h, int32_t *colour);
+void orc_cpr_decoupled(const void *h, double *vt, double *dinv);
+void orc_cpr_ilu_factors(const void *h, double *F);
+void orc_cpr_free(void *h);
+
+typedef struct {
+  int iters;
+  int restarts;
+  int converged;
+  double est_relres;
+  double true_relres;
+} orc_stats;
+
+int orc_fgmres(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+               const void *cpr, const double *rhs, double *x, double rtol, int restart, int maxit,
+               orc_stats *st, double *hist, int hist_cap);
+
+/* ---- adjoint ---- */
+void orc_outer_product(int64_t n, int b, const int64_t *rp, const int32_t *col,
+                       const double *lambda, const double *x, double *dA);
+int orc_chain_theta(int nx, int ny, int nz, int b, const double *k, double kvkh, double c_t,
+                    const double *M, const int64_t *rp, const int32_t *col, const double *dA,
+                    double *dtheta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
