@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of one Newton-step linear solve on a GB300.
+
+A step is one pass of the whole hot path over the 128x128x64, b = 4 synthetic
+thermal Jacobian (1,048,576 cells, 8 SAGD wells, 4,194,312 unknowns):
+transmissibility/Jacobian assembly on the GPU, full CPR-FPF setup (ABF
+decoupling, pressure AMG, colouring, block ILU(0)), and FGMRES(30) to a true
+FP64 relative residual of 1e-6 -- with the CPR stored and applied in FP32
+(the default) or FP64 (--precision fp64).  value = device milliseconds per
+step (lower is better), inputs resident in HBM.
+
+Multi-GPU: the path is one system per GPU ("replicas"); every rank solves its
+own copy and the step time is the maximum over ranks.
+
+--impl reference times the CPU oracle (plain C, FP64, single thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {"16x16x4_b4": 0, "128x128x64_b4": 1, "256x256x128_b5": 2, "64x64x32_b4": 3,
+             "512x256x64_b4": 4}
+METRIC = "CPR-FGMRES solve ms (assembly + CPR setup + FGMRES to true rel. res. 1e-6)"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="trs", choices=["trs", "reference"])
+    p.add_argument("--workload", default="128x128x64_b4", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--rtol", type=float, default=1e-6)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64-compare", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier_max(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------ oracle timing
+def oracle_sample(sysm, n_iter, iters_full):
+    """Times the CPU oracle on a bounded sample: assembly + CPR setup +
+    n_iter FGMRES iterations, extrapolated to iters_full iterations."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    Ao = O.assemble(sysm)
+    t1 = time.perf_counter()
+    cpr = O.CPR(Ao)
+    t2 = time.perf_counter()
+    res = O.fgmres(Ao, cpr, sysm.rhs, rtol=1e-30, maxit=n_iter)
+    t3 = time.perf_counter()
+    per_iter = (t3 - t2) / max(1, res.iters)
+    est_ms = 1e3 * ((t1 - t0) + (t2 - t1) + per_iter * iters_full)
+    return est_ms, {"assemble_s": t1 - t0, "setup_s": t2 - t1, "iter_s": per_iter, "iters_timed": res.iters,
+                    "wall_s": t3 - t0}
+
+
+# FGMRES iterations of the FP64 path on the 128x128x64 workload (the oracle
+# runs the same algorithm; used to scale the oracle's bounded sample).
+FULL_ITERS = {"128x128x64_b4": 30, "64x64x32_b4": 31, "16x16x4_b4": 18, "256x256x128_b5": 60,
+              "512x256x64_b4": 60}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1812_03952_gb300 import synthetic as S
+    sysm = S.config(WORKLOADS[args.workload])
+    n_iter = 1
+    times = []
+    detail = None
+    for step in range(args.warmup + args.steps):
+        est, detail = oracle_sample(sysm, n_iter, FULL_ITERS[args.workload])
+        if step >= args.warmup:
+            times.append(est)
+    value = statistics.median(times)
+    sample = (f"oracle assembly + CPR setup + {n_iter} FGMRES iteration on the full {args.workload} system, "
+              f"scaled to {FULL_ITERS[args.workload]} iterations")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "precision": "fp64 (CPU oracle)", "rtol": args.rtol},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample,
+                             "detail": detail},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1812_03952_gb300 import build as B
+    from paper_1812_03952_gb300 import synthetic as S
+    from paper_1812_03952_gb300 import trs
+
+    B.build()
+    trs.load()
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    sysm = S.config(WORKLOADS[args.workload])
+    ds = trs.DeviceSystem(sysm, dev)
+    A = ds.assemble()
+    M = trs.CPR(A, precision=args.precision)
+    x = torch.zeros_like(ds.rhs)
+    info = M.info()
+
+    def step():
+        ds.assemble()
+        M.update(A, reuse_amg=False)
+        _, res = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = trs.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            stats.append(r.stats)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches = trs.kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = barrier_max(ms, world)
+    last = stats[-1]
+    xt = x.cpu().numpy()
+
+    # true residual on the host as an independent check of the reported one
+    Aval = A.values()
+    rp, col = A.pattern()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    Ax = np.zeros_like(xt).reshape(-1, A.b)
+    np.add.at(Ax, rows, np.einsum("prc,pc->pr", Aval, xt.reshape(-1, A.b)[col]))
+    host_relres = float(np.linalg.norm(sysm.rhs - Ax.reshape(-1)) / np.linalg.norm(sysm.rhs))
+
+    # roofline of the operator block SpMV (FP64 values), timed alone
+    hbm, peak_kind = peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    xs = torch.randn(A.N, dtype=torch.float64, device=dev)
+    ys = torch.empty_like(xs)
+    durs = []
+    for it in range(23):
+        flush.fill_(float(it))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A.spmv(xs, ys)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 3:
+            durs.append(e0.elapsed_time(e1))
+    spmv_ms = statistics.median(durs)
+    spmv_bytes = A.nnzb * A.b * A.b * 8 + 2 * A.N * 8
+    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+
+    # FP64-preconditioner path on the same system, for the mixed/FP64 comparison
+    fp64 = None
+    if not args.no_fp64_compare and args.precision == "fp32":
+        M64 = trs.CPR(A, precision="fp64")
+        for _ in range(2):
+            ds.assemble()
+            M64.update(A, reuse_amg=False)
+            _, r64 = trs.fgmres_solve(A, M64, ds.rhs, x, rtol=args.rtol)
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(max(1, min(args.steps, 3))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ds.assemble()
+            M64.update(A, reuse_amg=False)
+            _, r64 = trs.fgmres_solve(A, M64, ds.rhs, x, rtol=args.rtol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        fp64 = {"ms_per_step": statistics.median(t64), "solve_ms": r64.stats["ms_solve"],
+                "setup_ms": r64.stats["ms_setup"], "iters": r64.stats["iters"],
+                "true_relres": r64.stats["true_relres"]}
+        del M64
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hk, hM, hacc, hwi, hlam, hb = (pin(sysm.k), pin(sysm.M.reshape(-1)), pin(sysm.acc.reshape(-1)),
+                                       pin(sysm.wi), pin(sysm.lam.reshape(-1)), pin(sysm.rhs))
+        hx = torch.empty(A.N, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * 8 for t in (hk, hM, hacc, hwi, hlam, hb))
+        d2h = hx.numel() * 8
+
+        def e2e_step():
+            for d, h in ((ds.k, hk), (ds.M, hM), (ds.acc, hacc), (ds.wi, hwi), (ds.lam, hlam),
+                         (ds.rhs, hb)):
+                d.copy_(h, non_blocking=True)
+            ds.assemble()
+            M.update(A, reuse_amg=False)
+            trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)
+            hx.copy_(x, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e = {"value": barrier_max(e0.elapsed_time(e1) / n_e2e, world), "unit": "ms",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, detail = oracle_sample(sysm, 1, last["iters"] if args.precision == "fp64" else
+                                    (fp64["iters"] if fp64 else FULL_ITERS[args.workload]))
+        cpu = {"value": est, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": "assembly + CPR setup + 1 FGMRES iteration of the FP64 oracle on the full system, "
+                         "scaled to the FP64 path's iteration count", "detail": detail}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
+                       "unknowns": sysm.n_unknowns,
+                       "precision": "FP32 CPR inside FP64 FGMRES" if args.precision == "fp32" else "FP64",
+                       "rtol": args.rtol, "restart": 30,
+                       "l2": "inputs larger than L2 (Jacobian inputs 0.9 GB, matrix 0.9 GB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iters": last["iters"], "true_relres": last["true_relres"], "host_true_relres": host_relres,
+            "breakdown_ms": {"setup": last["ms_setup"], "solve": last["ms_solve"]},
+            "amg_levels": info["n_levels"], "amg_rows": info["level_rows"], "n_colours": info["n_colours"],
+            "fp64_path": fp64,
+            "roofline": {"kernel": "k_spmv<4,double,double> (operator block SpMV)", "bound": "hbm",
+                         "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
+                         "traffic": None, "peak_kind": peak_kind, "launch_ms": spmv_ms,
+                         "algorithmic_bytes": spmv_bytes},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,279 @@
+/*
+ * trs.h -- C ABI of libtrs, a GB300 (sm_103a) solver for the block-sparse
+ * Jacobian systems of a fully implicit thermal reservoir model, after Liu &
+ * Chen, "A Scalable Thermal Reservoir Simulator for Giant Models on Parallel
+ * Computers" (arXiv 1812.03952).
+ *
+ * The system A x = b has b x b blocks numbered cell by cell with the well
+ * (bottom-hole-pressure) unknowns after the cells (Sec. "Linear Solver",
+ * Eq. mat-ja; Sec. "Linear System": well equations placed last).  A well's
+ * BHP is entry 0 of its padded b x b block; entries 1..b-1 of a well block
+ * are padding that the caller fills with an identity diagonal and zero RHS.
+ *
+ * The solve is restarted flexible GMRES, right-preconditioned by CPR-FPF
+ * (Sec. "Preconditioners", Algorithm pc-fpf) applied to the ABF-decoupled
+ * matrix D^-1 A (Sec. "Decoupling Methods", Eqs. decoupled-eq and
+ * decoupled-abf), with a pressure-AMG stage and a multicolour block ILU(0)
+ * "F" stage.  All arithmetic runs in CUDA kernels on the current device.
+ *
+ * Conventions for every entry point:
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is ordered on it.  Calls that return results to
+ *     the host synchronise that stream.
+ *   - "device pointer" arguments must point to memory of the current device,
+ *     "host pointer" arguments to host memory.  Vectors are FP64 arrays of
+ *     n_block_rows * b entries, block by block, owned by the caller.
+ *   - Handles (trs_bsr, trs_cpr) are owned by the library and released with
+ *     the matching *_destroy call.
+ *   - Every call returns a trs_status; no exception, abort or device trap
+ *     crosses the boundary.  trs_last_error() returns a thread-local
+ *     message describing the last failure.
+ */
+#ifndef TRS_H
+#define TRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t trs_status;
+
+#define TRS_OK 0
+#define TRS_ERR_INVALID (-1)          /* bad argument or malformed matrix */
+#define TRS_ERR_OOM (-2)              /* device allocation failed */
+#define TRS_ERR_CUDA (-3)             /* CUDA runtime error */
+#define TRS_ERR_SINGULAR_BLOCK (-4)   /* a diagonal block (or ILU pivot block) is singular */
+#define TRS_ERR_NAN (-5)              /* NaN or Inf met in a residual norm */
+#define TRS_ERR_NOT_CONVERGED (-6)    /* iteration limit reached; stats and x hold the last iterate */
+#define TRS_ERR_BREAKDOWN (-7)        /* Krylov breakdown without convergence */
+#define TRS_ERR_COARSENING (-8)       /* AMG coarsening stalled above the dense limit */
+#define TRS_ERR_UNSUPPORTED (-9)      /* block size or option outside the supported set */
+
+/* Preconditioner precision. */
+#define TRS_FP64 0          /* everything in FP64 */
+#define TRS_FP32_PREC 1     /* CPR stored and applied in FP32; Krylov basis, residuals,
+                               Givens/least squares and the coarsest LU stay FP64 */
+
+typedef struct trs_bsr trs_bsr;
+typedef struct trs_cpr trs_cpr;
+
+typedef struct {
+  int32_t precision;     /* TRS_FP64 or TRS_FP32_PREC */
+  double theta;          /* AMG strength threshold (default 0.08) */
+  int32_t coarse_max;    /* stop coarsening at <= coarse_max rows (default 1024) */
+  int32_t max_levels;    /* default 12 */
+  int32_t cheb_degree;   /* Chebyshev smoother degree (default 2) */
+  uint32_t seed;         /* seed of the MIS-2 and colouring priorities */
+} trs_cpr_opts;
+
+typedef struct {
+  double rtol;           /* stop when ||b - A x||_2 <= rtol ||b||_2 (true FP64 residual) */
+  int32_t restart;       /* Krylov subspace size per cycle, 1..64 (default 30) */
+  int32_t maxit;         /* total iteration limit (default 1000) */
+  int32_t use_x0;        /* 1: x holds the initial guess; 0: start from x = 0 */
+} trs_solve_opts;
+
+typedef struct {
+  int32_t iters;         /* Arnoldi steps */
+  int32_t restarts;      /* cycles after the first */
+  int32_t converged;
+  int32_t amg_levels;
+  int32_t n_colours;
+  double est_relres;     /* |g_{j+1}| / ||b|| at the last step */
+  double true_relres;    /* ||b - A x|| / ||b|| of the returned x, FP64 */
+  double ms_setup;       /* device time of the last trs_cpr_setup/update */
+  double ms_solve;       /* device time of this solve */
+} trs_solve_stats;
+
+typedef struct {
+  int64_t n_block_rows;
+  int32_t b;
+  int64_t nnzb;
+  int64_t n_cells;       /* rows on the structured 7-point grid (0 if none) */
+  int32_t grid[3];
+} trs_bsr_info;
+
+typedef struct {
+  int32_t n_levels;
+  int32_t n_colours;
+  int32_t precision;
+  int64_t level_rows[16];
+  int64_t level_nnz[16];
+  double level_lambda[16]; /* Gershgorin bound of D^-1 A per level */
+} trs_cpr_info;
+
+/* ------------------------------------------------------------------ matrix */
+
+/* Creates a device block matrix from a general BSR on the host.
+ * n_block_rows, b: block rows and block size (b in 1..5).
+ * row_ptr[n_block_rows+1] (int64), col_idx[nnzb] (int32): host pointers;
+ *   columns sorted and unique in each row, every row holds its diagonal
+ *   block, the block pattern is structurally symmetric.
+ * values: host pointer to nnzb*b*b doubles, each block row-major, or NULL
+ *   (zeros; fill later with trs_bsr_update_values).
+ * grid_dims: host pointer to {nx, ny, nz} when the first nx*ny*nz rows are
+ *   the cells of a structured grid (cell c = x + nx*(y + ny*z)) whose
+ *   couplings are the 7-point neighbours; other blocks (wells) go to a
+ *   general tail.  NULL: every row is stored in the general form.
+ * Errors: TRS_ERR_INVALID (checked on the host before any upload),
+ *   TRS_ERR_UNSUPPORTED, TRS_ERR_OOM, TRS_ERR_CUDA.  Inputs stay caller-owned. */
+trs_status trs_bsr_create(int64_t n_block_rows, int32_t b, const int64_t *row_ptr,
+                          const int32_t *col_idx, const double *values, const int32_t *grid_dims,
+                          void *stream, trs_bsr **out);
+
+/* Creates the block pattern of the synthetic thermal Jacobian: an nx*ny*nz
+ * grid with the 7-point two-point-flux stencil (Sec. "Numerical Methods"),
+ * plus n_wells well rows coupled to their perforated cells (Sec. "Well
+ * Modeling").  perf_well[n_perf], perf_cell[n_perf]: host pointers; a well
+ * perforates a cell at most once.  Values are zero until trs_bsr_assemble. */
+trs_status trs_bsr_create_synthetic(int32_t nx, int32_t ny, int32_t nz, int32_t b, int32_t n_wells,
+                                    int64_t n_perf, const int32_t *perf_well,
+                                    const int32_t *perf_cell, void *stream, trs_bsr **out);
+
+/* Assembles the values of a matrix made by trs_bsr_create_synthetic.
+ * perm: device pointer, n_cells doubles: permeability k (mD) if
+ *   perm_is_log == 0, else theta = ln k.
+ * T_f = c_t * 2 k_i k_j / (k_i + k_j) on every internal face (k scaled by
+ *   kvkh on z faces; T_f = 0 when k_i + k_j = 0): harmonic mean of Sec.
+ *   "Numerical Methods".  M: device, [n_cells][6][b][b] mobility block of
+ *   each directed face (directions -z,-y,-x,+x,+y,+z).  acc: device,
+ *   [n_cells][b][b].  A_ij = -T_f M_ij; A_ii = acc_i + sum_j T_f M_ij
+ *   + well terms.  wi: device [n_perf]; lam: device [n_perf][b].
+ *   Peaceman rate (Eq. well-model): cell row c gets +wi*lam[r] in its own
+ *   pressure column and -wi*lam[r] in the well's BHP column; well row
+ *   (fixed-rate form sum_m Q_m = c) gets sum_m wi_m*Lam_m on its diagonal
+ *   and -wi_m*Lam_m in column (c_m, 0), Lam_m = sum_r lam_m[r]. */
+trs_status trs_bsr_assemble(trs_bsr *A, const double *perm, int32_t perm_is_log, double kvkh,
+                            double c_t, const double *M, const double *acc, const double *wi,
+                            const double *lam, void *stream);
+
+/* Replaces all values.  values: nnzb*b*b doubles in the matrix's canonical
+ * BSR order (rows ascending, columns ascending; the order of trs_bsr_pattern),
+ * on the device if values_on_device, else on the host. */
+trs_status trs_bsr_update_values(trs_bsr *A, const double *values, int32_t values_on_device,
+                                 void *stream);
+
+/* Copies the values out in canonical BSR order (device or host pointer). */
+trs_status trs_bsr_get_values(const trs_bsr *A, double *values, int32_t values_on_device,
+                              void *stream);
+
+/* Multiplies every diagonal block by a per-row factor: A_ii <- s_i A_ii.
+ * s: device pointer, n_block_rows doubles. */
+trs_status trs_bsr_scale_diagonal(trs_bsr *A, const double *s, void *stream);
+
+/* Pattern of the canonical BSR order: row_ptr[n+1], col_idx[nnzb] (host). */
+trs_status trs_bsr_pattern(const trs_bsr *A, int64_t *row_ptr, int32_t *col_idx);
+trs_status trs_bsr_get_info(const trs_bsr *A, trs_bsr_info *info);
+
+/* y = alpha * op(A) x + beta * y, op = transpose ? A^T : A; x, y: device
+ * pointers, FP64.  The product with A is the block SpMV of the Krylov
+ * operator (sparse BLAS of Sec. "Linear Solver"); A^T is a gather of the
+ * transposed blocks (no explicit transpose is formed). */
+trs_status trs_bsr_spmv(const trs_bsr *A, double alpha, const double *x, double beta, double *y,
+                        int32_t transpose, void *stream);
+
+/* Forms A^T explicitly as a new matrix (blocks transposed). */
+trs_status trs_bsr_transpose(const trs_bsr *A, void *stream, trs_bsr **out);
+
+void trs_bsr_destroy(trs_bsr *A);
+
+/* ---------------------------------------------------------- preconditioner */
+
+/* Fills *opts with the defaults (FP64, theta 0.08, coarse_max 1024, 12 levels,
+ * Chebyshev degree 2). */
+void trs_cpr_default_opts(trs_cpr_opts *opts);
+
+/* Builds CPR-FPF for A: ABF decoupling D_i = A_ii inverted by Gauss-Jordan
+ * with row pivoting (GJE), Ã = D^-1 A; pressure matrix A_p = (Ã_ij)_00;
+ * aggregation AMG of A_p (strength, MIS-2, unsmoothed aggregates, Galerkin
+ * P^T A P, Chebyshev smoothing, dense LU at the coarsest level);
+ * Jones-Plassmann multicolouring and block ILU(0) of Ã.  The handle keeps a
+ * reference to nothing of A; A may change afterwards (see trs_cpr_update).
+ * Errors: TRS_ERR_SINGULAR_BLOCK, TRS_ERR_COARSENING, TRS_ERR_INVALID,
+ * TRS_ERR_OOM, TRS_ERR_CUDA. */
+trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *stream,
+                         trs_cpr **out);
+
+/* Refreshes M for new values of A with the same pattern.  reuse_amg = 1
+ * keeps the AMG hierarchy (aggregates and coarse operators) and rebuilds
+ * the decoupling, the level-0 pressure matrix and the ILU(0) factors;
+ * reuse_amg = 0 rebuilds everything. */
+trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void *stream);
+
+/* z = M^-1 v = CPR(Ã)^-1 (D^-1 v): one application of the preconditioner
+ * (device pointers, FP64; computed in the handle's precision). */
+trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *stream);
+
+trs_status trs_cpr_get_info(const trs_cpr *M, trs_cpr_info *info);
+
+/* Setup objects copied to host memory, for inspection and tests:
+ * aggregates of level l (n_l int32, -1 = not aggregated); colours
+ * (n_block_rows int32); decoupled blocks Ã in canonical BSR order and
+ * D^-1 (n_block_rows*b*b), FP64; level-l pressure operator in CSR
+ * (row_ptr n_l+1 int64, col nnz int32, val nnz double). */
+trs_status trs_cpr_get_aggregates(const trs_cpr *M, int32_t level, int32_t *agg);
+trs_status trs_cpr_get_colours(const trs_cpr *M, int32_t *colour);
+trs_status trs_cpr_get_decoupled(const trs_cpr *M, double *vt, double *dinv);
+trs_status trs_cpr_get_level(const trs_cpr *M, int32_t level, int64_t *row_ptr, int32_t *col,
+                             double *val);
+
+/* Applies one AMG V-cycle of the pressure hierarchy to r (device pointers,
+ * n_0 doubles): e = AMG(A_p)^-1 r. */
+trs_status trs_cpr_vcycle(const trs_cpr *M, const double *r, double *e, void *stream);
+
+void trs_cpr_destroy(trs_cpr *M);
+
+/* ------------------------------------------------------------------ solves */
+
+void trs_solve_default_opts(trs_solve_opts *opts);
+
+/* Solves A x = b by FGMRES(restart) right-preconditioned with M (built from
+ * A).  b, x: device pointers.  Convergence is decided on the true FP64
+ * residual.  TRS_ERR_NOT_CONVERGED still fills stats and leaves the last
+ * iterate in x. */
+trs_status trs_fgmres_solve(const trs_bsr *A, const trs_cpr *M, const double *b, double *x,
+                            const trs_solve_opts *opts, void *stream, trs_solve_stats *stats);
+
+/* The same solve with b and x in host memory; the copies are part of the
+ * call. */
+trs_status trs_fgmres_solve_host(const trs_bsr *A, const trs_cpr *M, const double *b_host,
+                                 double *x_host, const trs_solve_opts *opts, void *stream,
+                                 trs_solve_stats *stats);
+
+/* Adjoint of x = A^-1 b for a loss L(x) with g = dL/dx: solves
+ * A^T lambda = g with FGMRES and M_T (a CPR built on A^T, e.g. from
+ * trs_bsr_transpose), so dL/db = lambda; if dA is not NULL it receives
+ * dL/dA_ij = -lambda_i x_j^T for every stored block in canonical BSR
+ * order.  g, x, lambda, dA: device pointers. */
+trs_status trs_solve_adjoint(const trs_bsr *A, const trs_bsr *AT, const trs_cpr *M_T,
+                             const double *g, const double *x, double *lambda, double *dA,
+                             const trs_solve_opts *opts, void *stream, trs_solve_stats *stats);
+
+/* dA = -lambda_i x_j^T on every stored block (canonical order). */
+trs_status trs_outer_product(const trs_bsr *A, const double *lambda, const double *x, double *dA,
+                             void *stream);
+
+/* Gradient of L with respect to theta = ln k for a matrix assembled by
+ * trs_bsr_assemble with the same perm/kvkh/c_t/M:
+ *   dL/dT_f = lambda_i^T M_if (x_j - x_i) + lambda_j^T M_jf' (x_i - x_j),
+ *   dL/dtheta_i = sum_f dL/dT_f T_f k_j / (k_i + k_j).
+ * (the outer product -lambda x^T contracted with dA/dT_f, formed without
+ * storing dA).  dtheta: device pointer, n_cells doubles (overwritten). */
+trs_status trs_chain_theta(const trs_bsr *A, const double *perm, int32_t perm_is_log,
+                           double kvkh, double c_t, const double *M, const double *lambda,
+                           const double *x, double *dtheta, void *stream);
+
+/* --------------------------------------------------------------- misc */
+const char *trs_last_error(void);
+const char *trs_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads), for accounting of launch counts. */
+uint64_t trs_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

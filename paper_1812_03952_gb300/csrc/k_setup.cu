@@ -1,0 +1,1213 @@
+// Setup-phase kernels: value layout, synthetic assembly, ABF/GJE decoupling,
+// pressure extraction, aggregation AMG setup, multicolouring and block ILU(0)
+// factorisation.
+//
+// This translation unit is compiled with -fmad=false: every a*b+c is a
+// rounded product followed by a rounded sum, divisions and square roots are
+// IEEE, and every sum runs in the order stated next to it, so the integer
+// decisions taken from these values (strong connections, MIS-2, aggregates,
+// colours) are reproducible bit for bit by any implementation of the same
+// definitions.
+#include <algorithm>
+
+#include "trs_kernels.cuh"
+
+namespace trs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+inline unsigned grid_of(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// murmur3 32-bit finaliser (Appleby, MurmurHash3 "fmix32"): a reproducible
+// pseudo-random priority for every node.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint64_t node_key(int64_t i, uint32_t seed) {
+  return ((uint64_t)fmix32((uint32_t)i ^ seed) << 32) | (uint64_t)(uint32_t)i;
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kThreads * kScanItems;
+
+__global__ void k_scan_reduce(const int64_t *in, int64_t n, int64_t *bsum) {
+  __shared__ int64_t sm[kWarps];
+  int64_t base = (int64_t)blockIdx.x * kScanChunk, s = 0;
+  for (int k = threadIdx.x; k < kScanChunk; k += kThreads) {
+    int64_t i = base + k;
+    if (i < n) s += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kWarps; w++) t += sm[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_scan_bsums(int64_t *bsum, int64_t nb, int64_t *total) {
+  if (threadIdx.x != 0) return;
+  int64_t run = 0;
+  for (int64_t b = 0; b < nb; b++) {
+    int64_t v = bsum[b];
+    bsum[b] = run;
+    run += v;
+  }
+  if (total) *total = run;
+}
+
+__global__ void k_scan_apply(const int64_t *in, int64_t *out, int64_t n, const int64_t *bsum) {
+  __shared__ int64_t wsum[kWarps];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + k;
+    v[k] = i < n ? in[i] : 0;
+    s += v[k];
+  }
+  // exclusive scan of per-thread sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int64_t woff = 0;
+  for (int w = 0; w < warp; w++) woff += wsum[w];
+  int64_t run = bsum[blockIdx.x] + woff + incl - s;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int64_t i = base + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+}
+
+// ------------------------------------------------------- value layout
+__global__ void k_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval, int64_t nc,
+                                 double *ell, double *tval) {
+  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (idx >= nnzb * bb) return;
+  const int64_t p = idx / bb, e = idx % bb, loc = map[p];
+  if (loc < kSlots * nc) {
+    const int64_t s = loc / nc, row = loc % nc;
+    ell[(s * bb + e) * nc + row] = uval[idx];
+  } else {
+    tval[(loc - kSlots * nc) * bb + e] = uval[idx];
+  }
+}
+
+__global__ void k_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell,
+                                const double *tval, int64_t nc, double *uval) {
+  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (idx >= nnzb * bb) return;
+  const int64_t p = idx / bb, e = idx % bb, loc = map[p];
+  if (loc < kSlots * nc) {
+    const int64_t s = loc / nc, row = loc % nc;
+    uval[idx] = ell[(s * bb + e) * nc + row];
+  } else {
+    uval[idx] = tval[(loc - kSlots * nc) * bb + e];
+  }
+}
+
+// ------------------------------------------------------------ assembly
+// Harmonic-mean geometric transmissibility of one face (unit cell, unit
+// face), zero when both permeabilities vanish.
+__device__ __forceinline__ double face_T(double ki, double kj, int vertical, double kvkh, double c_t) {
+  if (vertical) { ki = kvkh * ki; kj = kvkh * kj; }
+  const double den = ki + kj;
+  if (den == 0.0) return 0.0;
+  const double num = (2.0 * ki) * kj;
+  return c_t * (num / den);
+}
+
+__device__ __forceinline__ double perm_of(const double *perm, int is_log, int64_t i) {
+  return is_log ? exp(perm[i]) : perm[i];
+}
+
+template <int B>
+__global__ void k_assemble_cells(Geom g, const uint8_t *emask, double *ell, double *tval, const double *perm,
+                                 int is_log, double kvkh, double c_t, const double *M, const double *acc,
+                                 const int64_t *cperf_ptr, const int64_t *cperf_idx, const int64_t *perf_cw,
+                                 const double *wi, const double *lam) {
+  constexpr int BB = B * B;
+  const int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (c >= g.nc) return;
+  const int64_t nc = g.nc;
+  double dg[BB];
+#pragma unroll
+  for (int e = 0; e < BB; e++) dg[e] = acc[c * BB + e];
+  const double kc = perm_of(perm, is_log, c);
+  const unsigned m = emask[c];
+  for (int d = 0; d < 6; d++) {
+    const int s = d < 3 ? d : d + 1;
+    if (!((m >> s) & 1u)) continue;
+    const int64_t j = c + g.off[s];
+    const double T = face_T(kc, perm_of(perm, is_log, j), d == 0 || d == 5, kvkh, c_t);
+    const double *Mij = M + (c * 6 + d) * BB;
+#pragma unroll
+    for (int e = 0; e < BB; e++) {
+      const double flux = T * Mij[e];
+      ell[((int64_t)s * BB + e) * nc + c] = -flux;
+      dg[e] = dg[e] + flux;
+    }
+  }
+  for (int64_t t = cperf_ptr[c]; t < cperf_ptr[c + 1]; t++) {
+    const int64_t mm = cperf_idx[t];
+    double *blk = tval + perf_cw[mm] * BB;
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      const double q = wi[mm] * lam[mm * B + r];
+      dg[r * B] = dg[r * B] + q;
+      blk[r * B] = -q;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) ell[((int64_t)kSelf * BB + e) * nc + c] = dg[e];
+}
+
+template <int B>
+__global__ void k_assemble_wells(int nw, double *tval, const int64_t *wperf_ptr, const int64_t *wperf_idx,
+                                 const int64_t *perf_wc, const int64_t *wdiag, const double *wi,
+                                 const double *lam) {
+  constexpr int BB = B * B;
+  const int w = blockIdx.x * kThreads + threadIdx.x;
+  if (w >= nw) return;
+  double sum = 0.0;
+  for (int64_t t = wperf_ptr[w]; t < wperf_ptr[w + 1]; t++) {
+    const int64_t mm = wperf_idx[t];
+    double Lam = 0.0;
+#pragma unroll
+    for (int r = 0; r < B; r++) Lam = Lam + lam[mm * B + r];
+    const double q = wi[mm] * Lam;
+    sum = sum + q;
+    tval[perf_wc[mm] * BB] = -q;
+  }
+  double *dgb = tval + wdiag[w] * BB;
+  dgb[0] = sum;
+#pragma unroll
+  for (int s = 1; s < B; s++) dgb[s * B + s] = 1.0;
+}
+
+template <int B>
+__global__ void k_scale_diag(Geom g, double *ell, double *tval, const int64_t *tdiag, const double *sc) {
+  constexpr int BB = B * B;
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= g.n_rows) return;
+  const double f = sc[i];
+  if (i < g.nc) {
+#pragma unroll
+    for (int e = 0; e < BB; e++) {
+      double *p = ell + ((int64_t)kSelf * BB + e) * g.nc + i;
+      *p = *p * f;
+    }
+  } else {
+    double *p = tval + tdiag[i - g.nc] * BB;
+#pragma unroll
+    for (int e = 0; e < BB; e++) p[e] = p[e] * f;
+  }
+}
+
+// ------------------------------------------------------------ decoupling
+// Gauss-Jordan inversion with row pivoting (GJE of Sec. "Decoupling
+// Methods"): pivot = first row of largest |a| in the column at or below the
+// diagonal; pivot row divided by the pivot; its multiple a(r,c) subtracted
+// from every other row.
+template <int B>
+__device__ bool gj_inverse(const double (&D)[B * B], double (&inv)[B * B]) {
+  double a[B * B];
+#pragma unroll
+  for (int e = 0; e < B * B; e++) { a[e] = D[e]; inv[e] = 0.0; }
+#pragma unroll
+  for (int r = 0; r < B; r++) inv[r * B + r] = 1.0;
+#pragma unroll
+  for (int c = 0; c < B; c++) {
+    int p = c;
+    double best = fabs(a[c * B + c]);
+#pragma unroll
+    for (int r = c + 1; r < B; r++) {
+      const double v = fabs(a[r * B + c]);
+      if (v > best) { best = v; p = r; }
+    }
+    if (best == 0.0 || !isfinite(best)) return false;
+#pragma unroll
+    for (int r = c + 1; r < B; r++) {
+      if (r == p) {
+#pragma unroll
+        for (int s = 0; s < B; s++) {
+          double t = a[c * B + s]; a[c * B + s] = a[r * B + s]; a[r * B + s] = t;
+          t = inv[c * B + s]; inv[c * B + s] = inv[r * B + s]; inv[r * B + s] = t;
+        }
+      }
+    }
+    const double piv = a[c * B + c];
+#pragma unroll
+    for (int s = 0; s < B; s++) {
+      a[c * B + s] = a[c * B + s] / piv;
+      inv[c * B + s] = inv[c * B + s] / piv;
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      if (r == c) continue;
+      const double f = a[r * B + c];
+#pragma unroll
+      for (int s = 0; s < B; s++) {
+        a[r * B + s] = a[r * B + s] - f * a[c * B + s];
+        inv[r * B + s] = inv[r * B + s] - f * inv[c * B + s];
+      }
+    }
+  }
+  return true;
+}
+
+// C = A * Bm (b x b), inner index ascending, first product then running sums
+template <int B>
+__device__ __forceinline__ void bmul(const double (&A)[B * B], const double (&Bm)[B * B], double (&C)[B * B]) {
+#pragma unroll
+  for (int r = 0; r < B; r++)
+#pragma unroll
+    for (int s = 0; s < B; s++) {
+      double acc = A[r * B] * Bm[s];
+#pragma unroll
+      for (int t = 1; t < B; t++) acc = acc + A[r * B + t] * Bm[t * B + s];
+      C[r * B + s] = acc;
+    }
+}
+
+template <int B>
+__global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_ell, double *at_tval,
+                           double *dinv, double *ap_ell, double *ap_tval, int *err) {
+  constexpr int BB = B * B;
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t nc = A.g.nc, n = A.g.n_rows;
+  if (i >= n) return;
+  double D[BB], Di[BB], blk[BB], out[BB];
+  const bool cell = i < nc;
+  const int64_t dtail = cell ? -1 : tdiag[i - nc];
+  if (cell) {
+#pragma unroll
+    for (int e = 0; e < BB; e++) D[e] = A.ell[((int64_t)kSelf * BB + e) * nc + i];
+  } else {
+#pragma unroll
+    for (int e = 0; e < BB; e++) D[e] = A.tval[dtail * BB + e];
+  }
+  if (!gj_inverse<B>(D, Di)) {
+    atomicExch(err, 1);
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) dinv[(int64_t)e * n + i] = Di[e];
+  if (cell) {
+    const unsigned m = A.emask[i];
+    for (int s = 0; s < kSlots; s++) {
+      if (!((m >> s) & 1u)) continue;
+      if (s == kSelf) {
+#pragma unroll
+        for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+        ap_ell[(int64_t)s * nc + i] = 1.0;
+        continue;
+      }
+#pragma unroll
+      for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
+      bmul<B>(Di, blk, out);
+#pragma unroll
+      for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = out[e];
+      ap_ell[(int64_t)s * nc + i] = out[0];
+    }
+  }
+  for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
+    if (t == dtail) {
+#pragma unroll
+      for (int e = 0; e < BB; e++) at_tval[t * BB + e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+      ap_tval[t] = 1.0;
+      continue;
+    }
+#pragma unroll
+    for (int e = 0; e < BB; e++) blk[e] = A.tval[t * BB + e];
+    bmul<B>(Di, blk, out);
+#pragma unroll
+    for (int e = 0; e < BB; e++) at_tval[t * BB + e] = out[e];
+    ap_tval[t] = out[0];
+  }
+}
+
+// ------------------------------------------------------- pressure CSR
+__global__ void k_ap_rowlen(Geom g, const uint8_t *emask, const int64_t *tptr, int64_t *len) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= g.n_rows) return;
+  int64_t l = tptr[i + 1] - tptr[i];
+  if (i < g.nc) l += __popc((unsigned)emask[i]);
+  len[i] = l;
+}
+
+// merge of the implicit ELL columns and the (sorted) tail columns
+__global__ void k_ap_fill(Geom g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
+                          const double *ap_ell, const double *ap_tval, const int64_t *rp, int32_t *col,
+                          double *val) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= g.n_rows) return;
+  int64_t q = rp[i], t = tptr[i];
+  const int64_t te = tptr[i + 1];
+  if (i < g.nc) {
+    const unsigned m = emask[i];
+    for (int s = 0; s < kSlots; s++) {
+      if (!((m >> s) & 1u)) continue;
+      const int64_t j = i + g.off[s];
+      while (t < te && tcol[t] < j) { col[q] = tcol[t]; val[q] = ap_tval[t]; q++; t++; }
+      col[q] = (int32_t)j;
+      val[q] = ap_ell[(int64_t)s * g.nc + i];
+      q++;
+    }
+  }
+  while (t < te) { col[q] = tcol[t]; val[q] = ap_tval[t]; q++; t++; }
+}
+
+__device__ __forceinline__ int64_t bsearch_col(const int64_t *rp, const int32_t *col, int64_t i, int64_t j) {
+  int64_t lo = rp[i], hi = rp[i + 1] - 1;
+  while (lo <= hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    const int64_t c = col[mid];
+    if (c == j) return mid;
+    if (c < j) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+__global__ void k_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, int64_t *dpos) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  dpos[i] = bsearch_col(rp, col, i, i);
+}
+
+// ------------------------------------------------------------- strength
+// j != i is strong if s = max(|a_ij|, |a_ji|) > 0 and s >= theta*sqrt(|a_ii a_jj|)
+__global__ void k_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                           const int64_t *dpos, double theta, uint8_t *sflag, int32_t *sdeg) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  const double aii = dpos[i] < 0 ? 0.0 : val[dpos[i]];
+  int32_t deg = 0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+    const int64_t j = col[p];
+    uint8_t f = 0;
+    if (j != i) {
+      const double ajj = dpos[j] < 0 ? 0.0 : val[dpos[j]];
+      const int64_t pt = bsearch_col(rp, col, j, i);
+      const double aij = fabs(val[p]), aji = pt < 0 ? 0.0 : fabs(val[pt]);
+      const double sv = aij > aji ? aij : aji;
+      const double thr = theta * sqrt(fabs(aii * ajj));
+      f = (sv > 0.0 && sv >= thr) ? 1 : 0;
+    }
+    sflag[p] = f;
+    deg += f;
+  }
+  sdeg[i] = deg;
+}
+
+// ----------------------------------------------------------------- MIS-2
+enum : int8_t { kOut = 0, kUndecided = 1, kIn = 2 };
+
+__global__ void k_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  state[i] = sdeg[i] > 0 ? kUndecided : kOut;
+}
+
+// out_i = max over {i} U strong(i) of the tuple (state, key); in_k == nullptr
+// means key = node_key(index)
+__global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
+                             const int8_t *in_s, const uint64_t *in_k, uint32_t seed, int8_t *out_s,
+                             uint64_t *out_k) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  int8_t ms = in_s[i];
+  uint64_t mk = in_k ? in_k[i] : node_key(i, seed);
+  for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+    if (!sflag[p]) continue;
+    const int64_t j = col[p];
+    const int8_t s = in_s[j];
+    const uint64_t k = in_k ? in_k[j] : node_key(j, seed);
+    if (s > ms || (s == ms && k > mk)) { ms = s; mk = k; }
+  }
+  out_s[i] = ms;
+  out_k[i] = mk;
+}
+
+__global__ void k_mis2_decide(int64_t n, uint32_t seed, const int8_t *t2s, const uint64_t *t2k, int8_t *state,
+                              unsigned long long *undecided) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  const int8_t s = state[i];
+  if (s != kUndecided) return;
+  if (t2s[i] == s && t2k[i] == node_key(i, seed)) {
+    state[i] = kIn;
+  } else if (t2s[i] == kIn) {
+    state[i] = kOut;
+  } else {
+    atomicAdd(undecided, 1ull);
+  }
+}
+
+__global__ void k_in_flag(int64_t n, const int8_t *state, int64_t *flag) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  flag[i] = state[i] == kIn ? 1 : 0;
+}
+
+// roots get their rank; strong neighbours of a root take the first root met
+// in column order
+__global__ void k_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
+                            const int32_t *sdeg, const int8_t *state, const int64_t *rootid, int32_t *first) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  int32_t a = -1;
+  if (state[i] == kIn) {
+    a = (int32_t)rootid[i];
+  } else if (sdeg[i] > 0) {
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++)
+      if (sflag[p] && state[col[p]] == kIn) { a = (int32_t)rootid[col[p]]; break; }
+  }
+  first[i] = a;
+}
+
+// the rest join the first-pass neighbour of largest |a_ij|, smaller id on ties
+__global__ void k_agg_pass2(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                            const uint8_t *sflag, const int32_t *sdeg, const int32_t *first, int32_t *agg) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  int32_t a = first[i];
+  if (a < 0 && sdeg[i] > 0) {
+    double best = -1.0;
+    int32_t pick = -1;
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+      if (!sflag[p]) continue;
+      const int32_t fj = first[col[p]];
+      if (fj < 0) continue;
+      const double v = fabs(val[p]);
+      if (v > best || (v == best && fj < pick)) { best = v; pick = fj; }
+    }
+    a = pick;
+  }
+  agg[i] = a;
+}
+
+__global__ void k_member_count(int64_t n, const int32_t *agg, int64_t *cnt) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  if (agg[i] >= 0) atomicAdd((unsigned long long *)&cnt[agg[i]], 1ull);
+}
+
+__global__ void k_member_fill(int64_t n, const int32_t *agg, const int64_t *mptr, int64_t *cursor,
+                              int32_t *midx) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  const int32_t a = agg[i];
+  if (a < 0) return;
+  const int64_t at = (int64_t)atomicAdd((unsigned long long *)&cursor[a], 1ull);
+  midx[mptr[a] + at] = (int32_t)i;
+}
+
+__global__ void k_member_sort(int64_t na, const int64_t *mptr, int32_t *midx) {
+  const int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (a >= na) return;
+  for (int64_t t = mptr[a] + 1; t < mptr[a + 1]; t++) {
+    const int32_t v = midx[t];
+    int64_t u = t - 1;
+    while (u >= mptr[a] && midx[u] > v) { midx[u + 1] = midx[u]; u--; }
+    midx[u + 1] = v;
+  }
+}
+
+// ------------------------------------------------------------- Galerkin
+// One warp per coarse row I: distinct coarse columns in ascending order by
+// repeated minimum search; each value is the running sum, from 0.0, over the
+// members of I in ascending order and their entries in ascending column
+// order.  fill == 0 counts, fill == 1 writes.
+__global__ void k_galerkin(int64_t na, const int64_t *rp, const int32_t *col, const double *val,
+                           const int32_t *agg, const int64_t *mptr, const int32_t *midx, int fill,
+                           int64_t *ccount, const int64_t *crp, int32_t *ccol, double *cval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t I = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
+  if (I >= na) return;
+  const int64_t m0 = mptr[I], m1 = mptr[I + 1];
+  int32_t cur = -1;
+  int64_t count = 0;
+  for (;;) {
+    int32_t mn = 0x7fffffff;
+    for (int64_t t = m0; t < m1; t++) {
+      const int64_t i = midx[t];
+      for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+        const int32_t J = agg[col[p]];
+        if (J > cur && J < mn) mn = J;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if (mn == 0x7fffffff) break;
+    if (fill) {
+      double s = 0.0;
+      for (int64_t t = m0; t < m1; t++) {
+        const int64_t i = midx[t];
+        const int64_t e = rp[i + 1];
+        for (int64_t base = rp[i]; base < e; base += 32) {
+          const int64_t p = base + lane;
+          const bool hit = p < e && agg[col[p]] == mn;
+          const double v = p < e ? val[p] : 0.0;
+          unsigned mask = __ballot_sync(0xffffffffu, hit);
+          while (mask) {
+            const int src = __ffs(mask) - 1;
+            s = s + __shfl_sync(0xffffffffu, v, src);
+            mask &= mask - 1;
+          }
+        }
+      }
+      if (lane == 0) {
+        ccol[crp[I] + count] = mn;
+        cval[crp[I] + count] = s;
+      }
+    }
+    count++;
+    cur = mn;
+  }
+  if (!fill && lane == 0) ccount[I] = count;
+}
+
+// ----------------------------------------------------- smoother set-up
+__global__ void k_gershgorin(int64_t n, const int64_t *rp, const double *val, const int64_t *dpos,
+                             double *dinv, unsigned long long *lam_bits) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = s + fabs(val[p]);
+  const double d = dpos[i] < 0 ? 0.0 : val[dpos[i]];
+  const double q = s / fabs(d);
+  dinv[i] = 1.0 / d;
+  atomicMax(lam_bits, (unsigned long long)__double_as_longlong(q));
+}
+
+// ------------------------------------------------- coarsest dense solve
+__global__ void k_csr_to_dense(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double *a) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t p = rp[i]; p < rp[i + 1]; p++) a[i * n + col[p]] = val[p];
+}
+
+// LU with partial pivoting (first row of largest |a| on ties), one block
+__global__ void __launch_bounds__(1024) k_dense_lu(int n, double *a, int *piv, int *err) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ int pk;
+  for (int k = 0; k < n; k++) {
+    double best = -1.0;
+    int bidx = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = fabs(a[(int64_t)i * n + k]);
+      if (v > best || (v == best && i < bidx)) { best = v; bidx = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = -1.0;
+      int i0 = n;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+        if (bv[w] > b0 || (bv[w] == b0 && bi[w] < i0)) { b0 = bv[w]; i0 = bi[w]; }
+      if (!(b0 > 0.0) || !isfinite(b0)) *err = 1;
+      pk = i0;
+      piv[k] = i0;
+    }
+    __syncthreads();
+    if (*err) return;
+    const int p = pk;
+    if (p != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double t = a[(int64_t)k * n + j];
+        a[(int64_t)k * n + j] = a[(int64_t)p * n + j];
+        a[(int64_t)p * n + j] = t;
+      }
+    __syncthreads();
+    const double akk = a[(int64_t)k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) a[(int64_t)i * n + k] = a[(int64_t)i * n + k] / akk;
+    __syncthreads();
+    const int64_t m = n - k - 1;
+    for (int64_t idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int64_t i = k + 1 + idx / m, j = k + 1 + idx % m;
+      a[i * n + j] = a[i * n + j] - a[i * n + k] * a[(int64_t)k * n + j];
+    }
+    __syncthreads();
+  }
+}
+
+// column j of the inverse: solve LU x = P e_j
+__global__ void k_dense_inv_cols(int n, const double *lu, const int *piv, double *inv, double *work) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double *x = work + (int64_t)j * n;
+  for (int i = 0; i < n; i++) x[i] = (i == j) ? 1.0 : 0.0;
+  for (int k = 0; k < n; k++)
+    if (piv[k] != k) { const double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+  for (int i = 0; i < n; i++) {
+    double s = x[i];
+    for (int k = 0; k < i; k++) s = s - lu[(int64_t)i * n + k] * x[k];
+    x[i] = s;
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    double s = x[i];
+    for (int k = i + 1; k < n; k++) s = s - lu[(int64_t)i * n + k] * x[k];
+    x[i] = s / lu[(int64_t)i * n + i];
+  }
+  for (int i = 0; i < n; i++) inv[(int64_t)i * n + j] = x[i];
+}
+
+// ------------------------------------------------------------ colouring
+// Jones-Plassmann round with first-fit colours; reads the colours of the
+// previous round only (double buffer), so the result does not depend on
+// thread timing.
+__global__ void k_colour_round(Geom g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
+                               uint32_t seed, const int32_t *cin, int32_t *cout, unsigned long long *coloured,
+                               int *overflow) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= g.n_rows) return;
+  const int32_t ci = cin[i];
+  cout[i] = ci;
+  if (ci >= 0) return;
+  const uint64_t ki = node_key(i, seed);
+  uint64_t used = 0;
+  bool ready = true;
+  if (i < g.nc) {
+    const unsigned m = emask[i];
+    for (int s = 0; s < kSlots; s++) {
+      if (s == kSelf || !((m >> s) & 1u)) continue;
+      const int64_t j = i + g.off[s];
+      const int32_t cj = cin[j];
+      if (cj < 0) {
+        if (node_key(j, seed) > ki) ready = false;
+      } else {
+        used |= 1ull << cj;
+      }
+    }
+  }
+  for (int64_t t = tptr[i]; t < tptr[i + 1]; t++) {
+    const int64_t j = tcol[t];
+    if (j == i) continue;
+    const int32_t cj = cin[j];
+    if (cj < 0) {
+      if (node_key(j, seed) > ki) ready = false;
+    } else {
+      used |= 1ull << cj;
+    }
+  }
+  if (!ready) return;
+  if (used == ~0ull) {
+    atomicExch(overflow, 1);
+    return;
+  }
+  cout[i] = __ffsll((long long)~used) - 1;
+  atomicAdd(coloured, 1ull);
+}
+
+__global__ void k_colour_count(Geom g, const int32_t *colour, unsigned long long *cnt, unsigned long long *cnt_cells) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= g.n_rows) return;
+  atomicAdd(&cnt[colour[i]], 1ull);
+  if (i < g.nc) atomicAdd(&cnt_cells[colour[i]], 1ull);
+}
+
+__global__ void k_colour_flag(int64_t n, const int32_t *colour, int c, int64_t *flag) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  flag[i] = colour[i] == c ? 1 : 0;
+}
+
+__global__ void k_colour_place(int64_t n, const int32_t *colour, int c, const int64_t *rank, int64_t base,
+                               int32_t *crow, int64_t *pos) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n || colour[i] != c) return;
+  const int64_t q = base + rank[i];
+  crow[q] = (int32_t)i;
+  pos[i] = q;
+}
+
+// ------------------------------------------------------------------ ILU(0)
+__global__ void k_ilu_lmask_len(Geom g, const uint8_t *emask, const int64_t *tptr, const int32_t *crow,
+                                const int64_t *pos, uint8_t *lmask, int64_t *len) {
+  const int64_t q = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (q >= g.n_rows) return;
+  const int64_t i = crow[q];
+  unsigned lm = 0;
+  if (i < g.nc) {
+    const unsigned m = emask[i];
+    for (int s = 0; s < kSlots; s++)
+      if (s != kSelf && ((m >> s) & 1u) && pos[i + g.off[s]] < q) lm |= 1u << s;
+  }
+  lmask[q] = (uint8_t)lm;
+  len[q] = tptr[i + 1] - tptr[i];
+}
+
+__global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol, const int32_t *crow,
+                                const int64_t *pos, const int64_t *ftptr, int32_t *ftcol, uint8_t *ftlow,
+                                int64_t *ftsrc) {
+  const int64_t q = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (q >= g.n_rows) return;
+  const int64_t i = crow[q];
+  int64_t u = ftptr[q];
+  for (int64_t t = tptr[i]; t < tptr[i + 1]; t++, u++) {
+    ftcol[u] = tcol[t];
+    ftlow[u] = pos[tcol[t]] < q ? 1 : 0;
+    ftsrc[u] = t;
+  }
+}
+
+template <int B>
+__global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const double *at_ell,
+                           const double *at_tval, const int64_t *ftsrc, int64_t nft, double *fell,
+                           double *ftval) {
+  constexpr int BB = B * B;
+  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t np = g.n_rows;
+  if (idx < np) {
+    const int64_t q = idx, i = crow[q];
+    const unsigned m = i < g.nc ? emask[i] : 0u;
+    for (int s = 0; s < kSlots; s++) {
+#pragma unroll
+      for (int e = 0; e < BB; e++) {
+        double v = 0.0;
+        if (s == kSelf) v = (e % (B + 1) == 0) ? 1.0 : 0.0;
+        else if ((m >> s) & 1u) v = at_ell[((int64_t)s * BB + e) * g.nc + i];
+        fell[((int64_t)s * BB + e) * np + q] = v;
+      }
+    }
+  }
+  if (idx < nft) {
+#pragma unroll
+    for (int e = 0; e < BB; e++) ftval[idx * BB + e] = at_tval[ftsrc[idx] * BB + e];
+  }
+}
+
+// Reference to one stored block of the factor: base pointer and stride.
+struct BRef {
+  double *p;
+  int64_t stride;
+};
+
+template <int B>
+__device__ __forceinline__ void bload(BRef r, double (&v)[B * B]) {
+#pragma unroll
+  for (int e = 0; e < B * B; e++) v[e] = r.p[e * r.stride];
+}
+template <int B>
+__device__ __forceinline__ void bstore(BRef r, const double (&v)[B * B]) {
+#pragma unroll
+  for (int e = 0; e < B * B; e++) r.p[e * r.stride] = v[e];
+}
+
+// entry k of row i (k != i) in factor storage, or p = nullptr
+template <int B>
+__device__ BRef ilu_find(const Geom &g, const uint8_t *emask, const int64_t *pos, const int64_t *ftptr,
+                         const int32_t *ftcol, double *fell, double *ftval, int64_t i, int64_t k) {
+  constexpr int BB = B * B;
+  const int64_t qi = pos[i], np = g.n_rows;
+  if (i < g.nc && k < g.nc) {
+    const int64_t d = k - i;
+    const unsigned m = emask[i];
+    for (int s = 0; s < kSlots; s++)
+      if (s != kSelf && ((m >> s) & 1u) && g.off[s] == d)
+        return BRef{fell + ((int64_t)s * BB) * np + qi, np};
+  }
+  int64_t lo = ftptr[qi], hi = ftptr[qi + 1] - 1;
+  while (lo <= hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    const int64_t c = ftcol[mid];
+    if (c == k) return BRef{ftval + mid * BB, 1};
+    if (c < k) lo = mid + 1; else hi = mid - 1;
+  }
+  return BRef{nullptr, 0};
+}
+
+// IKJ ILU(0) of the rows at positions [q0, q1) (one colour): for every
+// earlier-ordered k of row i in ascending order, L_ik = W_ik U_kk^-1 and
+// W_ij -= L_ik U_kj for later-ordered j of row i with (k, j) stored; then
+// U_ii^-1 replaces W_ii in slot 3.
+template <int B>
+__global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
+                             const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, double *fell,
+                             double *ftval, int64_t q0, int64_t q1, int *err) {
+  constexpr int BB = B * B;
+  const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (q >= q1) return;
+  const int64_t np = g.n_rows, i = crow[q];
+  const bool cell = i < g.nc;
+  const unsigned m = cell ? emask[i] : 0u;
+  const int64_t u0 = ftptr[q], u1 = ftptr[q + 1];
+  // the row's entries: slots 0..6 (cells) then tail entries u0..u1-1
+  const int n_ent = kSlots + (int)(u1 - u0);
+  auto ent_col = [&](int k) -> int64_t {
+    if (k < kSlots) return ((m >> k) & 1u) ? i + g.off[k] : -1;
+    return ftcol[u0 + (k - kSlots)];
+  };
+  auto ent_ref = [&](int k) -> BRef {
+    if (k < kSlots) return BRef{fell + ((int64_t)k * BB) * np + q, np};
+    return BRef{ftval + (u0 + (k - kSlots)) * BB, 1};
+  };
+  int64_t cur = -1;
+  for (;;) {
+    // next lower entry in ascending position
+    int kbest = -1;
+    int64_t pbest = q;
+    for (int k = 0; k < n_ent; k++) {
+      const int64_t c = ent_col(k);
+      if (c < 0 || c == i) continue;
+      const int64_t pc = pos[c];
+      if (pc > cur && pc < pbest) { pbest = pc; kbest = k; }
+    }
+    if (kbest < 0) break;
+    cur = pbest;
+    const int64_t kr = ent_col(kbest);
+    double W[BB], Uinv[BB], L[BB];
+    bload<B>(ent_ref(kbest), W);
+    bload<B>(BRef{fell + ((int64_t)kSelf * BB) * np + pbest, np}, Uinv);
+    bmul<B>(W, Uinv, L);
+    bstore<B>(ent_ref(kbest), L);
+    for (int k = 0; k < n_ent; k++) {
+      const int64_t j = ent_col(k);
+      if (j < 0 || pos[j] <= pbest) continue;
+      BRef ukj;
+      if (j == kr) continue;
+      ukj = ilu_find<B>(g, emask, pos, ftptr, ftcol, fell, ftval, kr, j);
+      if (!ukj.p) continue;
+      double U[BB], P[BB], Wij[BB];
+      bload<B>(ukj, U);
+      bmul<B>(L, U, P);
+      BRef wr = (j == i && cell) ? BRef{fell + ((int64_t)kSelf * BB) * np + q, np} : ent_ref(k);
+      bload<B>(wr, Wij);
+#pragma unroll
+      for (int e = 0; e < BB; e++) Wij[e] = Wij[e] - P[e];
+      bstore<B>(wr, Wij);
+    }
+  }
+  // diagonal: slot 3 for cells, the tail entry for other rows
+  double Wd[BB], inv[BB];
+  BRef dref{fell + ((int64_t)kSelf * BB) * np + q, np};
+  if (!cell) {
+    for (int k = kSlots; k < n_ent; k++)
+      if (ent_col(k) == i) { dref = ent_ref(k); break; }
+  }
+  bload<B>(dref, Wd);
+  if (!gj_inverse<B>(Wd, inv)) {
+    atomicExch(err, 1);
+    return;
+  }
+  bstore<B>(BRef{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+}
+
+}  // namespace
+
+// =============================================================== launchers
+void exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s) {
+  if (n <= 0) {
+    if (total) TRS_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+    return;
+  }
+  const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  DBuf<int64_t> bsum(nb);
+  k_scan_reduce<<<(unsigned)nb, kThreads, 0, s>>>(in, n, bsum.p);
+  TRS_LAUNCHED();
+  k_scan_bsums<<<1, 32, 0, s>>>(bsum.p, nb, total);
+  TRS_LAUNCHED();
+  k_scan_apply<<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, bsum.p);
+  TRS_LAUNCHED();
+  TRS_CUDA(cudaStreamSynchronize(s));  // bsum is freed on return
+}
+
+void launch_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval, int64_t nc, double *ell,
+                           double *tval, cudaStream_t s) {
+  if (!nnzb) return;
+  k_scatter_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(nnzb, bb, map, uval, nc, ell, tval);
+  TRS_LAUNCHED();
+}
+
+void launch_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell, const double *tval,
+                          int64_t nc, double *uval, cudaStream_t s) {
+  if (!nnzb) return;
+  k_gather_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(nnzb, bb, map, ell, tval, nc, uval);
+  TRS_LAUNCHED();
+}
+
+void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, double kvkh, double c_t,
+                     const double *M, const double *acc, const double *wi, const double *lam, cudaStream_t s) {
+  A->tval.zero(s);
+  TRS_DISPATCH_B(b, {
+    if (A->g.nc) {
+      k_assemble_cells<B><<<grid_of(A->g.nc), kThreads, 0, s>>>(
+          A->g, A->emask.p, A->ell.p, A->tval.p, perm, perm_is_log, kvkh, c_t, M, acc, A->cperf_ptr.p,
+          A->cperf_idx.p, A->perf_cw.p, wi, lam);
+      TRS_LAUNCHED();
+    }
+    if (A->n_wells)
+      k_assemble_wells<B><<<grid_of(A->n_wells), kThreads, 0, s>>>(A->n_wells, A->tval.p, A->wperf_ptr.p,
+                                                                   A->wperf_idx.p, A->perf_wc.p, A->wdiag.p,
+                                                                   wi, lam);
+  });
+  TRS_LAUNCHED();
+}
+
+void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, double *at_ell, double *at_tval,
+                     double *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
+  if (!A.g.n_rows) return;
+  TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, at_ell, at_tval, dinv,
+                                                                           ap_ell, ap_tval, err));
+  TRS_LAUNCHED();
+}
+
+void launch_ap_csr_rowlen(const Geom &g, const uint8_t *emask, const int64_t *tptr, int64_t *len, cudaStream_t s) {
+  k_ap_rowlen<<<grid_of(g.n_rows), kThreads, 0, s>>>(g, emask, tptr, len);
+  TRS_LAUNCHED();
+}
+
+void launch_ap_csr_fill(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
+                        const double *ap_ell, const double *ap_tval, const int64_t *rp, int32_t *col, double *val,
+                        cudaStream_t s) {
+  k_ap_fill<<<grid_of(g.n_rows), kThreads, 0, s>>>(g, emask, tptr, tcol, ap_ell, ap_tval, rp, col, val);
+  TRS_LAUNCHED();
+}
+
+void launch_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, int64_t *dpos, cudaStream_t s) {
+  if (!n) return;
+  k_diag_pos<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, dpos);
+  TRS_LAUNCHED();
+}
+
+void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const int64_t *dpos,
+                     double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s) {
+  if (!n) return;
+  k_strength<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, val, dpos, theta, sflag, sdeg);
+  TRS_LAUNCHED();
+}
+
+void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_t s) {
+  k_mis2_init<<<grid_of(n), kThreads, 0, s>>>(n, sdeg, state);
+  TRS_LAUNCHED();
+}
+
+void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int8_t *in_s,
+                       const uint64_t *in_k, uint32_t seed, int8_t *out_s, uint64_t *out_k, cudaStream_t s) {
+  k_mis2_sweep<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, sflag, in_s, in_k, seed, out_s, out_k);
+  TRS_LAUNCHED();
+}
+
+void launch_mis2_decide(int64_t n, uint32_t seed, const int8_t *t2s, const uint64_t *t2k, int8_t *state,
+                        unsigned long long *undecided, cudaStream_t s) {
+  k_mis2_decide<<<grid_of(n), kThreads, 0, s>>>(n, seed, t2s, t2k, state, undecided);
+  TRS_LAUNCHED();
+}
+
+void launch_in_flag(int64_t n, const int8_t *state, int64_t *flag, cudaStream_t s) {
+  k_in_flag<<<grid_of(n), kThreads, 0, s>>>(n, state, flag);
+  TRS_LAUNCHED();
+}
+
+void launch_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int32_t *sdeg,
+                      const int8_t *state, const int64_t *rootid, int32_t *first, cudaStream_t s) {
+  k_agg_pass1<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, sflag, sdeg, state, rootid, first);
+  TRS_LAUNCHED();
+}
+
+void launch_agg_pass2(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const uint8_t *sflag,
+                      const int32_t *sdeg, const int32_t *first, int32_t *agg, cudaStream_t s) {
+  k_agg_pass2<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, val, sflag, sdeg, first, agg);
+  TRS_LAUNCHED();
+}
+
+void launch_members(int64_t n, const int32_t *agg, int64_t n_agg, DBuf<int64_t> &mptr, DBuf<int32_t> &midx,
+                    cudaStream_t s) {
+  DBuf<int64_t> cnt(n_agg + 1), cursor(n_agg + 1);
+  cnt.zero(s);
+  cursor.zero(s);
+  mptr.alloc(n_agg + 1);
+  k_member_count<<<grid_of(n), kThreads, 0, s>>>(n, agg, cnt.p);
+  TRS_LAUNCHED();
+  exclusive_scan(cnt.p, mptr.p, n_agg + 1, nullptr, s);
+  int64_t total = 0;
+  TRS_CUDA(cudaMemcpyAsync(&total, mptr.p + n_agg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  midx.alloc(std::max<int64_t>(total, 1));
+  k_member_fill<<<grid_of(n), kThreads, 0, s>>>(n, agg, mptr.p, cursor.p, midx.p);
+  TRS_LAUNCHED();
+  k_member_sort<<<grid_of(n_agg), kThreads, 0, s>>>(n_agg, mptr.p, midx.p);
+  TRS_LAUNCHED();
+  TRS_CUDA(cudaStreamSynchronize(s));
+}
+
+void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int64_t *mptr, const int32_t *midx,
+                     Csr &C, cudaStream_t s) {
+  DBuf<int64_t> cnt(n_agg + 1);
+  cnt.zero(s);
+  const unsigned grid = (unsigned)((n_agg + kWarps - 1) / kWarps);
+  k_galerkin<<<grid, kThreads, 0, s>>>(n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 0, cnt.p, nullptr,
+                                       nullptr, nullptr);
+  TRS_LAUNCHED();
+  C.n = n_agg;
+  C.rp.alloc(n_agg + 1);
+  exclusive_scan(cnt.p, C.rp.p, n_agg + 1, nullptr, s);
+  TRS_CUDA(cudaMemcpyAsync(&C.nnz, C.rp.p + n_agg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  C.col.alloc(std::max<int64_t>(C.nnz, 1));
+  C.val.alloc(std::max<int64_t>(C.nnz, 1));
+  k_galerkin<<<grid, kThreads, 0, s>>>(n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 1, nullptr, C.rp.p,
+                                       C.col.p, C.val.p);
+  TRS_LAUNCHED();
+}
+
+double launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, cudaStream_t s) {
+  DBuf<unsigned long long> bits(1);
+  bits.zero(s);
+  k_gershgorin<<<grid_of(A.n), kThreads, 0, s>>>(A.n, A.rp.p, A.val.p, dpos, dinv, bits.p);
+  TRS_LAUNCHED();
+  unsigned long long h = 0;
+  TRS_CUDA(cudaMemcpyAsync(&h, bits.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  double lam;
+  std::memcpy(&lam, &h, sizeof(lam));
+  return lam;
+}
+
+int launch_dense_inverse(const Csr &A, DBuf<double> &inv, cudaStream_t s) {
+  const int n = (int)A.n;
+  DBuf<double> lu((size_t)n * n), work((size_t)n * n);
+  DBuf<int> piv(n), err(1);
+  lu.zero(s);
+  err.zero(s);
+  k_csr_to_dense<<<grid_of(n), kThreads, 0, s>>>(n, A.rp.p, A.col.p, A.val.p, lu.p);
+  TRS_LAUNCHED();
+  k_dense_lu<<<1, 1024, 0, s>>>(n, lu.p, piv.p, err.p);
+  TRS_LAUNCHED();
+  int herr = 0;
+  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  if (herr) return 1;
+  inv.alloc((size_t)n * n);
+  k_dense_inv_cols<<<(n + 127) / 128, 128, 0, s>>>(n, lu.p, piv.p, inv.p, work.p);
+  TRS_LAUNCHED();
+  TRS_CUDA(cudaStreamSynchronize(s));
+  return 0;
+}
+
+int launch_colour(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol, uint32_t seed,
+                  int32_t *colour, cudaStream_t s) {
+  const int64_t n = g.n_rows;
+  DBuf<int32_t> other(n);
+  DBuf<unsigned long long> cnt(1);
+  DBuf<int> overflow(1);
+  cnt.zero(s);
+  overflow.zero(s);
+  TRS_CUDA(cudaMemsetAsync(colour, 0xff, n * sizeof(int32_t), s));
+  int32_t *a = colour, *bbuf = other.p;
+  unsigned long long done = 0;
+  int rounds = 0;
+  while (done < (unsigned long long)n) {
+    k_colour_round<<<grid_of(n), kThreads, 0, s>>>(g, emask, tptr, tcol, seed, a, bbuf, cnt.p, overflow.p);
+    TRS_LAUNCHED();
+    std::swap(a, bbuf);
+    int ov = 0;
+    TRS_CUDA(cudaMemcpyAsync(&done, cnt.p, sizeof(done), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaMemcpyAsync(&ov, overflow.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+    if (ov) return -1;
+    if (++rounds > 100000) return -1;
+  }
+  if (a != colour) TRS_CUDA(cudaMemcpyAsync(colour, a, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  return rounds;
+}
+
+void launch_colour_order(const Geom &g, const int32_t *colour, int ncol, std::vector<int64_t> &cptr,
+                         std::vector<int64_t> &cmid, int32_t *crow, int64_t *pos, cudaStream_t s) {
+  const int64_t n = g.n_rows;
+  DBuf<unsigned long long> cnt(kMaxColours), cntc(kMaxColours);
+  cnt.zero(s);
+  cntc.zero(s);
+  k_colour_count<<<grid_of(n), kThreads, 0, s>>>(g, colour, cnt.p, cntc.p);
+  TRS_LAUNCHED();
+  auto hc = download(cnt.p, kMaxColours, s);
+  auto hcc = download(cntc.p, kMaxColours, s);
+  cptr.assign(ncol + 1, 0);
+  cmid.assign(ncol, 0);
+  for (int c = 0; c < ncol; c++) {
+    cptr[c + 1] = cptr[c] + (int64_t)hc[c];
+    cmid[c] = cptr[c] + (int64_t)hcc[c];
+  }
+  DBuf<int64_t> flag(n), rank(n);
+  for (int c = 0; c < ncol; c++) {
+    k_colour_flag<<<grid_of(n), kThreads, 0, s>>>(n, colour, c, flag.p);
+    TRS_LAUNCHED();
+    exclusive_scan(flag.p, rank.p, n, nullptr, s);
+    k_colour_place<<<grid_of(n), kThreads, 0, s>>>(n, colour, c, rank.p, cptr[c], crow, pos);
+    TRS_LAUNCHED();
+  }
+  TRS_CUDA(cudaStreamSynchronize(s));
+}
+
+void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
+                          const int32_t *crow, const int64_t *pos, uint8_t *lmask, DBuf<int64_t> &ftptr,
+                          DBuf<int32_t> &ftcol, DBuf<uint8_t> &ftlow, DBuf<int64_t> &ftsrc, cudaStream_t s) {
+  const int64_t n = g.n_rows;
+  DBuf<int64_t> len(n + 1);
+  len.zero(s);
+  k_ilu_lmask_len<<<grid_of(n), kThreads, 0, s>>>(g, emask, tptr, crow, pos, lmask, len.p);
+  TRS_LAUNCHED();
+  ftptr.alloc(n + 1);
+  exclusive_scan(len.p, ftptr.p, n + 1, nullptr, s);
+  int64_t nft = 0;
+  TRS_CUDA(cudaMemcpyAsync(&nft, ftptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  ftcol.alloc(std::max<int64_t>(nft, 1));
+  ftlow.alloc(std::max<int64_t>(nft, 1));
+  ftsrc.alloc(std::max<int64_t>(nft, 1));
+  k_ilu_tail_fill<<<grid_of(n), kThreads, 0, s>>>(g, tptr, tcol, crow, pos, ftptr.p, ftcol.p, ftlow.p, ftsrc.p);
+  TRS_LAUNCHED();
+}
+
+void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const double *at_ell,
+                     const double *at_tval, const int64_t *ftsrc, int64_t nft, double *fell, double *ftval,
+                     cudaStream_t s) {
+  const int64_t n = std::max<int64_t>(g.n_rows, nft);
+  TRS_DISPATCH_B(b, k_ilu_init<B><<<grid_of(n), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc, nft,
+                                                                  fell, ftval));
+  TRS_LAUNCHED();
+}
+
+void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
+                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, double *fell,
+                              double *ftval, int64_t q0, int64_t q1, int *err, cudaStream_t s) {
+  if (q1 <= q0) return;
+  TRS_DISPATCH_B(b, k_ilu_factor<B><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
+                                                                          ftlow, fell, ftval, q0, q1, err));
+  TRS_LAUNCHED();
+}
+
+void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s) {
+  if (!A->n) return;
+  TRS_DISPATCH_B(b, k_scale_diag<B><<<grid_of(A->n), kThreads, 0, s>>>(A->g, A->ell.p, A->tval.p, A->tdiag.p, sc));
+  TRS_LAUNCHED();
+}
+
+}  // namespace trs

@@ -1,0 +1,861 @@
+// Solve-phase kernels: block SpMV, multicolour ILU(0) sweeps, CPR residuals,
+// AMG V-cycle pieces and the FGMRES / CGS2 reductions.
+//
+// All reductions are deterministic: a fixed grid, warp shuffles in a fixed
+// pattern, per-block partial sums, and the last block to finish summing the
+// partials in block order.
+#include "trs_kernels.cuh"
+
+namespace trs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRedStride = kMaxRestart + 16;  // room for the last 16-wide chunk
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ double to_d(T v) { return static_cast<double>(v); }
+
+// ------------------------------------------------------------ block SpMV
+template <int B, class TA, class TX>
+__device__ __forceinline__ void cell_row_apply(const MatView<TA> &A, int64_t i, const TX *__restrict__ x,
+                                               double (&acc)[B]) {
+  constexpr int BB = B * B;
+  const int64_t nc = A.g.nc;
+  const unsigned m = A.emask[i];
+#pragma unroll
+  for (int s = 0; s < kSlots; s++) {
+    if (!((m >> s) & 1u)) continue;
+    const int64_t j = i + A.g.off[s];
+    double xj[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) xj[c] = to_d(x[j * B + c]);
+    const TA *blk = A.ell + (int64_t)s * BB * nc + i;
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[(int64_t)(r * B + c) * nc]), xj[c], acc[r]);
+  }
+  for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
+    const int64_t j = A.tcol[t];
+    const TA *blk = A.tval + t * BB;
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(x[j * B + c]), acc[r]);
+  }
+}
+
+// one warp, one long row (all entries in the tail); result valid on every lane
+template <int B, class TA, class TX>
+__device__ __forceinline__ void long_row_apply(const MatView<TA> &A, int64_t i, const TX *__restrict__ x,
+                                               double (&acc)[B], int lane) {
+  constexpr int BB = B * B;
+  for (int64_t t = A.tptr[i] + lane; t < A.tptr[i + 1]; t += 32) {
+    const int64_t j = A.tcol[t];
+    const TA *blk = A.tval + t * BB;
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(x[j * B + c]), acc[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
+}
+
+template <int B, class TA, class TX>
+__global__ void __launch_bounds__(kThreads) k_spmv(MatView<TA> A, const TX *__restrict__ x,
+                                                   double *__restrict__ y, double alpha, double beta,
+                                                   int64_t cell_blocks) {
+  if (blockIdx.x < cell_blocks) {
+    const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (i >= A.g.nc) return;
+    double acc[B] = {};
+    cell_row_apply<B>(A, i, x, acc);
+#pragma unroll
+    for (int r = 0; r < B; r++)
+      y[i * B + r] = (beta == 0.0) ? alpha * acc[r] : fma(alpha, acc[r], beta * y[i * B + r]);
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = A.g.nc + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
+    if (i >= A.g.n_rows) return;
+    double acc[B] = {};
+    long_row_apply<B>(A, i, x, acc, lane);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < B; r++)
+        y[i * B + r] = (beta == 0.0) ? alpha * acc[r] : fma(alpha, acc[r], beta * y[i * B + r]);
+  }
+}
+
+inline int64_t cell_blocks_of(int64_t nc) { return (nc + kThreads - 1) / kThreads; }
+inline int64_t long_blocks_of(int64_t nl) { return (nl + kWarps - 1) / kWarps; }
+
+// ----------------------------------------------------- reduction helpers
+template <int KC>
+__device__ void block_partial(double (&acc)[KC], double *__restrict__ dst) {
+  __shared__ double sm[kWarps][KC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < KC; u++) {
+    double v = warp_sum(acc[u]);
+    if (lane == 0) sm[warp][u] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < KC) {
+    double s = 0.0;
+    for (int w = 0; w < kWarps; w++) s += sm[w][threadIdx.x];
+    dst[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Called by every block after its partials are stored.  The last block sums
+// the partials of all blocks in block order into out[0..K-1]; if sqrt_out,
+// out[K] also receives sqrt(out[K-1]).
+__device__ void last_block_finish(const double *partial, unsigned int *counter, int K, double *out,
+                                  int sqrt_out) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  __shared__ double sm[kWarps];
+  for (int k = 0; k < K; k++) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) s += __ldcg(partial + (int64_t)b * kRedStride + k);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; w++) t += sm[w];
+      out[k] = t;
+      if (sqrt_out && k == K - 1) out[K] = sqrt(t);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// r = rhs - A x and ||r||^2 (out[0]), sqrt in out[1]
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_true_residual(MatView<double> A, const double *__restrict__ x,
+                                                            const double *__restrict__ rhs,
+                                                            double *__restrict__ r, int64_t cell_blocks,
+                                                            int64_t rows_per_block_long, double *partial,
+                                                            unsigned int *counter, double *out) {
+  // grid-stride over cell rows and long rows so that the grid stays fixed
+  double acc2[1] = {0.0};
+  const int64_t nc = A.g.nc, nl = A.g.n_rows - nc;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nc; i += (int64_t)gridDim.x * kThreads) {
+    double acc[B] = {};
+    cell_row_apply<B>(A, i, x, acc);
+#pragma unroll
+    for (int rr = 0; rr < B; rr++) {
+      const double v = rhs[i * B + rr] - acc[rr];
+      r[i * B + rr] = v;
+      acc2[0] = fma(v, v, acc2[0]);
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); w < nl; w += (int64_t)gridDim.x * kWarps) {
+    const int64_t i = nc + w;
+    double acc[B] = {};
+    long_row_apply<B>(A, i, x, acc, lane);
+    if (lane == 0)
+#pragma unroll
+      for (int rr = 0; rr < B; rr++) {
+        const double v = rhs[i * B + rr] - acc[rr];
+        r[i * B + rr] = v;
+        acc2[0] = fma(v, v, acc2[0]);
+      }
+  }
+  (void)cell_blocks; (void)rows_per_block_long;
+  block_partial<1>(acc2, partial + (int64_t)blockIdx.x * kRedStride);
+  last_block_finish(partial, counter, 1, out, 1);
+}
+
+__global__ void __launch_bounds__(kThreads) k_norm2(const double *__restrict__ x, int64_t n, double *partial,
+                                                    unsigned int *counter, double *out) {
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    acc[0] = fma(x[i], x[i], acc[0]);
+  block_partial<1>(acc, partial + (int64_t)blockIdx.x * kRedStride);
+  last_block_finish(partial, counter, 1, out, 1);
+}
+
+// ----------------------------------------------------------- D^-1 scale
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__restrict__ w,
+                                                     const double *__restrict__ div, double *__restrict__ vout,
+                                                     const T *__restrict__ dinv, T *__restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  double v[B];
+  const double d = div ? *div : 1.0;
+#pragma unroll
+  for (int c = 0; c < B; c++) {
+    v[c] = div ? w[i * B + c] / d : w[i * B + c];
+    if (vout) vout[i * B + c] = v[c];
+  }
+#pragma unroll
+  for (int r = 0; r < B; r++) {
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) acc = fma(dinv[(int64_t)(r * B + c) * n + i], static_cast<T>(v[c]), acc);
+    f[i * B + r] = acc;
+  }
+}
+
+// ------------------------------------------------------------ ILU sweeps
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__restrict__ rhs, T *y, int64_t q0,
+                                                      int64_t q1, int64_t q2, int64_t cell_blocks) {
+  constexpr int BB = B * B;
+  const int64_t np = F.g.n_rows;
+  if (blockIdx.x < cell_blocks) {
+    const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (q >= q1) return;
+    const int64_t i = F.crow[q];
+    T t[B];
+#pragma unroll
+    for (int r = 0; r < B; r++) t[r] = rhs[i * B + r];
+    const unsigned lm = F.lmask[q];
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      if (!((lm >> s) & 1u)) continue;
+      const int64_t j = i + F.g.off[s];
+      T yj[B];
+#pragma unroll
+      for (int c = 0; c < B; c++) yj[c] = y[j * B + c];
+      const T *blk = F.fell + (int64_t)s * BB * np + q;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) t[r] = fma(-blk[(int64_t)(r * B + c) * np], yj[c], t[r]);
+    }
+    for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
+      if (!F.ftlow[u]) continue;
+      const int64_t j = F.ftcol[u];
+      const T *blk = F.ftval + u * BB;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) t[r] = fma(-blk[r * B + c], y[j * B + c], t[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) y[i * B + r] = t[r];
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = q1 + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
+    if (q >= q2) return;
+    const int64_t i = F.crow[q];
+    double acc[B] = {};
+    for (int64_t u = F.ftptr[q] + lane; u < F.ftptr[q + 1]; u += 32) {
+      if (!F.ftlow[u]) continue;
+      const int64_t j = F.ftcol[u];
+      const T *blk = F.ftval + u * BB;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(y[j * B + c]), acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < B; r++) y[i * B + r] = static_cast<T>(to_d(rhs[i * B + r]) - acc[r]);
+  }
+}
+
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_t q0, int64_t q1, int64_t q2,
+                                                      int64_t cell_blocks, const T *__restrict__ y1,
+                                                      const T *__restrict__ e0, T *__restrict__ zout) {
+  constexpr int BB = B * B;
+  const int64_t np = F.g.n_rows;
+  T t[B];
+  int64_t i, q;
+  bool active;
+  if (blockIdx.x < cell_blocks) {
+    q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    active = q < q1;
+    if (!active) return;
+    i = F.crow[q];
+#pragma unroll
+    for (int r = 0; r < B; r++) t[r] = y[i * B + r];
+    const unsigned um = F.emask[i] & ~(unsigned)F.lmask[q] & ~(1u << kSelf);
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      if (!((um >> s) & 1u)) continue;
+      const int64_t j = i + F.g.off[s];
+      T yj[B];
+#pragma unroll
+      for (int c = 0; c < B; c++) yj[c] = y[j * B + c];
+      const T *blk = F.fell + (int64_t)s * BB * np + q;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) t[r] = fma(-blk[(int64_t)(r * B + c) * np], yj[c], t[r]);
+    }
+    for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
+      const int64_t j = F.ftcol[u];
+      if (F.ftlow[u] || j == i) continue;
+      const T *blk = F.ftval + u * BB;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) t[r] = fma(-blk[r * B + c], y[j * B + c], t[r]);
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    q = q1 + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
+    if (q >= q2) return;
+    i = F.crow[q];
+    double acc[B] = {};
+    for (int64_t u = F.ftptr[q] + lane; u < F.ftptr[q + 1]; u += 32) {
+      const int64_t j = F.ftcol[u];
+      if (F.ftlow[u] || j == i) continue;
+      const T *blk = F.ftval + u * BB;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(y[j * B + c]), acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
+    if (lane != 0) return;
+#pragma unroll
+    for (int r = 0; r < B; r++) t[r] = static_cast<T>(to_d(y[i * B + r]) - acc[r]);
+  }
+  // x_i = U_ii^-1 t
+  const T *dg = F.fell + (int64_t)kSelf * BB * np + q;
+  T xv[B];
+#pragma unroll
+  for (int r = 0; r < B; r++) {
+    T a = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) a = fma(dg[(int64_t)(r * B + c) * np], t[c], a);
+    xv[r] = a;
+  }
+#pragma unroll
+  for (int r = 0; r < B; r++) y[i * B + r] = xv[r];
+  if (zout) {
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      T base = y1[i * B + r];
+      if (r == 0) base = base + e0[i];
+      zout[i * B + r] = base + xv[r];
+    }
+  }
+}
+
+// --------------------------------------------------- CPR residuals on Ã
+// rp_i = f_i0 - (Ã y)_i0, Ã_ii = I
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__restrict__ f,
+                                                      const T *__restrict__ y, T *__restrict__ rp,
+                                                      int64_t cell_blocks) {
+  constexpr int BB = B * B;
+  if (blockIdx.x < cell_blocks) {
+    const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (i >= At.g.nc) return;
+    const int64_t nc = At.g.nc;
+    T acc = y[i * B];
+    const unsigned m = At.emask[i] & ~(1u << kSelf);
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      if (!((m >> s) & 1u)) continue;
+      const int64_t j = i + At.g.off[s];
+      const T *blk = At.ell + (int64_t)s * BB * nc + i;
+#pragma unroll
+      for (int c = 0; c < B; c++) acc = fma(blk[(int64_t)c * nc], y[j * B + c], acc);
+    }
+    for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
+      const int64_t j = At.tcol[t];
+      if (j == i) continue;
+      const T *blk = At.tval + t * BB;
+#pragma unroll
+      for (int c = 0; c < B; c++) acc = fma(blk[c], y[j * B + c], acc);
+    }
+    rp[i] = f[i * B] - acc;
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = At.g.nc + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
+    if (i >= At.g.n_rows) return;
+    double acc = 0.0;
+    for (int64_t t = At.tptr[i] + lane; t < At.tptr[i + 1]; t += 32) {
+      const int64_t j = At.tcol[t];
+      if (j == i) continue;
+      const T *blk = At.tval + t * BB;
+#pragma unroll
+      for (int c = 0; c < B; c++) acc = fma(to_d(blk[c]), to_d(y[j * B + c]), acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) rp[i] = static_cast<T>(to_d(f[i * B]) - (to_d(y[i * B]) + acc));
+  }
+}
+
+// r = f - Ã y2 with y2 = y1 + e0 in entry 0 of every block
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T *__restrict__ f,
+                                                         const T *__restrict__ y1, const T *__restrict__ e0,
+                                                         T *__restrict__ r, int64_t cell_blocks) {
+  constexpr int BB = B * B;
+  if (blockIdx.x < cell_blocks) {
+    const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (i >= At.g.nc) return;
+    const int64_t nc = At.g.nc;
+    T acc[B];
+#pragma unroll
+    for (int rr = 0; rr < B; rr++) acc[rr] = y1[i * B + rr];
+    acc[0] = acc[0] + e0[i];
+    const unsigned m = At.emask[i] & ~(1u << kSelf);
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      if (!((m >> s) & 1u)) continue;
+      const int64_t j = i + At.g.off[s];
+      T yj[B];
+#pragma unroll
+      for (int c = 0; c < B; c++) yj[c] = y1[j * B + c];
+      yj[0] = yj[0] + e0[j];
+      const T *blk = At.ell + (int64_t)s * BB * nc + i;
+#pragma unroll
+      for (int rr = 0; rr < B; rr++)
+#pragma unroll
+        for (int c = 0; c < B; c++) acc[rr] = fma(blk[(int64_t)(rr * B + c) * nc], yj[c], acc[rr]);
+    }
+    for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
+      const int64_t j = At.tcol[t];
+      if (j == i) continue;
+      T yj[B];
+#pragma unroll
+      for (int c = 0; c < B; c++) yj[c] = y1[j * B + c];
+      yj[0] = yj[0] + e0[j];
+      const T *blk = At.tval + t * BB;
+#pragma unroll
+      for (int rr = 0; rr < B; rr++)
+#pragma unroll
+        for (int c = 0; c < B; c++) acc[rr] = fma(blk[rr * B + c], yj[c], acc[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < B; rr++) r[i * B + rr] = f[i * B + rr] - acc[rr];
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = At.g.nc + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
+    if (i >= At.g.n_rows) return;
+    double acc[B] = {};
+    for (int64_t t = At.tptr[i] + lane; t < At.tptr[i + 1]; t += 32) {
+      const int64_t j = At.tcol[t];
+      if (j == i) continue;
+      const T *blk = At.tval + t * BB;
+#pragma unroll
+      for (int c = 0; c < B; c++) {
+        double yj = to_d(y1[j * B + c]);
+        if (c == 0) yj += to_d(e0[j]);
+#pragma unroll
+        for (int rr = 0; rr < B; rr++) acc[rr] = fma(to_d(blk[rr * B + c]), yj, acc[rr]);
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < B; rr++) acc[rr] = warp_sum(acc[rr]);
+    if (lane == 0)
+#pragma unroll
+      for (int rr = 0; rr < B; rr++) {
+        double own = to_d(y1[i * B + rr]);
+        if (rr == 0) own += to_d(e0[i]);
+        r[i * B + rr] = static_cast<T>(to_d(f[i * B + rr]) - (own + acc[rr]));
+      }
+  }
+}
+
+// ------------------------------------------------------------- AMG pieces
+template <class T>
+__device__ __forceinline__ T scalar_rowdot(const ScalarOp<T> &op, int64_t i, const T *__restrict__ x) {
+  T acc = T(0);
+  if (op.is_ell) {
+    if (i < op.g.nc) {
+      const unsigned m = op.emask[i];
+#pragma unroll
+      for (int s = 0; s < kSlots; s++)
+        if ((m >> s) & 1u) acc = fma(op.ell[(int64_t)s * op.g.nc + i], x[i + op.g.off[s]], acc);
+    }
+    for (int64_t t = op.tptr[i]; t < op.tptr[i + 1]; t++) acc = fma(op.tval[t], x[op.tcol[t]], acc);
+  } else {
+    for (int64_t p = op.rp[i]; p < op.rp[i + 1]; p++) acc = fma(op.val[p], x[op.col[p]], acc);
+  }
+  return acc;
+}
+
+template <class T>
+__global__ void k_cheb_init(int64_t n, const T *__restrict__ r, const T *__restrict__ dinv, T inv_theta,
+                            T *__restrict__ d, T *__restrict__ e) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  d[i] = (dinv[i] * r[i]) * inv_theta;
+  e[i] = T(0);
+}
+
+template <class T>
+__global__ void k_cheb_resid_init(ScalarOp<T> op, const T *__restrict__ r, const T *__restrict__ e,
+                                  const T *__restrict__ dinv, T inv_theta, T *__restrict__ res,
+                                  T *__restrict__ d) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= op.n) return;
+  const T v = r[i] - scalar_rowdot(op, i, e);
+  res[i] = v;
+  d[i] = (dinv[i] * v) * inv_theta;
+}
+
+// res -= A d; dn = c1 d + c2 D^-1 res; e = (e + d) [+ dn if last]
+template <class T>
+__global__ void k_cheb_step(ScalarOp<T> op, const T *res_in, T *res_out, const T *__restrict__ d,
+                            const T *__restrict__ dinv, T c1, T c2, T *__restrict__ dn, T *__restrict__ e,
+                            int last) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= op.n) return;
+  const T rv = res_in[i] - scalar_rowdot(op, i, d);
+  res_out[i] = rv;
+  const T di = d[i];
+  const T nv = fma(c1, di, c2 * (dinv[i] * rv));
+  const T ev = e[i] + di;
+  if (last) {
+    e[i] = ev + nv;
+  } else {
+    e[i] = ev;
+    dn[i] = nv;
+  }
+}
+
+template <class T>
+__global__ void k_scalar_resid(ScalarOp<T> op, const T *__restrict__ r, const T *__restrict__ e,
+                               T *__restrict__ res) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= op.n) return;
+  res[i] = r[i] - scalar_rowdot(op, i, e);
+}
+
+template <class T>
+__global__ void k_restrict(int64_t nc, const int64_t *__restrict__ mptr, const int32_t *__restrict__ midx,
+                           const T *__restrict__ res, T *__restrict__ rc) {
+  const int64_t I = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (I >= nc) return;
+  T s = T(0);
+  for (int64_t t = mptr[I]; t < mptr[I + 1]; t++) s = s + res[midx[t]];
+  rc[I] = s;
+}
+
+template <class T>
+__global__ void k_prolong(int64_t n, const int32_t *__restrict__ agg, const T *__restrict__ ec,
+                          T *__restrict__ e) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  const int32_t a = agg[i];
+  if (a >= 0) e[i] = e[i] + ec[a];
+}
+
+template <class T>
+__global__ void k_dense_gemv(int64_t n, const double *__restrict__ Minv, const T *__restrict__ r,
+                             T *__restrict__ e) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc = fma(Minv[i * n + j], to_d(r[j]), acc);
+  acc = warp_sum(acc);
+  if (lane == 0) e[i] = static_cast<T>(acc);
+}
+
+// ------------------------------------------------------- FGMRES / CGS2
+template <int KC>
+__global__ void __launch_bounds__(kThreads) k_multidot(const double *__restrict__ V, int64_t N, int K,
+                                                       const double *__restrict__ w, double *partial,
+                                                       unsigned int *counter, double *out) {
+  // out[k] = <V_k, w> for k < K, out[K] = <w, w>
+  const int KT = K + 1;
+  for (int k0 = 0; k0 < KT; k0 += KC) {
+    double acc[KC] = {};
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+      const double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < KC; u++) {
+        const int k = k0 + u;
+        if (k < K) acc[u] = fma(V[(int64_t)k * N + i], wi, acc[u]);
+        else if (k == K) acc[u] = fma(wi, wi, acc[u]);
+      }
+    }
+    block_partial<KC>(acc, partial + (int64_t)blockIdx.x * kRedStride + k0);
+  }
+  last_block_finish(partial, counter, KT, out, 0);
+}
+
+// w -= sum_k h_k V_k; if want_norm: out[0] = ||w||^2
+__global__ void __launch_bounds__(kThreads) k_cgs_update(const double *__restrict__ V, int64_t N, int K,
+                                                         const double *__restrict__ h, double *__restrict__ w,
+                                                         int want_norm, double *partial, unsigned int *counter,
+                                                         double *out) {
+  __shared__ double sh[kMaxRestart + 1];
+  for (int k = threadIdx.x; k < K; k += kThreads) sh[k] = h[k];
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+    double v = w[i];
+    for (int k = 0; k < K; k++) v = fma(-sh[k], V[(int64_t)k * N + i], v);
+    w[i] = v;
+    acc[0] = fma(v, v, acc[0]);
+  }
+  if (!want_norm) return;
+  block_partial<1>(acc, partial + (int64_t)blockIdx.x * kRedStride);
+  last_block_finish(partial, counter, 1, out, 0);
+}
+
+// Arnoldi column j of H (row-major, m columns): h1 + h2, norm; Givens.
+// status[0] = |g_{j+1}| / ||b||, status[1] = breakdown flag, hnorm[0] = h_{j+1,j}
+__global__ void k_givens(int j, int m, double *H, const double *h1, const double *h2, const double *hn2,
+                         const double *wn2, double *cs, double *sn, double *g, double *hnorm,
+                         double *status, double inv_bnorm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k <= j; k++) H[k * m + j] = h1[k] + h2[k];
+  const double hn = sqrt(hn2[0]);
+  H[(j + 1) * m + j] = hn;
+  for (int k = 0; k < j; k++) {
+    const double a = H[k * m + j], c = H[(k + 1) * m + j];
+    H[k * m + j] = cs[k] * a + sn[k] * c;
+    H[(k + 1) * m + j] = -sn[k] * a + cs[k] * c;
+  }
+  const double a = H[j * m + j], c = H[(j + 1) * m + j];
+  const double d = sqrt(a * a + c * c);
+  cs[j] = a / d;
+  sn[j] = c / d;
+  H[j * m + j] = d;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  hnorm[0] = hn;
+  status[0] = fabs(g[j + 1]) * inv_bnorm;
+  status[1] = (hn <= 1e-14 * sqrt(wn2[0])) ? 1.0 : 0.0;
+}
+
+__global__ void k_lsq(int jdone, int m, const double *H, const double *g, double *y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = jdone - 1; i >= 0; i--) {
+    double s = g[i];
+    for (int k = i + 1; k < jdone; k++) s = s - H[i * m + k] * y[k];
+    y[i] = s / H[i * m + i];
+  }
+}
+
+template <class TZ>
+__global__ void __launch_bounds__(kThreads) k_xupdate(const TZ *__restrict__ Z, int64_t N, int K,
+                                                      const double *__restrict__ y, double *__restrict__ x) {
+  __shared__ double sy[kMaxRestart];
+  for (int k = threadIdx.x; k < K; k += kThreads) sy[k] = y[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+    double v = x[i];
+    for (int k = 0; k < K; k++) v = fma(sy[k], to_d(Z[(int64_t)k * N + i]), v);
+    x[i] = v;
+  }
+}
+
+template <class TS, class TD>
+__global__ void k_cast(const TS *__restrict__ a, TD *__restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    b[i] = static_cast<TD>(a[i]);
+}
+
+inline unsigned grid_of(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+// ================================================================ launchers
+template <class TA, class TX>
+void launch_spmv(int b, const MatView<TA> &A, const TX *x, double *y, double alpha, double beta,
+                 cudaStream_t s) {
+  const int64_t cb = cell_blocks_of(A.g.nc), lb = long_blocks_of(A.g.n_rows - A.g.nc);
+  if (cb + lb == 0) return;
+  TRS_DISPATCH_B(b, k_spmv<B, TA, TX><<<(unsigned)(cb + lb), kThreads, 0, s>>>(A, x, y, alpha, beta, cb));
+  TRS_LAUNCHED();
+}
+template void launch_spmv<double, double>(int, const MatView<double> &, const double *, double *, double,
+                                          double, cudaStream_t);
+template void launch_spmv<double, float>(int, const MatView<double> &, const float *, double *, double,
+                                         double, cudaStream_t);
+
+void launch_true_residual(int b, const MatView<double> &A, const double *x, const double *rhs, double *r,
+                          const RedScratch &red, double *out_norm2, cudaStream_t s) {
+  TRS_DISPATCH_B(b, k_true_residual<B><<<red.grid, kThreads, 0, s>>>(A, x, rhs, r, 0, 0, red.partial,
+                                                                      red.counter, out_norm2));
+  TRS_LAUNCHED();
+}
+
+void launch_norm2(const double *x, int64_t n, const RedScratch &red, double *out, cudaStream_t s) {
+  k_norm2<<<red.grid, kThreads, 0, s>>>(x, n, red.partial, red.counter, out);
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_dscale(int b, int64_t n_rows, const double *w, const double *div, double *vout, const T *dinv, T *f,
+                   cudaStream_t s) {
+  if (!n_rows) return;
+  TRS_DISPATCH_B(b, k_dscale<B, T><<<grid_of(n_rows), kThreads, 0, s>>>(n_rows, w, div, vout, dinv, f));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, int64_t q1, int64_t q2,
+                    cudaStream_t s) {
+  const int64_t cb = cell_blocks_of(q1 - q0), lb = long_blocks_of(q2 - q1);
+  if (cb + lb == 0) return;
+  TRS_DISPATCH_B(b, k_ilu_fwd<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, rhs, y, q0, q1, q2, cb));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2, const T *y1,
+                    const T *e0, T *zout, cudaStream_t s) {
+  const int64_t cb = cell_blocks_of(q1 - q0), lb = long_blocks_of(q2 - q1);
+  if (cb + lb == 0) return;
+  TRS_DISPATCH_B(b, k_ilu_bwd<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0,
+                                                                             zout));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, cudaStream_t s) {
+  const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
+  if (cb + lb == 0) return;
+  TRS_DISPATCH_B(b, k_resid_p<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y, rp, cb));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r,
+                       cudaStream_t s) {
+  const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
+  if (cb + lb == 0) return;
+  TRS_DISPATCH_B(b, k_resid_full<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y1, e0, r, cb));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_cheb_init(int64_t n, const T *r, const T *dinv, double inv_theta, T *d, T *e, cudaStream_t s) {
+  if (!n) return;
+  k_cheb_init<T><<<grid_of(n), kThreads, 0, s>>>(n, r, dinv, static_cast<T>(inv_theta), d, e);
+  TRS_LAUNCHED();
+}
+template <class T>
+void launch_cheb_resid_init(const ScalarOp<T> &op, const T *r, const T *e, const T *dinv, double inv_theta,
+                            T *res, T *d, cudaStream_t s) {
+  if (!op.n) return;
+  k_cheb_resid_init<T><<<grid_of(op.n), kThreads, 0, s>>>(op, r, e, dinv, static_cast<T>(inv_theta), res, d);
+  TRS_LAUNCHED();
+}
+template <class T>
+void launch_cheb_step(const ScalarOp<T> &op, const T *res_in, T *res_out, const T *d, const T *dinv, double c1,
+                      double c2, T *dn, T *e, int last, cudaStream_t s) {
+  if (!op.n) return;
+  k_cheb_step<T><<<grid_of(op.n), kThreads, 0, s>>>(op, res_in, res_out, d, dinv, static_cast<T>(c1),
+                                                    static_cast<T>(c2), dn, e, last);
+  TRS_LAUNCHED();
+}
+template <class T>
+void launch_scalar_resid(const ScalarOp<T> &op, const T *r, const T *e, T *res, cudaStream_t s) {
+  if (!op.n) return;
+  k_scalar_resid<T><<<grid_of(op.n), kThreads, 0, s>>>(op, r, e, res);
+  TRS_LAUNCHED();
+}
+template <class T>
+void launch_restrict(int64_t nc, const int64_t *mptr, const int32_t *midx, const T *res, T *rc, cudaStream_t s) {
+  if (!nc) return;
+  k_restrict<T><<<grid_of(nc), kThreads, 0, s>>>(nc, mptr, midx, res, rc);
+  TRS_LAUNCHED();
+}
+template <class T>
+void launch_prolong(int64_t n, const int32_t *agg, const T *ec, T *e, cudaStream_t s) {
+  if (!n) return;
+  k_prolong<T><<<grid_of(n), kThreads, 0, s>>>(n, agg, ec, e);
+  TRS_LAUNCHED();
+}
+template <class T>
+void launch_dense_gemv(int64_t n, const double *Minv, const T *r, T *e, cudaStream_t s) {
+  if (!n) return;
+  k_dense_gemv<T><<<(unsigned)((n + kWarps - 1) / kWarps), kThreads, 0, s>>>(n, Minv, r, e);
+  TRS_LAUNCHED();
+}
+
+void launch_multidot(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
+                     cudaStream_t s) {
+  k_multidot<16><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
+  TRS_LAUNCHED();
+}
+void launch_cgs_update(const double *V, int64_t N, int K, const double *h, double *w, int want_norm,
+                       const RedScratch &red, double *out, cudaStream_t s) {
+  k_cgs_update<<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, want_norm, red.partial, red.counter, out);
+  TRS_LAUNCHED();
+}
+void launch_givens(int j, int m, double *H, const double *h1, const double *h2, const double *hn2,
+                   const double *wn2, double *cs, double *sn, double *g, double *hnorm_out, double *status,
+                   double inv_bnorm, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(j, m, H, h1, h2, hn2, wn2, cs, sn, g, hnorm_out, status, inv_bnorm);
+  TRS_LAUNCHED();
+}
+void launch_lsq(int jdone, int m, const double *H, const double *g, double *y, cudaStream_t s) {
+  k_lsq<<<1, 32, 0, s>>>(jdone, m, H, g, y);
+  TRS_LAUNCHED();
+}
+template <class TZ>
+void launch_xupdate(const TZ *Z, int64_t N, int K, const double *y, double *x, cudaStream_t s) {
+  if (!N || !K) return;
+  unsigned grid = grid_of(N);
+  if (grid > 152u * 16u) grid = 152u * 16u;
+  k_xupdate<TZ><<<grid, kThreads, 0, s>>>(Z, N, K, y, x);
+  TRS_LAUNCHED();
+}
+template <class TS, class TD>
+void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
+  if (!n) return;
+  unsigned grid = grid_of(n);
+  if (grid > 152u * 16u) grid = 152u * 16u;
+  k_cast<TS, TD><<<grid, kThreads, 0, s>>>(src, dst, n);
+  TRS_LAUNCHED();
+}
+
+#define TRS_INST_T(T)                                                                                       \
+  template void launch_dscale<T>(int, int64_t, const double *, const double *, double *, const T *, T *,     \
+                                 cudaStream_t);                                                             \
+  template void launch_ilu_fwd<T>(int, const IluView<T> &, const T *, T *, int64_t, int64_t, int64_t,        \
+                                  cudaStream_t);                                                            \
+  template void launch_ilu_bwd<T>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,        \
+                                  const T *, T *, cudaStream_t);                                            \
+  template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, T *, cudaStream_t);        \
+  template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *,         \
+                                     cudaStream_t);                                                         \
+  template void launch_cheb_init<T>(int64_t, const T *, const T *, double, T *, T *, cudaStream_t);         \
+  template void launch_cheb_resid_init<T>(const ScalarOp<T> &, const T *, const T *, const T *, double, T *, \
+                                          T *, cudaStream_t);                                               \
+  template void launch_cheb_step<T>(const ScalarOp<T> &, const T *, T *, const T *, const T *, double,      \
+                                    double, T *, T *, int, cudaStream_t);                                   \
+  template void launch_scalar_resid<T>(const ScalarOp<T> &, const T *, const T *, T *, cudaStream_t);       \
+  template void launch_restrict<T>(int64_t, const int64_t *, const int32_t *, const T *, T *, cudaStream_t); \
+  template void launch_prolong<T>(int64_t, const int32_t *, const T *, T *, cudaStream_t);                  \
+  template void launch_dense_gemv<T>(int64_t, const double *, const T *, T *, cudaStream_t);                \
+  template void launch_xupdate<T>(const T *, int64_t, int, const double *, double *, cudaStream_t);
+
+TRS_INST_T(double)
+TRS_INST_T(float)
+template void launch_cast<double, float>(const double *, float *, int64_t, cudaStream_t);
+template void launch_cast<float, double>(const float *, double *, int64_t, cudaStream_t);
+template void launch_cast<double, double>(const double *, double *, int64_t, cudaStream_t);
+
+}  // namespace trs

@@ -1,0 +1,727 @@
+// Host runtime for the CPR-FPF preconditioner and the FGMRES solve.
+//
+// Setup (Sec. "Decoupling Methods", Sec. "Preconditioners"):
+//   ABF/GJE decoupling -> pressure matrix -> aggregation AMG hierarchy ->
+//   multicolouring -> block ILU(0) -> optional FP32 copies.
+// Application, with f = D^-1 v (Algorithm pc-fpf read from its prose):
+//   y1 = F^-1 f; r1_p = (f - Ã y1)_0; e = V-cycle(r1_p);
+//   r2 = f - Ã (y1 + Pi_p e); z = y1 + Pi_p e + F^-1 r2.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+
+#include "trs_api_common.cuh"
+
+namespace trs {
+
+namespace {
+thread_local std::string g_last_error;
+
+constexpr uint32_t kLevelSeedMul = 0x9E3779B9u;
+constexpr uint32_t kColourSeedXor = 0x85EBCA77u;
+constexpr int kRedGridMax = 152 * 8;
+
+template <class T>
+T *tp(const DBuf<char> &b) { return reinterpret_cast<T *>(b.p); }
+
+void alloc_vec(DBuf<char> &b, int64_t n, size_t elem) { b.alloc(std::max<int64_t>(n, 1) * elem); }
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    TRS_CUDA(cudaEventCreate(&a));
+    TRS_CUDA(cudaEventCreate(&b));
+    TRS_CUDA(cudaEventRecord(a, s));
+  }
+  double stop() {
+    TRS_CUDA(cudaEventRecord(b, s));
+    TRS_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    TRS_CUDA(cudaEventElapsedTime(&ms, a, b));
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// ------------------------------------------------------------ AMG setup
+void build_hierarchy(trs_cpr *M, cudaStream_t s) {
+  const trs_cpr_opts &o = M->opts;
+  auto &lev = M->lev;
+  for (int l = 0;; l++) {
+    Level &F = lev[l];
+    const int64_t n = F.A.n;
+    F.dpos.alloc(std::max<int64_t>(n, 1));
+    launch_diag_pos(n, F.A.rp.p, F.A.col.p, F.dpos.p, s);
+    F.dinv64.alloc(std::max<int64_t>(n, 1));
+    F.lam = launch_gershgorin_dinv(F.A, F.dpos.p, F.dinv64.p, s);
+    if (n <= o.coarse_max || l + 1 >= o.max_levels) break;
+    const int64_t nnz = F.A.nnz;
+    DBuf<uint8_t> sflag(std::max<int64_t>(nnz, 1));
+    DBuf<int32_t> sdeg(n);
+    launch_strength(n, F.A.rp.p, F.A.col.p, F.A.val.p, F.dpos.p, o.theta, sflag.p, sdeg.p, s);
+    // MIS-2 rounds
+    const uint32_t seed = o.seed ^ (kLevelSeedMul * (uint32_t)(l + 1));
+    DBuf<int8_t> state(n), s1(n), s2(n);
+    DBuf<uint64_t> k1(n), k2(n);
+    DBuf<unsigned long long> und(1);
+    launch_mis2_init(n, sdeg.p, state.p, s);
+    for (int round = 0;; round++) {
+      TRS_REQUIRE(round < 10000, TRS_ERR_COARSENING, "MIS-2 did not terminate");
+      und.zero(s);
+      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, nullptr, seed, s1.p, k1.p, s);
+      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, s1.p, k1.p, seed, s2.p, k2.p, s);
+      launch_mis2_decide(n, seed, s2.p, k2.p, state.p, und.p, s);
+      unsigned long long left = 0;
+      TRS_CUDA(cudaMemcpyAsync(&left, und.p, sizeof(left), cudaMemcpyDeviceToHost, s));
+      TRS_CUDA(cudaStreamSynchronize(s));
+      if (!left) break;
+    }
+    // aggregates
+    DBuf<int64_t> flag(n + 1), rootid(n + 1);
+    flag.zero(s);
+    launch_in_flag(n, state.p, flag.p, s);
+    exclusive_scan(flag.p, rootid.p, n + 1, nullptr, s);
+    int64_t n_agg = 0;
+    TRS_CUDA(cudaMemcpyAsync(&n_agg, rootid.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+    if (n_agg == 0 || 10 * n_agg >= 9 * n) break;
+    DBuf<int32_t> first(n);
+    F.agg.alloc(n);
+    launch_agg_pass1(n, F.A.rp.p, F.A.col.p, sflag.p, sdeg.p, state.p, rootid.p, first.p, s);
+    launch_agg_pass2(n, F.A.rp.p, F.A.col.p, F.A.val.p, sflag.p, sdeg.p, first.p, F.agg.p, s);
+    F.n_agg = n_agg;
+    launch_members(n, F.agg.p, n_agg, F.mptr, F.midx, s);
+    lev.emplace_back();
+    launch_galerkin(lev[l].A, lev[l].agg.p, n_agg, lev[l].mptr.p, lev[l].midx.p, lev[l + 1].A, s);
+    TRS_CUDA(cudaStreamSynchronize(s));
+  }
+  Level &C = lev.back();
+  TRS_REQUIRE(C.A.n <= kDenseMax, TRS_ERR_COARSENING, "AMG coarsening stalled above the dense-solve limit");
+  TRS_REQUIRE(launch_dense_inverse(C.A, M->cinv, s) == 0, TRS_ERR_SINGULAR_BLOCK, "coarsest AMG matrix is singular");
+}
+
+// --------------------------------------------------- decoupling + ILU
+void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s) {
+  const int b = M->b, bb = b * b;
+  const int64_t n = M->n, nc = M->g.nc;
+  DBuf<int> err(1);
+  err.zero(s);
+  launch_decouple(b, A->view(), A->tdiag.p, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
+                  M->ap_tval64.p, err.p, s);
+  int herr = 0;
+  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  TRS_REQUIRE(!herr, TRS_ERR_SINGULAR_BLOCK, "a diagonal block is singular");
+  if (rebuild_amg) {
+    M->lev.clear();
+    M->lev.emplace_back();
+    Csr &C0 = M->lev[0].A;
+    C0.n = n;
+    C0.rp.alloc(n + 1);
+    DBuf<int64_t> len(n + 1);
+    len.zero(s);
+    launch_ap_csr_rowlen(M->g, M->emask.p, M->tptr.p, len.p, s);
+    exclusive_scan(len.p, C0.rp.p, n + 1, nullptr, s);
+    TRS_CUDA(cudaMemcpyAsync(&C0.nnz, C0.rp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+    C0.col.alloc(C0.nnz);
+    C0.val.alloc(C0.nnz);
+    launch_ap_csr_fill(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->ap_ell64.p, M->ap_tval64.p, C0.rp.p, C0.col.p,
+                       C0.val.p, s);
+    build_hierarchy(M, s);
+  }
+  // block ILU(0) on Ã
+  launch_ilu_init(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft, M->fell64.p,
+                  M->ftval64.p, s);
+  err.zero(s);
+  for (int c = 0; c < M->ncol; c++)
+    launch_ilu_factor_colour(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
+                             M->fell64.p, M->ftval64.p, M->cptr[c], M->cptr[c + 1], err.p, s);
+  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  TRS_REQUIRE(!herr, TRS_ERR_SINGULAR_BLOCK, "a block ILU(0) pivot block is singular");
+  if (M->prec == TRS_FP32_PREC) {
+    auto cast = [&](DBuf<double> &src, DBuf<float> &dst, int64_t cnt) {
+      if (dst.n < (size_t)std::max<int64_t>(cnt, 1)) dst.alloc(std::max<int64_t>(cnt, 1));
+      launch_cast<double, float>(src.p, dst.p, cnt, s);
+    };
+    cast(M->at_ell64, M->at_ell32, (int64_t)kSlots * bb * nc);
+    cast(M->at_tval64, M->at_tval32, M->ntail * bb);
+    cast(M->dinv64, M->dinv32, (int64_t)bb * n);
+    cast(M->ap_ell64, M->ap_ell32, (int64_t)kSlots * nc);
+    cast(M->ap_tval64, M->ap_tval32, M->ntail);
+    cast(M->fell64, M->fell32, (int64_t)kSlots * bb * n);
+    cast(M->ftval64, M->ftval32, M->nft * bb);
+    for (size_t l = 0; l < M->lev.size(); l++) {
+      Level &L = M->lev[l];
+      cast(L.dinv64, L.dinv32, L.A.n);
+      if (l > 0) cast(L.A.val, L.val32, L.A.nnz);
+    }
+  }
+  TRS_CUDA(cudaStreamSynchronize(s));
+}
+
+void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
+  const int b = A->b, bb = b * b;
+  const int64_t n = A->n, nc = A->g.nc;
+  M->b = b;
+  M->n = n;
+  M->N = n * b;
+  M->g = A->g;
+  M->ntail = A->ntail;
+  M->nnzb = A->nnzb;
+  auto copy_d2d = [&](auto &dst, const auto &src, int64_t cnt) {
+    using E = std::remove_reference_t<decltype(*src.p)>;
+    dst.alloc(std::max<int64_t>(cnt, 1));
+    if (cnt) TRS_CUDA(cudaMemcpyAsync(dst.p, src.p, cnt * sizeof(E), cudaMemcpyDeviceToDevice, s));
+  };
+  copy_d2d(M->emask, A->emask, nc);
+  copy_d2d(M->tptr, A->tptr, n + 1);
+  copy_d2d(M->tcol, A->tcol, A->ntail);
+  copy_d2d(M->tdiag, A->tdiag, n - nc);
+  copy_d2d(M->map, A->map, A->nnzb);
+  M->at_ell64.alloc(std::max<int64_t>((int64_t)kSlots * bb * nc, 1));
+  M->at_ell64.zero(s);
+  M->at_tval64.alloc(std::max<int64_t>(A->ntail * bb, 1));
+  M->dinv64.alloc((size_t)bb * n);
+  M->ap_ell64.alloc(std::max<int64_t>((int64_t)kSlots * nc, 1));
+  M->ap_ell64.zero(s);
+  M->ap_tval64.alloc(std::max<int64_t>(A->ntail, 1));
+  // colouring of the block pattern and the colour-major order
+  M->colour.alloc(n);
+  const int rounds = launch_colour(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->opts.seed ^ kColourSeedXor,
+                                   M->colour.p, s);
+  TRS_REQUIRE(rounds >= 0, TRS_ERR_UNSUPPORTED, "more than 64 colours needed");
+  {
+    auto hc = download(M->colour.p, n, s);
+    int mx = 0;
+    for (auto c : hc) mx = std::max(mx, c + 1);
+    M->ncol = mx;
+  }
+  M->crow.alloc(n);
+  M->pos.alloc(n);
+  launch_colour_order(M->g, M->colour.p, M->ncol, M->cptr, M->cmid, M->crow.p, M->pos.p, s);
+  M->lmask.alloc(n);
+  launch_ilu_structure(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->crow.p, M->pos.p, M->lmask.p, M->ftptr, M->ftcol,
+                       M->ftlow, M->ftsrc, s);
+  M->nft = M->ntail;
+  M->fell64.alloc((size_t)kSlots * bb * n);
+  M->ftval64.alloc(std::max<int64_t>(M->nft * bb, 1));
+  build_values(M, A, true, s);
+  // work vectors
+  const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
+  alloc_vec(M->wf, M->N, es);
+  alloc_vec(M->wy, M->N, es);
+  alloc_vec(M->wr, M->N, es);
+  alloc_vec(M->wx, M->N, es);
+  alloc_vec(M->wz, M->N, es);
+  for (auto &L : M->lev) {
+    alloc_vec(L.r, L.A.n, es);
+    alloc_vec(L.e, L.A.n, es);
+    alloc_vec(L.res, L.A.n, es);
+    alloc_vec(L.d, L.A.n, es);
+    alloc_vec(L.dn, L.A.n, es);
+  }
+}
+
+// ------------------------------------------------------------ application
+template <class T>
+struct Prec {
+  static const T *dinv(const trs_cpr *M);
+};
+
+template <class T>
+MatView<T> at_view(const trs_cpr *M) {
+  MatView<T> v{M->g, M->emask.p, M->tptr.p, M->tcol.p, nullptr, nullptr};
+  if constexpr (std::is_same<T, float>::value) { v.ell = M->at_ell32.p; v.tval = M->at_tval32.p; }
+  else { v.ell = M->at_ell64.p; v.tval = M->at_tval64.p; }
+  return v;
+}
+
+template <class T>
+IluView<T> ilu_view(const trs_cpr *M) {
+  IluView<T> v{M->g, M->crow.p, M->emask.p, M->lmask.p, M->ftptr.p, M->ftcol.p, M->ftlow.p, nullptr, nullptr};
+  if constexpr (std::is_same<T, float>::value) { v.fell = M->fell32.p; v.ftval = M->ftval32.p; }
+  else { v.fell = M->fell64.p; v.ftval = M->ftval64.p; }
+  return v;
+}
+
+template <class T>
+const T *dinv_of(const trs_cpr *M) {
+  if constexpr (std::is_same<T, float>::value) return M->dinv32.p;
+  else return M->dinv64.p;
+}
+
+template <class T>
+ScalarOp<T> level_op(const trs_cpr *M, int l) {
+  ScalarOp<T> op{};
+  const Level &L = M->lev[l];
+  op.n = L.A.n;
+  if (l == 0) {
+    op.is_ell = 1;
+    op.g = M->g;
+    op.emask = M->emask.p;
+    op.tptr = M->tptr.p;
+    op.tcol = M->tcol.p;
+    if constexpr (std::is_same<T, float>::value) { op.ell = M->ap_ell32.p; op.tval = M->ap_tval32.p; }
+    else { op.ell = M->ap_ell64.p; op.tval = M->ap_tval64.p; }
+  } else {
+    op.is_ell = 0;
+    op.rp = L.A.rp.p;
+    op.col = L.A.col.p;
+    if constexpr (std::is_same<T, float>::value) op.val = L.val32.p;
+    else op.val = L.A.val.p;
+  }
+  return op;
+}
+
+template <class T>
+const T *level_dinv(const Level &L) {
+  if constexpr (std::is_same<T, float>::value) return L.dinv32.p;
+  else return L.dinv64.p;
+}
+
+// Chebyshev smoothing of degree >= 2 (Saad, Alg. 12.1 on D^-1 A over
+// [0.3 lam, lam]); zero_init starts from e = 0.
+template <class T>
+void chebyshev(const trs_cpr *M, int l, const T *r, T *e, bool zero_init, cudaStream_t s) {
+  const Level &L = M->lev[l];
+  const ScalarOp<T> op = level_op<T>(M, l);
+  const double alpha = 0.3 * L.lam, beta = L.lam;
+  const double theta = (beta + alpha) / 2.0, delta = (beta - alpha) / 2.0;
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  T *res = tp<T>(L.res), *d = tp<T>(L.d), *dn = tp<T>(L.dn);
+  const T *dinv = level_dinv<T>(L);
+  const T *res_in = res;
+  if (zero_init) {
+    launch_cheb_init<T>(L.A.n, r, dinv, 1.0 / theta, d, e, s);
+    res_in = r;
+  } else {
+    launch_cheb_resid_init<T>(op, r, e, dinv, 1.0 / theta, res, d, s);
+  }
+  const int deg = M->opts.cheb_degree;
+  for (int k = 1; k < deg; k++) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rho_new * rho, c2 = (2.0 * rho_new) / delta;
+    const int last = (k == deg - 1);
+    launch_cheb_step<T>(op, res_in, res, d, dinv, c1, c2, dn, e, last, s);
+    res_in = res;
+    std::swap(d, dn);
+    rho = rho_new;
+  }
+}
+
+template <class T>
+void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
+  const int L = (int)M->lev.size();
+  const Level &Lv = M->lev[l];
+  if (l == L - 1) {
+    launch_dense_gemv<T>(Lv.A.n, M->cinv.p, r, e, s);
+    return;
+  }
+  chebyshev<T>(M, l, r, e, true, s);
+  launch_scalar_resid<T>(level_op<T>(M, l), r, e, tp<T>(Lv.res), s);
+  const Level &C = M->lev[l + 1];
+  launch_restrict<T>(C.A.n, Lv.mptr.p, Lv.midx.p, tp<T>(Lv.res), tp<T>(C.r), s);
+  vcycle<T>(M, l + 1, tp<T>(C.r), tp<T>(C.e), s);
+  launch_prolong<T>(Lv.A.n, Lv.agg.p, tp<T>(C.e), e, s);
+  chebyshev<T>(M, l, r, e, false, s);
+}
+
+template <class T>
+void ilu_solve(const trs_cpr *M, const T *rhs, T *y, const T *y1, const T *e0, T *zout, cudaStream_t s) {
+  const IluView<T> F = ilu_view<T>(M);
+  for (int c = 0; c < M->ncol; c++) launch_ilu_fwd<T>(M->b, F, rhs, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], s);
+  for (int c = M->ncol - 1; c >= 0; c--)
+    launch_ilu_bwd<T>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout, s);
+}
+
+// z = CPR(Ã)^-1 f (f already scaled by D^-1), written to z (precision T)
+template <class T>
+void cpr_apply_scaled(const trs_cpr *M, T *z, cudaStream_t s) {
+  T *f = tp<T>(M->wf), *y = tp<T>(M->wy), *r = tp<T>(M->wr), *x = tp<T>(M->wx);
+  const Level &L0 = M->lev[0];
+  ilu_solve<T>(M, f, y, nullptr, nullptr, nullptr, s);
+  launch_resid_p<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.r), s);
+  vcycle<T>(M, 0, tp<T>(L0.r), tp<T>(L0.e), s);
+  launch_resid_full<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.e), r, s);
+  ilu_solve<T>(M, r, x, y, tp<T>(L0.e), z, s);
+}
+
+template <class T>
+void cpr_apply_full(const trs_cpr *M, const double *v, const double *div, double *vout, T *z, cudaStream_t s) {
+  launch_dscale<T>(M->b, M->n, v, div, vout, dinv_of<T>(M), tp<T>(M->wf), s);
+  cpr_apply_scaled<T>(M, z, s);
+}
+
+// -------------------------------------------------------------- FGMRES
+void ensure_workspace(trs_cpr *M, int m) {
+  if (M->ws_m >= m) return;
+  const int64_t N = M->N;
+  const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
+  M->V.alloc((size_t)(m + 1) * N);
+  M->Z.alloc((size_t)m * N * es);
+  M->w.alloc(N);
+  M->r.alloc(N);
+  M->H.alloc((size_t)(m + 1) * m);
+  M->cs.alloc(m);
+  M->sn.alloc(m);
+  M->gv.alloc(m + 1);
+  M->h1.alloc(m + 2);
+  M->h2.alloc(m + 2);
+  M->hn2.alloc(2);
+  M->hnorm.alloc(2);
+  M->status.alloc(2);
+  M->yv.alloc(m);
+  M->norms.alloc(4);
+  M->red_grid = (int)std::min<int64_t>(kRedGridMax, std::max<int64_t>(1, (N + 255) / 256));
+  M->partial.alloc((size_t)M->red_grid * (kMaxRestart + 16));
+  M->counter.alloc(1);
+  M->counter.zero(0);
+  TRS_CUDA(cudaDeviceSynchronize());
+  M->ws_m = m;
+}
+
+template <class T>
+trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, const trs_solve_opts &o,
+                  cudaStream_t s, trs_solve_stats *st) {
+  const int m = o.restart;
+  const int64_t N = M->N;
+  ensure_workspace(M, m);
+  const RedScratch red{M->partial.p, M->counter.p, M->red_grid};
+  const MatView<double> Av = A->view();
+  T *Z = tp<T>(M->Z);
+  double *V = M->V.p;
+  trs_solve_stats local{};
+  Timer timer(s);
+  launch_norm2(b, N, red, M->norms.p + 2, s);
+  double hb[2];
+  TRS_CUDA(cudaMemcpyAsync(hb, M->norms.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = hb[1];
+  TRS_REQUIRE(std::isfinite(bnorm), TRS_ERR_NAN, "the right-hand side holds NaN or Inf");
+  if (!o.use_x0) TRS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+  trs_status result = TRS_ERR_NOT_CONVERGED;
+  if (bnorm == 0.0) {
+    TRS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    local.converged = 1;
+    result = TRS_OK;
+  }
+  int iters = 0, cycles = 0;
+  double relres = 0.0;
+  while (result != TRS_OK) {
+    launch_true_residual(M->b, Av, x, b, M->r.p, red, M->norms.p, s);
+    double hn[2];
+    TRS_CUDA(cudaMemcpyAsync(hn, M->norms.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+    relres = hn[1] / bnorm;
+    local.true_relres = relres;
+    if (!std::isfinite(relres)) { result = TRS_ERR_NAN; break; }
+    if (relres <= o.rtol) { result = TRS_OK; local.converged = 1; break; }
+    if (iters >= o.maxit) break;
+    TRS_CUDA(cudaMemsetAsync(M->gv.p, 0, (m + 1) * sizeof(double), s));
+    TRS_CUDA(cudaMemcpyAsync(M->gv.p, M->norms.p + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int jdone = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m; j++) {
+      double *vj = V + (int64_t)j * N;
+      T *zj = Z + (int64_t)j * N;
+      if (j == 0) cpr_apply_full<T>(M, M->r.p, M->norms.p + 1, vj, zj, s);
+      else cpr_apply_full<T>(M, M->w.p, M->hnorm.p, vj, zj, s);
+      launch_spmv<double, T>(M->b, Av, zj, M->w.p, 1.0, 0.0, s);
+      launch_multidot(V, N, j + 1, M->w.p, red, M->h1.p, s);
+      launch_cgs_update(V, N, j + 1, M->h1.p, M->w.p, 0, red, nullptr, s);
+      launch_multidot(V, N, j + 1, M->w.p, red, M->h2.p, s);
+      launch_cgs_update(V, N, j + 1, M->h2.p, M->w.p, 1, red, M->hn2.p, s);
+      launch_givens(j, m, M->H.p, M->h1.p, M->h2.p, M->hn2.p, M->h1.p + j + 1, M->cs.p, M->sn.p, M->gv.p,
+                    M->hnorm.p, M->status.p, 1.0 / bnorm, s);
+      iters++;
+      double hs[2];
+      TRS_CUDA(cudaMemcpyAsync(hs, M->status.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      TRS_CUDA(cudaStreamSynchronize(s));
+      local.est_relres = hs[0];
+      if (!std::isfinite(hs[0])) { result = TRS_ERR_NAN; break; }
+      breakdown = hs[1] != 0.0;
+      if (hs[0] <= o.rtol || iters >= o.maxit || breakdown) { jdone = j + 1; break; }
+      jdone = j + 1;
+    }
+    if (result == TRS_ERR_NAN) break;
+    launch_lsq(jdone, m, M->H.p, M->gv.p, M->yv.p, s);
+    launch_xupdate<T>(Z, N, jdone, M->yv.p, x, s);
+    cycles++;
+    if (breakdown && local.est_relres > o.rtol) {
+      // x is exact in the Krylov space; a last true-residual check follows
+    }
+  }
+  local.iters = iters;
+  local.restarts = cycles > 0 ? cycles - 1 : 0;
+  local.amg_levels = (int)M->lev.size();
+  local.n_colours = M->ncol;
+  local.ms_setup = M->ms_setup;
+  local.ms_solve = timer.stop();
+  if (st) *st = local;
+  return result;
+}
+
+trs_status run_solve(const trs_bsr *A, trs_cpr *M, const double *b, double *x, const trs_solve_opts *opts,
+                     cudaStream_t s, trs_solve_stats *st) {
+  trs_solve_opts o;
+  trs_solve_default_opts(&o);
+  if (opts) o = *opts;
+  TRS_REQUIRE(A && M && b && x, TRS_ERR_INVALID, "NULL argument");
+  TRS_REQUIRE(A->n == M->n && A->b == M->b, TRS_ERR_INVALID, "matrix and preconditioner sizes differ");
+  TRS_REQUIRE(o.restart >= 1 && o.restart <= kMaxRestart, TRS_ERR_INVALID, "restart must be 1..64");
+  TRS_REQUIRE(o.maxit >= 1 && o.rtol > 0.0, TRS_ERR_INVALID, "maxit must be >= 1 and rtol > 0");
+  if (M->prec == TRS_FP32_PREC) return fgmres<float>(A, M, b, x, o, s, st);
+  return fgmres<double>(A, M, b, x, o, s, st);
+}
+
+}  // namespace
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace trs
+
+using namespace trs;
+
+extern "C" {
+
+void trs_cpr_default_opts(trs_cpr_opts *o) {
+  if (!o) return;
+  o->precision = TRS_FP64;
+  o->theta = 0.08;
+  o->coarse_max = 1024;
+  o->max_levels = 12;
+  o->cheb_degree = 2;
+  o->seed = 0x5EED1812u;
+}
+
+void trs_solve_default_opts(trs_solve_opts *o) {
+  if (!o) return;
+  o->rtol = 1e-6;
+  o->restart = 30;
+  o->maxit = 1000;
+  o->use_x0 = 0;
+}
+
+trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *stream, trs_cpr **out) {
+  return guarded([&] {
+    TRS_REQUIRE(A && out, TRS_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    trs_cpr_opts o;
+    trs_cpr_default_opts(&o);
+    if (opts) o = *opts;
+    TRS_REQUIRE(o.precision == TRS_FP64 || o.precision == TRS_FP32_PREC, TRS_ERR_INVALID, "unknown precision");
+    TRS_REQUIRE(o.cheb_degree >= 2 && o.cheb_degree <= 8, TRS_ERR_UNSUPPORTED, "Chebyshev degree must be 2..8");
+    TRS_REQUIRE(o.max_levels >= 1 && o.max_levels <= kMaxLevels, TRS_ERR_INVALID, "max_levels must be 1..16");
+    TRS_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= kDenseMax, TRS_ERR_INVALID, "coarse_max must be 1..4096");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto M = std::make_unique<trs_cpr>();
+    M->opts = o;
+    M->prec = o.precision;
+    Timer t(s);
+    setup_all(M.get(), A, s);
+    M->ms_setup = t.stop();
+    *out = M.release();
+  });
+}
+
+trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(M && A, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(A->n == M->n && A->b == M->b && A->nnzb == M->nnzb, TRS_ERR_INVALID, "pattern differs");
+    cudaStream_t s = (cudaStream_t)stream;
+    Timer t(s);
+    build_values(M, A, reuse_amg == 0, s);
+    if (reuse_amg == 0) {
+      const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
+      for (auto &L : M->lev) {
+        alloc_vec(L.r, L.A.n, es);
+        alloc_vec(L.e, L.A.n, es);
+        alloc_vec(L.res, L.A.n, es);
+        alloc_vec(L.d, L.A.n, es);
+        alloc_vec(L.dn, L.A.n, es);
+      }
+    }
+    M->ms_setup = t.stop();
+  });
+}
+
+trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(M && v && z, TRS_ERR_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (M->prec == TRS_FP32_PREC) {
+      cpr_apply_full<float>(M, v, nullptr, nullptr, tp<float>(M->wz), s);
+      launch_cast<float, double>(tp<float>(M->wz), z, M->N, s);
+    } else {
+      cpr_apply_full<double>(M, v, nullptr, nullptr, z, s);
+    }
+  });
+}
+
+trs_status trs_cpr_vcycle(const trs_cpr *M, const double *r, double *e, void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(M && r && e, TRS_ERR_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &L0 = M->lev[0];
+    if (M->prec == TRS_FP32_PREC) {
+      launch_cast<double, float>(r, tp<float>(L0.r), L0.A.n, s);
+      vcycle<float>(M, 0, tp<float>(L0.r), tp<float>(L0.e), s);
+      launch_cast<float, double>(tp<float>(L0.e), e, L0.A.n, s);
+    } else {
+      vcycle<double>(M, 0, r, e, s);
+    }
+  });
+}
+
+trs_status trs_cpr_get_info(const trs_cpr *M, trs_cpr_info *info) {
+  return guarded([&] {
+    TRS_REQUIRE(M && info, TRS_ERR_INVALID, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_levels = (int)M->lev.size();
+    info->n_colours = M->ncol;
+    info->precision = M->prec;
+    for (size_t l = 0; l < M->lev.size() && l < 16; l++) {
+      info->level_rows[l] = M->lev[l].A.n;
+      info->level_nnz[l] = M->lev[l].A.nnz;
+      info->level_lambda[l] = M->lev[l].lam;
+    }
+  });
+}
+
+trs_status trs_cpr_get_aggregates(const trs_cpr *M, int32_t level, int32_t *agg) {
+  return guarded([&] {
+    TRS_REQUIRE(M && agg, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(level >= 0 && level < (int)M->lev.size(), TRS_ERR_INVALID, "level out of range");
+    const Level &L = M->lev[level];
+    if (L.agg.p) {
+      auto h = download(L.agg.p, L.A.n, 0);
+      std::copy(h.begin(), h.end(), agg);
+    } else {
+      std::fill(agg, agg + L.A.n, -1);
+    }
+  });
+}
+
+trs_status trs_cpr_get_colours(const trs_cpr *M, int32_t *colour) {
+  return guarded([&] {
+    TRS_REQUIRE(M && colour, TRS_ERR_INVALID, "NULL argument");
+    auto h = download(M->colour.p, M->n, 0);
+    std::copy(h.begin(), h.end(), colour);
+  });
+}
+
+trs_status trs_cpr_get_decoupled(const trs_cpr *M, double *vt, double *dinv) {
+  return guarded([&] {
+    TRS_REQUIRE(M, TRS_ERR_INVALID, "NULL argument");
+    const int bb = M->b * M->b;
+    if (vt) {
+      DBuf<double> stage(std::max<int64_t>(M->nnzb * bb, 1));
+      launch_gather_values(M->nnzb, bb, M->map.p, M->at_ell64.p, M->at_tval64.p, M->g.nc, stage.p, 0);
+      auto h = download(stage.p, M->nnzb * bb, 0);
+      std::copy(h.begin(), h.end(), vt);
+    }
+    if (dinv) {
+      auto h = download(M->dinv64.p, (size_t)bb * M->n, 0);
+      for (int64_t i = 0; i < M->n; i++)
+        for (int e = 0; e < bb; e++) dinv[i * bb + e] = h[(size_t)e * M->n + i];
+    }
+  });
+}
+
+trs_status trs_cpr_get_level(const trs_cpr *M, int32_t level, int64_t *row_ptr, int32_t *col, double *val) {
+  return guarded([&] {
+    TRS_REQUIRE(M && row_ptr && col && val, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(level >= 0 && level < (int)M->lev.size(), TRS_ERR_INVALID, "level out of range");
+    const Csr &C = M->lev[level].A;
+    auto a = download(C.rp.p, C.n + 1, 0);
+    auto b = download(C.col.p, C.nnz, 0);
+    auto c = download(C.val.p, C.nnz, 0);
+    std::copy(a.begin(), a.end(), row_ptr);
+    std::copy(b.begin(), b.end(), col);
+    std::copy(c.begin(), c.end(), val);
+  });
+}
+
+void trs_cpr_destroy(trs_cpr *M) { delete M; }
+
+trs_status trs_fgmres_solve(const trs_bsr *A, const trs_cpr *M, const double *b, double *x,
+                            const trs_solve_opts *opts, void *stream, trs_solve_stats *stats) {
+  trs_status st = TRS_OK;
+  trs_status g = guarded([&] { st = run_solve(A, const_cast<trs_cpr *>(M), b, x, opts, (cudaStream_t)stream, stats); });
+  if (g != TRS_OK) return g;
+  if (st == TRS_ERR_NOT_CONVERGED) set_last_error("iteration limit reached before the tolerance");
+  if (st == TRS_ERR_NAN) set_last_error("NaN or Inf in a residual norm");
+  return st;
+}
+
+trs_status trs_fgmres_solve_host(const trs_bsr *A, const trs_cpr *M, const double *b_host, double *x_host,
+                                 const trs_solve_opts *opts, void *stream, trs_solve_stats *stats) {
+  trs_status st = TRS_OK;
+  trs_status g = guarded([&] {
+    TRS_REQUIRE(A && M && b_host && x_host, TRS_ERR_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double> db(M->N), dx(M->N);
+    db.upload(b_host, M->N, s);
+    trs_solve_opts o;
+    trs_solve_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.use_x0) dx.upload(x_host, M->N, s);
+    st = run_solve(A, const_cast<trs_cpr *>(M), db.p, dx.p, &o, s, stats);
+    TRS_CUDA(cudaMemcpyAsync(x_host, dx.p, M->N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+  });
+  return g != TRS_OK ? g : st;
+}
+
+trs_status trs_solve_adjoint(const trs_bsr *A, const trs_bsr *AT, const trs_cpr *M_T, const double *g,
+                             const double *x, double *lambda, double *dA, const trs_solve_opts *opts, void *stream,
+                             trs_solve_stats *stats) {
+  trs_status st = TRS_OK;
+  trs_status gs = guarded([&] {
+    TRS_REQUIRE(A && AT && M_T && g && lambda, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(AT->n == A->n && AT->b == A->b && AT->nnzb == A->nnzb, TRS_ERR_INVALID, "AT is not A^T-shaped");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_solve(AT, const_cast<trs_cpr *>(M_T), g, lambda, opts, s, stats);
+    if (dA) {
+      TRS_REQUIRE(x, TRS_ERR_INVALID, "x is required for dA");
+      launch_outer_product(A->b, *A, lambda, x, dA, s);
+    }
+  });
+  return gs != TRS_OK ? gs : st;
+}
+
+trs_status trs_outer_product(const trs_bsr *A, const double *lambda, const double *x, double *dA, void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(A && lambda && x && dA, TRS_ERR_INVALID, "NULL argument");
+    launch_outer_product(A->b, *A, lambda, x, dA, (cudaStream_t)stream);
+  });
+}
+
+trs_status trs_chain_theta(const trs_bsr *A, const double *perm, int32_t perm_is_log, double kvkh, double c_t,
+                           const double *M, const double *lambda, const double *x, double *dtheta, void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(A && perm && M && lambda && x && dtheta, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(A->structured, TRS_ERR_INVALID, "the chain needs a structured (grid) matrix");
+    launch_chain_theta(A->b, *A, perm, perm_is_log, kvkh, c_t, M, lambda, x, dtheta, (cudaStream_t)stream);
+  });
+}
+
+const char *trs_last_error(void) { return g_last_error.c_str(); }
+
+const char *trs_version(void) { return "trs 0.1 (sm_103a)"; }
+
+uint64_t trs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal declarations of libtrs (not part of the C ABI).
+//
+// Block matrices live in an "ELL-7 + tail" layout:
+//   * the first nc rows are cells of an nx*ny*nz grid; their couplings to the
+//     six 7-point neighbours and to themselves sit in seven slots ordered by
+//     ascending column (-z, -y, -x, self, +x, +y, +z), stored structure-of-
+//     arrays: ell[(slot * bb + e) * nc + row], e = r*b + c of the b x b block.
+//     Columns are implicit (row + kSlotOff[slot]); emask[row] bit s says
+//     whether slot s is stored (the caller's pattern), so coalesced
+//     row-parallel loads need no column indices.
+//   * every other block (well columns of perforated cells, all blocks of the
+//     well rows, everything for unstructured matrices) is in a block-CSR tail
+//     over all rows: tptr[n_rows+1], tcol[ntail], tval[t * bb + e].
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/trs.h"
+
+namespace trs {
+
+constexpr int kMaxB = 5;
+constexpr int kSlots = 7;
+constexpr int kSelf = 3;
+constexpr int kMaxLevels = 16;
+constexpr int kDenseMax = 4096;
+constexpr int kMaxColours = 64;
+constexpr int kMaxRestart = 64;
+
+struct Error : std::runtime_error {
+  trs_status code;
+  Error(trs_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define TRS_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      throw ::trs::Error(e_ == cudaErrorMemoryAllocation ? TRS_ERR_OOM : TRS_ERR_CUDA,         \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+// Every kernel launch is followed by TRS_LAUNCHED(), which checks the launch
+// and counts it (trs_kernel_launches()).
+void note_launch();
+#define TRS_LAUNCHED()                                                                         \
+  do {                                                                                         \
+    ::trs::note_launch();                                                                      \
+    TRS_CUDA(cudaGetLastError());                                                              \
+  } while (0)
+#define TRS_REQUIRE(cond, code, msg)                                                           \
+  do {                                                                                         \
+    if (!(cond)) throw ::trs::Error((code), (msg));                                            \
+  } while (0)
+
+// Owning device buffer (move-only).
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  explicit DBuf(size_t count) { alloc(count); }
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf &operator=(DBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    n = count;
+    if (count) TRS_CUDA(cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T)));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void upload(const T *h, size_t count, cudaStream_t s) {
+    if (count) TRS_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void zero(cudaStream_t s) {
+    if (n) TRS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  T *get() const { return p; }
+};
+
+template <class T>
+std::vector<T> download(const T *d, size_t count, cudaStream_t s) {
+  std::vector<T> h(count);
+  if (count) {
+    TRS_CUDA(cudaMemcpyAsync(h.data(), d, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+  }
+  return h;
+}
+
+// Geometry of the structured part.
+struct Geom {
+  int64_t nc;       // cells
+  int64_t n_rows;   // cells + other rows
+  int64_t off[kSlots];
+  int nx, ny, nz;
+};
+
+inline Geom make_geom(int nx, int ny, int nz, int64_t n_rows) {
+  Geom g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.nc = (int64_t)nx * ny * nz;
+  g.n_rows = n_rows;
+  const int64_t sxy = (int64_t)nx * ny;
+  int64_t o[kSlots] = {-sxy, -(int64_t)nx, -1, 0, 1, nx, sxy};
+  for (int s = 0; s < kSlots; s++) g.off[s] = o[s];
+  return g;
+}
+
+// Device view of a block (or scalar, bb = 1) matrix in ELL-7 + tail form.
+template <class T>
+struct MatView {
+  Geom g;
+  const uint8_t *emask;   // [nc]
+  const int64_t *tptr;    // [n_rows + 1]
+  const int32_t *tcol;    // [ntail]
+  const T *ell;           // [7][bb][nc]
+  const T *tval;          // [ntail][bb]
+};
+
+}  // namespace trs
+
+// The handles of the C ABI.
+struct trs_bsr {
+  int b = 0;
+  int64_t n = 0, nnzb = 0, ntail = 0;
+  trs::Geom g{};
+  bool structured = false;
+  trs::DBuf<uint8_t> emask;
+  trs::DBuf<int64_t> tptr;
+  trs::DBuf<int32_t> tcol;
+  trs::DBuf<double> ell, tval;
+  trs::DBuf<int64_t> tdiag;   // [n - nc] tail index of the diagonal block of each non-cell row
+  // canonical BSR order: internal location of each block, row and column
+  trs::DBuf<int64_t> map;
+  trs::DBuf<int32_t> urow, ucol;
+  std::vector<int64_t> h_rp;
+  std::vector<int32_t> h_col;
+  // tail entries grouped by column (for the transposed product)
+  trs::DBuf<int64_t> tc_ptr, tc_src;
+  trs::DBuf<int32_t> tc_row;
+  // synthetic assembly bookkeeping
+  bool synthetic = false;
+  int n_wells = 0;
+  int64_t n_perf = 0;
+  trs::DBuf<int64_t> cperf_ptr, cperf_idx, wperf_ptr, wperf_idx;   // perforations by cell / well
+  trs::DBuf<int32_t> perf_cell, perf_well;
+  trs::DBuf<int64_t> perf_cw, perf_wc, wdiag;                      // tail slots of (c,w), (w,c), (w,w)
+
+  template <class T = double>
+  trs::MatView<T> view() const {
+    return trs::MatView<T>{g, emask.p, tptr.p, tcol.p, ell.p, tval.p};
+  }
+};
