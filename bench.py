@@ -32,7 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {"16x16x4_b4": 0, "128x128x64_b4": 1, "256x256x128_b5": 2, "64x64x32_b4": 3,
-             "512x256x64_b4": 4}
+             "512x256x64_b4": 4, "96x96x48_b4": None}
+
+
+def make_workload(name):
+    from paper_1812_03952_gb300 import synthetic as S
+    if WORKLOADS[name] is None:      # mid-size case for profiler captures (matrix > L2, < 2 GB total)
+        return S.small_system(96, 96, 48, 4, seed=77, sigma=1.5, n_pairs=4, kvkh=0.1, name=name)
+    return S.config(WORKLOADS[name])
 METRIC = "CPR-FGMRES solve ms (assembly + CPR setup + FGMRES to true rel. res. 1e-6)"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -41,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="trs", choices=["trs", "reference"])
     p.add_argument("--workload", default="128x128x64_b4", choices=sorted(WORKLOADS))
@@ -161,8 +168,8 @@ def oracle_sample(sysm, n_iter, iters_full):
 
 # FGMRES iterations of the FP64 path on the 128x128x64 workload (the oracle
 # runs the same algorithm; used to scale the oracle's bounded sample).
-FULL_ITERS = {"128x128x64_b4": 30, "64x64x32_b4": 31, "16x16x4_b4": 18, "256x256x128_b5": 60,
-              "512x256x64_b4": 60}
+FULL_ITERS = {"128x128x64_b4": 12, "64x64x32_b4": 31, "16x16x4_b4": 18, "256x256x128_b5": 60,
+              "512x256x64_b4": 60, "96x96x48_b4": 12}
 
 
 def run_reference(args):
@@ -170,7 +177,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1812_03952_gb300 import synthetic as S
-    sysm = S.config(WORKLOADS[args.workload])
+    sysm = make_workload(args.workload)
     n_iter = 1
     times = []
     detail = None
@@ -207,7 +214,7 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    sysm = S.config(WORKLOADS[args.workload])
+    sysm = make_workload(args.workload)
     ds = trs.DeviceSystem(sysm, dev)
     A = ds.assemble()
     M = trs.CPR(A, precision=args.precision)
