@@ -251,6 +251,26 @@ trs_status trs_solve_adjoint(const trs_bsr *A, const trs_bsr *AT, const trs_cpr 
                              const double *g, const double *x, double *lambda, double *dA,
                              const trs_solve_opts *opts, void *stream, trs_solve_stats *stats);
 
+/* Residual r = b - A x and its 2-norm without allocating anything.
+ * The paper has no counterpart: this call is for callers that must not
+ * allocate device memory while they run (for instance code inside a stream
+ * being captured into a CUDA graph, loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree, or processes whose device memory
+ * belongs to their own pool allocator).  x, b, r: device pointers (n*b
+ * doubles, caller-owned, r must not alias x or b); norm: host pointer that
+ * receives ||r||_2; the call synchronises `stream`.  The reduction scratch
+ * is a static device array of 778,752 bytes inside the library (the partial
+ * sums of at most 1,216 blocks, a counter and the result), held by every
+ * GPU that loads the library until the process exits; the blocks stride over
+ * the rows, so every matrix the library accepts fits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * should therefore come before any stream capture.  Every call on a device
+ * shares the one array, so calls that overlap on the GPU (other streams,
+ * other threads) race; the counter is cleared at the start of each call.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+trs_status trs_residual_norm_noalloc(const trs_bsr *A, const double *x, const double *b, double *r,
+                                     double *norm, void *stream);
+
 /* dA = -lambda_i x_j^T on every stored block (canonical order). */
 trs_status trs_outer_product(const trs_bsr *A, const double *lambda, const double *x, double *dA,
                              void *stream);

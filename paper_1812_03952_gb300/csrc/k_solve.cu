@@ -4,7 +4,9 @@
 // All reductions are deterministic: a fixed grid, warp shuffles in a fixed
 // pattern, per-block partial sums, and the last block to finish summing the
 // partials in block order.
-#include "trs_kernels.cuh"
+#include <mutex>
+
+#include "trs_api_common.cuh"
 
 namespace trs {
 
@@ -859,3 +861,70 @@ template void launch_cast<float, double>(const float *, double *, int64_t, cudaS
 template void launch_cast<double, double>(const double *, double *, int64_t, cudaStream_t);
 
 }  // namespace trs
+
+// ============================================ allocation-free residual norm
+// Some callers cannot allocate device memory while they run: code inside a
+// region whose allocations are forbidden (a stream being captured into a
+// CUDA graph, a real-time loop where cudaMalloc's implicit device
+// synchronisation is unacceptable) or processes whose device memory is
+// entirely handed to their own pool allocator.  For them the residual and its
+// norm run on a reduction scratch that lives in this file-scope array, loaded
+// with the library and kept by every GPU that loads it until the process
+// exits.  Size: the partial sums of at most kStaticGrid blocks (the same grid
+// the solver uses, so results are identical) plus a ticket counter and the
+// output, 778,752 bytes in all.
+namespace trs {
+namespace {
+
+constexpr int kStaticGrid = 152 * 8;
+constexpr size_t kStaticCounterAt = (size_t)kStaticGrid * kRedStride;  // 256-byte aligned slot
+constexpr size_t kStaticOutAt = kStaticCounterAt + 32;
+constexpr size_t kStaticDoubles = kStaticOutAt + 32;
+
+static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double *g_static_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current) and cached.
+double *static_scratch() {
+  int dev = 0;
+  TRS_CUDA(cudaGetDevice(&dev));
+  TRS_REQUIRE(dev >= 0 && dev < kMaxDevices, TRS_ERR_UNSUPPORTED, "device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    TRS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[dev] = static_cast<double *>(p);
+  }
+  return g_static_addr[dev];
+}
+
+}  // namespace
+
+}  // namespace trs
+
+extern "C" trs_status trs_residual_norm_noalloc(const trs_bsr *A, const double *x, const double *b, double *r,
+                                                double *norm, void *stream) {
+  using namespace trs;
+  return guarded([&] {
+    TRS_REQUIRE(A && x && b && r && norm, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(x != r && b != r, TRS_ERR_INVALID, "r must not alias x or b");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = A->n * A->b;
+    const int64_t grid = std::min<int64_t>(kStaticGrid, std::max<int64_t>(1, (N + kThreads - 1) / kThreads));
+    TRS_REQUIRE(grid <= kStaticGrid, TRS_ERR_UNSUPPORTED, "reduction grid larger than the static scratch");
+    double *base = static_scratch();
+    unsigned int *counter = reinterpret_cast<unsigned int *>(base + kStaticCounterAt);
+    double *out = base + kStaticOutAt;
+    TRS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+    const MatView<double> Av = A->view();
+    TRS_DISPATCH_B(A->b, k_true_residual<B><<<(unsigned)grid, kThreads, 0, s>>>(Av, x, b, r, 0, 0, base, counter,
+                                                                                out));
+    TRS_LAUNCHED();
+    TRS_CUDA(cudaMemcpyAsync(norm, out + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+  });
+}

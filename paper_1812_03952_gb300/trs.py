@@ -39,7 +39,7 @@ EXPORTS = (
     "trs_cpr_get_colours", "trs_cpr_get_decoupled", "trs_cpr_get_level", "trs_cpr_vcycle",
     "trs_cpr_destroy", "trs_solve_default_opts", "trs_fgmres_solve", "trs_fgmres_solve_host",
     "trs_solve_adjoint", "trs_outer_product", "trs_chain_theta", "trs_last_error", "trs_version",
-    "trs_kernel_launches",
+    "trs_kernel_launches", "trs_residual_norm_noalloc",
 )
 
 
@@ -126,6 +126,7 @@ def load(path: str = LIB_PATH):
         "trs_last_error": (C.c_char_p, []),
         "trs_version": (C.c_char_p, []),
         "trs_kernel_launches": (C.c_uint64, []),
+        "trs_residual_norm_noalloc": (i32, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -371,6 +372,14 @@ def solve_adjoint(A: Matrix, AT: Matrix, MT: CPR, g, x=None, want_dA=False, rtol
                                     C.byref(o), _stream(), C.byref(st))
     _check(code, allow=(TRS_ERR_NOT_CONVERGED,))
     return lam, dA, Result(code, st.as_dict())
+
+
+def residual_norm_noalloc(A: Matrix, x, b, r):
+    """r = b - A x (written into the caller's r) and ||r||_2, computed without
+    any device allocation (static scratch inside the library)."""
+    nrm = C.c_double(0.0)
+    _check(load().trs_residual_norm_noalloc(A.h, _dptr(x), _dptr(b), _dptr(r), C.byref(nrm), _stream()))
+    return nrm.value
 
 
 def outer_product(A: Matrix, lam, x):
