@@ -57,6 +57,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
+    p.add_argument("--sequence", type=int, default=0,
+                   help="time a sequence of this many Newton-like systems (diagonal blocks rescaled by "
+                        "seeded +-20%% factors, AMG hierarchy rebuilt every --reuse steps, forward and adjoint "
+                        "solve per system) instead of single solves")
+    p.add_argument("--reuse", type=int, default=5)
     return p.parse_args()
 
 
@@ -199,11 +204,85 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------ Newton-like sequence
+def run_sequence(args):
+    """Total device time of a sequence of Newton-like systems: per system,
+    assembly, diagonal rescaling, CPR refresh (full rebuild every
+    args.reuse systems, AMG reused otherwise), forward solve, transpose,
+    CPR on A^T (same reuse), adjoint solve and the dL/dtheta chain."""
+    import torch
+    from paper_1812_03952_gb300 import build as B
+    from paper_1812_03952_gb300 import synthetic as S
+    from paper_1812_03952_gb300 import trs
+    B.build()
+    trs.load()
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    sysm = make_workload(args.workload)
+    ds = trs.DeviceSystem(sysm, dev)
+    scales = torch.from_numpy(S.diagonal_scalings(sysm.n_rows, args.sequence, S.SEED_BASE + 99)).to(dev)
+    g = torch.zeros(sysm.n_unknowns, dtype=torch.float64, device=dev)
+    g[torch.from_numpy(np.unique(sysm.perf_cell).astype(np.int64) * sysm.b).to(dev)] = 1.0
+    A = ds.assemble()
+    M = trs.CPR(A, precision=args.precision)
+    AT = A.transpose()
+    MT = trs.CPR(AT, precision=args.precision)
+    x = torch.zeros_like(ds.rhs)
+    records = []
+
+    def run_all(record):
+        for k in range(args.sequence):
+            ds.assemble()
+            A.scale_diagonal(scales[k].contiguous())
+            reuse = (k % args.reuse) != 0
+            M.update(A, reuse_amg=reuse)
+            _, rf = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)
+            A.transpose(into=AT)
+            MT.update(AT, reuse_amg=reuse)
+            lam, _, ra = trs.solve_adjoint(A, AT, MT, g, x, rtol=args.rtol)
+            trs.chain_theta(A, ds.k, ds.M, lam, x, sysm.kvkh, sysm.c_t)
+            if record:
+                records.append({"step": k, "amg": "reused" if reuse else "rebuilt",
+                                "fwd_iters": rf.stats["iters"], "fwd_relres": rf.stats["true_relres"],
+                                "adj_iters": ra.stats["iters"], "adj_relres": ra.stats["true_relres"],
+                                "fwd_ms": rf.stats["ms_solve"], "adj_ms": ra.stats["ms_solve"]})
+
+    for _ in range(max(1, args.warmup)):
+        run_all(False)
+    torch.cuda.synchronize()
+    barrier(world)
+    l0 = trs.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            records.clear()
+            run_all(True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = barrier_max(e0.elapsed_time(e1) / args.steps, world)
+    if rank == 0:
+        line = {"metric": f"Newton-like sequence of {args.sequence} systems: forward + adjoint CPR-FGMRES total ms",
+                "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64+f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
+                           "unknowns": sysm.n_unknowns, "systems": args.sequence, "amg_rebuild_every": args.reuse,
+                           "rtol": args.rtol, "precision": args.precision,
+                           "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+                "per_system": records, "clocks": clk.summary(), "gpu_launches": trs.kernel_launches() - l0}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sequence:
+        return run_sequence(args)
     import torch
     from paper_1812_03952_gb300 import build as B
     from paper_1812_03952_gb300 import synthetic as S

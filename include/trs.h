@@ -22,7 +22,9 @@
  *     the host synchronise that stream.
  *   - "device pointer" arguments must point to memory of the current device,
  *     "host pointer" arguments to host memory.  Vectors are FP64 arrays of
- *     n_block_rows * b entries, block by block, owned by the caller.
+ *     n_block_rows * b entries, block by block, owned by the caller; device
+ *     vectors must be 16-byte aligned (cudaMalloc and the PyTorch allocator
+ *     return 256-byte aligned memory), else TRS_ERR_INVALID.
  *   - Handles (trs_bsr, trs_cpr) are owned by the library and released with
  *     the matching *_destroy call.
  *   - Every call returns a trs_status; no exception, abort or device trap
@@ -62,7 +64,7 @@ typedef struct trs_cpr trs_cpr;
 typedef struct {
   int32_t precision;     /* TRS_FP64 or TRS_FP32_PREC */
   double theta;          /* AMG strength threshold (default 0.08) */
-  int32_t coarse_max;    /* stop coarsening at <= coarse_max rows (default 1024) */
+  int32_t coarse_max;    /* stop coarsening at <= coarse_max rows (default 64) */
   int32_t max_levels;    /* default 12 */
   int32_t cheb_degree;   /* Chebyshev smoother degree (default 2) */
   uint32_t seed;         /* seed of the MIS-2 and colouring priorities */
@@ -177,11 +179,15 @@ trs_status trs_bsr_spmv(const trs_bsr *A, double alpha, const double *x, double 
 /* Forms A^T explicitly as a new matrix (blocks transposed). */
 trs_status trs_bsr_transpose(const trs_bsr *A, void *stream, trs_bsr **out);
 
+/* Refreshes the values of AT = trs_bsr_transpose(A0) from A, which must have
+ * A0's pattern (for example A0 itself after new values): (A^T)_ij = (A_ji)^T. */
+trs_status trs_bsr_transpose_values(const trs_bsr *A, trs_bsr *AT, void *stream);
+
 void trs_bsr_destroy(trs_bsr *A);
 
 /* ---------------------------------------------------------- preconditioner */
 
-/* Fills *opts with the defaults (FP64, theta 0.08, coarse_max 1024, 12 levels,
+/* Fills *opts with the defaults (FP64, theta 0.08, coarse_max 64, 12 levels,
  * Chebyshev degree 2). */
 void trs_cpr_default_opts(trs_cpr_opts *opts);
 

@@ -299,7 +299,7 @@ def dense_lu_solve(A, rhs):
 
 
 class AMG:
-    def __init__(self, n, rp, col, val, theta=0.08, coarse_max=1024, max_levels=12,
+    def __init__(self, n, rp, col, val, theta=0.08, coarse_max=64, max_levels=12,
                  cheb_degree=2, seed=12345):
         st = C.c_int(0)
         self.h = lib().orc_amg_setup(n, rp, col, np.ascontiguousarray(val, dtype=np.float64),
@@ -388,7 +388,7 @@ class BILU0:
 
 
 #: default CPR options (the same defaults as the CUDA library)
-CPR_DEFAULTS = dict(theta=0.08, coarse_max=1024, max_levels=12, cheb_degree=2, seed=0x5EED1812)
+CPR_DEFAULTS = dict(theta=0.08, coarse_max=64, max_levels=12, cheb_degree=2, seed=0x5EED1812)
 
 
 class CPR:

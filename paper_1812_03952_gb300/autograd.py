@@ -44,7 +44,7 @@ class SolveContext:
 
     def adjoint(self, theta, x, g):
         A = self.assemble(theta)
-        self.AT = A.transpose()
+        self.AT = A.transpose(into=self.AT)
         if self.MT is None:
             self.MT = trs.CPR(self.AT, precision=self.precision)
         else:

@@ -534,45 +534,97 @@ __global__ void k_member_sort(int64_t na, const int64_t *mptr, int32_t *midx) {
 }
 
 // ------------------------------------------------------------- Galerkin
-// One warp per coarse row I: distinct coarse columns in ascending order by
-// repeated minimum search; each value is the running sum, from 0.0, over the
-// members of I in ascending order and their entries in ascending column
-// order.  fill == 0 counts, fill == 1 writes.
-__global__ void k_galerkin(int64_t na, const int64_t *rp, const int32_t *col, const double *val,
-                           const int32_t *agg, const int64_t *mptr, const int32_t *midx, int fill,
-                           int64_t *ccount, const int64_t *crp, int32_t *ccol, double *cval) {
-  const int lane = threadIdx.x & 31;
-  const int64_t I = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
+// One warp per coarse row I.  The (J, a) pairs of the members of I (members
+// ascending, entries in column order) are staged in shared memory; the
+// distinct coarse columns are taken in ascending order by repeated minimum
+// search, and each value is the running sum, from 0.0, of the matching
+// pairs in staging order.  Rows longer than the staging area read the pairs
+// from global memory in the same order.  fill == 0 counts, fill == 1 writes.
+constexpr int kGalCap = 256;
+
+__device__ __forceinline__ int32_t warp_min_i32(int32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t *rp, const int32_t *col,
+                                                       const double *val, const int32_t *agg, const int64_t *mptr,
+                                                       const int32_t *midx, int fill, int64_t *ccount,
+                                                       const int64_t *crp, int32_t *ccol, double *cval,
+                                                       int32_t *long_rows, int *n_long) {
+  __shared__ int32_t sJ[kWarps][kGalCap];
+  __shared__ double sV[kWarps][kGalCap];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t I = blockIdx.x * (int64_t)kWarps + wid;
   if (I >= na) return;
   const int64_t m0 = mptr[I], m1 = mptr[I + 1];
+  // stage
+  int total = 0;
+  bool staged = true;
+  for (int64_t t = m0; t < m1; t++) {
+    const int64_t i = midx[t];
+    const int64_t p0 = rp[i], len = rp[i + 1] - p0;
+    if (total + len > kGalCap) { staged = false; break; }
+    for (int64_t k = lane; k < len; k += 32) {
+      sJ[wid][total + k] = agg[col[p0 + k]];
+      sV[wid][total + k] = val[p0 + k];
+    }
+    total += (int)len;
+  }
+  __syncwarp();
+  if (!staged) {  // handled by k_galerkin_long
+    if (!fill && lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)I;
+    return;
+  }
   int32_t cur = -1;
   int64_t count = 0;
   for (;;) {
     int32_t mn = 0x7fffffff;
-    for (int64_t t = m0; t < m1; t++) {
-      const int64_t i = midx[t];
-      for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
-        const int32_t J = agg[col[p]];
+    if (staged) {
+      for (int k = lane; k < total; k += 32) {
+        const int32_t J = sJ[wid][k];
         if (J > cur && J < mn) mn = J;
       }
+    } else {
+      for (int64_t t = m0; t < m1; t++) {
+        const int64_t i = midx[t];
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+          const int32_t J = agg[col[p]];
+          if (J > cur && J < mn) mn = J;
+        }
+      }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mn = warp_min_i32(mn);
     if (mn == 0x7fffffff) break;
     if (fill) {
       double s = 0.0;
-      for (int64_t t = m0; t < m1; t++) {
-        const int64_t i = midx[t];
-        const int64_t e = rp[i + 1];
-        for (int64_t base = rp[i]; base < e; base += 32) {
-          const int64_t p = base + lane;
-          const bool hit = p < e && agg[col[p]] == mn;
-          const double v = p < e ? val[p] : 0.0;
+      if (staged) {
+        for (int base = 0; base < total; base += 32) {
+          const int k = base + lane;
+          const bool hit = k < total && sJ[wid][k] == mn;
+          const double v = k < total ? sV[wid][k] : 0.0;
           unsigned mask = __ballot_sync(0xffffffffu, hit);
           while (mask) {
             const int src = __ffs(mask) - 1;
             s = s + __shfl_sync(0xffffffffu, v, src);
             mask &= mask - 1;
+          }
+        }
+      } else {
+        for (int64_t t = m0; t < m1; t++) {
+          const int64_t i = midx[t];
+          const int64_t e = rp[i + 1];
+          for (int64_t base = rp[i]; base < e; base += 32) {
+            const int64_t p = base + lane;
+            const bool hit = p < e && agg[col[p]] == mn;
+            const double v = p < e ? val[p] : 0.0;
+            unsigned mask = __ballot_sync(0xffffffffu, hit);
+            while (mask) {
+              const int src = __ffs(mask) - 1;
+              s = s + __shfl_sync(0xffffffffu, v, src);
+              mask &= mask - 1;
+            }
           }
         }
       }
@@ -585,6 +637,111 @@ __global__ void k_galerkin(int64_t na, const int64_t *rp, const int32_t *col, co
     cur = mn;
   }
   if (!fill && lane == 0) ccount[I] = count;
+}
+
+// Long coarse rows: one block per row.  The (J, a) pairs are staged in
+// shared memory under the key (J << 32 | sequence number), bitonic-sorted,
+// and each run of equal J is summed by one thread in sequence order (the
+// same order as the warp path and the definition above).
+constexpr int kGalLongMax = 8192;
+
+// exclusive scan of one int per thread over the block; returns the total
+__device__ int block_exclusive_scan(int v, int &excl) {
+  __shared__ int ws[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  int woff = 0, total = 0;
+  for (int w = 0; w < kWarps; w++) {
+    if (w < warp) woff += ws[w];
+    total += ws[w];
+  }
+  excl = woff + inc - v;
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_galerkin_long(const int64_t *rp, const int32_t *col, const double *val,
+                                                            const int32_t *agg, const int64_t *mptr,
+                                                            const int32_t *midx, const int32_t *long_rows,
+                                                            const int *n_long, int fill, int64_t *ccount,
+                                                            const int64_t *crp, int32_t *ccol, double *cval,
+                                                            int *err) {
+  extern __shared__ unsigned long long gsm[];
+  unsigned long long *key = gsm;                                     // [kGalLongMax]
+  double *sv = reinterpret_cast<double *>(gsm + kGalLongMax);        // [kGalLongMax]
+  const uint64_t kPad = ~0ull;
+  for (int r = blockIdx.x; r < *n_long; r += gridDim.x) {
+    const int64_t I = long_rows[r];
+    const int64_t m0 = mptr[I], m1 = mptr[I + 1];
+    // stage: member offsets by a block scan over chunks of members
+    int64_t base = 0;
+    bool overflow = false;
+    for (int64_t c0 = m0; c0 < m1; c0 += kThreads) {
+      const int64_t t = c0 + threadIdx.x;
+      int64_t i = -1, len = 0;
+      if (t < m1) {
+        i = midx[t];
+        len = rp[i + 1] - rp[i];
+      }
+      int off = 0;
+      const int tot = block_exclusive_scan((int)len, off);
+      if (base + tot > kGalLongMax) { overflow = true; break; }
+      for (int64_t k = 0; k < len; k++) {
+        const int64_t p = rp[i] + k, q = base + off + k;
+        const int32_t J = agg[col[p]];
+        key[q] = J >= 0 ? (((unsigned long long)(uint32_t)J << 32) | (unsigned long long)q) : kPad;
+        sv[q] = val[p];
+      }
+      base += tot;
+    }
+    if (overflow) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      __syncthreads();
+      continue;
+    }
+    int P = 1;
+    while (P < base) P <<= 1;
+    for (int q = (int)base + threadIdx.x; q < P; q += kThreads) key[q] = kPad;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = threadIdx.x; q < P; q += kThreads) {
+          const int x = q ^ j;
+          if (x > q) {
+            const unsigned long long a = key[q], b = key[x];
+            const bool up = (q & k) == 0;
+            if ((a > b) == up) { key[q] = b; key[x] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    // runs of equal J
+    int64_t seg_base = 0;
+    for (int c0 = 0; c0 < P; c0 += kThreads) {
+      const int q = c0 + threadIdx.x;
+      int start = 0;
+      if (q < P && key[q] != kPad) start = (q == 0 || (key[q] >> 32) != (key[q - 1] >> 32)) ? 1 : 0;
+      int before = 0;
+      const int tot = block_exclusive_scan(start, before);
+      if (fill && start) {
+        const unsigned long long J = key[q] >> 32;
+        double sum = 0.0;
+        for (int m = q; m < P && key[m] != kPad && (key[m] >> 32) == J; m++) sum = sum + sv[key[m] & 0xffffffffull];
+        ccol[crp[I] + seg_base + before] = (int32_t)J;
+        cval[crp[I] + seg_base + before] = sum;
+      }
+      seg_base += tot;
+    }
+    if (!fill && threadIdx.x == 0) ccount[I] = seg_base;
+    __syncthreads();
+  }
 }
 
 // ----------------------------------------------------- smoother set-up
@@ -601,81 +758,190 @@ __global__ void k_gershgorin(int64_t n, const int64_t *rp, const double *val, co
 }
 
 // ------------------------------------------------- coarsest dense solve
-__global__ void k_csr_to_dense(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double *a) {
+// Inverse of the coarsest operator by Gauss-Jordan elimination on the
+// augmented matrix [A | I] (n x 2n, row-major) with partial pivoting (first
+// row of largest |a| in the column on ties).  One launch per pivot step k:
+// every block eliminates column k from its rows and reports the candidate
+// pivot of column k+1 among them; the last block to finish swaps and scales
+// the next pivot row.  The right half ends as A^-1.
+__global__ void k_csr_to_aug(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double *aug) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
-  for (int64_t p = rp[i]; p < rp[i + 1]; p++) a[i * n + col[p]] = val[p];
+  for (int64_t p = rp[i]; p < rp[i + 1]; p++) aug[i * 2 * n + col[p]] = val[p];
+  aug[i * 2 * n + n + i] = 1.0;
 }
 
-// LU with partial pivoting (first row of largest |a| on ties), one block
-__global__ void __launch_bounds__(1024) k_dense_lu(int n, double *a, int *piv, int *err) {
-  __shared__ double bv[32];
-  __shared__ int bi[32];
-  __shared__ int pk;
-  for (int k = 0; k < n; k++) {
-    double best = -1.0;
-    int bidx = n;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-      const double v = fabs(a[(int64_t)i * n + k]);
-      if (v > best || (v == best && i < bidx)) { best = v; bidx = i; }
+// block-wide argmax of (value, row) with ties to the smaller row
+__device__ void block_argmax(double &v, int &r) {
+  __shared__ double sv[kWarps];
+  __shared__ int sr[kWarps];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+    if (ov > v || (ov == v && orr < r)) { v = ov; r = orr; }
+  }
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = v; sr[threadIdx.x >> 5] = r; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kWarps; w++)
+      if (sv[w] > sv[0] || (sv[w] == sv[0] && sr[w] < sr[0])) { sv[0] = sv[w]; sr[0] = sr[w]; }
+  }
+  __syncthreads();
+  v = sv[0];
+  r = sr[0];
+  __syncthreads();
+}
+
+// swap row k with the pivot row p and divide it by the pivot (one block)
+__device__ void gj_pivot_row(int n, int k, int p, double *aug, int *err) {
+  const int64_t w = 2 * (int64_t)n;
+  // rows updated by other blocks are read around L1 (__ldcg)
+  if (p != k) {
+    for (int64_t j = threadIdx.x; j < w; j += kThreads) {
+      const double t = __ldcg(aug + k * w + j);
+      aug[k * w + j] = __ldcg(aug + p * w + j);
+      aug[p * w + j] = t;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+  } else {
+    for (int64_t j = threadIdx.x; j < w; j += kThreads) aug[k * w + j] = __ldcg(aug + k * w + j);
+  }
+  __syncthreads();
+  const double piv = aug[k * w + k];
+  if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+    if (threadIdx.x == 0) *err = 1;
+    return;
+  }
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < w; j += kThreads) aug[k * w + j] = aug[k * w + j] / piv;
+}
+
+__global__ void __launch_bounds__(kThreads) k_gj_first(int n, double *aug, int *err) {
+  const int64_t w = 2 * (int64_t)n;
+  double v = -1.0;
+  int r = n;
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    const double a = fabs(aug[i * w]);
+    if (a > v || (a == v && i < r)) { v = a; r = i; }
+  }
+  block_argmax(v, r);
+  gj_pivot_row(n, 0, r, aug, err);
+}
+
+__global__ void __launch_bounds__(kThreads) k_gj_step(int n, int k, double *aug, double *pv, int *pr,
+                                                     unsigned int *counter, int *err) {
+  const int64_t w = 2 * (int64_t)n;
+  if (*err) return;
+  double v = -1.0;
+  int r = n;
+  // rows of this block: blockIdx.x, blockIdx.x + gridDim.x, ...
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    if (i == k) continue;
+    const double f = aug[i * w + k];
+    __syncthreads();  // every thread holds the multiplier before column k is overwritten
+    if (f != 0.0)
+      for (int64_t j = k + threadIdx.x; j < w; j += kThreads) aug[i * w + j] = aug[i * w + j] - f * aug[k * w + j];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && i > k && k + 1 < n) {
+      const double a = fabs(aug[i * w + k + 1]);
+      if (a > v || (a == v && i < r)) { v = a; r = i; }
+    }
+  }
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = v;
+    pr[blockIdx.x] = r;
+  }
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) *counter = 0u;
+  if (k + 1 >= n) return;
+  v = -1.0;
+  r = n;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
+    const double bv = __ldcg(pv + b);
+    const int br = __ldcg(pr + b);
+    if (bv > v || (bv == v && br < r)) { v = bv; r = br; }
+  }
+  block_argmax(v, r);
+  gj_pivot_row(n, k + 1, r, aug, err);
+}
+
+// The same Gauss-Jordan inverse for n <= kDenseSmall, in shared memory by one
+// block of 1024 threads.
+constexpr int kDenseSmall = 64;
+
+__global__ void __launch_bounds__(1024) k_gj_small(int n, const int64_t *rp, const int32_t *col,
+                                                   const double *val, double *inv, int *err) {
+  __shared__ double a[kDenseSmall][2 * kDenseSmall];
+  __shared__ double fk[kDenseSmall];
+  __shared__ double bv[32];
+  __shared__ int br[32];
+  __shared__ int piv_row;
+  const int w = 2 * n, tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * w; e += nt) a[e / w][e % w] = 0.0;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++) a[i][col[p]] = val[p];
+    a[i][n + i] = 1.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; k++) {
+    double v = -1.0;
+    int r = n;
+    for (int i = k + tid; i < n; i += nt) {
+      const double x = fabs(a[i][k]);
+      if (x > v || (x == v && i < r)) { v = x; r = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+      if (ov > v || (ov == v && orr < r)) { v = ov; r = orr; }
+    }
+    if ((tid & 31) == 0) { bv[tid >> 5] = v; br[tid >> 5] = r; }
+    __syncthreads();
+    if (tid == 0) {
       double b0 = -1.0;
-      int i0 = n;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++)
-        if (bv[w] > b0 || (bv[w] == b0 && bi[w] < i0)) { b0 = bv[w]; i0 = bi[w]; }
+      int r0 = n;
+      for (int x = 0; x < nt / 32; x++)
+        if (bv[x] > b0 || (bv[x] == b0 && br[x] < r0)) { b0 = bv[x]; r0 = br[x]; }
       if (!(b0 > 0.0) || !isfinite(b0)) *err = 1;
-      pk = i0;
-      piv[k] = i0;
+      piv_row = r0;
     }
     __syncthreads();
     if (*err) return;
-    const int p = pk;
+    const int p = piv_row;
     if (p != k)
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double t = a[(int64_t)k * n + j];
-        a[(int64_t)k * n + j] = a[(int64_t)p * n + j];
-        a[(int64_t)p * n + j] = t;
+      for (int j = tid; j < w; j += nt) {
+        const double t = a[k][j];
+        a[k][j] = a[p][j];
+        a[p][j] = t;
       }
     __syncthreads();
-    const double akk = a[(int64_t)k * n + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) a[(int64_t)i * n + k] = a[(int64_t)i * n + k] / akk;
+    const double pv = a[k][k];
     __syncthreads();
-    const int64_t m = n - k - 1;
-    for (int64_t idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      const int64_t i = k + 1 + idx / m, j = k + 1 + idx % m;
-      a[i * n + j] = a[i * n + j] - a[i * n + k] * a[(int64_t)k * n + j];
+    for (int j = tid; j < w; j += nt) a[k][j] = a[k][j] / pv;
+    for (int i = tid; i < n; i += nt) fk[i] = a[i][k];   // multipliers, before column k changes
+    __syncthreads();
+    for (int e = tid; e < n * (w - k); e += nt) {
+      const int i = e / (w - k), j = k + e % (w - k);
+      if (i != k) a[i][j] = a[i][j] - fk[i] * a[k][j];
     }
     __syncthreads();
   }
+  for (int e = tid; e < n * n; e += nt) inv[e] = a[e / n][n + e % n];
 }
 
-// column j of the inverse: solve LU x = P e_j
-__global__ void k_dense_inv_cols(int n, const double *lu, const int *piv, double *inv, double *work) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double *x = work + (int64_t)j * n;
-  for (int i = 0; i < n; i++) x[i] = (i == j) ? 1.0 : 0.0;
-  for (int k = 0; k < n; k++)
-    if (piv[k] != k) { const double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
-  for (int i = 0; i < n; i++) {
-    double s = x[i];
-    for (int k = 0; k < i; k++) s = s - lu[(int64_t)i * n + k] * x[k];
-    x[i] = s;
-  }
-  for (int i = n - 1; i >= 0; i--) {
-    double s = x[i];
-    for (int k = i + 1; k < n; k++) s = s - lu[(int64_t)i * n + k] * x[k];
-    x[i] = s / lu[(int64_t)i * n + i];
-  }
-  for (int i = 0; i < n; i++) inv[(int64_t)i * n + j] = x[i];
+__global__ void k_aug_to_inv(int64_t n, const double *aug, double *inv) {
+  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  inv[idx] = aug[i * 2 * n + n + j];
 }
 
 // ------------------------------------------------------------ colouring
@@ -919,23 +1185,138 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
   bstore<B>(BRef{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
 }
 
+// The same factorisation for rows held entirely in the tail (wells, general
+// rows), one warp per row: the next earlier-ordered k is found by a warp
+// minimum over the row's entries, L_ik = W_ik U_kk^-1 is formed, and the
+// entries (k, j) of row k, later-ordered than k, are matched by binary
+// search in row i and update W_ij, each lane one entry of row k.
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint8_t *emask, const int32_t *crow,
+                                                              const int64_t *pos, const int64_t *ftptr,
+                                                              const int32_t *ftcol, double *fell, double *ftval,
+                                                              int64_t q1, int64_t q2, int *err) {
+  constexpr int BB = B * B;
+  const int lane = threadIdx.x & 31;
+  const int64_t q = q1 + blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
+  if (q >= q2) return;
+  const int64_t np = g.n_rows, i = crow[q];
+  const int64_t u0 = ftptr[q], u1 = ftptr[q + 1];
+  // the row's columns and their positions, cached per warp when short enough
+  constexpr int kCache = 384;
+  __shared__ int32_t s_col[kWarps][kCache];
+  __shared__ int64_t s_pos[kWarps][kCache];
+  const int wid = threadIdx.x >> 5;
+  const bool cached = (u1 - u0) <= kCache;
+  if (cached)
+    for (int64_t u = u0 + lane; u < u1; u += 32) {
+      s_col[wid][u - u0] = ftcol[u];
+      s_pos[wid][u - u0] = pos[ftcol[u]];
+    }
+  __syncwarp();
+  auto col_at = [&](int64_t u) -> int64_t { return cached ? s_col[wid][u - u0] : ftcol[u]; };
+  auto pos_at = [&](int64_t u) -> int64_t { return cached ? s_pos[wid][u - u0] : pos[ftcol[u]]; };
+  int64_t cur = -1;
+  for (;;) {
+    long long pb = q, ub = -1;
+    for (int64_t u = u0 + lane; u < u1; u += 32) {
+      const int64_t c = col_at(u);
+      if (c == i) continue;
+      const int64_t pc = pos_at(u);
+      if (pc > cur && pc < pb) { pb = pc; ub = u; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long opb = __shfl_xor_sync(0xffffffffu, pb, o);
+      const long long oub = __shfl_xor_sync(0xffffffffu, ub, o);
+      if (opb < pb) { pb = opb; ub = oub; }
+    }
+    if (ub < 0) break;
+    cur = pb;
+    const int64_t kr = col_at(ub);
+    double W[BB], Uinv[BB], L[BB];
+    bload<B>(BRef{ftval + ub * BB, 1}, W);
+    bload<B>(BRef{fell + ((int64_t)kSelf * BB) * np + pb, np}, Uinv);
+    bmul<B>(W, Uinv, L);
+    __syncwarp();
+    if (lane == 0) bstore<B>(BRef{ftval + ub * BB, 1}, L);
+    const int64_t ku0 = ftptr[pb], ku1 = ftptr[pb + 1];
+    const int nk = kSlots + (int)(ku1 - ku0);
+    const unsigned mk = kr < g.nc ? emask[kr] : 0u;
+    for (int e = lane; e < nk; e += 32) {
+      int64_t j;
+      BRef ukj;
+      if (e < kSlots) {
+        if (e == kSelf || !((mk >> e) & 1u)) continue;
+        j = kr + g.off[e];
+        ukj = BRef{fell + ((int64_t)e * BB) * np + pb, np};
+      } else {
+        const int64_t uk = ku0 + (e - kSlots);
+        j = ftcol[uk];
+        if (j == kr) continue;
+        ukj = BRef{ftval + uk * BB, 1};
+      }
+      if (pos[j] <= pb) continue;
+      int64_t lo = u0, hi = u1 - 1, found = -1;
+      while (lo <= hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        const int64_t c = col_at(mid);
+        if (c == j) { found = mid; break; }
+        if (c < j) lo = mid + 1; else hi = mid - 1;
+      }
+      if (found < 0) continue;
+      double U[BB], P[BB], Wij[BB];
+      bload<B>(ukj, U);
+      bmul<B>(L, U, P);
+      bload<B>(BRef{ftval + found * BB, 1}, Wij);
+#pragma unroll
+      for (int x = 0; x < BB; x++) Wij[x] = Wij[x] - P[x];
+      bstore<B>(BRef{ftval + found * BB, 1}, Wij);
+    }
+    __syncwarp();
+  }
+  if (lane != 0) return;
+  int64_t lo = u0, hi = u1 - 1, dg = -1;
+  while (lo <= hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    const int64_t c = col_at(mid);
+    if (c == i) { dg = mid; break; }
+    if (c < i) lo = mid + 1; else hi = mid - 1;
+  }
+  double Wd[BB], inv[BB];
+  if (dg < 0) { atomicExch(err, 1); return; }
+  bload<B>(BRef{ftval + dg * BB, 1}, Wd);
+  if (!gj_inverse<B>(Wd, inv)) {
+    atomicExch(err, 1);
+    return;
+  }
+  bstore<B>(BRef{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+}
+
 }  // namespace
 
 // =============================================================== launchers
+void keep_pool_memory() {
+  int dev = 0;
+  TRS_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  TRS_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = UINT64_MAX;
+  TRS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+}
+
 void exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s) {
   if (n <= 0) {
     if (total) TRS_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
     return;
   }
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-  DBuf<int64_t> bsum(nb);
+  TBuf<int64_t> bsum(nb, s);
   k_scan_reduce<<<(unsigned)nb, kThreads, 0, s>>>(in, n, bsum.p);
   TRS_LAUNCHED();
   k_scan_bsums<<<1, 32, 0, s>>>(bsum.p, nb, total);
   TRS_LAUNCHED();
   k_scan_apply<<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, bsum.p);
   TRS_LAUNCHED();
-  TRS_CUDA(cudaStreamSynchronize(s));  // bsum is freed on return
 }
 
 void launch_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval, int64_t nc, double *ell,
@@ -1039,86 +1420,114 @@ void launch_agg_pass2(int64_t n, const int64_t *rp, const int32_t *col, const do
 
 void launch_members(int64_t n, const int32_t *agg, int64_t n_agg, DBuf<int64_t> &mptr, DBuf<int32_t> &midx,
                     cudaStream_t s) {
-  DBuf<int64_t> cnt(n_agg + 1), cursor(n_agg + 1);
-  cnt.zero(s);
-  cursor.zero(s);
-  mptr.alloc(n_agg + 1);
+  TBuf<int64_t> cnt(n_agg + 1, s), cursor(n_agg + 1, s);
+  cnt.zero();
+  cursor.zero();
+  if (mptr.n < (size_t)(n_agg + 1)) mptr.alloc(n_agg + 1);
   k_member_count<<<grid_of(n), kThreads, 0, s>>>(n, agg, cnt.p);
   TRS_LAUNCHED();
   exclusive_scan(cnt.p, mptr.p, n_agg + 1, nullptr, s);
-  int64_t total = 0;
-  TRS_CUDA(cudaMemcpyAsync(&total, mptr.p + n_agg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TRS_CUDA(cudaStreamSynchronize(s));
-  midx.alloc(std::max<int64_t>(total, 1));
+  if (midx.n < (size_t)std::max<int64_t>(n, 1)) midx.alloc(std::max<int64_t>(n, 1));  // members <= n
   k_member_fill<<<grid_of(n), kThreads, 0, s>>>(n, agg, mptr.p, cursor.p, midx.p);
   TRS_LAUNCHED();
   k_member_sort<<<grid_of(n_agg), kThreads, 0, s>>>(n_agg, mptr.p, midx.p);
   TRS_LAUNCHED();
-  TRS_CUDA(cudaStreamSynchronize(s));
 }
 
 void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int64_t *mptr, const int32_t *midx,
                      Csr &C, cudaStream_t s) {
-  DBuf<int64_t> cnt(n_agg + 1);
-  cnt.zero(s);
+  static bool attr_set = false;
+  const size_t long_smem = (size_t)kGalLongMax * (sizeof(unsigned long long) + sizeof(double));
+  if (!attr_set) {
+    TRS_CUDA(cudaFuncSetAttribute(k_galerkin_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)long_smem));
+    attr_set = true;
+  }
+  TBuf<int64_t> cnt(n_agg + 1, s);
+  TBuf<int32_t> long_rows(std::max<int64_t>(n_agg, 1), s);
+  TBuf<int> n_long(1, s), err(1, s);
+  cnt.zero();
+  n_long.zero();
+  err.zero();
   const unsigned grid = (unsigned)((n_agg + kWarps - 1) / kWarps);
+  const unsigned long_grid = 152;
   k_galerkin<<<grid, kThreads, 0, s>>>(n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 0, cnt.p, nullptr,
-                                       nullptr, nullptr);
+                                       nullptr, nullptr, long_rows.p, n_long.p);
+  TRS_LAUNCHED();
+  k_galerkin_long<<<long_grid, kThreads, long_smem, s>>>(F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
+                                                         n_long.p, 0, cnt.p, nullptr, nullptr, nullptr, err.p);
   TRS_LAUNCHED();
   C.n = n_agg;
-  C.rp.alloc(n_agg + 1);
+  if (C.rp.n < (size_t)(n_agg + 1)) C.rp.alloc(n_agg + 1);
   exclusive_scan(cnt.p, C.rp.p, n_agg + 1, nullptr, s);
+  int herr = 0;
   TRS_CUDA(cudaMemcpyAsync(&C.nnz, C.rp.p + n_agg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaStreamSynchronize(s));
-  C.col.alloc(std::max<int64_t>(C.nnz, 1));
-  C.val.alloc(std::max<int64_t>(C.nnz, 1));
+  TRS_REQUIRE(!herr, TRS_ERR_UNSUPPORTED, "a coarse AMG row has more than 8192 Galerkin contributions");
+  if (C.col.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.col.alloc(std::max<int64_t>(C.nnz, 1));
+  if (C.val.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.val.alloc(std::max<int64_t>(C.nnz, 1));
   k_galerkin<<<grid, kThreads, 0, s>>>(n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 1, nullptr, C.rp.p,
-                                       C.col.p, C.val.p);
+                                       C.col.p, C.val.p, long_rows.p, n_long.p);
+  TRS_LAUNCHED();
+  k_galerkin_long<<<long_grid, kThreads, long_smem, s>>>(F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
+                                                         n_long.p, 1, nullptr, C.rp.p, C.col.p, C.val.p, err.p);
   TRS_LAUNCHED();
 }
 
-double launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, cudaStream_t s) {
-  DBuf<unsigned long long> bits(1);
-  bits.zero(s);
-  k_gershgorin<<<grid_of(A.n), kThreads, 0, s>>>(A.n, A.rp.p, A.val.p, dpos, dinv, bits.p);
+void launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, unsigned long long *lam_bits,
+                            cudaStream_t s) {
+  TRS_CUDA(cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), s));
+  k_gershgorin<<<grid_of(A.n), kThreads, 0, s>>>(A.n, A.rp.p, A.val.p, dpos, dinv, lam_bits);
   TRS_LAUNCHED();
-  unsigned long long h = 0;
-  TRS_CUDA(cudaMemcpyAsync(&h, bits.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-  TRS_CUDA(cudaStreamSynchronize(s));
-  double lam;
-  std::memcpy(&lam, &h, sizeof(lam));
-  return lam;
 }
 
 int launch_dense_inverse(const Csr &A, DBuf<double> &inv, cudaStream_t s) {
   const int n = (int)A.n;
-  DBuf<double> lu((size_t)n * n), work((size_t)n * n);
-  DBuf<int> piv(n), err(1);
-  lu.zero(s);
-  err.zero(s);
-  k_csr_to_dense<<<grid_of(n), kThreads, 0, s>>>(n, A.rp.p, A.col.p, A.val.p, lu.p);
+  if (n <= kDenseSmall) {
+    TBuf<int> err(1, s);
+    err.zero();
+    if (inv.n < (size_t)std::max(n * n, 1)) inv.alloc((size_t)std::max(n * n, 1));
+    k_gj_small<<<1, 1024, 0, s>>>(n, A.rp.p, A.col.p, A.val.p, inv.p, err.p);
+    TRS_LAUNCHED();
+    int herr = 0;
+    TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+    return herr ? 1 : 0;
+  }
+  TBuf<double> aug((size_t)2 * n * n, s);
+  const int grid = std::max(1, std::min(n, 152 * 4));
+  TBuf<double> pv(grid, s);
+  TBuf<int> pr(grid, s), err(1, s);
+  TBuf<unsigned int> counter(1, s);
+  aug.zero();
+  err.zero();
+  counter.zero();
+  k_csr_to_aug<<<grid_of(n), kThreads, 0, s>>>(n, A.rp.p, A.col.p, A.val.p, aug.p);
   TRS_LAUNCHED();
-  k_dense_lu<<<1, 1024, 0, s>>>(n, lu.p, piv.p, err.p);
+  k_gj_first<<<1, kThreads, 0, s>>>(n, aug.p, err.p);
   TRS_LAUNCHED();
+  for (int k = 0; k < n; k++) {
+    k_gj_step<<<grid, kThreads, 0, s>>>(n, k, aug.p, pv.p, pr.p, counter.p, err.p);
+    TRS_LAUNCHED();
+  }
   int herr = 0;
   TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaStreamSynchronize(s));
   if (herr) return 1;
-  inv.alloc((size_t)n * n);
-  k_dense_inv_cols<<<(n + 127) / 128, 128, 0, s>>>(n, lu.p, piv.p, inv.p, work.p);
+  if (inv.n < (size_t)n * n) inv.alloc((size_t)n * n);
+  k_aug_to_inv<<<grid_of((int64_t)n * n), kThreads, 0, s>>>(n, aug.p, inv.p);
   TRS_LAUNCHED();
-  TRS_CUDA(cudaStreamSynchronize(s));
   return 0;
 }
 
 int launch_colour(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol, uint32_t seed,
                   int32_t *colour, cudaStream_t s) {
   const int64_t n = g.n_rows;
-  DBuf<int32_t> other(n);
-  DBuf<unsigned long long> cnt(1);
-  DBuf<int> overflow(1);
-  cnt.zero(s);
-  overflow.zero(s);
+  TBuf<int32_t> other(n, s);
+  TBuf<unsigned long long> cnt(1, s);
+  TBuf<int> overflow(1, s);
+  cnt.zero();
+  overflow.zero();
   TRS_CUDA(cudaMemsetAsync(colour, 0xff, n * sizeof(int32_t), s));
   int32_t *a = colour, *bbuf = other.p;
   unsigned long long done = 0;
@@ -1142,9 +1551,9 @@ int launch_colour(const Geom &g, const uint8_t *emask, const int64_t *tptr, cons
 void launch_colour_order(const Geom &g, const int32_t *colour, int ncol, std::vector<int64_t> &cptr,
                          std::vector<int64_t> &cmid, int32_t *crow, int64_t *pos, cudaStream_t s) {
   const int64_t n = g.n_rows;
-  DBuf<unsigned long long> cnt(kMaxColours), cntc(kMaxColours);
-  cnt.zero(s);
-  cntc.zero(s);
+  TBuf<unsigned long long> cnt(kMaxColours, s), cntc(kMaxColours, s);
+  cnt.zero();
+  cntc.zero();
   k_colour_count<<<grid_of(n), kThreads, 0, s>>>(g, colour, cnt.p, cntc.p);
   TRS_LAUNCHED();
   auto hc = download(cnt.p, kMaxColours, s);
@@ -1155,7 +1564,7 @@ void launch_colour_order(const Geom &g, const int32_t *colour, int ncol, std::ve
     cptr[c + 1] = cptr[c] + (int64_t)hc[c];
     cmid[c] = cptr[c] + (int64_t)hcc[c];
   }
-  DBuf<int64_t> flag(n), rank(n);
+  TBuf<int64_t> flag(n, s), rank(n, s);
   for (int c = 0; c < ncol; c++) {
     k_colour_flag<<<grid_of(n), kThreads, 0, s>>>(n, colour, c, flag.p);
     TRS_LAUNCHED();
@@ -1170,8 +1579,8 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
                           const int32_t *crow, const int64_t *pos, uint8_t *lmask, DBuf<int64_t> &ftptr,
                           DBuf<int32_t> &ftcol, DBuf<uint8_t> &ftlow, DBuf<int64_t> &ftsrc, cudaStream_t s) {
   const int64_t n = g.n_rows;
-  DBuf<int64_t> len(n + 1);
-  len.zero(s);
+  TBuf<int64_t> len(n + 1, s);
+  len.zero();
   k_ilu_lmask_len<<<grid_of(n), kThreads, 0, s>>>(g, emask, tptr, crow, pos, lmask, len.p);
   TRS_LAUNCHED();
   ftptr.alloc(n + 1);
@@ -1197,11 +1606,18 @@ void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *
 
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
                               const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, double *fell,
-                              double *ftval, int64_t q0, int64_t q1, int *err, cudaStream_t s) {
-  if (q1 <= q0) return;
-  TRS_DISPATCH_B(b, k_ilu_factor<B><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
-                                                                          ftlow, fell, ftval, q0, q1, err));
-  TRS_LAUNCHED();
+                              double *ftval, int64_t q0, int64_t q1, int64_t q2, int *err, cudaStream_t s) {
+  if (q1 > q0) {
+    TRS_DISPATCH_B(b, k_ilu_factor<B><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
+                                                                            ftlow, fell, ftval, q0, q1, err));
+    TRS_LAUNCHED();
+  }
+  if (q2 > q1) {
+    const unsigned grid = (unsigned)((q2 - q1 + kWarps - 1) / kWarps);
+    TRS_DISPATCH_B(b, k_ilu_factor_long<B><<<grid, kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol, fell,
+                                                                     ftval, q1, q2, err));
+    TRS_LAUNCHED();
+  }
 }
 
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s) {

@@ -25,6 +25,39 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <class T>
 __device__ __forceinline__ double to_d(T v) { return static_cast<double>(v); }
 
+// b consecutive entries of a block vector (16-byte aligned for b = 2, 4:
+// the base pointers come from cudaMalloc-class allocations and block starts
+// are multiples of b entries), with 128-bit accesses where they fit.
+template <int B, class T>
+__device__ __forceinline__ void load_blk(const T *p, T (&v)[B]) {
+  if constexpr (B == 4 && sizeof(T) == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (B == 4 && sizeof(T) == 8) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else if constexpr (B == 2 && sizeof(T) == 8) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    v[0] = a.x; v[1] = a.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < B; c++) v[c] = p[c];
+  }
+}
+
+template <int B, class T>
+__device__ __forceinline__ void store_blk(T *p, const T (&v)[B]) {
+  if constexpr (B == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (B == 4 && sizeof(T) == 8) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < B; c++) p[c] = v[c];
+  }
+}
+
 // ------------------------------------------------------------ block SpMV
 template <int B, class TA, class TX>
 __device__ __forceinline__ void cell_row_apply(const MatView<TA> &A, int64_t i, const TX *__restrict__ x,
@@ -36,9 +69,11 @@ __device__ __forceinline__ void cell_row_apply(const MatView<TA> &A, int64_t i, 
   for (int s = 0; s < kSlots; s++) {
     if (!((m >> s) & 1u)) continue;
     const int64_t j = i + A.g.off[s];
+    TX xv[B];
+    load_blk<B>(x + j * B, xv);
     double xj[B];
 #pragma unroll
-    for (int c = 0; c < B; c++) xj[c] = to_d(x[j * B + c]);
+    for (int c = 0; c < B; c++) xj[c] = to_d(xv[c]);
     const TA *blk = A.ell + (int64_t)s * BB * nc + i;
 #pragma unroll
     for (int r = 0; r < B; r++)
@@ -204,12 +239,13 @@ __global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   double v[B];
-  const double d = div ? *div : 1.0;
+  load_blk<B>(w + i * B, v);
+  if (div) {
+    const double rd = 1.0 / *div;
 #pragma unroll
-  for (int c = 0; c < B; c++) {
-    v[c] = div ? w[i * B + c] / d : w[i * B + c];
-    if (vout) vout[i * B + c] = v[c];
+    for (int c = 0; c < B; c++) v[c] = v[c] * rd;
   }
+  if (vout) store_blk<B>(vout + i * B, v);
 #pragma unroll
   for (int r = 0; r < B; r++) {
     T acc = T(0);
@@ -230,16 +266,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
     if (q >= q1) return;
     const int64_t i = F.crow[q];
     T t[B];
-#pragma unroll
-    for (int r = 0; r < B; r++) t[r] = rhs[i * B + r];
+    load_blk<B>(rhs + i * B, t);
     const unsigned lm = F.lmask[q];
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (!((lm >> s) & 1u)) continue;
       const int64_t j = i + F.g.off[s];
       T yj[B];
-#pragma unroll
-      for (int c = 0; c < B; c++) yj[c] = y[j * B + c];
+      load_blk<B>(y + j * B, yj);
       const T *blk = F.fell + (int64_t)s * BB * np + q;
 #pragma unroll
       for (int r = 0; r < B; r++)
@@ -255,8 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
 #pragma unroll
         for (int c = 0; c < B; c++) t[r] = fma(-blk[r * B + c], y[j * B + c], t[r]);
     }
-#pragma unroll
-    for (int r = 0; r < B; r++) y[i * B + r] = t[r];
+    store_blk<B>(y + i * B, t);
   } else {
     const int lane = threadIdx.x & 31;
     const int64_t q = q1 + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
@@ -294,16 +327,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     active = q < q1;
     if (!active) return;
     i = F.crow[q];
-#pragma unroll
-    for (int r = 0; r < B; r++) t[r] = y[i * B + r];
+    load_blk<B>(y + i * B, t);
     const unsigned um = F.emask[i] & ~(unsigned)F.lmask[q] & ~(1u << kSelf);
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (!((um >> s) & 1u)) continue;
       const int64_t j = i + F.g.off[s];
       T yj[B];
-#pragma unroll
-      for (int c = 0; c < B; c++) yj[c] = y[j * B + c];
+      load_blk<B>(y + j * B, yj);
       const T *blk = F.fell + (int64_t)s * BB * np + q;
 #pragma unroll
       for (int r = 0; r < B; r++)
@@ -350,15 +381,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     for (int c = 0; c < B; c++) a = fma(dg[(int64_t)(r * B + c) * np], t[c], a);
     xv[r] = a;
   }
-#pragma unroll
-  for (int r = 0; r < B; r++) y[i * B + r] = xv[r];
+  store_blk<B>(y + i * B, xv);
   if (zout) {
+    T zb[B];
+    load_blk<B>(y1 + i * B, zb);
+    zb[0] = zb[0] + e0[i];
 #pragma unroll
-    for (int r = 0; r < B; r++) {
-      T base = y1[i * B + r];
-      if (r == 0) base = base + e0[i];
-      zout[i * B + r] = base + xv[r];
-    }
+    for (int r = 0; r < B; r++) zb[r] = zb[r] + xv[r];
+    store_blk<B>(zout + i * B, zb);
   }
 }
 
@@ -419,8 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
     if (i >= At.g.nc) return;
     const int64_t nc = At.g.nc;
     T acc[B];
-#pragma unroll
-    for (int rr = 0; rr < B; rr++) acc[rr] = y1[i * B + rr];
+    load_blk<B>(y1 + i * B, acc);
     acc[0] = acc[0] + e0[i];
     const unsigned m = At.emask[i] & ~(1u << kSelf);
 #pragma unroll
@@ -428,8 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
       if (!((m >> s) & 1u)) continue;
       const int64_t j = i + At.g.off[s];
       T yj[B];
-#pragma unroll
-      for (int c = 0; c < B; c++) yj[c] = y1[j * B + c];
+      load_blk<B>(y1 + j * B, yj);
       yj[0] = yj[0] + e0[j];
       const T *blk = At.ell + (int64_t)s * BB * nc + i;
 #pragma unroll
@@ -450,8 +478,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
 #pragma unroll
         for (int c = 0; c < B; c++) acc[rr] = fma(blk[rr * B + c], yj[c], acc[rr]);
     }
+    T fv[B];
+    load_blk<B>(f + i * B, fv);
 #pragma unroll
-    for (int rr = 0; rr < B; rr++) r[i * B + rr] = f[i * B + rr] - acc[rr];
+    for (int rr = 0; rr < B; rr++) fv[rr] = fv[rr] - acc[rr];
+    store_blk<B>(r + i * B, fv);
   } else {
     const int lane = threadIdx.x & 31;
     const int64_t i = At.g.nc + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
@@ -619,6 +650,89 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update(const double *__restric
   if (!want_norm) return;
   block_partial<1>(acc, partial + (int64_t)blockIdx.x * kRedStride);
   last_block_finish(partial, counter, 1, out, 0);
+}
+
+// ---- CGS2 in three passes over V (K + 1 <= KM outputs per reduction) ----
+// Partial sums are stored [k][block] so that the last block reduces each k
+// with one warp and coalesced loads, in block order.
+__device__ void last_block_finish_kb(const double *partial, unsigned int *counter, int K, double *out) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < K; k += kWarps) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (int64_t)k * gridDim.x + b);
+    s = warp_sum(s);
+    if (lane == 0) out[k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <int KM>
+__device__ void block_partial_kb(double (&acc)[KM], int K, double *partial) {
+  __shared__ double sm[kWarps][KM];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < KM; u++) {
+    if (u < K) {
+      const double v = warp_sum(acc[u]);
+      if (lane == 0) sm[warp][u] = v;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += kThreads) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; w++) t += sm[w][k];
+    partial[(int64_t)k * gridDim.x + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// out[k] = <V_k, w> for k < K, out[K] = <w, w>
+template <int KM>
+__global__ void __launch_bounds__(kThreads) k_cgs_dots(const double *__restrict__ V, int64_t N, int K,
+                                                       const double *__restrict__ w, double *partial,
+                                                       unsigned int *counter, double *out) {
+  double acc[KM] = {};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+    const double wi = w[i];
+#pragma unroll
+    for (int u = 0; u < KM; u++) {
+      if (u < K) acc[u] = fma(V[(int64_t)u * N + i], wi, acc[u]);
+      else if (u == K) acc[u] = fma(wi, wi, acc[u]);
+    }
+  }
+  block_partial_kb<KM>(acc, K + 1, partial);
+  last_block_finish_kb(partial, counter, K + 1, out);
+}
+
+// w -= sum_k h_k V_k; out[k] = <V_k, w> with the updated w
+template <int KM>
+__global__ void __launch_bounds__(kThreads) k_cgs_update_dots(const double *__restrict__ V, int64_t N, int K,
+                                                              const double *__restrict__ h, double *__restrict__ w,
+                                                              double *partial, unsigned int *counter, double *out) {
+  __shared__ double sh[KM];
+  for (int k = threadIdx.x; k < K; k += kThreads) sh[k] = h[k];
+  __syncthreads();
+  double acc[KM] = {};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+    double t = w[i];
+#pragma unroll
+    for (int u = 0; u < KM; u++)
+      if (u < K) t = fma(-sh[u], V[(int64_t)u * N + i], t);
+    w[i] = t;
+#pragma unroll
+    for (int u = 0; u < KM; u++)
+      if (u < K) acc[u] = fma(V[(int64_t)u * N + i], t, acc[u]);
+  }
+  block_partial_kb<KM>(acc, K, partial);
+  last_block_finish_kb(partial, counter, K, out);
 }
 
 // Arnoldi column j of H (row-major, m columns): h1 + h2, norm; Givens.
@@ -806,6 +920,25 @@ void launch_cgs_update(const double *V, int64_t N, int K, const double *h, doubl
   k_cgs_update<<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, want_norm, red.partial, red.counter, out);
   TRS_LAUNCHED();
 }
+void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
+                     cudaStream_t s) {
+  if (K + 1 <= 8) k_cgs_dots<8><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
+  else if (K + 1 <= 16) k_cgs_dots<16><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
+  else if (K + 1 <= 32) k_cgs_dots<32><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
+  else throw Error(TRS_ERR_UNSUPPORTED, "fused CGS2 supports at most 31 basis vectors");
+  TRS_LAUNCHED();
+}
+void launch_cgs_update_dots(const double *V, int64_t N, int K, const double *h, double *w, const RedScratch &red,
+                            double *out, cudaStream_t s) {
+  if (K <= 8)
+    k_cgs_update_dots<8><<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, red.partial, red.counter, out);
+  else if (K <= 16)
+    k_cgs_update_dots<16><<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, red.partial, red.counter, out);
+  else if (K <= 32)
+    k_cgs_update_dots<32><<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, red.partial, red.counter, out);
+  else throw Error(TRS_ERR_UNSUPPORTED, "fused CGS2 supports at most 31 basis vectors");
+  TRS_LAUNCHED();
+}
 void launch_givens(int j, int m, double *H, const double *h1, const double *h2, const double *hn2,
                    const double *wn2, double *cs, double *sn, double *g, double *hnorm_out, double *status,
                    double inv_bnorm, cudaStream_t s) {
@@ -912,6 +1045,9 @@ extern "C" trs_status trs_residual_norm_noalloc(const trs_bsr *A, const double *
   return guarded([&] {
     TRS_REQUIRE(A && x && b && r && norm, TRS_ERR_INVALID, "NULL argument");
     TRS_REQUIRE(x != r && b != r, TRS_ERR_INVALID, "r must not alias x or b");
+    require_aligned(x, "x");
+    require_aligned(b, "b");
+    require_aligned(r, "r");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = A->n * A->b;
     const int64_t grid = std::min<int64_t>(kStaticGrid, std::max<int64_t>(1, (N + kThreads - 1) / kThreads));

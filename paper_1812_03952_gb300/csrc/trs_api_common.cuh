@@ -30,6 +30,11 @@ trs_status guarded(F &&f) {
 }
 
 void validate_pattern(int64_t n, int b, const int64_t *rp, const int32_t *col);
+
+// Device vectors are read and written with 128-bit accesses.
+inline void require_aligned(const void *p, const char *what) {
+  TRS_REQUIRE(((uintptr_t)p & 15u) == 0, TRS_ERR_INVALID, std::string(what) + " must be 16-byte aligned");
+}
 void build_layout(trs_bsr *A, int64_t n, int b, const int64_t *rp, const int32_t *col, const int32_t *grid,
                   cudaStream_t s);
 void upload_values(trs_bsr *A, const double *values, bool on_device, cudaStream_t s);
@@ -66,7 +71,9 @@ struct trs_cpr {
   trs::DBuf<double> at_ell64, at_tval64, dinv64, ap_ell64, ap_tval64;
   trs::DBuf<float> at_ell32, at_tval32, dinv32, ap_ell32, ap_tval32;
   // pressure AMG
-  std::vector<trs::Level> lev;
+  std::vector<trs::Level> lev;   // lev[0 .. nlev-1] active; extra entries keep their buffers
+  int nlev = 0;
+  trs::DBuf<unsigned long long> lam_bits;
   trs::DBuf<double> cinv;      // inverse of the coarsest operator
   // multicolour block ILU(0)
   int ncol = 0;

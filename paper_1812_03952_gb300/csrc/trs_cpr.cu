@@ -48,105 +48,128 @@ struct Timer {
 };
 
 // ------------------------------------------------------------ AMG setup
+template <class T>
+void reserve(DBuf<T> &b, int64_t n) {
+  if (b.n < (size_t)std::max<int64_t>(n, 1)) b.alloc(std::max<int64_t>(n, 1));
+}
+
 void build_hierarchy(trs_cpr *M, cudaStream_t s) {
   const trs_cpr_opts &o = M->opts;
   auto &lev = M->lev;
+  reserve(M->lam_bits, kMaxLevels);
+  int nlev = 1;
   for (int l = 0;; l++) {
     Level &F = lev[l];
     const int64_t n = F.A.n;
-    F.dpos.alloc(std::max<int64_t>(n, 1));
+    reserve(F.dpos, n);
     launch_diag_pos(n, F.A.rp.p, F.A.col.p, F.dpos.p, s);
-    F.dinv64.alloc(std::max<int64_t>(n, 1));
-    F.lam = launch_gershgorin_dinv(F.A, F.dpos.p, F.dinv64.p, s);
+    reserve(F.dinv64, n);
+    launch_gershgorin_dinv(F.A, F.dpos.p, F.dinv64.p, M->lam_bits.p + l, s);
     if (n <= o.coarse_max || l + 1 >= o.max_levels) break;
     const int64_t nnz = F.A.nnz;
-    DBuf<uint8_t> sflag(std::max<int64_t>(nnz, 1));
-    DBuf<int32_t> sdeg(n);
+    TBuf<uint8_t> sflag(std::max<int64_t>(nnz, 1), s);
+    TBuf<int32_t> sdeg(n, s);
     launch_strength(n, F.A.rp.p, F.A.col.p, F.A.val.p, F.dpos.p, o.theta, sflag.p, sdeg.p, s);
-    // MIS-2 rounds
+    // MIS-2 rounds; the undecided count is read every second round (an extra
+    // round after completion changes nothing)
     const uint32_t seed = o.seed ^ (kLevelSeedMul * (uint32_t)(l + 1));
-    DBuf<int8_t> state(n), s1(n), s2(n);
-    DBuf<uint64_t> k1(n), k2(n);
-    DBuf<unsigned long long> und(1);
+    TBuf<int8_t> state(n, s), s1(n, s), s2(n, s);
+    TBuf<uint64_t> k1(n, s), k2(n, s);
+    TBuf<unsigned long long> und(1, s);
     launch_mis2_init(n, sdeg.p, state.p, s);
     for (int round = 0;; round++) {
       TRS_REQUIRE(round < 10000, TRS_ERR_COARSENING, "MIS-2 did not terminate");
-      und.zero(s);
+      und.zero();
       launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, nullptr, seed, s1.p, k1.p, s);
       launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, s1.p, k1.p, seed, s2.p, k2.p, s);
       launch_mis2_decide(n, seed, s2.p, k2.p, state.p, und.p, s);
+      if (round % 2 == 0) continue;
       unsigned long long left = 0;
       TRS_CUDA(cudaMemcpyAsync(&left, und.p, sizeof(left), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
       if (!left) break;
     }
     // aggregates
-    DBuf<int64_t> flag(n + 1), rootid(n + 1);
-    flag.zero(s);
+    TBuf<int64_t> flag(n + 1, s), rootid(n + 1, s);
+    flag.zero();
     launch_in_flag(n, state.p, flag.p, s);
     exclusive_scan(flag.p, rootid.p, n + 1, nullptr, s);
     int64_t n_agg = 0;
     TRS_CUDA(cudaMemcpyAsync(&n_agg, rootid.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TRS_CUDA(cudaStreamSynchronize(s));
     if (n_agg == 0 || 10 * n_agg >= 9 * n) break;
-    DBuf<int32_t> first(n);
-    F.agg.alloc(n);
+    TBuf<int32_t> first(n, s);
+    reserve(F.agg, n);
     launch_agg_pass1(n, F.A.rp.p, F.A.col.p, sflag.p, sdeg.p, state.p, rootid.p, first.p, s);
     launch_agg_pass2(n, F.A.rp.p, F.A.col.p, F.A.val.p, sflag.p, sdeg.p, first.p, F.agg.p, s);
     F.n_agg = n_agg;
     launch_members(n, F.agg.p, n_agg, F.mptr, F.midx, s);
-    lev.emplace_back();
+    if ((int)lev.size() < l + 2) lev.emplace_back();
     launch_galerkin(lev[l].A, lev[l].agg.p, n_agg, lev[l].mptr.p, lev[l].midx.p, lev[l + 1].A, s);
-    TRS_CUDA(cudaStreamSynchronize(s));
+    nlev = l + 2;
   }
-  Level &C = lev.back();
+  M->nlev = nlev;
+  Level &C = lev[nlev - 1];
+  C.n_agg = 0;
   TRS_REQUIRE(C.A.n <= kDenseMax, TRS_ERR_COARSENING, "AMG coarsening stalled above the dense-solve limit");
   TRS_REQUIRE(launch_dense_inverse(C.A, M->cinv, s) == 0, TRS_ERR_SINGULAR_BLOCK, "coarsest AMG matrix is singular");
+  unsigned long long bits[kMaxLevels];
+  TRS_CUDA(cudaMemcpyAsync(bits, M->lam_bits.p, nlev * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  for (int l = 0; l < nlev; l++) std::memcpy(&lev[l].lam, &bits[l], sizeof(double));
+}
+
+void alloc_level_vectors(trs_cpr *M) {
+  const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
+  for (int l = 0; l < M->nlev; l++) {
+    Level &L = M->lev[l];
+    const int64_t bytes = std::max<int64_t>(L.A.n, 1) * (int64_t)es;
+    reserve(L.r, bytes);
+    reserve(L.e, bytes);
+    reserve(L.res, bytes);
+    reserve(L.d, bytes);
+    reserve(L.dn, bytes);
+  }
 }
 
 // --------------------------------------------------- decoupling + ILU
 void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s) {
   const int b = M->b, bb = b * b;
   const int64_t n = M->n, nc = M->g.nc;
-  DBuf<int> err(1);
-  err.zero(s);
+  TBuf<int> err(1, s);
+  err.zero();
   launch_decouple(b, A->view(), A->tdiag.p, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
                   M->ap_tval64.p, err.p, s);
-  int herr = 0;
-  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TRS_CUDA(cudaStreamSynchronize(s));
-  TRS_REQUIRE(!herr, TRS_ERR_SINGULAR_BLOCK, "a diagonal block is singular");
   if (rebuild_amg) {
-    M->lev.clear();
-    M->lev.emplace_back();
+    if (M->lev.empty()) M->lev.emplace_back();
     Csr &C0 = M->lev[0].A;
     C0.n = n;
-    C0.rp.alloc(n + 1);
-    DBuf<int64_t> len(n + 1);
-    len.zero(s);
+    reserve(C0.rp, n + 1);
+    TBuf<int64_t> len(n + 1, s);
+    len.zero();
     launch_ap_csr_rowlen(M->g, M->emask.p, M->tptr.p, len.p, s);
     exclusive_scan(len.p, C0.rp.p, n + 1, nullptr, s);
+    int herr0 = 0;
     TRS_CUDA(cudaMemcpyAsync(&C0.nnz, C0.rp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaMemcpyAsync(&herr0, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     TRS_CUDA(cudaStreamSynchronize(s));
-    C0.col.alloc(C0.nnz);
-    C0.val.alloc(C0.nnz);
+    TRS_REQUIRE(!herr0, TRS_ERR_SINGULAR_BLOCK, "a diagonal block is singular");
+    reserve(C0.col, C0.nnz);
+    reserve(C0.val, C0.nnz);
     launch_ap_csr_fill(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->ap_ell64.p, M->ap_tval64.p, C0.rp.p, C0.col.p,
                        C0.val.p, s);
     build_hierarchy(M, s);
+    alloc_level_vectors(M);
   }
   // block ILU(0) on Ã
   launch_ilu_init(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft, M->fell64.p,
                   M->ftval64.p, s);
-  err.zero(s);
   for (int c = 0; c < M->ncol; c++)
     launch_ilu_factor_colour(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
-                             M->fell64.p, M->ftval64.p, M->cptr[c], M->cptr[c + 1], err.p, s);
-  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TRS_CUDA(cudaStreamSynchronize(s));
-  TRS_REQUIRE(!herr, TRS_ERR_SINGULAR_BLOCK, "a block ILU(0) pivot block is singular");
+                             M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], err.p, s);
   if (M->prec == TRS_FP32_PREC) {
     auto cast = [&](DBuf<double> &src, DBuf<float> &dst, int64_t cnt) {
-      if (dst.n < (size_t)std::max<int64_t>(cnt, 1)) dst.alloc(std::max<int64_t>(cnt, 1));
+      reserve(dst, cnt);
       launch_cast<double, float>(src.p, dst.p, cnt, s);
     };
     cast(M->at_ell64, M->at_ell32, (int64_t)kSlots * bb * nc);
@@ -156,13 +179,16 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
     cast(M->ap_tval64, M->ap_tval32, M->ntail);
     cast(M->fell64, M->fell32, (int64_t)kSlots * bb * n);
     cast(M->ftval64, M->ftval32, M->nft * bb);
-    for (size_t l = 0; l < M->lev.size(); l++) {
+    for (int l = 0; l < M->nlev; l++) {
       Level &L = M->lev[l];
       cast(L.dinv64, L.dinv32, L.A.n);
       if (l > 0) cast(L.A.val, L.val32, L.A.nnz);
     }
   }
+  int herr = 0;
+  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaStreamSynchronize(s));
+  TRS_REQUIRE(!herr, TRS_ERR_SINGULAR_BLOCK, "a singular diagonal or block ILU(0) pivot block");
 }
 
 void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
@@ -174,6 +200,7 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   M->g = A->g;
   M->ntail = A->ntail;
   M->nnzb = A->nnzb;
+  keep_pool_memory();
   auto copy_d2d = [&](auto &dst, const auto &src, int64_t cnt) {
     using E = std::remove_reference_t<decltype(*src.p)>;
     dst.alloc(std::max<int64_t>(cnt, 1));
@@ -219,13 +246,6 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   alloc_vec(M->wr, M->N, es);
   alloc_vec(M->wx, M->N, es);
   alloc_vec(M->wz, M->N, es);
-  for (auto &L : M->lev) {
-    alloc_vec(L.r, L.A.n, es);
-    alloc_vec(L.e, L.A.n, es);
-    alloc_vec(L.res, L.A.n, es);
-    alloc_vec(L.d, L.A.n, es);
-    alloc_vec(L.dn, L.A.n, es);
-  }
 }
 
 // ------------------------------------------------------------ application
@@ -318,7 +338,7 @@ void chebyshev(const trs_cpr *M, int l, const T *r, T *e, bool zero_init, cudaSt
 
 template <class T>
 void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
-  const int L = (int)M->lev.size();
+  const int L = M->nlev;
   const Level &Lv = M->lev[l];
   if (l == L - 1) {
     launch_dense_gemv<T>(Lv.A.n, M->cinv.p, r, e, s);
@@ -434,9 +454,15 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
       if (j == 0) cpr_apply_full<T>(M, M->r.p, M->norms.p + 1, vj, zj, s);
       else cpr_apply_full<T>(M, M->w.p, M->hnorm.p, vj, zj, s);
       launch_spmv<double, T>(M->b, Av, zj, M->w.p, 1.0, 0.0, s);
-      launch_multidot(V, N, j + 1, M->w.p, red, M->h1.p, s);
-      launch_cgs_update(V, N, j + 1, M->h1.p, M->w.p, 0, red, nullptr, s);
-      launch_multidot(V, N, j + 1, M->w.p, red, M->h2.p, s);
+      // CGS2: h1 = V^T w (and ||w||^2); w -= V h1 with h2 = V^T w fused; w -= V h2 with ||w||^2
+      if (j + 2 <= 32) {
+        launch_cgs_dots(V, N, j + 1, M->w.p, red, M->h1.p, s);
+        launch_cgs_update_dots(V, N, j + 1, M->h1.p, M->w.p, red, M->h2.p, s);
+      } else {
+        launch_multidot(V, N, j + 1, M->w.p, red, M->h1.p, s);
+        launch_cgs_update(V, N, j + 1, M->h1.p, M->w.p, 0, red, nullptr, s);
+        launch_multidot(V, N, j + 1, M->w.p, red, M->h2.p, s);
+      }
       launch_cgs_update(V, N, j + 1, M->h2.p, M->w.p, 1, red, M->hn2.p, s);
       launch_givens(j, m, M->H.p, M->h1.p, M->h2.p, M->hn2.p, M->h1.p + j + 1, M->cs.p, M->sn.p, M->gv.p,
                     M->hnorm.p, M->status.p, 1.0 / bnorm, s);
@@ -460,7 +486,7 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
   }
   local.iters = iters;
   local.restarts = cycles > 0 ? cycles - 1 : 0;
-  local.amg_levels = (int)M->lev.size();
+  local.amg_levels = M->nlev;
   local.n_colours = M->ncol;
   local.ms_setup = M->ms_setup;
   local.ms_solve = timer.stop();
@@ -475,6 +501,8 @@ trs_status run_solve(const trs_bsr *A, trs_cpr *M, const double *b, double *x, c
   if (opts) o = *opts;
   TRS_REQUIRE(A && M && b && x, TRS_ERR_INVALID, "NULL argument");
   TRS_REQUIRE(A->n == M->n && A->b == M->b, TRS_ERR_INVALID, "matrix and preconditioner sizes differ");
+  require_aligned(b, "b");
+  require_aligned(x, "x");
   TRS_REQUIRE(o.restart >= 1 && o.restart <= kMaxRestart, TRS_ERR_INVALID, "restart must be 1..64");
   TRS_REQUIRE(o.maxit >= 1 && o.rtol > 0.0, TRS_ERR_INVALID, "maxit must be >= 1 and rtol > 0");
   if (M->prec == TRS_FP32_PREC) return fgmres<float>(A, M, b, x, o, s, st);
@@ -500,7 +528,7 @@ void trs_cpr_default_opts(trs_cpr_opts *o) {
   if (!o) return;
   o->precision = TRS_FP64;
   o->theta = 0.08;
-  o->coarse_max = 1024;
+  o->coarse_max = 64;
   o->max_levels = 12;
   o->cheb_degree = 2;
   o->seed = 0x5EED1812u;
@@ -543,16 +571,6 @@ trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void 
     cudaStream_t s = (cudaStream_t)stream;
     Timer t(s);
     build_values(M, A, reuse_amg == 0, s);
-    if (reuse_amg == 0) {
-      const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
-      for (auto &L : M->lev) {
-        alloc_vec(L.r, L.A.n, es);
-        alloc_vec(L.e, L.A.n, es);
-        alloc_vec(L.res, L.A.n, es);
-        alloc_vec(L.d, L.A.n, es);
-        alloc_vec(L.dn, L.A.n, es);
-      }
-    }
     M->ms_setup = t.stop();
   });
 }
@@ -560,6 +578,8 @@ trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void 
 trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *stream) {
   return guarded([&] {
     TRS_REQUIRE(M && v && z, TRS_ERR_INVALID, "NULL argument");
+    require_aligned(v, "v");
+    require_aligned(z, "z");
     cudaStream_t s = (cudaStream_t)stream;
     if (M->prec == TRS_FP32_PREC) {
       cpr_apply_full<float>(M, v, nullptr, nullptr, tp<float>(M->wz), s);
@@ -589,10 +609,10 @@ trs_status trs_cpr_get_info(const trs_cpr *M, trs_cpr_info *info) {
   return guarded([&] {
     TRS_REQUIRE(M && info, TRS_ERR_INVALID, "NULL argument");
     std::memset(info, 0, sizeof(*info));
-    info->n_levels = (int)M->lev.size();
+    info->n_levels = M->nlev;
     info->n_colours = M->ncol;
     info->precision = M->prec;
-    for (size_t l = 0; l < M->lev.size() && l < 16; l++) {
+    for (int l = 0; l < M->nlev && l < 16; l++) {
       info->level_rows[l] = M->lev[l].A.n;
       info->level_nnz[l] = M->lev[l].A.nnz;
       info->level_lambda[l] = M->lev[l].lam;
@@ -603,9 +623,9 @@ trs_status trs_cpr_get_info(const trs_cpr *M, trs_cpr_info *info) {
 trs_status trs_cpr_get_aggregates(const trs_cpr *M, int32_t level, int32_t *agg) {
   return guarded([&] {
     TRS_REQUIRE(M && agg, TRS_ERR_INVALID, "NULL argument");
-    TRS_REQUIRE(level >= 0 && level < (int)M->lev.size(), TRS_ERR_INVALID, "level out of range");
+    TRS_REQUIRE(level >= 0 && level < M->nlev, TRS_ERR_INVALID, "level out of range");
     const Level &L = M->lev[level];
-    if (L.agg.p) {
+    if (level < M->nlev - 1) {
       auto h = download(L.agg.p, L.A.n, 0);
       std::copy(h.begin(), h.end(), agg);
     } else {
@@ -643,7 +663,7 @@ trs_status trs_cpr_get_decoupled(const trs_cpr *M, double *vt, double *dinv) {
 trs_status trs_cpr_get_level(const trs_cpr *M, int32_t level, int64_t *row_ptr, int32_t *col, double *val) {
   return guarded([&] {
     TRS_REQUIRE(M && row_ptr && col && val, TRS_ERR_INVALID, "NULL argument");
-    TRS_REQUIRE(level >= 0 && level < (int)M->lev.size(), TRS_ERR_INVALID, "level out of range");
+    TRS_REQUIRE(level >= 0 && level < M->nlev, TRS_ERR_INVALID, "level out of range");
     const Csr &C = M->lev[level].A;
     auto a = download(C.rp.p, C.n + 1, 0);
     auto b = download(C.col.p, C.nnz, 0);

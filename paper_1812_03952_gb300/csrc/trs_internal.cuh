@@ -92,6 +92,29 @@ struct DBuf {
   T *get() const { return p; }
 };
 
+// Stream-ordered temporary device buffer (cudaMallocAsync / cudaFreeAsync on
+// the stream that uses it): no device-wide synchronisation on free.
+template <class T>
+struct TBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  TBuf(size_t count, cudaStream_t st) : n(count), s(st) {
+    if (count) TRS_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&p), count * sizeof(T), s));
+  }
+  TBuf(const TBuf &) = delete;
+  TBuf &operator=(const TBuf &) = delete;
+  ~TBuf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  void zero() {
+    if (n) TRS_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+};
+
+// Keeps freed stream-ordered memory in the current device's pool.
+void keep_pool_memory();
+
 template <class T>
 std::vector<T> download(const T *d, size_t count, cudaStream_t s) {
   std::vector<T> h(count);
@@ -150,6 +173,9 @@ struct trs_bsr {
   trs::DBuf<int32_t> urow, ucol;
   std::vector<int64_t> h_rp;
   std::vector<int32_t> h_col;
+  // for a matrix made by trs_bsr_transpose: canonical index in the source of
+  // each canonical block (refresh with trs_bsr_transpose_values)
+  trs::DBuf<int64_t> tsrc;
   // tail entries grouped by column (for the transposed product)
   trs::DBuf<int64_t> tc_ptr, tc_src;
   trs::DBuf<int32_t> tc_row;

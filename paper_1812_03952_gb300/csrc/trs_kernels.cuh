@@ -100,6 +100,10 @@ void launch_multidot(const double *V, int64_t N, int K, const double *w, const R
                      double *out, cudaStream_t s);
 void launch_cgs_update(const double *V, int64_t N, int K, const double *h, double *w,
                        int want_dots, const RedScratch &red, double *out, cudaStream_t s);
+void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const RedScratch &red,
+                     double *out, cudaStream_t s);
+void launch_cgs_update_dots(const double *V, int64_t N, int K, const double *h, double *w,
+                            const RedScratch &red, double *out, cudaStream_t s);
 void launch_givens(int j, int m, double *H, const double *h1, const double *h2,
                    const double *hn2, const double *wn2, double *cs, double *sn, double *g,
                    double *hnorm_out, double *relres_out, double inv_bnorm, cudaStream_t s);
@@ -164,7 +168,8 @@ void launch_members(int64_t n, const int32_t *agg, int64_t n_agg, DBuf<int64_t> 
                     DBuf<int32_t> &midx, cudaStream_t s);
 void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int64_t *mptr,
                      const int32_t *midx, Csr &C, cudaStream_t s);
-double launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, cudaStream_t s);
+void launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, unsigned long long *lam_bits,
+                            cudaStream_t s);
 int launch_dense_inverse(const Csr &A, DBuf<double> &inv, cudaStream_t s);
 int launch_colour(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
                   uint32_t seed, int32_t *colour, cudaStream_t s);
@@ -180,7 +185,7 @@ void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow,
                               const int64_t *pos, const int64_t *ftptr, const int32_t *ftcol,
                               const uint8_t *ftlow, double *fell, double *ftval, int64_t q0, int64_t q1,
-                              int *err, cudaStream_t s);
+                              int64_t q2, int *err, cudaStream_t s);
 
 // ------------------------------------------------------------- k_adjoint
 void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double alpha, double beta,

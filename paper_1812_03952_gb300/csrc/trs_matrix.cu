@@ -153,7 +153,7 @@ void upload_values(trs_bsr *A, const double *values, bool on_device, cudaStream_
     launch_scatter_values(A->nnzb, bb, A->map.p, values, A->g.nc, A->ell.p, A->tval.p, s);
   } else {
     DBuf<double> stage(std::max<int64_t>(cnt, 1));
-    stage.upload(values, cnt, s);
+    TRS_CUDA(cudaMemcpyAsync(stage.p, values, cnt * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_scatter_values(A->nnzb, bb, A->map.p, stage.p, A->g.nc, A->ell.p, A->tval.p, s);
     TRS_CUDA(cudaStreamSynchronize(s));
   }
@@ -338,6 +338,8 @@ trs_status trs_bsr_spmv(const trs_bsr *A, double alpha, const double *x, double 
   return guarded([&] {
     TRS_REQUIRE(A && x && y, TRS_ERR_INVALID, "NULL argument");
     TRS_REQUIRE(x != y, TRS_ERR_INVALID, "x and y must not alias");
+    require_aligned(x, "x");
+    require_aligned(y, "y");
     if (transpose) launch_spmv_t(A->b, *A, x, y, alpha, beta, (cudaStream_t)stream);
     else launch_spmv<double, double>(A->b, A->view(), x, y, alpha, beta, (cudaStream_t)stream);
   });
@@ -363,12 +365,22 @@ trs_status trs_bsr_transpose(const trs_bsr *A, void *stream, trs_bsr **out) {
     auto T = std::make_unique<trs_bsr>();
     const int32_t grid[3] = {A->g.nx, A->g.ny, A->g.nz};
     build_layout(T.get(), n, A->b, rp.data(), col.data(), A->structured ? grid : nullptr, s);
-    DBuf<int64_t> dsrc(src.size());
-    dsrc.upload(src.data(), nnzb, s);
-    launch_transpose_values(A->b * A->b, nnzb, dsrc.p, A->map.p, A->ell.p, A->tval.p, A->g.nc, T->map.p,
+    T->tsrc.alloc(src.size());
+    T->tsrc.upload(src.data(), nnzb, s);
+    launch_transpose_values(A->b * A->b, nnzb, T->tsrc.p, A->map.p, A->ell.p, A->tval.p, A->g.nc, T->map.p,
                             T->ell.p, T->tval.p, A->b, s);
     TRS_CUDA(cudaStreamSynchronize(s));
     *out = T.release();
+  });
+}
+
+trs_status trs_bsr_transpose_values(const trs_bsr *A, trs_bsr *AT, void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(A && AT, TRS_ERR_INVALID, "NULL argument");
+    TRS_REQUIRE(AT->tsrc.p && AT->n == A->n && AT->b == A->b && AT->nnzb == A->nnzb && AT->g.nc == A->g.nc,
+                TRS_ERR_INVALID, "AT was not made by trs_bsr_transpose of a matrix with A's pattern");
+    launch_transpose_values(A->b * A->b, A->nnzb, AT->tsrc.p, A->map.p, A->ell.p, A->tval.p, A->g.nc, AT->map.p,
+                            AT->ell.p, AT->tval.p, A->b, (cudaStream_t)stream);
   });
 }
 

@@ -34,7 +34,7 @@ TRS_FP32_PREC = 1
 EXPORTS = (
     "trs_bsr_create", "trs_bsr_create_synthetic", "trs_bsr_assemble", "trs_bsr_update_values",
     "trs_bsr_get_values", "trs_bsr_scale_diagonal", "trs_bsr_pattern", "trs_bsr_get_info",
-    "trs_bsr_spmv", "trs_bsr_transpose", "trs_bsr_destroy", "trs_cpr_default_opts", "trs_cpr_setup",
+    "trs_bsr_spmv", "trs_bsr_transpose", "trs_bsr_transpose_values", "trs_bsr_destroy", "trs_cpr_default_opts", "trs_cpr_setup",
     "trs_cpr_update", "trs_cpr_apply", "trs_cpr_get_info", "trs_cpr_get_aggregates",
     "trs_cpr_get_colours", "trs_cpr_get_decoupled", "trs_cpr_get_level", "trs_cpr_vcycle",
     "trs_cpr_destroy", "trs_solve_default_opts", "trs_fgmres_solve", "trs_fgmres_solve_host",
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "trs_bsr_get_info": (i32, [vp, C.POINTER(BsrInfo)]),
         "trs_bsr_spmv": (i32, [vp, f64, vp, f64, vp, i32, vp]),
         "trs_bsr_transpose": (i32, [vp, vp, C.POINTER(vp)]),
+        "trs_bsr_transpose_values": (i32, [vp, vp, vp]),
         "trs_bsr_destroy": (None, [vp]),
         "trs_cpr_default_opts": (None, [C.POINTER(CprOpts)]),
         "trs_cpr_setup": (i32, [vp, C.POINTER(CprOpts), vp, C.POINTER(vp)]),
@@ -240,7 +241,11 @@ class Matrix:
         _check(load().trs_bsr_spmv(self.h, alpha, _dptr(x), beta, _dptr(y), int(transpose), _stream()))
         return y
 
-    def transpose(self):
+    def transpose(self, into=None):
+        """A^T as a new matrix, or refreshed in place into an earlier transpose."""
+        if into is not None:
+            _check(load().trs_bsr_transpose_values(self.h, into.h, _stream()))
+            return into
         out = C.c_void_p()
         _check(load().trs_bsr_transpose(self.h, _stream(), C.byref(out)))
         return Matrix(out)

@@ -132,13 +132,16 @@ def test_setup_bit_exact(trs, oracle, synth, case):
 
 
 # ------------------------------------------------------------ applications
+@pytest.mark.parametrize("coarse_max", [40, 400], ids=["smem-coarsest", "multiblock-coarsest"])
 @pytest.mark.parametrize("case", CASES, ids=_case_id)
-def test_vcycle_and_cpr_apply_parity(trs, oracle, synth, case):
+def test_vcycle_and_cpr_apply_parity(trs, oracle, synth, case, coarse_max):
+    """One V-cycle and one CPR application against the oracle; coarse_max 400
+    leaves a coarsest level above 64 rows (multi-launch Gauss-Jordan inverse)."""
     s = _sys(synth, **case)
     ds = _gpu_system(trs, s)
     Ao = oracle.assemble(s)
-    M = trs.CPR(ds.A, coarse_max=40)
-    Mo = oracle.CPR(Ao, coarse_max=40)
+    M = trs.CPR(ds.A, coarse_max=coarse_max)
+    Mo = oracle.CPR(Ao, coarse_max=coarse_max)
     rng = np.random.default_rng(2)
     r = rng.standard_normal(Ao.n)
     e = M.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
