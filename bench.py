@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--sequence", type=int, default=0,
-                   help="time a sequence of this many Newton-like systems (diagonal blocks rescaled by "
+                   help="time a sequence of this many Newton-like systems (accumulation blocks rescaled by "
                         "seeded +-20%% factors, AMG hierarchy rebuilt every --reuse steps, forward and adjoint "
                         "solve per system) instead of single solves")
     p.add_argument("--reuse", type=int, default=5)
@@ -137,11 +137,14 @@ def dist_setup(n_gpus):
 
 
 def barrier_max(value, world):
+    """Maximum of a per-rank value over all ranks (the step time of the
+    slowest replica)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -207,7 +210,7 @@ def run_reference(args):
 # ------------------------------------------------------ Newton-like sequence
 def run_sequence(args):
     """Total device time of a sequence of Newton-like systems: per system,
-    assembly, diagonal rescaling, CPR refresh (full rebuild every
+    accumulation blocks rescaled by seeded (1 + 0.2 u) factors, assembly, CPR refresh (full rebuild every
     args.reuse systems, AMG reused otherwise), forward solve, transpose,
     CPR on A^T (same reuse), adjoint solve and the dL/dtheta chain."""
     import torch
@@ -221,7 +224,11 @@ def run_sequence(args):
     stream = torch.cuda.current_stream()
     sysm = make_workload(args.workload)
     ds = trs.DeviceSystem(sysm, dev)
-    scales = torch.from_numpy(S.diagonal_scalings(sysm.n_rows, args.sequence, S.SEED_BASE + 99)).to(dev)
+    # per-system factors (1 + 0.2 u) on each cell's accumulation block: the
+    # part of the diagonal block a Newton update of the state changes
+    scales = torch.from_numpy(S.diagonal_scalings(sysm.n_cells, args.sequence, S.SEED_BASE + 99)).to(dev)
+    acc0 = ds.acc.clone()
+    bb = sysm.b * sysm.b
     g = torch.zeros(sysm.n_unknowns, dtype=torch.float64, device=dev)
     g[torch.from_numpy(np.unique(sysm.perf_cell).astype(np.int64) * sysm.b).to(dev)] = 1.0
     A = ds.assemble()
@@ -233,8 +240,8 @@ def run_sequence(args):
 
     def run_all(record):
         for k in range(args.sequence):
+            torch.mul(acc0.view(-1, bb), scales[k].view(-1, 1), out=ds.acc.view(-1, bb))
             ds.assemble()
-            A.scale_diagonal(scales[k].contiguous())
             reuse = (k % args.reuse) != 0
             M.update(A, reuse_amg=reuse)
             _, rf = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)

@@ -228,20 +228,20 @@ __global__ void k_scale_diag(Geom g, double *ell, double *tval, const int64_t *t
 // Methods"): pivot = first row of largest |a| in the column at or below the
 // diagonal; pivot row divided by the pivot; its multiple a(r,c) subtracted
 // from every other row.
-template <int B>
-__device__ bool gj_inverse(const double (&D)[B * B], double (&inv)[B * B]) {
-  double a[B * B];
+template <int B, class T = double>
+__device__ bool gj_inverse(const T (&D)[B * B], T (&inv)[B * B]) {
+  T a[B * B];
 #pragma unroll
-  for (int e = 0; e < B * B; e++) { a[e] = D[e]; inv[e] = 0.0; }
+  for (int e = 0; e < B * B; e++) { a[e] = D[e]; inv[e] = T(0); }
 #pragma unroll
-  for (int r = 0; r < B; r++) inv[r * B + r] = 1.0;
+  for (int r = 0; r < B; r++) inv[r * B + r] = T(1);
 #pragma unroll
   for (int c = 0; c < B; c++) {
     int p = c;
-    double best = fabs(a[c * B + c]);
+    T best = fabs(a[c * B + c]);
 #pragma unroll
     for (int r = c + 1; r < B; r++) {
-      const double v = fabs(a[r * B + c]);
+      const T v = fabs(a[r * B + c]);
       if (v > best) { best = v; p = r; }
     }
     if (best == 0.0 || !isfinite(best)) return false;
@@ -250,12 +250,12 @@ __device__ bool gj_inverse(const double (&D)[B * B], double (&inv)[B * B]) {
       if (r == p) {
 #pragma unroll
         for (int s = 0; s < B; s++) {
-          double t = a[c * B + s]; a[c * B + s] = a[r * B + s]; a[r * B + s] = t;
+          T t = a[c * B + s]; a[c * B + s] = a[r * B + s]; a[r * B + s] = t;
           t = inv[c * B + s]; inv[c * B + s] = inv[r * B + s]; inv[r * B + s] = t;
         }
       }
     }
-    const double piv = a[c * B + c];
+    const T piv = a[c * B + c];
 #pragma unroll
     for (int s = 0; s < B; s++) {
       a[c * B + s] = a[c * B + s] / piv;
@@ -264,7 +264,7 @@ __device__ bool gj_inverse(const double (&D)[B * B], double (&inv)[B * B]) {
 #pragma unroll
     for (int r = 0; r < B; r++) {
       if (r == c) continue;
-      const double f = a[r * B + c];
+      const T f = a[r * B + c];
 #pragma unroll
       for (int s = 0; s < B; s++) {
         a[r * B + s] = a[r * B + s] - f * a[c * B + s];
@@ -276,13 +276,13 @@ __device__ bool gj_inverse(const double (&D)[B * B], double (&inv)[B * B]) {
 }
 
 // C = A * Bm (b x b), inner index ascending, first product then running sums
-template <int B>
-__device__ __forceinline__ void bmul(const double (&A)[B * B], const double (&Bm)[B * B], double (&C)[B * B]) {
+template <int B, class T = double>
+__device__ __forceinline__ void bmul(const T (&A)[B * B], const T (&Bm)[B * B], T (&C)[B * B]) {
 #pragma unroll
   for (int r = 0; r < B; r++)
 #pragma unroll
     for (int s = 0; s < B; s++) {
-      double acc = A[r * B] * Bm[s];
+      T acc = A[r * B] * Bm[s];
 #pragma unroll
       for (int t = 1; t < B; t++) acc = acc + A[r * B + t] * Bm[t * B + s];
       C[r * B + s] = acc;
@@ -343,6 +343,80 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_e
 #pragma unroll
     for (int e = 0; e < BB; e++) at_tval[t * BB + e] = out[e];
     ap_tval[t] = out[0];
+  }
+}
+
+// The same decoupling for the FP32 preconditioner: D_i^-1 and the pressure
+// entries (Ã_ij)_00 are formed in FP64 exactly as above (they decide the
+// aggregates); the blocks Ã_ij = D_i^-1 A_ij and D_i^-1 are stored in FP32,
+// the product taken in FP32.
+template <int B>
+__global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, float *at_ell, float *at_tval,
+                                 float *dinv, double *ap_ell, double *ap_tval, int *err) {
+  constexpr int BB = B * B;
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t nc = A.g.nc, n = A.g.n_rows;
+  if (i >= n) return;
+  double D[BB], Di[BB];
+  float Df[BB], bf[BB], of[BB];
+  const bool cell = i < nc;
+  const int64_t dtail = cell ? -1 : tdiag[i - nc];
+  if (cell) {
+#pragma unroll
+    for (int e = 0; e < BB; e++) D[e] = A.ell[((int64_t)kSelf * BB + e) * nc + i];
+  } else {
+#pragma unroll
+    for (int e = 0; e < BB; e++) D[e] = A.tval[dtail * BB + e];
+  }
+  if (!gj_inverse<B>(D, Di)) {
+    atomicExch(err, 1);
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) {
+    Df[e] = (float)Di[e];
+    dinv[(int64_t)e * n + i] = Df[e];
+  }
+  // (D^-1 A)_00: first product then running sum over the inner index
+  auto p00 = [&](const double *blk, int64_t stride) {
+    double acc = Di[0] * blk[0];
+#pragma unroll
+    for (int t = 1; t < B; t++) acc = acc + Di[t] * blk[(int64_t)(t * B) * stride];
+    return acc;
+  };
+  if (cell) {
+    const unsigned m = A.emask[i];
+    for (int s = 0; s < kSlots; s++) {
+      if (!((m >> s) & 1u)) continue;
+      if (s == kSelf) {
+#pragma unroll
+        for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = (e % (B + 1) == 0) ? 1.f : 0.f;
+        ap_ell[(int64_t)s * nc + i] = 1.0;
+        continue;
+      }
+      const double *blk = A.ell + ((int64_t)s * BB) * nc + i;
+      ap_ell[(int64_t)s * nc + i] = p00(blk, nc);
+#pragma unroll
+      for (int e = 0; e < BB; e++) bf[e] = (float)blk[(int64_t)e * nc];
+      bmul<B, float>(Df, bf, of);
+#pragma unroll
+      for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = of[e];
+    }
+  }
+  for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
+    if (t == dtail) {
+#pragma unroll
+      for (int e = 0; e < BB; e++) at_tval[t * BB + e] = (e % (B + 1) == 0) ? 1.f : 0.f;
+      ap_tval[t] = 1.0;
+      continue;
+    }
+    const double *blk = A.tval + t * BB;
+    ap_tval[t] = p00(blk, 1);
+#pragma unroll
+    for (int e = 0; e < BB; e++) bf[e] = (float)blk[e];
+    bmul<B, float>(Df, bf, of);
+#pragma unroll
+    for (int e = 0; e < BB; e++) at_tval[t * BB + e] = of[e];
   }
 }
 
@@ -1043,10 +1117,10 @@ __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol
   }
 }
 
-template <int B>
-__global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const double *at_ell,
-                           const double *at_tval, const int64_t *ftsrc, int64_t nft, double *fell,
-                           double *ftval) {
+template <int B, class T>
+__global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
+                           const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell,
+                           T *ftval) {
   constexpr int BB = B * B;
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t np = g.n_rows;
@@ -1056,8 +1130,8 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
     for (int s = 0; s < kSlots; s++) {
 #pragma unroll
       for (int e = 0; e < BB; e++) {
-        double v = 0.0;
-        if (s == kSelf) v = (e % (B + 1) == 0) ? 1.0 : 0.0;
+        T v = T(0);
+        if (s == kSelf) v = (e % (B + 1) == 0) ? T(1) : T(0);
         else if ((m >> s) & 1u) v = at_ell[((int64_t)s * BB + e) * g.nc + i];
         fell[((int64_t)s * BB + e) * np + q] = v;
       }
@@ -1070,26 +1144,27 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
 }
 
 // Reference to one stored block of the factor: base pointer and stride.
+template <class T>
 struct BRef {
-  double *p;
+  T *p;
   int64_t stride;
 };
 
-template <int B>
-__device__ __forceinline__ void bload(BRef r, double (&v)[B * B]) {
+template <int B, class T>
+__device__ __forceinline__ void bload(BRef<T> r, T (&v)[B * B]) {
 #pragma unroll
   for (int e = 0; e < B * B; e++) v[e] = r.p[e * r.stride];
 }
-template <int B>
-__device__ __forceinline__ void bstore(BRef r, const double (&v)[B * B]) {
+template <int B, class T>
+__device__ __forceinline__ void bstore(BRef<T> r, const T (&v)[B * B]) {
 #pragma unroll
   for (int e = 0; e < B * B; e++) r.p[e * r.stride] = v[e];
 }
 
 // entry k of row i (k != i) in factor storage, or p = nullptr
-template <int B>
-__device__ BRef ilu_find(const Geom &g, const uint8_t *emask, const int64_t *pos, const int64_t *ftptr,
-                         const int32_t *ftcol, double *fell, double *ftval, int64_t i, int64_t k) {
+template <int B, class T>
+__device__ BRef<T> ilu_find(const Geom &g, const uint8_t *emask, const int64_t *pos, const int64_t *ftptr,
+                         const int32_t *ftcol, T *fell, T *ftval, int64_t i, int64_t k) {
   constexpr int BB = B * B;
   const int64_t qi = pos[i], np = g.n_rows;
   if (i < g.nc && k < g.nc) {
@@ -1097,26 +1172,26 @@ __device__ BRef ilu_find(const Geom &g, const uint8_t *emask, const int64_t *pos
     const unsigned m = emask[i];
     for (int s = 0; s < kSlots; s++)
       if (s != kSelf && ((m >> s) & 1u) && g.off[s] == d)
-        return BRef{fell + ((int64_t)s * BB) * np + qi, np};
+        return BRef<T>{fell + ((int64_t)s * BB) * np + qi, np};
   }
   int64_t lo = ftptr[qi], hi = ftptr[qi + 1] - 1;
   while (lo <= hi) {
     const int64_t mid = lo + (hi - lo) / 2;
     const int64_t c = ftcol[mid];
-    if (c == k) return BRef{ftval + mid * BB, 1};
+    if (c == k) return BRef<T>{ftval + mid * BB, 1};
     if (c < k) lo = mid + 1; else hi = mid - 1;
   }
-  return BRef{nullptr, 0};
+  return BRef<T>{nullptr, 0};
 }
 
 // IKJ ILU(0) of the rows at positions [q0, q1) (one colour): for every
 // earlier-ordered k of row i in ascending order, L_ik = W_ik U_kk^-1 and
 // W_ij -= L_ik U_kj for later-ordered j of row i with (k, j) stored; then
 // U_ii^-1 replaces W_ii in slot 3.
-template <int B>
+template <int B, class T>
 __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
-                             const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, double *fell,
-                             double *ftval, int64_t q0, int64_t q1, int *err) {
+                             const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, T *fell,
+                             T *ftval, int64_t q0, int64_t q1, int *err) {
   constexpr int BB = B * B;
   const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (q >= q1) return;
@@ -1130,9 +1205,9 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
     if (k < kSlots) return ((m >> k) & 1u) ? i + g.off[k] : -1;
     return ftcol[u0 + (k - kSlots)];
   };
-  auto ent_ref = [&](int k) -> BRef {
-    if (k < kSlots) return BRef{fell + ((int64_t)k * BB) * np + q, np};
-    return BRef{ftval + (u0 + (k - kSlots)) * BB, 1};
+  auto ent_ref = [&](int k) -> BRef<T> {
+    if (k < kSlots) return BRef<T>{fell + ((int64_t)k * BB) * np + q, np};
+    return BRef<T>{ftval + (u0 + (k - kSlots)) * BB, 1};
   };
   int64_t cur = -1;
   for (;;) {
@@ -1148,41 +1223,41 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
     if (kbest < 0) break;
     cur = pbest;
     const int64_t kr = ent_col(kbest);
-    double W[BB], Uinv[BB], L[BB];
-    bload<B>(ent_ref(kbest), W);
-    bload<B>(BRef{fell + ((int64_t)kSelf * BB) * np + pbest, np}, Uinv);
-    bmul<B>(W, Uinv, L);
-    bstore<B>(ent_ref(kbest), L);
+    T W[BB], Uinv[BB], L[BB];
+    bload<B, T>(ent_ref(kbest), W);
+    bload<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + pbest, np}, Uinv);
+    bmul<B, T>(W, Uinv, L);
+    bstore<B, T>(ent_ref(kbest), L);
     for (int k = 0; k < n_ent; k++) {
       const int64_t j = ent_col(k);
       if (j < 0 || pos[j] <= pbest) continue;
-      BRef ukj;
+      BRef<T> ukj;
       if (j == kr) continue;
-      ukj = ilu_find<B>(g, emask, pos, ftptr, ftcol, fell, ftval, kr, j);
+      ukj = ilu_find<B, T>(g, emask, pos, ftptr, ftcol, fell, ftval, kr, j);
       if (!ukj.p) continue;
-      double U[BB], P[BB], Wij[BB];
-      bload<B>(ukj, U);
-      bmul<B>(L, U, P);
-      BRef wr = (j == i && cell) ? BRef{fell + ((int64_t)kSelf * BB) * np + q, np} : ent_ref(k);
-      bload<B>(wr, Wij);
+      T U[BB], P[BB], Wij[BB];
+      bload<B, T>(ukj, U);
+      bmul<B, T>(L, U, P);
+      BRef<T> wr = (j == i && cell) ? BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np} : ent_ref(k);
+      bload<B, T>(wr, Wij);
 #pragma unroll
       for (int e = 0; e < BB; e++) Wij[e] = Wij[e] - P[e];
-      bstore<B>(wr, Wij);
+      bstore<B, T>(wr, Wij);
     }
   }
   // diagonal: slot 3 for cells, the tail entry for other rows
-  double Wd[BB], inv[BB];
-  BRef dref{fell + ((int64_t)kSelf * BB) * np + q, np};
+  T Wd[BB], inv[BB];
+  BRef<T> dref{fell + ((int64_t)kSelf * BB) * np + q, np};
   if (!cell) {
     for (int k = kSlots; k < n_ent; k++)
       if (ent_col(k) == i) { dref = ent_ref(k); break; }
   }
-  bload<B>(dref, Wd);
-  if (!gj_inverse<B>(Wd, inv)) {
+  bload<B, T>(dref, Wd);
+  if (!gj_inverse<B, T>(Wd, inv)) {
     atomicExch(err, 1);
     return;
   }
-  bstore<B>(BRef{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
 }
 
 // The same factorisation for rows held entirely in the tail (wells, general
@@ -1190,10 +1265,10 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
 // minimum over the row's entries, L_ik = W_ik U_kk^-1 is formed, and the
 // entries (k, j) of row k, later-ordered than k, are matched by binary
 // search in row i and update W_ij, each lane one entry of row k.
-template <int B>
+template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint8_t *emask, const int32_t *crow,
                                                               const int64_t *pos, const int64_t *ftptr,
-                                                              const int32_t *ftcol, double *fell, double *ftval,
+                                                              const int32_t *ftcol, T *fell, T *ftval,
                                                               int64_t q1, int64_t q2, int *err) {
   constexpr int BB = B * B;
   const int lane = threadIdx.x & 31;
@@ -1233,46 +1308,76 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
     if (ub < 0) break;
     cur = pb;
     const int64_t kr = col_at(ub);
-    double W[BB], Uinv[BB], L[BB];
-    bload<B>(BRef{ftval + ub * BB, 1}, W);
-    bload<B>(BRef{fell + ((int64_t)kSelf * BB) * np + pb, np}, Uinv);
-    bmul<B>(W, Uinv, L);
-    __syncwarp();
-    if (lane == 0) bstore<B>(BRef{ftval + ub * BB, 1}, L);
+    // L = W_ik U_kk^-1, one entry per lane (first product, then running sum)
+    __shared__ T s_L[kWarps][BB];
+    __shared__ int64_t s_dst[kWarps][32];
+    __shared__ int64_t s_src[kWarps][32];
+    __shared__ int64_t s_srcs[kWarps][32];
     const int64_t ku0 = ftptr[pb], ku1 = ftptr[pb + 1];
-    const int nk = kSlots + (int)(ku1 - ku0);
-    const unsigned mk = kr < g.nc ? emask[kr] : 0u;
-    for (int e = lane; e < nk; e += 32) {
-      int64_t j;
-      BRef ukj;
-      if (e < kSlots) {
-        if (e == kSelf || !((mk >> e) & 1u)) continue;
-        j = kr + g.off[e];
-        ukj = BRef{fell + ((int64_t)e * BB) * np + pb, np};
-      } else {
-        const int64_t uk = ku0 + (e - kSlots);
-        j = ftcol[uk];
-        if (j == kr) continue;
-        ukj = BRef{ftval + uk * BB, 1};
-      }
-      if (pos[j] <= pb) continue;
-      int64_t lo = u0, hi = u1 - 1, found = -1;
-      while (lo <= hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        const int64_t c = col_at(mid);
-        if (c == j) { found = mid; break; }
-        if (c < j) lo = mid + 1; else hi = mid - 1;
-      }
-      if (found < 0) continue;
-      double U[BB], P[BB], Wij[BB];
-      bload<B>(ukj, U);
-      bmul<B>(L, U, P);
-      bload<B>(BRef{ftval + found * BB, 1}, Wij);
+    if (lane < BB) {
+      const int r = lane / B, c = lane % B;
+      const T *W = ftval + ub * BB;
+      const T *U = fell + ((int64_t)kSelf * BB) * np + pb;
+      T acc = W[r * B] * U[(int64_t)c * np];
 #pragma unroll
-      for (int x = 0; x < BB; x++) Wij[x] = Wij[x] - P[x];
-      bstore<B>(BRef{ftval + found * BB, 1}, Wij);
+      for (int t = 1; t < B; t++) acc = acc + W[r * B + t] * U[(int64_t)(t * B + c) * np];
+      s_L[wid][lane] = acc;
     }
     __syncwarp();
+    if (lane < BB) ftval[ub * BB + lane] = s_L[wid][lane];
+    // entries (k, j) of row k later than k with j stored in row i: lane e
+    // resolves entry e of row k (slots first, then the tail)
+    const int nk = kSlots + (int)(ku1 - ku0);
+    const unsigned mk = kr < g.nc ? emask[kr] : 0u;
+    for (int e0 = 0; e0 < nk; e0 += 32) {
+      const int e = e0 + lane;
+      int64_t dst = -1, src = 0, srcs = 1;
+      if (e < nk) {
+        int64_t j = -1;
+        if (e < kSlots) {
+          if (e != kSelf && ((mk >> e) & 1u)) {
+            j = kr + g.off[e];
+            src = ((int64_t)e * BB) * np + pb;  // into fell
+            srcs = -np;                          // negative stride marks fell
+          }
+        } else {
+          const int64_t uk = ku0 + (e - kSlots);
+          j = ftcol[uk];
+          if (j == kr) j = -1;
+          src = uk * BB;
+        }
+        if (j >= 0 && pos[j] > pb) {
+          int64_t lo = u0, hi = u1 - 1;
+          while (lo <= hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            const int64_t c = col_at(mid);
+            if (c == j) { dst = mid; break; }
+            if (c < j) lo = mid + 1; else hi = mid - 1;
+          }
+        }
+      }
+      s_dst[wid][lane] = dst;
+      s_src[wid][lane] = src;
+      s_srcs[wid][lane] = srcs;
+      __syncwarp();
+      const int cnt = min(32, nk - e0);
+      // W_ij -= L U_kj, one (entry, element) pair per lane
+      for (int task = lane; task < cnt * BB; task += 32) {
+        const int ent = task / BB, el = task % BB;
+        const int64_t d = s_dst[wid][ent];
+        if (d < 0) continue;
+        const int r = el / B, c = el % B;
+        const int64_t sb = s_src[wid][ent], ss = s_srcs[wid][ent];
+        const T *U = ss < 0 ? fell + sb : ftval + sb;
+        const int64_t st = ss < 0 ? np : 1;
+        T acc = s_L[wid][r * B] * U[(int64_t)c * st];
+#pragma unroll
+        for (int t = 1; t < B; t++) acc = acc + s_L[wid][r * B + t] * U[(int64_t)(t * B + c) * st];
+        T *Wp = ftval + d * BB + el;
+        *Wp = *Wp - acc;
+      }
+      __syncwarp();
+    }
   }
   if (lane != 0) return;
   int64_t lo = u0, hi = u1 - 1, dg = -1;
@@ -1282,14 +1387,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
     if (c == i) { dg = mid; break; }
     if (c < i) lo = mid + 1; else hi = mid - 1;
   }
-  double Wd[BB], inv[BB];
+  T Wd[BB], inv[BB];
   if (dg < 0) { atomicExch(err, 1); return; }
-  bload<B>(BRef{ftval + dg * BB, 1}, Wd);
-  if (!gj_inverse<B>(Wd, inv)) {
+  bload<B, T>(BRef<T>{ftval + dg * BB, 1}, Wd);
+  if (!gj_inverse<B, T>(Wd, inv)) {
     atomicExch(err, 1);
     return;
   }
-  bstore<B>(BRef{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
 }
 
 }  // namespace
@@ -1356,6 +1461,14 @@ void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, doub
   if (!A.g.n_rows) return;
   TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, at_ell, at_tval, dinv,
                                                                            ap_ell, ap_tval, err));
+  TRS_LAUNCHED();
+}
+
+void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, float *at_ell, float *at_tval,
+                           float *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
+  if (!A.g.n_rows) return;
+  TRS_DISPATCH_B(b, k_decouple_mixed<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, at_ell, at_tval, dinv,
+                                                                                 ap_ell, ap_tval, err));
   TRS_LAUNCHED();
 }
 
@@ -1595,30 +1708,41 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
   TRS_LAUNCHED();
 }
 
-void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const double *at_ell,
-                     const double *at_tval, const int64_t *ftsrc, int64_t nft, double *fell, double *ftval,
-                     cudaStream_t s) {
+template <class T>
+void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
+                     const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell, T *ftval, cudaStream_t s) {
   const int64_t n = std::max<int64_t>(g.n_rows, nft);
-  TRS_DISPATCH_B(b, k_ilu_init<B><<<grid_of(n), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc, nft,
-                                                                  fell, ftval));
+  TRS_DISPATCH_B(b, k_ilu_init<B, T><<<grid_of(n), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc, nft,
+                                                                     fell, ftval));
   TRS_LAUNCHED();
 }
+template void launch_ilu_init<double>(int, const Geom &, const uint8_t *, const int32_t *, const double *,
+                                      const double *, const int64_t *, int64_t, double *, double *, cudaStream_t);
+template void launch_ilu_init<float>(int, const Geom &, const uint8_t *, const int32_t *, const float *,
+                                     const float *, const int64_t *, int64_t, float *, float *, cudaStream_t);
 
+template <class T>
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
-                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, double *fell,
-                              double *ftval, int64_t q0, int64_t q1, int64_t q2, int *err, cudaStream_t s) {
+                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, T *fell, T *ftval,
+                              int64_t q0, int64_t q1, int64_t q2, int *err, cudaStream_t s) {
   if (q1 > q0) {
-    TRS_DISPATCH_B(b, k_ilu_factor<B><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
-                                                                            ftlow, fell, ftval, q0, q1, err));
+    TRS_DISPATCH_B(b, k_ilu_factor<B, T><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
+                                                                               ftlow, fell, ftval, q0, q1, err));
     TRS_LAUNCHED();
   }
   if (q2 > q1) {
     const unsigned grid = (unsigned)((q2 - q1 + kWarps - 1) / kWarps);
-    TRS_DISPATCH_B(b, k_ilu_factor_long<B><<<grid, kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol, fell,
-                                                                     ftval, q1, q2, err));
+    TRS_DISPATCH_B(b, k_ilu_factor_long<B, T><<<grid, kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol, fell,
+                                                                        ftval, q1, q2, err));
     TRS_LAUNCHED();
   }
 }
+template void launch_ilu_factor_colour<double>(int, const Geom &, const uint8_t *, const int32_t *, const int64_t *,
+                                               const int64_t *, const int32_t *, const uint8_t *, double *,
+                                               double *, int64_t, int64_t, int64_t, int *, cudaStream_t);
+template void launch_ilu_factor_colour<float>(int, const Geom &, const uint8_t *, const int32_t *, const int64_t *,
+                                              const int64_t *, const int32_t *, const uint8_t *, float *, float *,
+                                              int64_t, int64_t, int64_t, int *, cudaStream_t);
 
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s) {
   if (!A->n) return;

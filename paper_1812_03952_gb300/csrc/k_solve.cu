@@ -313,10 +313,10 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
   }
 }
 
-template <int B, class T>
+template <int B, class T, class TZ>
 __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_t q0, int64_t q1, int64_t q2,
                                                       int64_t cell_blocks, const T *__restrict__ y1,
-                                                      const T *__restrict__ e0, T *__restrict__ zout) {
+                                                      const T *__restrict__ e0, TZ *__restrict__ zout) {
   constexpr int BB = B * B;
   const int64_t np = F.g.n_rows;
   T t[B];
@@ -386,9 +386,10 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     T zb[B];
     load_blk<B>(y1 + i * B, zb);
     zb[0] = zb[0] + e0[i];
+    TZ zo[B];
 #pragma unroll
-    for (int r = 0; r < B; r++) zb[r] = zb[r] + xv[r];
-    store_blk<B>(zout + i * B, zb);
+    for (int r = 0; r < B; r++) zo[r] = static_cast<TZ>(zb[r] + xv[r]);
+    store_blk<B>(zout + i * B, zo);
   }
 }
 
@@ -607,6 +608,91 @@ __global__ void k_dense_gemv(int64_t n, const double *__restrict__ Minv, const T
   for (int64_t j = lane; j < n; j += 32) acc = fma(Minv[i * n + j], to_d(r[j]), acc);
   acc = warp_sum(acc);
   if (lane == 0) e[i] = static_cast<T>(acc);
+}
+
+// The V-cycle from level h.l0 down, by one block of 1024 threads: the same
+// Chebyshev, residual, restriction, coarsest solve and prolongation steps as
+// the per-level kernels above (identical arithmetic), separated by block
+// barriers instead of launches.
+template <class T>
+__device__ __forceinline__ T csr_rowdot(const CoarseLevel<T> &L, int64_t i, const T *x) {
+  T acc = T(0);
+  for (int64_t p = L.rp[i]; p < L.rp[i + 1]; p++) acc = fma(L.val[p], x[L.col[p]], acc);
+  return acc;
+}
+
+template <class T>
+__device__ void coarse_cheb(const CoarseLevel<T> &L, int deg, bool zero_init) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const T *r = L.r;
+  T *e = L.e, *res = L.res, *d = L.d, *dn = L.dn;
+  if (zero_init) {
+    for (int64_t i = tid; i < L.n; i += nt) {
+      d[i] = (L.dinv[i] * r[i]) * L.inv_theta;
+      e[i] = T(0);
+    }
+  } else {
+    for (int64_t i = tid; i < L.n; i += nt) {
+      const T v = r[i] - csr_rowdot(L, i, e);
+      res[i] = v;
+      d[i] = (L.dinv[i] * v) * L.inv_theta;
+    }
+  }
+  __syncthreads();
+  const T *res_in = zero_init ? r : res;
+  for (int k = 1; k < deg; k++) {
+    const int last = (k == deg - 1);
+    for (int64_t i = tid; i < L.n; i += nt) {
+      const T rv = res_in[i] - csr_rowdot(L, i, d);
+      res[i] = rv;
+      const T di = d[i];
+      const T nv = fma(L.c1[k], di, L.c2[k] * (L.dinv[i] * rv));
+      const T ev = e[i] + di;
+      if (last) e[i] = ev + nv;
+      else { e[i] = ev; dn[i] = nv; }
+    }
+    __syncthreads();
+    res_in = res;
+    T *t = d; d = dn; dn = t;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseHierarchy<T> h) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int last = h.nlev - 1;
+  for (int l = h.l0; l < last; l++) {
+    const CoarseLevel<T> &L = h.lv[l];
+    coarse_cheb(L, h.deg, true);
+    for (int64_t i = tid; i < L.n; i += nt) L.res[i] = L.r[i] - csr_rowdot(L, i, L.e);
+    __syncthreads();
+    const CoarseLevel<T> &C = h.lv[l + 1];
+    for (int64_t I = tid; I < C.n; I += nt) {
+      T acc = T(0);
+      for (int64_t t = L.mptr[I]; t < L.mptr[I + 1]; t++) acc = acc + L.res[L.midx[t]];
+      C.r[I] = acc;
+    }
+    __syncthreads();
+  }
+  {
+    const CoarseLevel<T> &C = h.lv[last];
+    for (int64_t i = tid; i < C.n; i += nt) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < C.n; j++) acc = fma(h.cinv[i * C.n + j], to_d(C.r[j]), acc);
+      C.e[i] = static_cast<T>(acc);
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= h.l0; l--) {
+    const CoarseLevel<T> &L = h.lv[l];
+    const CoarseLevel<T> &C = h.lv[l + 1];
+    for (int64_t i = tid; i < L.n; i += nt) {
+      const int32_t a = L.agg[i];
+      if (a >= 0) L.e[i] = L.e[i] + C.e[a];
+    }
+    __syncthreads();
+    coarse_cheb(L, h.deg, false);
+  }
 }
 
 // ------------------------------------------------------- FGMRES / CGS2
@@ -837,13 +923,13 @@ void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, 
   TRS_LAUNCHED();
 }
 
-template <class T>
+template <class T, class TZ>
 void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2, const T *y1,
-                    const T *e0, T *zout, cudaStream_t s) {
+                    const T *e0, TZ *zout, cudaStream_t s) {
   const int64_t cb = cell_blocks_of(q1 - q0), lb = long_blocks_of(q2 - q1);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_ilu_bwd<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0,
-                                                                             zout));
+  TRS_DISPATCH_B(b, k_ilu_bwd<B, T, TZ><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0,
+                                                                                 zout));
   TRS_LAUNCHED();
 }
 
@@ -957,6 +1043,14 @@ void launch_xupdate(const TZ *Z, int64_t N, int K, const double *y, double *x, c
   k_xupdate<TZ><<<grid, kThreads, 0, s>>>(Z, N, K, y, x);
   TRS_LAUNCHED();
 }
+template <class T>
+void launch_vcycle_coarse(const CoarseHierarchy<T> &h, cudaStream_t s) {
+  k_vcycle_coarse<T><<<1, 1024, 0, s>>>(h);
+  TRS_LAUNCHED();
+}
+template void launch_vcycle_coarse<float>(const CoarseHierarchy<float> &, cudaStream_t);
+template void launch_vcycle_coarse<double>(const CoarseHierarchy<double> &, cudaStream_t);
+
 template <class TS, class TD>
 void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
   if (!n) return;
@@ -971,8 +1065,8 @@ void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
                                  cudaStream_t);                                                             \
   template void launch_ilu_fwd<T>(int, const IluView<T> &, const T *, T *, int64_t, int64_t, int64_t,        \
                                   cudaStream_t);                                                            \
-  template void launch_ilu_bwd<T>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,        \
-                                  const T *, T *, cudaStream_t);                                            \
+  template void launch_ilu_bwd<T, double>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,\
+                                          const T *, double *, cudaStream_t);                               \
   template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, T *, cudaStream_t);        \
   template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *,         \
                                      cudaStream_t);                                                         \
@@ -989,6 +1083,8 @@ void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
 
 TRS_INST_T(double)
 TRS_INST_T(float)
+template void launch_ilu_bwd<float, float>(int, const IluView<float> &, float *, int64_t, int64_t, int64_t,
+                                           const float *, const float *, float *, cudaStream_t);
 template void launch_cast<double, float>(const double *, float *, int64_t, cudaStream_t);
 template void launch_cast<float, double>(const float *, double *, int64_t, cudaStream_t);
 template void launch_cast<double, double>(const double *, double *, int64_t, cudaStream_t);

@@ -138,8 +138,13 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   const int64_t n = M->n, nc = M->g.nc;
   TBuf<int> err(1, s);
   err.zero();
-  launch_decouple(b, A->view(), A->tdiag.p, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
-                  M->ap_tval64.p, err.p, s);
+  const bool mixed = M->prec == TRS_FP32_PREC;
+  if (mixed)
+    launch_decouple_mixed(b, A->view(), A->tdiag.p, M->at_ell32.p, M->at_tval32.p, M->dinv32.p, M->ap_ell64.p,
+                          M->ap_tval64.p, err.p, s);
+  else
+    launch_decouple(b, A->view(), A->tdiag.p, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
+                    M->ap_tval64.p, err.p, s);
   if (rebuild_amg) {
     if (M->lev.empty()) M->lev.emplace_back();
     Csr &C0 = M->lev[0].A;
@@ -161,24 +166,28 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
     build_hierarchy(M, s);
     alloc_level_vectors(M);
   }
-  // block ILU(0) on Ã
-  launch_ilu_init(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft, M->fell64.p,
-                  M->ftval64.p, s);
-  for (int c = 0; c < M->ncol; c++)
-    launch_ilu_factor_colour(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
-                             M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], err.p, s);
-  if (M->prec == TRS_FP32_PREC) {
+  // block ILU(0) on Ã, in the preconditioner's precision
+  if (mixed) {
+    launch_ilu_init<float>(b, M->g, M->emask.p, M->crow.p, M->at_ell32.p, M->at_tval32.p, M->ftsrc.p, M->nft,
+                           M->fell32.p, M->ftval32.p, s);
+    for (int c = 0; c < M->ncol; c++)
+      launch_ilu_factor_colour<float>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
+                                      M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], err.p, s);
+  } else {
+    launch_ilu_init<double>(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft,
+                            M->fell64.p, M->ftval64.p, s);
+    for (int c = 0; c < M->ncol; c++)
+      launch_ilu_factor_colour<double>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p,
+                                       M->ftlow.p, M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c],
+                                       M->cptr[c + 1], err.p, s);
+  }
+  if (mixed) {
     auto cast = [&](DBuf<double> &src, DBuf<float> &dst, int64_t cnt) {
       reserve(dst, cnt);
       launch_cast<double, float>(src.p, dst.p, cnt, s);
     };
-    cast(M->at_ell64, M->at_ell32, (int64_t)kSlots * bb * nc);
-    cast(M->at_tval64, M->at_tval32, M->ntail * bb);
-    cast(M->dinv64, M->dinv32, (int64_t)bb * n);
     cast(M->ap_ell64, M->ap_ell32, (int64_t)kSlots * nc);
     cast(M->ap_tval64, M->ap_tval32, M->ntail);
-    cast(M->fell64, M->fell32, (int64_t)kSlots * bb * n);
-    cast(M->ftval64, M->ftval32, M->nft * bb);
     for (int l = 0; l < M->nlev; l++) {
       Level &L = M->lev[l];
       cast(L.dinv64, L.dinv32, L.A.n);
@@ -211,10 +220,17 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   copy_d2d(M->tcol, A->tcol, A->ntail);
   copy_d2d(M->tdiag, A->tdiag, n - nc);
   copy_d2d(M->map, A->map, A->nnzb);
-  M->at_ell64.alloc(std::max<int64_t>((int64_t)kSlots * bb * nc, 1));
-  M->at_ell64.zero(s);
-  M->at_tval64.alloc(std::max<int64_t>(A->ntail * bb, 1));
-  M->dinv64.alloc((size_t)bb * n);
+  if (M->prec == TRS_FP32_PREC) {
+    M->at_ell32.alloc(std::max<int64_t>((int64_t)kSlots * bb * nc, 1));
+    M->at_ell32.zero(s);
+    M->at_tval32.alloc(std::max<int64_t>(A->ntail * bb, 1));
+    M->dinv32.alloc((size_t)bb * n);
+  } else {
+    M->at_ell64.alloc(std::max<int64_t>((int64_t)kSlots * bb * nc, 1));
+    M->at_ell64.zero(s);
+    M->at_tval64.alloc(std::max<int64_t>(A->ntail * bb, 1));
+    M->dinv64.alloc((size_t)bb * n);
+  }
   M->ap_ell64.alloc(std::max<int64_t>((int64_t)kSlots * nc, 1));
   M->ap_ell64.zero(s);
   M->ap_tval64.alloc(std::max<int64_t>(A->ntail, 1));
@@ -236,8 +252,13 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   launch_ilu_structure(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->crow.p, M->pos.p, M->lmask.p, M->ftptr, M->ftcol,
                        M->ftlow, M->ftsrc, s);
   M->nft = M->ntail;
-  M->fell64.alloc((size_t)kSlots * bb * n);
-  M->ftval64.alloc(std::max<int64_t>(M->nft * bb, 1));
+  if (M->prec == TRS_FP32_PREC) {
+    M->fell32.alloc((size_t)kSlots * bb * n);
+    M->ftval32.alloc(std::max<int64_t>(M->nft * bb, 1));
+  } else {
+    M->fell64.alloc((size_t)kSlots * bb * n);
+    M->ftval64.alloc(std::max<int64_t>(M->nft * bb, 1));
+  }
   build_values(M, A, true, s);
   // work vectors
   const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
@@ -336,10 +357,66 @@ void chebyshev(const trs_cpr *M, int l, const T *r, T *e, bool zero_init, cudaSt
   }
 }
 
+// First level handled by the single-block coarse kernel (rows <= 4096 on it
+// and below), or nlev if none.
+int coarse_fuse_level(const trs_cpr *M) {
+  int l0 = M->nlev;
+  while (l0 > 1 && M->lev[l0 - 1].A.n <= kCoarseFuseRows) l0--;
+  return l0;
+}
+
+template <class T>
+CoarseHierarchy<T> coarse_hierarchy(const trs_cpr *M, int l0) {
+  CoarseHierarchy<T> h{};
+  h.l0 = l0;
+  h.nlev = M->nlev;
+  h.deg = M->opts.cheb_degree;
+  h.cinv = M->cinv.p;
+  for (int l = l0; l < M->nlev; l++) {
+    const Level &L = M->lev[l];
+    CoarseLevel<T> &c = h.lv[l];
+    c.n = L.A.n;
+    c.rp = L.A.rp.p;
+    c.col = L.A.col.p;
+    if constexpr (std::is_same<T, float>::value) c.val = L.val32.p;
+    else c.val = L.A.val.p;
+    c.dinv = level_dinv<T>(L);
+    c.agg = L.agg.p;
+    c.mptr = L.mptr.p;
+    c.midx = L.midx.p;
+    const double alpha = 0.3 * L.lam, beta = L.lam;
+    const double theta = (beta + alpha) / 2.0, delta = (beta - alpha) / 2.0;
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    c.inv_theta = static_cast<T>(1.0 / theta);
+    for (int k = 1; k < h.deg && k < kMaxCheb; k++) {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      c.c1[k] = static_cast<T>(rho_new * rho);
+      c.c2[k] = static_cast<T>((2.0 * rho_new) / delta);
+      rho = rho_new;
+    }
+    c.r = tp<T>(L.r);
+    c.e = tp<T>(L.e);
+    c.res = tp<T>(L.res);
+    c.d = tp<T>(L.d);
+    c.dn = tp<T>(L.dn);
+  }
+  return h;
+}
+
 template <class T>
 void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
   const int L = M->nlev;
   const Level &Lv = M->lev[l];
+  if (l == L - 1 && l == 0) {
+    launch_dense_gemv<T>(Lv.A.n, M->cinv.p, r, e, s);
+    return;
+  }
+  if (l > 0 && l == coarse_fuse_level(M)) {
+    // r and e are this level's own buffers (written by the restriction above)
+    launch_vcycle_coarse<T>(coarse_hierarchy<T>(M, l), s);
+    return;
+  }
   if (l == L - 1) {
     launch_dense_gemv<T>(Lv.A.n, M->cinv.p, r, e, s);
     return;
@@ -353,28 +430,28 @@ void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
   chebyshev<T>(M, l, r, e, false, s);
 }
 
-template <class T>
-void ilu_solve(const trs_cpr *M, const T *rhs, T *y, const T *y1, const T *e0, T *zout, cudaStream_t s) {
+template <class T, class TZ>
+void ilu_solve(const trs_cpr *M, const T *rhs, T *y, const T *y1, const T *e0, TZ *zout, cudaStream_t s) {
   const IluView<T> F = ilu_view<T>(M);
   for (int c = 0; c < M->ncol; c++) launch_ilu_fwd<T>(M->b, F, rhs, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], s);
   for (int c = M->ncol - 1; c >= 0; c--)
-    launch_ilu_bwd<T>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout, s);
+    launch_ilu_bwd<T, TZ>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout, s);
 }
 
-// z = CPR(Ã)^-1 f (f already scaled by D^-1), written to z (precision T)
+// z = CPR(Ã)^-1 f (f already scaled by D^-1), written to z in FP64
 template <class T>
-void cpr_apply_scaled(const trs_cpr *M, T *z, cudaStream_t s) {
+void cpr_apply_scaled(const trs_cpr *M, double *z, cudaStream_t s) {
   T *f = tp<T>(M->wf), *y = tp<T>(M->wy), *r = tp<T>(M->wr), *x = tp<T>(M->wx);
   const Level &L0 = M->lev[0];
-  ilu_solve<T>(M, f, y, nullptr, nullptr, nullptr, s);
+  ilu_solve<T, T>(M, f, y, nullptr, nullptr, (T *)nullptr, s);
   launch_resid_p<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.r), s);
   vcycle<T>(M, 0, tp<T>(L0.r), tp<T>(L0.e), s);
   launch_resid_full<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.e), r, s);
-  ilu_solve<T>(M, r, x, y, tp<T>(L0.e), z, s);
+  ilu_solve<T, double>(M, r, x, y, tp<T>(L0.e), z, s);
 }
 
 template <class T>
-void cpr_apply_full(const trs_cpr *M, const double *v, const double *div, double *vout, T *z, cudaStream_t s) {
+void cpr_apply_full(const trs_cpr *M, const double *v, const double *div, double *vout, double *z, cudaStream_t s) {
   launch_dscale<T>(M->b, M->n, v, div, vout, dinv_of<T>(M), tp<T>(M->wf), s);
   cpr_apply_scaled<T>(M, z, s);
 }
@@ -383,9 +460,8 @@ void cpr_apply_full(const trs_cpr *M, const double *v, const double *div, double
 void ensure_workspace(trs_cpr *M, int m) {
   if (M->ws_m >= m) return;
   const int64_t N = M->N;
-  const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
   M->V.alloc((size_t)(m + 1) * N);
-  M->Z.alloc((size_t)m * N * es);
+  M->Z.alloc((size_t)m * N * sizeof(double));
   M->w.alloc(N);
   M->r.alloc(N);
   M->H.alloc((size_t)(m + 1) * m);
@@ -415,7 +491,7 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
   ensure_workspace(M, m);
   const RedScratch red{M->partial.p, M->counter.p, M->red_grid};
   const MatView<double> Av = A->view();
-  T *Z = tp<T>(M->Z);
+  double *Z = tp<double>(M->Z);
   double *V = M->V.p;
   trs_solve_stats local{};
   Timer timer(s);
@@ -450,10 +526,10 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
     bool breakdown = false;
     for (int j = 0; j < m; j++) {
       double *vj = V + (int64_t)j * N;
-      T *zj = Z + (int64_t)j * N;
+      double *zj = Z + (int64_t)j * N;
       if (j == 0) cpr_apply_full<T>(M, M->r.p, M->norms.p + 1, vj, zj, s);
       else cpr_apply_full<T>(M, M->w.p, M->hnorm.p, vj, zj, s);
-      launch_spmv<double, T>(M->b, Av, zj, M->w.p, 1.0, 0.0, s);
+      launch_spmv<double, double>(M->b, Av, zj, M->w.p, 1.0, 0.0, s);
       // CGS2: h1 = V^T w (and ||w||^2); w -= V h1 with h2 = V^T w fused; w -= V h2 with ||w||^2
       if (j + 2 <= 32) {
         launch_cgs_dots(V, N, j + 1, M->w.p, red, M->h1.p, s);
@@ -478,7 +554,7 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
     }
     if (result == TRS_ERR_NAN) break;
     launch_lsq(jdone, m, M->H.p, M->gv.p, M->yv.p, s);
-    launch_xupdate<T>(Z, N, jdone, M->yv.p, x, s);
+    launch_xupdate<double>(Z, N, jdone, M->yv.p, x, s);
     cycles++;
     if (breakdown && local.est_relres > o.rtol) {
       // x is exact in the Krylov space; a last true-residual check follows
@@ -582,8 +658,7 @@ trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *str
     require_aligned(z, "z");
     cudaStream_t s = (cudaStream_t)stream;
     if (M->prec == TRS_FP32_PREC) {
-      cpr_apply_full<float>(M, v, nullptr, nullptr, tp<float>(M->wz), s);
-      launch_cast<float, double>(tp<float>(M->wz), z, M->N, s);
+      cpr_apply_full<float>(M, v, nullptr, nullptr, z, s);
     } else {
       cpr_apply_full<double>(M, v, nullptr, nullptr, z, s);
     }
@@ -646,14 +721,28 @@ trs_status trs_cpr_get_decoupled(const trs_cpr *M, double *vt, double *dinv) {
   return guarded([&] {
     TRS_REQUIRE(M, TRS_ERR_INVALID, "NULL argument");
     const int bb = M->b * M->b;
+    const bool mixed = M->prec == TRS_FP32_PREC;
+    DBuf<double> ell64, tval64, dinv64;
+    const double *ellp = M->at_ell64.p, *tvalp = M->at_tval64.p, *dinvp = M->dinv64.p;
+    if (mixed) {  // FP32 copies, widened
+      ell64.alloc(M->at_ell32.n);
+      tval64.alloc(M->at_tval32.n);
+      dinv64.alloc(M->dinv32.n);
+      launch_cast<float, double>(M->at_ell32.p, ell64.p, M->at_ell32.n, 0);
+      launch_cast<float, double>(M->at_tval32.p, tval64.p, M->at_tval32.n, 0);
+      launch_cast<float, double>(M->dinv32.p, dinv64.p, M->dinv32.n, 0);
+      ellp = ell64.p;
+      tvalp = tval64.p;
+      dinvp = dinv64.p;
+    }
     if (vt) {
       DBuf<double> stage(std::max<int64_t>(M->nnzb * bb, 1));
-      launch_gather_values(M->nnzb, bb, M->map.p, M->at_ell64.p, M->at_tval64.p, M->g.nc, stage.p, 0);
+      launch_gather_values(M->nnzb, bb, M->map.p, ellp, tvalp, M->g.nc, stage.p, 0);
       auto h = download(stage.p, M->nnzb * bb, 0);
       std::copy(h.begin(), h.end(), vt);
     }
     if (dinv) {
-      auto h = download(M->dinv64.p, (size_t)bb * M->n, 0);
+      auto h = download(dinvp, (size_t)bb * M->n, 0);
       for (int64_t i = 0; i < M->n; i++)
         for (int e = 0; e < bb; e++) dinv[i * bb + e] = h[(size_t)e * M->n + i];
     }

@@ -47,6 +47,36 @@ struct ScalarOp {
   const T *val;
 };
 
+// Coarse part of the AMG hierarchy run by one block (levels with few rows).
+constexpr int kMaxCheb = 8;
+constexpr int kCoarseFuseRows = 4096;
+
+template <class T>
+struct CoarseLevel {
+  int64_t n;
+  const int64_t *rp;
+  const int32_t *col;
+  const T *val;
+  const T *dinv;
+  const int32_t *agg;       // aggregates into the next level (not on the coarsest)
+  const int64_t *mptr;      // members of the next level's rows
+  const int32_t *midx;
+  T inv_theta;
+  T c1[kMaxCheb];
+  T c2[kMaxCheb];
+  T *r, *e, *res, *d, *dn;
+};
+
+template <class T>
+struct CoarseHierarchy {
+  int l0, nlev, deg;        // levels l0 .. nlev-1 run in one block; Chebyshev degree
+  const double *cinv;       // inverse of the coarsest operator
+  CoarseLevel<T> lv[kMaxLevels];
+};
+
+template <class T>
+void launch_vcycle_coarse(const CoarseHierarchy<T> &h, cudaStream_t s);
+
 // Reduction scratch: per-block partial sums and a ticket counter.
 struct RedScratch {
   double *partial;        // [grid][kMaxRestart + 16]
@@ -68,9 +98,9 @@ void launch_dscale(int b, int64_t n_rows, const double *w, const double *hnorm2,
 template <class T>
 void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, int64_t q1,
                     int64_t q2, cudaStream_t s);
-template <class T>
+template <class T, class TZ>
 void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2,
-                    const T *y1, const T *e0, T *zout, cudaStream_t s);
+                    const T *y1, const T *e0, TZ *zout, cudaStream_t s);
 template <class T>
 void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, cudaStream_t s);
 template <class T>
@@ -179,13 +209,17 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
                           const int32_t *crow, const int64_t *pos, uint8_t *lmask, DBuf<int64_t> &ftptr,
                           DBuf<int32_t> &ftcol, DBuf<uint8_t> &ftlow, DBuf<int64_t> &ftsrc,
                           cudaStream_t s);
-void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const double *at_ell,
-                     const double *at_tval, const int64_t *ftsrc, int64_t nft, double *fell, double *ftval,
-                     cudaStream_t s);
+template <class T>
+void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
+                     const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell, T *ftval, cudaStream_t s);
+template <class T>
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow,
                               const int64_t *pos, const int64_t *ftptr, const int32_t *ftcol,
-                              const uint8_t *ftlow, double *fell, double *ftval, int64_t q0, int64_t q1,
+                              const uint8_t *ftlow, T *fell, T *ftval, int64_t q0, int64_t q1,
                               int64_t q2, int *err, cudaStream_t s);
+void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, float *at_ell,
+                           float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err,
+                           cudaStream_t s);
 
 // ------------------------------------------------------------- k_adjoint
 void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double alpha, double beta,

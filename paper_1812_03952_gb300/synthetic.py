@@ -236,8 +236,9 @@ def config(index: int) -> SyntheticSystem:
 
 
 def diagonal_scalings(n_rows: int, steps: int, seed: int, amplitude: float = 0.2):
-    """Per-step, per-block-row factors (1 + amplitude*u), u ~ U(-1, 1), for a
-    sequence of Newton-like systems whose diagonal blocks are rescaled."""
+    """Per-step, per-row factors (1 + amplitude*u), u ~ U(-1, 1), for a
+    sequence of Newton-like systems (applied to the cells' accumulation
+    blocks, or to whole diagonal blocks by trs_bsr_scale_diagonal)."""
     rng = np.random.default_rng(seed)
     return 1.0 + amplitude * rng.uniform(-1.0, 1.0, size=(steps, n_rows))
 
