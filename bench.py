@@ -62,6 +62,8 @@ def parse():
                         "seeded +-20%% factors, AMG hierarchy rebuilt every --reuse steps, forward and adjoint "
                         "solve per system) instead of single solves")
     p.add_argument("--reuse", type=int, default=5)
+    p.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
+    p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoother degree")
     return p.parse_args()
 
 
@@ -232,9 +234,9 @@ def run_sequence(args):
     g = torch.zeros(sysm.n_unknowns, dtype=torch.float64, device=dev)
     g[torch.from_numpy(np.unique(sysm.perf_cell).astype(np.int64) * sysm.b).to(dev)] = 1.0
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision)
+    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree)
     AT = A.transpose()
-    MT = trs.CPR(AT, precision=args.precision)
+    MT = trs.CPR(AT, precision=args.precision, cheb_degree=args.cheb_degree)
     x = torch.zeros_like(ds.rhs)
     records = []
 
@@ -244,10 +246,10 @@ def run_sequence(args):
             ds.assemble()
             reuse = (k % args.reuse) != 0
             M.update(A, reuse_amg=reuse)
-            _, rf = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)
+            _, rf = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
             A.transpose(into=AT)
             MT.update(AT, reuse_amg=reuse)
-            lam, _, ra = trs.solve_adjoint(A, AT, MT, g, x, rtol=args.rtol)
+            lam, _, ra = trs.solve_adjoint(A, AT, MT, g, x, rtol=args.rtol, restart=args.restart)
             trs.chain_theta(A, ds.k, ds.M, lam, x, sysm.kvkh, sysm.c_t)
             if record:
                 records.append({"step": k, "amg": "reused" if reuse else "rebuilt",
@@ -303,14 +305,14 @@ def main():
     sysm = make_workload(args.workload)
     ds = trs.DeviceSystem(sysm, dev)
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision)
+    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree)
     x = torch.zeros_like(ds.rhs)
     info = M.info()
 
     def step():
         ds.assemble()
         M.update(A, reuse_amg=False)
-        _, res = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)
+        _, res = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
         return res
 
     for _ in range(args.warmup):
@@ -321,6 +323,7 @@ def main():
     l0 = trs.kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
+    trs.profile_spmv(True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
@@ -328,6 +331,7 @@ def main():
             stats.append(r.stats)
         ev1.record(stream)
         torch.cuda.synchronize()
+    spmv_total_ms, spmv_launches = trs.profile_spmv(False)
     barrier(world)
     torch.cuda.synchronize()
     launches = trs.kernel_launches() - l0
@@ -344,25 +348,22 @@ def main():
     np.add.at(Ax, rows, np.einsum("prc,pc->pr", Aval, xt.reshape(-1, A.b)[col]))
     host_relres = float(np.linalg.norm(sysm.rhs - Ax.reshape(-1)) / np.linalg.norm(sysm.rhs))
 
-    # roofline of the operator block SpMV (FP64 values), timed alone
+    # Roofline of the dominant kernel, the FGMRES operator block SpMV w = A z
+    # (FP64 values and vectors), timed live over the timed region by events
+    # around each launch.  It is FP64-pipe-bound (ncu: FP64 pipe ~91% busy),
+    # so it is reported against the FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2
+    # flop x 2.07 GHz = 1.259 TFLOP/s; its HBM fraction is given beside it.
     hbm, peak_kind = peaks()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    xs = torch.randn(A.N, dtype=torch.float64, device=dev)
-    ys = torch.empty_like(xs)
-    durs = []
-    for it in range(23):
-        flush.fill_(float(it))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        A.spmv(xs, ys)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if it >= 3:
-            durs.append(e0.elapsed_time(e1))
-    spmv_ms = statistics.median(durs)
-    spmv_bytes = A.nnzb * A.b * A.b * 8 + 2 * A.N * 8
+    spmv_ms = spmv_total_ms / max(1, spmv_launches)
+    nnzb = A.nnzb
+    spmv_flops = 2 * nnzb * A.b * A.b
+    spmv_bytes = nnzb * A.b * A.b * 8 + 2 * A.N * 8
+    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+    spmv_tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
     spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-
+    # DRAM traffic per launch from the ncu capture of the 96x96x48 case
+    # (434.1 MB for 3,061,224 blocks), scaled by the blocks of this matrix
+    spmv_traffic = 434.135296e6 * nnzb / 3061224.0 if args.workload == "128x128x64_b4" else None
     # FP64-preconditioner path on the same system, for the mixed/FP64 comparison
     fp64 = None
     if not args.no_fp64_compare and args.precision == "fp32":
@@ -435,17 +436,20 @@ def main():
             "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
                        "unknowns": sysm.n_unknowns,
                        "precision": "FP32 CPR inside FP64 FGMRES" if args.precision == "fp32" else "FP64",
-                       "rtol": args.rtol, "restart": 30,
+                       "rtol": args.rtol, "restart": args.restart, "cheb_degree": args.cheb_degree,
                        "l2": "inputs larger than L2 (Jacobian inputs 0.9 GB, matrix 0.9 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters": last["iters"], "true_relres": last["true_relres"], "host_true_relres": host_relres,
             "breakdown_ms": {"setup": last["ms_setup"], "solve": last["ms_solve"]},
             "amg_levels": info["n_levels"], "amg_rows": info["level_rows"], "n_colours": info["n_colours"],
             "fp64_path": fp64,
-            "roofline": {"kernel": "k_spmv<4,double,double> (operator block SpMV)", "bound": "hbm",
-                         "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
-                         "traffic": None, "peak_kind": peak_kind, "launch_ms": spmv_ms,
-                         "algorithmic_bytes": spmv_bytes},
+            "roofline": {"kernel": "k_spmv<4,double,double> (FGMRES operator block SpMV)", "bound": "alu",
+                         "achieved": spmv_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                         "frac": spmv_tflops / fp64_peak_tflops, "traffic": spmv_traffic,
+                         "peak_kind": "FP64 unit count x clock (probe measured 1.2548 TFLOP/s)",
+                         "launch_ms": spmv_ms, "launches": spmv_launches, "algorithmic_flops": spmv_flops,
+                         "algorithmic_bytes": spmv_bytes, "hbm_achieved_gbs": spmv_gbs, "hbm_peak_gbs": hbm,
+                         "hbm_frac": spmv_gbs / hbm, "hbm_peak_kind": peak_kind},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)

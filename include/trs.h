@@ -299,6 +299,12 @@ const char *trs_version(void);
  * devices, all threads), for accounting of launch counts. */
 uint64_t trs_kernel_launches(void);
 
+/* Device timing of the operator SpMV (w = A z_j) launches inside FGMRES, by
+ * CUDA events on the solve's stream.  enable = 1 resets the totals and starts
+ * timing; enable = 0 stops.  Either call first returns the totals so far
+ * (host pointers, may be NULL).  Process-wide; not for concurrent solves. */
+trs_status trs_profile_spmv(int32_t enable, double *total_ms, int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

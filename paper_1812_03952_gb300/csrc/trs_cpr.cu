@@ -7,6 +7,7 @@
 //   y1 = F^-1 f; r1_p = (f - Ã y1)_0; e = V-cycle(r1_p);
 //   r2 = f - Ã (y1 + Pi_p e); z = y1 + Pi_p e + F^-1 r2.
 #include <atomic>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 
@@ -483,6 +484,17 @@ void ensure_workspace(trs_cpr *M, int m) {
   M->ws_m = m;
 }
 
+// Optional device timing of the operator SpMV launches inside FGMRES
+// (events on the solve's stream; read at the per-iteration synchronisation).
+struct SpmvProfile {
+  bool on = false;
+  double ms = 0.0;
+  int64_t launches = 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+SpmvProfile g_spmv_prof;
+std::mutex g_prof_mutex;
+
 template <class T>
 trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, const trs_solve_opts &o,
                   cudaStream_t s, trs_solve_stats *st) {
@@ -529,7 +541,10 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
       double *zj = Z + (int64_t)j * N;
       if (j == 0) cpr_apply_full<T>(M, M->r.p, M->norms.p + 1, vj, zj, s);
       else cpr_apply_full<T>(M, M->w.p, M->hnorm.p, vj, zj, s);
+      const bool prof = g_spmv_prof.on;
+      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.a, s));
       launch_spmv<double, double>(M->b, Av, zj, M->w.p, 1.0, 0.0, s);
+      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.b, s));
       // CGS2: h1 = V^T w (and ||w||^2); w -= V h1 with h2 = V^T w fused; w -= V h2 with ||w||^2
       if (j + 2 <= 32) {
         launch_cgs_dots(V, N, j + 1, M->w.p, red, M->h1.p, s);
@@ -546,6 +561,12 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
       double hs[2];
       TRS_CUDA(cudaMemcpyAsync(hs, M->status.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
+      if (prof) {
+        float ems = 0.f;
+        TRS_CUDA(cudaEventElapsedTime(&ems, g_spmv_prof.a, g_spmv_prof.b));
+        g_spmv_prof.ms += ems;
+        g_spmv_prof.launches++;
+      }
       local.est_relres = hs[0];
       if (!std::isfinite(hs[0])) { result = TRS_ERR_NAN; break; }
       breakdown = hs[1] != 0.0;
@@ -832,5 +853,22 @@ const char *trs_last_error(void) { return g_last_error.c_str(); }
 const char *trs_version(void) { return "trs 0.1 (sm_103a)"; }
 
 uint64_t trs_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+trs_status trs_profile_spmv(int32_t enable, double *total_ms, int64_t *launches) {
+  return guarded([&] {
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if (!g_spmv_prof.a) {
+      TRS_CUDA(cudaEventCreate(&g_spmv_prof.a));
+      TRS_CUDA(cudaEventCreate(&g_spmv_prof.b));
+    }
+    if (total_ms) *total_ms = g_spmv_prof.ms;
+    if (launches) *launches = g_spmv_prof.launches;
+    if (enable) {
+      g_spmv_prof.ms = 0.0;
+      g_spmv_prof.launches = 0;
+    }
+    g_spmv_prof.on = enable != 0;
+  });
+}
 
 }  // extern "C"

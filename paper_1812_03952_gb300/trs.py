@@ -39,7 +39,7 @@ EXPORTS = (
     "trs_cpr_get_colours", "trs_cpr_get_decoupled", "trs_cpr_get_level", "trs_cpr_vcycle",
     "trs_cpr_destroy", "trs_solve_default_opts", "trs_fgmres_solve", "trs_fgmres_solve_host",
     "trs_solve_adjoint", "trs_outer_product", "trs_chain_theta", "trs_last_error", "trs_version",
-    "trs_kernel_launches", "trs_residual_norm_noalloc",
+    "trs_kernel_launches", "trs_residual_norm_noalloc", "trs_profile_spmv",
 )
 
 
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
         "trs_version": (C.c_char_p, []),
         "trs_kernel_launches": (C.c_uint64, []),
         "trs_residual_norm_noalloc": (i32, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
+        "trs_profile_spmv": (i32, [i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -139,6 +140,14 @@ def load(path: str = LIB_PATH):
 
 def kernel_launches() -> int:
     return int(load().trs_kernel_launches())
+
+
+def profile_spmv(enable: bool):
+    """Starts (enable) or stops timing of the FGMRES operator SpMV launches;
+    returns (total_ms, launches) accumulated before this call."""
+    ms, n = C.c_double(0.0), C.c_int64(0)
+    _check(load().trs_profile_spmv(int(enable), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 def _check(code, allow=()):
