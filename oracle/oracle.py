@@ -140,6 +140,9 @@ def lib():
         L.orc_fgmres.restype = C.c_int
         L.orc_fgmres.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, C.c_void_p, f64p, f64p,
                                  C.c_double, C.c_int, C.c_int, C.POINTER(_Stats), f64p, C.c_int]
+        L.orc_bicgstab.restype = C.c_int
+        L.orc_bicgstab.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, C.c_void_p, f64p, f64p,
+                                   C.c_double, C.c_int, C.POINTER(_Stats), f64p, C.c_int]
         L.orc_outer_product.restype = None
         L.orc_outer_product.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, f64p, f64p]
         L.orc_chain_theta.restype = C.c_int
@@ -460,6 +463,19 @@ def fgmres(A: BSR, cpr: CPR, rhs, rtol=1e-10, restart=30, maxit=1000, x0=None, h
                               np.ascontiguousarray(rhs, dtype=np.float64), x, rtol, restart,
                               maxit, C.byref(st), hist, hist_cap)
     _check(status, "fgmres")
+    nh = min(hist_cap, st.iters + 1)
+    return SolveResult(x, status, st.iters, st.restarts, bool(st.converged), st.est_relres,
+                       st.true_relres, hist[:nh].copy())
+
+
+def bicgstab(A: BSR, cpr: CPR, rhs, rtol=1e-10, maxit=1000, x0=None, hist_cap=4096):
+    x = np.zeros(A.n * A.b) if x0 is None else np.array(x0, dtype=np.float64)
+    st = _Stats()
+    hist = np.zeros(hist_cap)
+    status = lib().orc_bicgstab(A.n, A.b, A.rp, A.col, A.val.reshape(-1), cpr.h,
+                                np.ascontiguousarray(rhs, dtype=np.float64), x, rtol, maxit,
+                                C.byref(st), hist, hist_cap)
+    _check(status, "bicgstab")
     nh = min(hist_cap, st.iters + 1)
     return SolveResult(x, status, st.iters, st.restarts, bool(st.converged), st.est_relres,
                        st.true_relres, hist[:nh].copy())

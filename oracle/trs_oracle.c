@@ -1182,6 +1182,91 @@ int orc_fgmres(int64_t n, int b, const int64_t *rp, const int32_t *col, const do
 }
 
 /* ======================================================================
+ * BiCGSTAB (van der Vorst 1992), right-preconditioned with the same
+ * CPR-FPF: the Krylov solver of every run in the paper (Examples num-sagd,
+ * sca-230m, ...; Sec. "Linear Solver" lists it among the solvers).  With
+ * shadow residual r^ = r0 and rho = <r^, r>:
+ *   p = r + beta (p - omega v), beta = (rho / rho_old)(alpha / omega);
+ *   p^ = M^-1 p;  v = A p^;  alpha = rho / <r^, v>;  s = r - alpha v;
+ *   (if ||s|| <= rtol ||b||: x += alpha p^ and stop)
+ *   s^ = M^-1 s;  t = A s^;  omega = <t, s> / <t, t>;
+ *   x += alpha p^ + omega s^;  r = s - omega t.
+ * A recurrence residual below rtol is confirmed on the true residual; if
+ * the true residual is still above, the iteration restarts from it.
+ * ====================================================================== */
+int orc_bicgstab(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                 const void *cpr, const double *rhs, double *x, double rtol, int maxit, orc_stats *st,
+                 double *hist, int hist_cap) {
+  const int64_t N = n * b;
+  memset(st, 0, sizeof(*st));
+  double bnorm = sqrt(dot(N, rhs, rhs));
+  if (bnorm == 0.0) {
+    for (int64_t e = 0; e < N; e++) x[e] = 0.0;
+    st->converged = 1;
+    return ORC_OK;
+  }
+  double *r = malloc(sizeof(double) * (size_t)N), *rh = malloc(sizeof(double) * (size_t)N);
+  double *p = calloc((size_t)N, sizeof(double)), *v = calloc((size_t)N, sizeof(double));
+  double *ph = malloc(sizeof(double) * (size_t)N), *s = malloc(sizeof(double) * (size_t)N);
+  double *sh = malloc(sizeof(double) * (size_t)N), *t = malloc(sizeof(double) * (size_t)N);
+  int iters = 0, nh = 0, converged = 0, status = ORC_OK;
+  double relres = 1.0;
+  for (;;) {  /* (re)start from the true residual */
+    memcpy(r, rhs, sizeof(double) * (size_t)N);
+    orc_bsr_spmv(n, b, rp, col, val, x, r, -1.0, 1.0);
+    relres = sqrt(dot(N, r, r)) / bnorm;
+    st->true_relres = relres;
+    if (hist && nh < hist_cap && iters == 0) hist[nh++] = relres;
+    if (relres <= rtol) { converged = 1; break; }
+    if (iters >= maxit) break;
+    if (!isfinite(relres)) { status = ORC_SINGULAR; break; }
+    memcpy(rh, r, sizeof(double) * (size_t)N);
+    for (int64_t e = 0; e < N; e++) { p[e] = 0.0; v[e] = 0.0; }
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    int restart = 0;
+    while (iters < maxit) {
+      const double rho = dot(N, rh, r);
+      if (rho == 0.0 || !isfinite(rho)) { restart = 1; break; }
+      const double beta = (rho / rho_old) * (alpha / omega);
+      for (int64_t e = 0; e < N; e++) p[e] = r[e] + beta * (p[e] - omega * v[e]);
+      orc_cpr_apply(cpr, p, ph);
+      for (int64_t e = 0; e < N; e++) v[e] = 0.0;
+      orc_bsr_spmv(n, b, rp, col, val, ph, v, 1.0, 0.0);
+      alpha = rho / dot(N, rh, v);
+      for (int64_t e = 0; e < N; e++) s[e] = r[e] - alpha * v[e];
+      iters++;
+      const double snorm = sqrt(dot(N, s, s)) / bnorm;
+      if (snorm <= rtol) {
+        for (int64_t e = 0; e < N; e++) x[e] = x[e] + alpha * ph[e];
+        relres = snorm;
+        if (hist && nh < hist_cap) hist[nh++] = relres;
+        restart = 1;
+        break;
+      }
+      orc_cpr_apply(cpr, s, sh);
+      for (int64_t e = 0; e < N; e++) t[e] = 0.0;
+      orc_bsr_spmv(n, b, rp, col, val, sh, t, 1.0, 0.0);
+      omega = dot(N, t, s) / dot(N, t, t);
+      for (int64_t e = 0; e < N; e++) x[e] = x[e] + alpha * ph[e] + omega * sh[e];
+      for (int64_t e = 0; e < N; e++) r[e] = s[e] - omega * t[e];
+      relres = sqrt(dot(N, r, r)) / bnorm;
+      if (hist && nh < hist_cap) hist[nh++] = relres;
+      rho_old = rho;
+      if (relres <= rtol || omega == 0.0 || !isfinite(relres)) { restart = 1; break; }
+    }
+    st->restarts++;
+    st->est_relres = relres;
+    if (!restart) break;   /* maxit reached inside the loop */
+  }
+  if (st->restarts > 0) st->restarts--;
+  st->iters = iters;
+  st->converged = converged;
+  free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);
+  if (status) return status;
+  return converged ? ORC_OK : ORC_NOT_CONVERGED;
+}
+
+/* ======================================================================
  * Adjoint.  For L(x) with x = A^-1 b and g = dL/dx: A^T lambda = g gives
  * dL/db = lambda and dL/dA_ij = -lambda_i x_j^T on every stored block.
  * Chain to theta = log k through the assembly above: for the face between

@@ -118,6 +118,11 @@ int orc_fgmres(int64_t n, int b, const int64_t *rp, const int32_t *col, const do
                const void *cpr, const double *rhs, double *x, double rtol, int restart, int maxit,
                orc_stats *st, double *hist, int hist_cap);
 
+/* Right-preconditioned BiCGSTAB (the Krylov solver of the paper's runs). */
+int orc_bicgstab(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                 const void *cpr, const double *rhs, double *x, double rtol, int maxit, orc_stats *st,
+                 double *hist, int hist_cap);
+
 /* ---- adjoint ---- */
 void orc_outer_product(int64_t n, int b, const int64_t *rp, const int32_t *col,
                        const double *lambda, const double *x, double *dA);

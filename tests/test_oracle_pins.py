@@ -514,6 +514,54 @@ def test_fgmres_config0(oracle, synth):
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) < 1e-8
 
 
+# --------------------------------------------------------------- BiCGSTAB
+@pytest.mark.parametrize("shape", [(2, 2, 2, 4), (5, 4, 3, 5), (8, 8, 2, 4)])
+def test_bicgstab_matches_direct_solve(oracle, synth, shape):
+    nx, ny, nz, b = shape
+    s = synth.small_system(nx, ny, nz, b, seed=sum(shape) + 1, n_pairs=1 if nz > 1 else 0)
+    A = oracle.assemble(s)
+    res = oracle.bicgstab(A, oracle.CPR(A), s.rhs, rtol=1e-10)
+    As = A.to_scipy().tocsc()
+    x = spl.spsolve(As, s.rhs)
+    cond = np.linalg.cond(As.toarray())
+    assert res.converged and res.true_relres <= 1e-10
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= max(1e-12, cond * 1e-10)
+
+
+def test_bicgstab_iterates_match_scipy(oracle, synth):
+    """The k-th iterate equals that of scipy's right-preconditioned BiCGSTAB
+    (same van der Vorst recurrences, shadow residual r0) with M = CPR."""
+    s = synth.small_system(7, 6, 4, 4, seed=29, n_pairs=1)
+    A = oracle.assemble(s)
+    cpr = oracle.CPR(A)
+    As = A.to_scipy().tocsr()
+    N = A.n * A.b
+    Mop = spl.LinearOperator((N, N), matvec=lambda v: cpr.apply(np.asarray(v).reshape(-1)))
+    for k in (1, 2, 3, 5):
+        mine = oracle.bicgstab(A, cpr, s.rhs, rtol=1e-15, maxit=k)
+        assert mine.iters == k and not mine.converged
+        ref, _ = spl.bicgstab(As, s.rhs, rtol=1e-30, atol=0.0, maxiter=k, M=Mop)
+        np.testing.assert_allclose(mine.x, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_bicgstab_exact_preconditioner_one_step(oracle, synth):
+    """With M = A^-1 (no flux: CPR^-1 D^-1 = A^-1) the first half step gives s = 0."""
+    s = tiny(synth, 4, 4, 2, 4, seed=16, n_pairs=0)
+    s.k[:] = 0.0
+    A = oracle.assemble(s)
+    res = oracle.bicgstab(A, oracle.CPR(A), s.rhs, rtol=1e-12)
+    assert res.iters == 1 and res.converged
+    x = spl.spsolve(A.to_scipy().tocsc(), s.rhs)
+    np.testing.assert_allclose(res.x, x, rtol=1e-12, atol=1e-14)
+
+
+def test_bicgstab_zero_rhs(oracle, synth):
+    s = tiny(synth, 3, 3, 2, 4, seed=5)
+    A = oracle.assemble(s)
+    res = oracle.bicgstab(A, oracle.CPR(A), np.zeros(A.n * A.b))
+    assert res.converged and res.iters == 0 and np.all(res.x == 0)
+
+
 # --------------------------------------------------------------- adjoint
 def test_transpose_dot_product(oracle, synth):
     s = tiny(synth, 5, 4, 3, 4, seed=19)
