@@ -1209,24 +1209,26 @@ int orc_bicgstab(int64_t n, int b, const int64_t *rp, const int32_t *col, const 
   double *p = calloc((size_t)N, sizeof(double)), *v = calloc((size_t)N, sizeof(double));
   double *ph = malloc(sizeof(double) * (size_t)N), *s = malloc(sizeof(double) * (size_t)N);
   double *sh = malloc(sizeof(double) * (size_t)N), *t = malloc(sizeof(double) * (size_t)N);
-  int iters = 0, nh = 0, converged = 0, status = ORC_OK;
+  int iters = 0, nh = 0, cycles = 0, converged = 0, status = ORC_OK;
   double relres = 1.0;
-  for (;;) {  /* (re)start from the true residual */
+  /* Every cycle starts from the true residual of the current x, and the
+   * solve ends there too, so true_relres always belongs to the returned x. */
+  for (;;) {
     memcpy(r, rhs, sizeof(double) * (size_t)N);
     orc_bsr_spmv(n, b, rp, col, val, x, r, -1.0, 1.0);
     relres = sqrt(dot(N, r, r)) / bnorm;
     st->true_relres = relres;
     if (hist && nh < hist_cap && iters == 0) hist[nh++] = relres;
+    if (!isfinite(relres)) { status = ORC_SINGULAR; break; }
     if (relres <= rtol) { converged = 1; break; }
     if (iters >= maxit) break;
-    if (!isfinite(relres)) { status = ORC_SINGULAR; break; }
+    cycles++;
     memcpy(rh, r, sizeof(double) * (size_t)N);
     for (int64_t e = 0; e < N; e++) { p[e] = 0.0; v[e] = 0.0; }
     double rho_old = 1.0, alpha = 1.0, omega = 1.0;
-    int restart = 0;
     while (iters < maxit) {
       const double rho = dot(N, rh, r);
-      if (rho == 0.0 || !isfinite(rho)) { restart = 1; break; }
+      if (rho == 0.0 || !isfinite(rho)) break;          /* breakdown: restart */
       const double beta = (rho / rho_old) * (alpha / omega);
       for (int64_t e = 0; e < N; e++) p[e] = r[e] + beta * (p[e] - omega * v[e]);
       orc_cpr_apply(cpr, p, ph);
@@ -1236,11 +1238,10 @@ int orc_bicgstab(int64_t n, int b, const int64_t *rp, const int32_t *col, const 
       for (int64_t e = 0; e < N; e++) s[e] = r[e] - alpha * v[e];
       iters++;
       const double snorm = sqrt(dot(N, s, s)) / bnorm;
-      if (snorm <= rtol) {
+      if (snorm <= rtol) {                               /* half step suffices */
         for (int64_t e = 0; e < N; e++) x[e] = x[e] + alpha * ph[e];
         relres = snorm;
         if (hist && nh < hist_cap) hist[nh++] = relres;
-        restart = 1;
         break;
       }
       orc_cpr_apply(cpr, s, sh);
@@ -1252,13 +1253,11 @@ int orc_bicgstab(int64_t n, int b, const int64_t *rp, const int32_t *col, const 
       relres = sqrt(dot(N, r, r)) / bnorm;
       if (hist && nh < hist_cap) hist[nh++] = relres;
       rho_old = rho;
-      if (relres <= rtol || omega == 0.0 || !isfinite(relres)) { restart = 1; break; }
+      if (relres <= rtol || omega == 0.0 || !isfinite(relres)) break;
     }
-    st->restarts++;
     st->est_relres = relres;
-    if (!restart) break;   /* maxit reached inside the loop */
   }
-  if (st->restarts > 0) st->restarts--;
+  st->restarts = cycles > 0 ? cycles - 1 : 0;
   st->iters = iters;
   st->converged = converged;
   free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);

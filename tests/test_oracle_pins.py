@@ -542,6 +542,9 @@ def test_bicgstab_iterates_match_scipy(oracle, synth):
         assert mine.iters == k and not mine.converged
         ref, _ = spl.bicgstab(As, s.rhs, rtol=1e-30, atol=0.0, maxiter=k, M=Mop)
         np.testing.assert_allclose(mine.x, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+        # the reported true residual is that of the returned iterate
+        tr = np.linalg.norm(s.rhs - As @ mine.x) / np.linalg.norm(s.rhs)
+        np.testing.assert_allclose(mine.true_relres, tr, rtol=1e-10)
 
 
 def test_bicgstab_exact_preconditioner_one_step(oracle, synth):
