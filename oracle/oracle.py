@@ -42,7 +42,14 @@ class _Stats(C.Structure):
 
 class _CprOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
-                ("cheb_degree", C.c_int), ("seed", C.c_uint32)]
+                ("cheb_degree", C.c_int), ("seed", C.c_uint32), ("stages", C.c_int),
+                ("decoupling", C.c_int)]
+
+
+#: CPR stage orderings and decoupling methods (Sec. "Preconditioners",
+#: Sec. "Decoupling Methods")
+STAGES = {"fpf": 0, "fp": 1, "pf": 2}
+DECOUPLINGS = {"abf": 0, "none": 1, "frs": 2, "frs+abf": 3}
 
 
 _lib = None
@@ -68,6 +75,8 @@ def lib():
         L.orc_pattern_symmetric.argtypes = [C.c_int64, i64p, i32p]
         L.orc_gj_inverse.restype = C.c_int
         L.orc_gj_inverse.argtypes = [C.c_int, f64p, f64p]
+        L.orc_decouple_mode.restype = C.c_int
+        L.orc_decouple_mode.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, C.c_int, f64p, f64p]
         L.orc_decouple.restype = C.c_int
         L.orc_decouple.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, f64p, f64p]
         L.orc_pressure_matrix.restype = None
@@ -234,11 +243,11 @@ def gj_inverse(D):
     return inv.reshape(b, b)
 
 
-def decouple(A: BSR):
+def decouple(A: BSR, mode="abf"):
     vt = np.zeros_like(A.val)
     dinv = np.zeros((A.n, A.b, A.b))
-    _check(lib().orc_decouple(A.n, A.b, A.rp, A.col, A.val.reshape(-1), vt.reshape(-1),
-                              dinv.reshape(-1)), "decouple")
+    _check(lib().orc_decouple_mode(A.n, A.b, A.rp, A.col, A.val.reshape(-1), DECOUPLINGS[mode],
+                                   vt.reshape(-1), dinv.reshape(-1)), "decouple")
     return vt, dinv
 
 
@@ -391,7 +400,8 @@ class BILU0:
 
 
 #: default CPR options (the same defaults as the CUDA library)
-CPR_DEFAULTS = dict(theta=0.08, coarse_max=64, max_levels=12, cheb_degree=2, seed=0x5EED1812)
+CPR_DEFAULTS = dict(theta=0.08, coarse_max=64, max_levels=12, cheb_degree=2, seed=0x5EED1812,
+                    stages="fpf", decoupling="abf")
 
 
 class CPR:
@@ -399,7 +409,7 @@ class CPR:
         o = dict(CPR_DEFAULTS)
         o.update(kw)
         self.opts = _CprOpts(o["theta"], o["coarse_max"], o["max_levels"], o["cheb_degree"],
-                             o["seed"])
+                             o["seed"], STAGES[o["stages"]], DECOUPLINGS[o["decoupling"]])
         st = C.c_int(0)
         self.A = A
         self.h = lib().orc_cpr_setup(A.n, A.b, A.rp, A.col, A.val.reshape(-1),

@@ -376,25 +376,61 @@ static void block_vec(int b, const double *A, const double *x, double *y) {
   }
 }
 
-int orc_decouple(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
-                 double *vt, double *dinv) {
+/* Decoupling D^-1 A of Eq. decoupled-eq, block row by block row, with the
+ * left factor D_i^-1 chosen by `mode` (Sec. "Decoupling Methods"):
+ *   ORC_DEC_ABF      D_i^-1 = A_ii^-1 (Eq. decoupled-abf; the inverse by
+ *                    Gauss-Jordan elimination with partial row pivoting, so
+ *                    the same operator also serves for GJE); Ã_ii = I exactly;
+ *   ORC_DEC_NONE     D_i^-1 = I, Ã = A;
+ *   ORC_DEC_FRS      D_i^-1 = R (Eq. decoupled-frs: ones in the first row and
+ *                    on the diagonal), which adds every row into the pressure
+ *                    row;
+ *   ORC_DEC_FRS_ABF  the two-stage FRS+ABF: A' = R A, then ABF of A', so
+ *                    D_i^-1 = (R A_ii)^-1 R and Ã_ii = I exactly.
+ * Every product is block_mul (inner index ascending). */
+int orc_decouple_mode(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                      int mode, double *vt, double *dinv) {
+  if (mode < ORC_DEC_ABF || mode > ORC_DEC_FRS_ABF || b < 1 || b > ORC_MAX_B) return ORC_INVALID;
   const int64_t bb = (int64_t)b * b;
+  double R[ORC_MAX_B * ORC_MAX_B], Ai[ORC_MAX_B * ORC_MAX_B], Rd[ORC_MAX_B * ORC_MAX_B];
+  for (int r = 0; r < b; r++)
+    for (int c = 0; c < b; c++) R[r * b + c] = (r == 0 || r == c) ? 1.0 : 0.0;
+  const int unit = (mode == ORC_DEC_ABF || mode == ORC_DEC_FRS_ABF);
   for (int64_t i = 0; i < n; i++) {
     int64_t dp = find_entry(rp, col, i, i);
     if (dp < 0) return ORC_INVALID;
     double *Di = dinv + i * bb;
-    int st = orc_gj_inverse(b, val + dp * bb, Di);
-    if (st) return st;
+    if (mode == ORC_DEC_NONE) {
+      for (int e = 0; e < bb; e++) Di[e] = (e % (b + 1) == 0) ? 1.0 : 0.0;
+    } else if (mode == ORC_DEC_FRS) {
+      for (int e = 0; e < bb; e++) Di[e] = R[e];
+    } else if (mode == ORC_DEC_ABF) {
+      int st = orc_gj_inverse(b, val + dp * bb, Di);
+      if (st) return st;
+    } else {
+      block_mul(b, R, val + dp * bb, Rd);
+      int st = orc_gj_inverse(b, Rd, Ai);
+      if (st) return st;
+      block_mul(b, Ai, R, Di);
+    }
     for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
-      if (p == dp) {
+      if (p == dp && unit) {
         for (int e = 0; e < bb; e++) vt[p * bb + e] = 0.0;
         for (int r = 0; r < b; r++) vt[p * bb + r * b + r] = 1.0;
+      } else if (mode == ORC_DEC_FRS_ABF) {
+        block_mul(b, R, val + p * bb, Rd);
+        block_mul(b, Ai, Rd, vt + p * bb);
       } else {
         block_mul(b, Di, val + p * bb, vt + p * bb);
       }
     }
   }
   return ORC_OK;
+}
+
+int orc_decouple(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                 double *vt, double *dinv) {
+  return orc_decouple_mode(n, b, rp, col, val, ORC_DEC_ABF, vt, dinv);
 }
 
 /* Pressure matrix A_PP of Algorithm pc-fpf: entry (0,0) of every decoupled
@@ -983,6 +1019,7 @@ typedef struct {
   void *ilu;
   int32_t *colour;
   int n_colours;
+  int stages;
 } orc_cpr;
 
 void orc_cpr_free(void *hv) {
@@ -1006,7 +1043,9 @@ void *orc_cpr_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, con
   memcpy(h->col, col, sizeof(int32_t) * (size_t)nnz);
   h->vt = malloc(sizeof(double) * nz1(nnz * bb));
   h->dinv = malloc(sizeof(double) * nz1(n * bb));
-  int st = orc_decouple(n, b, rp, col, val, h->vt, h->dinv);
+  if (opts->stages < ORC_CPR_FPF || opts->stages > ORC_CPR_PF) { *status = ORC_INVALID; orc_cpr_free(h); return NULL; }
+  h->stages = opts->stages;
+  int st = orc_decouple_mode(n, b, rp, col, val, opts->decoupling, h->vt, h->dinv);
   if (st) { *status = st; orc_cpr_free(h); return NULL; }
   double *ap = malloc(sizeof(double) * nz1(nnz));
   orc_pressure_matrix(n, b, rp, col, h->vt, ap);
@@ -1023,6 +1062,16 @@ void *orc_cpr_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, con
   return h;
 }
 
+/* z = CPR(Ã)^-1 D^-1 v.  With f = D^-1 v, F = the block ILU(0) of Ã,
+ * P = AMG(A_PP)^-1 one V-cycle, Pi_r = restriction to the pressure entries
+ * and Pi_p = prolongation into them (entry 0 of every block):
+ *   FPF (Algorithm pc-fpf): y1 = F^-1 f; r1 = f - Ã y1;
+ *        y2 = y1 + Pi_p P Pi_r r1; r2 = f - Ã y2; z = y2 + F^-1 r2;
+ *   FP:  the first three steps, z = y2;
+ *   PF:  y1 = Pi_p P Pi_r f; r1 = f - Ã y1; z = y1 + F^-1 r1.
+ * (CPR-FP and CPR-PF are the two-stage orderings the paper compares with
+ * CPR-FPF, Sec. "Preconditioners" and the tables of Sec. "Numerical
+ * Performance".) */
 void orc_cpr_apply(const void *hv, const double *v, double *z) {
   const orc_cpr *h = hv;
   const int64_t n = h->n, N = n * h->b;
@@ -1030,18 +1079,32 @@ void orc_cpr_apply(const void *hv, const double *v, double *z) {
   const int64_t bb = (int64_t)b * b;
   double *f = calloc((size_t)N, sizeof(double)), *y = calloc((size_t)N, sizeof(double));
   double *r = malloc(sizeof(double) * (size_t)N);
-  double *rp_ = malloc(sizeof(double) * (size_t)n), *ep = malloc(sizeof(double) * (size_t)n);
+  double *rp_ = calloc((size_t)n, sizeof(double)), *ep = calloc((size_t)n, sizeof(double));
   for (int64_t i = 0; i < n; i++) block_vec(b, h->dinv + i * bb, v + i * b, f + i * b);
-  orc_bilu0_solve(h->ilu, f, y);                                           /* y1 */
-  memcpy(r, f, sizeof(double) * (size_t)N);
-  orc_bsr_spmv(n, b, h->rp, h->col, h->vt, y, r, -1.0, 1.0);              /* r1 */
-  for (int64_t i = 0; i < n; i++) rp_[i] = r[i * b];
-  orc_amg_vcycle(h->amg, rp_, ep);
-  for (int64_t i = 0; i < n; i++) y[i * b] = y[i * b] + ep[i];            /* y2 */
-  memcpy(r, f, sizeof(double) * (size_t)N);
-  orc_bsr_spmv(n, b, h->rp, h->col, h->vt, y, r, -1.0, 1.0);              /* r2 */
-  orc_bilu0_solve(h->ilu, r, z);
-  for (int64_t e = 0; e < N; e++) z[e] = y[e] + z[e];
+  if (h->stages == ORC_CPR_PF) {
+    for (int64_t i = 0; i < n; i++) rp_[i] = f[i * b];
+    orc_amg_vcycle(h->amg, rp_, ep);
+    for (int64_t i = 0; i < n; i++) y[i * b] = ep[i];                       /* y1, y = 0 elsewhere */
+    memcpy(r, f, sizeof(double) * (size_t)N);
+    orc_bsr_spmv(n, b, h->rp, h->col, h->vt, y, r, -1.0, 1.0);              /* r1 */
+    orc_bilu0_solve(h->ilu, r, z);
+    for (int64_t e = 0; e < N; e++) z[e] = y[e] + z[e];
+  } else {
+    orc_bilu0_solve(h->ilu, f, y);                                           /* y1 */
+    memcpy(r, f, sizeof(double) * (size_t)N);
+    orc_bsr_spmv(n, b, h->rp, h->col, h->vt, y, r, -1.0, 1.0);              /* r1 */
+    for (int64_t i = 0; i < n; i++) rp_[i] = r[i * b];
+    orc_amg_vcycle(h->amg, rp_, ep);
+    for (int64_t i = 0; i < n; i++) y[i * b] = y[i * b] + ep[i];            /* y2 */
+    if (h->stages == ORC_CPR_FP) {
+      memcpy(z, y, sizeof(double) * (size_t)N);
+    } else {
+      memcpy(r, f, sizeof(double) * (size_t)N);
+      orc_bsr_spmv(n, b, h->rp, h->col, h->vt, y, r, -1.0, 1.0);            /* r2 */
+      orc_bilu0_solve(h->ilu, r, z);
+      for (int64_t e = 0; e < N; e++) z[e] = y[e] + z[e];
+    }
+  }
   free(f); free(y); free(r); free(rp_); free(ep);
 }
 

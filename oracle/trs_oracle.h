@@ -43,7 +43,14 @@ int orc_bsr_transpose(int64_t n, int b, const int64_t *rp, const int32_t *col, c
 int orc_pattern_symmetric(int64_t n, const int64_t *rp, const int32_t *col);
 
 /* ---- decoupling ---- */
+#define ORC_MAX_B 8
+#define ORC_DEC_ABF 0      /* D_i = A_ii (ABF; GJE computes the same operator) */
+#define ORC_DEC_NONE 1     /* no decoupling */
+#define ORC_DEC_FRS 2      /* full row sum */
+#define ORC_DEC_FRS_ABF 3  /* FRS, then ABF */
 int orc_gj_inverse(int b, const double *D, double *inv);
+int orc_decouple_mode(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
+                      int mode, double *vt, double *dinv);
 int orc_decouple(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
                  double *vt, double *dinv);
 void orc_pressure_matrix(int64_t n, int b, const int64_t *rp, const int32_t *col,
@@ -88,12 +95,17 @@ void orc_bilu0_factors(const void *h, double *F);
 void orc_bilu0_free(void *h);
 
 /* ---- CPR-FPF preconditioner and FGMRES ---- */
+#define ORC_CPR_FPF 0   /* F, P, F (Algorithm pc-fpf) */
+#define ORC_CPR_FP 1    /* F, then P */
+#define ORC_CPR_PF 2    /* P, then F */
 typedef struct {
   double theta;      /* AMG strength threshold */
   int coarse_max;    /* stop coarsening at n <= coarse_max */
   int max_levels;
   int cheb_degree;
   uint32_t seed;
+  int stages;        /* ORC_CPR_FPF / FP / PF */
+  int decoupling;    /* ORC_DEC_* */
 } orc_cpr_opts;
 
 void *orc_cpr_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,

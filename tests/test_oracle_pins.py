@@ -208,6 +208,39 @@ def test_frs_then_abf_equals_abf(oracle, synth):
     np.testing.assert_allclose(vt2, vt, rtol=1e-9, atol=1e-11)
 
 
+@pytest.mark.parametrize("mode", ["none", "frs", "frs+abf"])
+def test_decoupling_modes(oracle, synth, mode):
+    """Sec. Decoupling Methods: Ã_ij = D_i^-1 A_ij for every stored block with
+    D_i^-1 = I (none), R = ones in the first row and on the diagonal (FRS,
+    Eq. decoupled-frs: all rows added into the pressure row), or
+    (R A_ii)^-1 R (FRS then ABF), which equals A_ii^-1 and leaves Ã_ii = I."""
+    s = tiny(synth, 4, 3, 3, 4, seed=9)
+    A = oracle.assemble(s)
+    vt, dinv = oracle.decouple(A, mode)
+    b = s.b
+    R = np.eye(b)
+    R[0, :] = 1.0
+    rows = A.row_of_block()
+    if mode == "none":
+        np.testing.assert_array_equal(vt, A.val)
+        np.testing.assert_array_equal(dinv, np.broadcast_to(np.eye(b), dinv.shape))
+    elif mode == "frs":
+        np.testing.assert_array_equal(dinv, np.broadcast_to(R, dinv.shape))
+        # the pressure row is the column sum; the other rows are untouched
+        np.testing.assert_array_equal(vt[:, 1:, :], A.val[:, 1:, :])
+        np.testing.assert_allclose(vt[:, 0, :], A.val.sum(axis=1), rtol=1e-15,
+                                   atol=1e-15 * np.abs(A.val).max())
+    else:
+        vt_abf, dinv_abf = oracle.decouple(A, "abf")
+        diag = A.col == rows
+        np.testing.assert_array_equal(vt[diag], np.broadcast_to(np.eye(b), vt[diag].shape))
+        np.testing.assert_allclose(vt, vt_abf, rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(dinv, dinv_abf, rtol=1e-9, atol=1e-11 * np.abs(dinv_abf).max())
+    if mode != "frs+abf":
+        np.testing.assert_allclose(np.einsum("prs,pst->prt", dinv[rows], A.val), vt, rtol=1e-14,
+                                   atol=1e-15 * np.abs(A.val).max())
+
+
 def test_pressure_matrix_scalar_case(oracle, synth):
     """For b = 1 the pressure matrix is the Jacobi-scaled matrix D^-1 A."""
     s = tiny(synth, 4, 3, 3, 1, seed=8)
@@ -460,6 +493,36 @@ def test_cpr_right_preconditioner_identity(oracle, synth):
     # CPR(Ã)^-1 u with u = D^-1 (D u):
     Du = np.einsum("irs,is->ir", np.linalg.inv(dinv), Atw.reshape(A.n, A.b)).reshape(-1)
     np.testing.assert_allclose(cpr.apply(Aw), cpr.apply(Du), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("decoupling", ["abf", "none", "frs"])
+@pytest.mark.parametrize("stages", ["fpf", "fp", "pf"])
+def test_cpr_stage_error_propagation(oracle, synth, stages, decoupling):
+    """A multiplicative combination of stages has the product of the stage
+    error operators as its error operator.  With F = ILU(0)(Ã)^-1 and
+    P = Pi_p AMG(A_PP)^-1 Pi_r as dense operators, the preconditioner B of
+    CPR(Ã) satisfies I - B Ã = (I - FÃ)(I - PÃ)(I - FÃ) for FPF,
+    (I - PÃ)(I - FÃ) for FP (F first) and (I - FÃ)(I - PÃ) for PF."""
+    s = tiny(synth, 4, 3, 3, 3, seed=23, n_pairs=1)
+    A = oracle.assemble(s)
+    cpr = oracle.CPR(A, stages=stages, decoupling=decoupling, coarse_max=8)
+    vt, dinv = cpr.decoupled()
+    n, b = A.n, A.b
+    N = n * b
+    At = oracle.BSR(n, b, A.rp, A.col, vt).to_dense()
+    ilu = oracle.BILU0(A, vt, cpr.colours())
+    I = np.eye(N)
+    Fm = np.column_stack([ilu.solve(I[:, k]) for k in range(N)])
+    Pp = np.column_stack([cpr.amg.vcycle(np.eye(n)[:, k]) for k in range(n)])
+    Pm = np.zeros((N, N))
+    Pm[np.ix_(np.arange(n) * b, np.arange(n) * b)] = Pp
+    EF, EP = I - Fm @ At, I - Pm @ At
+    E = {"fpf": EF @ EP @ EF, "fp": EP @ EF, "pf": EF @ EP}[stages]
+    B = (I - E) @ np.linalg.inv(At)
+    v = np.random.default_rng(24).standard_normal(N)
+    f = np.einsum("irs,is->ir", dinv, v.reshape(n, b)).reshape(-1)
+    want = B @ f
+    np.testing.assert_allclose(cpr.apply(v), want, rtol=0, atol=1e-9 * np.abs(want).max())
 
 
 def test_cpr_scalar_reduces_to_ilu_plus_amg(oracle, synth):
