@@ -64,6 +64,10 @@ def parse():
     p.add_argument("--reuse", type=int, default=5)
     p.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoother degree")
+    p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"],
+                   help="outer Krylov method of the timed step")
+    p.add_argument("--no-krylov-compare", action="store_true",
+                   help="skip timing the other Krylov method on the same system")
     return p.parse_args()
 
 
@@ -246,10 +250,11 @@ def run_sequence(args):
             ds.assemble()
             reuse = (k % args.reuse) != 0
             M.update(A, reuse_amg=reuse)
-            _, rf = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+            _, rf = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
             A.transpose(into=AT)
             MT.update(AT, reuse_amg=reuse)
-            lam, _, ra = trs.solve_adjoint(A, AT, MT, g, x, rtol=args.rtol, restart=args.restart)
+            lam, _, ra = trs.solve_adjoint(A, AT, MT, g, x, rtol=args.rtol, restart=args.restart,
+                                           method=args.krylov)
             trs.chain_theta(A, ds.k, ds.M, lam, x, sysm.kvkh, sysm.c_t)
             if record:
                 records.append({"step": k, "amg": "reused" if reuse else "rebuilt",
@@ -272,7 +277,8 @@ def run_sequence(args):
         torch.cuda.synchronize()
     ms = barrier_max(e0.elapsed_time(e1) / args.steps, world)
     if rank == 0:
-        line = {"metric": f"Newton-like sequence of {args.sequence} systems: forward + adjoint CPR-FGMRES total ms",
+        line = {"metric": f"Newton-like sequence of {args.sequence} systems: forward + adjoint CPR-"
+                          f"{args.krylov.upper()} total ms",
                 "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64+f32" if args.precision == "fp32" else "f64", "data": "synthetic",
@@ -312,7 +318,7 @@ def main():
     def step():
         ds.assemble()
         M.update(A, reuse_amg=False)
-        _, res = trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+        _, res = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
         return res
 
     for _ in range(args.warmup):
@@ -348,9 +354,9 @@ def main():
     np.add.at(Ax, rows, np.einsum("prc,pc->pr", Aval, xt.reshape(-1, A.b)[col]))
     host_relres = float(np.linalg.norm(sysm.rhs - Ax.reshape(-1)) / np.linalg.norm(sysm.rhs))
 
-    # Roofline of the dominant kernel, the FGMRES operator block SpMV w = A z
-    # (FP64 values and vectors), timed live over the timed region by events
-    # around each launch.  It is FP64-pipe-bound (ncu: FP64 pipe ~91% busy),
+    # Roofline of the dominant kernel, the Krylov operator block SpMV w = A z
+    # (FP64 values and vectors; with BiCGSTAB fused with its dot products),
+    # timed live over the timed region by events around each launch.  It is FP64-pipe-bound (ncu: FP64 pipe ~91% busy),
     # so it is reported against the FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2
     # flop x 2.07 GHz = 1.259 TFLOP/s; its HBM fraction is given beside it.
     hbm, peak_kind = peaks()
@@ -363,7 +369,29 @@ def main():
     spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     # DRAM traffic per launch from the ncu capture of the 96x96x48 case
     # (434.1 MB for 3,061,224 blocks), scaled by the blocks of this matrix
-    spmv_traffic = 434.135296e6 * nnzb / 3061224.0 if args.workload == "128x128x64_b4" else None
+    spmv_traffic = (434.135296e6 * nnzb / 3061224.0
+                    if args.workload == "128x128x64_b4" and args.krylov == "fgmres" else None)
+    # the other Krylov method on the same system and preconditioner
+    other = None
+    if not args.no_krylov_compare:
+        alt = "bicgstab" if args.krylov == "fgmres" else "fgmres"
+        for _ in range(2):
+            ds.assemble()
+            M.update(A, reuse_amg=False)
+            trs.krylov_solve(alt, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+        torch.cuda.synchronize()
+        ta = []
+        for _ in range(max(1, min(args.steps, 5))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ds.assemble()
+            M.update(A, reuse_amg=False)
+            _, ra = trs.krylov_solve(alt, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ta.append(e0.elapsed_time(e1))
+        other = {"method": alt, "ms_per_step": statistics.median(ta), "solve_ms": ra.stats["ms_solve"],
+                 "iters": ra.stats["iters"], "true_relres": ra.stats["true_relres"]}
     # FP64-preconditioner path on the same system, for the mixed/FP64 comparison
     fp64 = None
     if not args.no_fp64_compare and args.precision == "fp32":
@@ -371,7 +399,7 @@ def main():
         for _ in range(2):
             ds.assemble()
             M64.update(A, reuse_amg=False)
-            _, r64 = trs.fgmres_solve(A, M64, ds.rhs, x, rtol=args.rtol)
+            _, r64 = trs.krylov_solve(args.krylov, A, M64, ds.rhs, x, rtol=args.rtol, restart=args.restart)
         torch.cuda.synchronize()
         t64 = []
         for _ in range(max(1, min(args.steps, 3))):
@@ -379,7 +407,7 @@ def main():
             e0.record(stream)
             ds.assemble()
             M64.update(A, reuse_amg=False)
-            _, r64 = trs.fgmres_solve(A, M64, ds.rhs, x, rtol=args.rtol)
+            _, r64 = trs.krylov_solve(args.krylov, A, M64, ds.rhs, x, rtol=args.rtol, restart=args.restart)
             e1.record(stream)
             torch.cuda.synchronize()
             t64.append(e0.elapsed_time(e1))
@@ -404,7 +432,7 @@ def main():
                 d.copy_(h, non_blocking=True)
             ds.assemble()
             M.update(A, reuse_amg=False)
-            trs.fgmres_solve(A, M, ds.rhs, x, rtol=args.rtol)
+            trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
             hx.copy_(x, non_blocking=True)
 
         e2e_step()
@@ -428,22 +456,25 @@ def main():
                          "scaled to the FP64 path's iteration count", "detail": detail}
 
     if rank == 0:
+        kname = ("k_spmv<4,double,double> (FGMRES operator block SpMV)" if args.krylov == "fgmres" else
+                 "k_bicg_spmv<4,1|2> (BiCGSTAB operator block SpMV fused with its dot products)")
         line = {
-            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if args.krylov == "fgmres" else METRIC.replace("FGMRES", "BiCGSTAB"), "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
                        "unknowns": sysm.n_unknowns,
-                       "precision": "FP32 CPR inside FP64 FGMRES" if args.precision == "fp32" else "FP64",
+                       "krylov": args.krylov,
+                       "precision": "FP32 CPR inside FP64 Krylov" if args.precision == "fp32" else "FP64",
                        "rtol": args.rtol, "restart": args.restart, "cheb_degree": args.cheb_degree,
                        "l2": "inputs larger than L2 (Jacobian inputs 0.9 GB, matrix 0.9 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters": last["iters"], "true_relres": last["true_relres"], "host_true_relres": host_relres,
             "breakdown_ms": {"setup": last["ms_setup"], "solve": last["ms_solve"]},
             "amg_levels": info["n_levels"], "amg_rows": info["level_rows"], "n_colours": info["n_colours"],
-            "fp64_path": fp64,
-            "roofline": {"kernel": "k_spmv<4,double,double> (FGMRES operator block SpMV)", "bound": "alu",
+            "fp64_path": fp64, "other_krylov": other,
+            "roofline": {"kernel": kname, "bound": "alu",
                          "achieved": spmv_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                          "frac": spmv_tflops / fp64_peak_tflops, "traffic": spmv_traffic,
                          "peak_kind": "FP64 unit count x clock (probe measured 1.2548 TFLOP/s)",

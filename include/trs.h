@@ -61,6 +61,29 @@ typedef int32_t trs_status;
 typedef struct trs_bsr trs_bsr;
 typedef struct trs_cpr trs_cpr;
 
+/* CPR stage ordering (trs_cpr_opts.stages), Sec. "Preconditioners".  With
+ * f = D^-1 v, F = block ILU(0) of Ã and P = one AMG V-cycle on A_PP:
+ *   FPF (Algorithm pc-fpf): y = F^-1 f; y += Pi_p P (f - Ã y)_p; z = y + F^-1 (f - Ã y);
+ *   FP:  the first two steps, z = y;
+ *   PF:  y = Pi_p P f_p; z = y + F^-1 (f - Ã y). */
+#define TRS_CPR_FPF 0
+#define TRS_CPR_FP 1
+#define TRS_CPR_PF 2
+
+/* Decoupling D^-1 A (trs_cpr_opts.decoupling), Sec. "Decoupling Methods":
+ *   ABF: D_i = A_ii (Eq. decoupled-abf), inverted by Gauss-Jordan elimination
+ *        with partial row pivoting, which is also the GJE decoupling;
+ *   NONE: D_i = I;
+ *   FRS: D_i^-1 = R, ones in the first row and on the diagonal (Eq.
+ *        decoupled-frs): every equation is added into the pressure row;
+ *   FRS_ABF: the two-stage FRS+ABF, D_i^-1 = (R A_ii)^-1 R.
+ * The dynamic row sum (DRS) of the paper is defined only by citation and is
+ * not offered. */
+#define TRS_DEC_ABF 0
+#define TRS_DEC_NONE 1
+#define TRS_DEC_FRS 2
+#define TRS_DEC_FRS_ABF 3
+
 typedef struct {
   int32_t precision;     /* TRS_FP64 or TRS_FP32_PREC */
   double theta;          /* AMG strength threshold (default 0.08) */
@@ -68,22 +91,31 @@ typedef struct {
   int32_t max_levels;    /* default 12 */
   int32_t cheb_degree;   /* Chebyshev smoother degree (default 2) */
   uint32_t seed;         /* seed of the MIS-2 and colouring priorities */
+  int32_t stages;        /* TRS_CPR_FPF (default), TRS_CPR_FP or TRS_CPR_PF */
+  int32_t decoupling;    /* TRS_DEC_ABF (default), TRS_DEC_NONE, TRS_DEC_FRS, TRS_DEC_FRS_ABF */
 } trs_cpr_opts;
+
+/* Krylov method (trs_solve_opts.method). */
+#define TRS_FGMRES 0        /* restarted flexible GMRES with CGS2 */
+#define TRS_BICGSTAB 1      /* BiCGSTAB (van der Vorst), the solver of the paper's runs */
 
 typedef struct {
   double rtol;           /* stop when ||b - A x||_2 <= rtol ||b||_2 (true FP64 residual) */
-  int32_t restart;       /* Krylov subspace size per cycle, 1..64 (default 30) */
-  int32_t maxit;         /* total iteration limit (default 1000) */
+  int32_t restart;       /* FGMRES subspace size per cycle, 1..64 (default 30) */
+  int32_t maxit;         /* total iteration limit (default 1000; one BiCGSTAB
+                            iteration applies A and M twice) */
   int32_t use_x0;        /* 1: x holds the initial guess; 0: start from x = 0 */
+  int32_t method;        /* TRS_FGMRES (default) or TRS_BICGSTAB: read by
+                            trs_solve_adjoint; the named solve calls set it */
 } trs_solve_opts;
 
 typedef struct {
-  int32_t iters;         /* Arnoldi steps */
+  int32_t iters;         /* Arnoldi steps (FGMRES) or iterations (BiCGSTAB) */
   int32_t restarts;      /* cycles after the first */
   int32_t converged;
   int32_t amg_levels;
   int32_t n_colours;
-  double est_relres;     /* |g_{j+1}| / ||b|| at the last step */
+  double est_relres;     /* recurrence residual / ||b|| at the last step */
   double true_relres;    /* ||b - A x|| / ||b|| of the returned x, FP64 */
   double ms_setup;       /* device time of the last trs_cpr_setup/update */
   double ms_solve;       /* device time of this solve */
@@ -248,8 +280,23 @@ trs_status trs_fgmres_solve_host(const trs_bsr *A, const trs_cpr *M, const doubl
                                  double *x_host, const trs_solve_opts *opts, void *stream,
                                  trs_solve_stats *stats);
 
+/* Solves A x = b by BiCGSTAB right-preconditioned with M: the Krylov
+ * method of every run in the paper (Sec. "Numerical Studies", subsections
+ * "Numerical Performance" and "Scalability").  Same arguments, errors and true-residual test as
+ * trs_fgmres_solve; opts->restart is not used.  A cycle ends when the
+ * recurrence residual meets rtol, or on breakdown (rho = 0 or omega = 0); the
+ * next cycle restarts from the true FP64 residual with r^ = r. */
+trs_status trs_bicgstab_solve(const trs_bsr *A, const trs_cpr *M, const double *b, double *x,
+                              const trs_solve_opts *opts, void *stream, trs_solve_stats *stats);
+
+/* trs_bicgstab_solve with b and x in host memory; the copies are part of
+ * the call. */
+trs_status trs_bicgstab_solve_host(const trs_bsr *A, const trs_cpr *M, const double *b_host,
+                                   double *x_host, const trs_solve_opts *opts, void *stream,
+                                   trs_solve_stats *stats);
+
 /* Adjoint of x = A^-1 b for a loss L(x) with g = dL/dx: solves
- * A^T lambda = g with FGMRES and M_T (a CPR built on A^T, e.g. from
+ * A^T lambda = g with opts->method (FGMRES by default) and M_T (a CPR built on A^T, e.g. from
  * trs_bsr_transpose), so dL/db = lambda; if dA is not NULL it receives
  * dL/dA_ij = -lambda_i x_j^T for every stored block in canonical BSR
  * order.  g, x, lambda, dA: device pointers. */

@@ -289,15 +289,70 @@ __device__ __forceinline__ void bmul(const T (&A)[B * B], const T (&Bm)[B * B], 
     }
 }
 
+// Left factor D_i^-1 of block row i (Sec. "Decoupling Methods"), by mode:
+// ABF: A_ii^-1 (Gauss-Jordan with partial pivoting); NONE: I; FRS: R (ones
+// in the first row and on the diagonal, adding every row into the pressure
+// row); FRS+ABF: (R A_ii)^-1 R, with Ai = (R A_ii)^-1 kept for the blocks.
 template <int B>
-__global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_ell, double *at_tval,
+__device__ __forceinline__ void frs_matrix(double (&R)[B * B]) {
+#pragma unroll
+  for (int r = 0; r < B; r++)
+#pragma unroll
+    for (int c = 0; c < B; c++) R[r * B + c] = (r == 0 || r == c) ? 1.0 : 0.0;
+}
+
+template <int B>
+__device__ bool decoupling_factor(int mode, const double (&D)[B * B], double (&Dm)[B * B], double (&Ai)[B * B]) {
+  constexpr int BB = B * B;
+  if (mode == TRS_DEC_NONE) {
+#pragma unroll
+    for (int e = 0; e < BB; e++) Dm[e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+    return true;
+  }
+  if (mode == TRS_DEC_FRS) {
+    frs_matrix<B>(Dm);
+    return true;
+  }
+  if (mode == TRS_DEC_FRS_ABF) {
+    double R[BB], Rd[BB];
+    frs_matrix<B>(R);
+    bmul<B>(R, D, Rd);
+    if (!gj_inverse<B>(Rd, Ai)) return false;
+    bmul<B>(Ai, R, Dm);
+    return true;
+  }
+  return gj_inverse<B>(D, Dm);
+}
+
+// Ã_ij = D_i^-1 A_ij; for FRS+ABF in the order of the two stages, Ai (R A_ij).
+template <int B>
+__device__ __forceinline__ void decouple_block(int mode, const double (&Dm)[B * B], const double (&Ai)[B * B],
+                                               const double (&blk)[B * B], double (&out)[B * B]) {
+  if (mode == TRS_DEC_FRS_ABF) {
+    double R[B * B], Rb[B * B];
+    frs_matrix<B>(R);
+    bmul<B>(R, blk, Rb);
+    bmul<B>(Ai, Rb, out);
+  } else {
+    bmul<B>(Dm, blk, out);
+  }
+}
+
+__device__ __forceinline__ bool unit_diagonal(int mode) { return mode == TRS_DEC_ABF || mode == TRS_DEC_FRS_ABF; }
+
+// Decoupling of one block row per thread: D_i^-1 ([bb][n]), Ã = D^-1 A in
+// the ELL/tail layout of A (diagonal exactly I for ABF and FRS+ABF), and
+// the pressure entries (Ã_ij)_00.
+template <int B>
+__global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, double *at_ell, double *at_tval,
                            double *dinv, double *ap_ell, double *ap_tval, int *err) {
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t nc = A.g.nc, n = A.g.n_rows;
   if (i >= n) return;
-  double D[BB], Di[BB], blk[BB], out[BB];
+  double D[BB], Dm[BB], Ai[BB], blk[BB], out[BB];
   const bool cell = i < nc;
+  const bool unit = unit_diagonal(mode);
   const int64_t dtail = cell ? -1 : tdiag[i - nc];
   if (cell) {
 #pragma unroll
@@ -306,17 +361,17 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_e
 #pragma unroll
     for (int e = 0; e < BB; e++) D[e] = A.tval[dtail * BB + e];
   }
-  if (!gj_inverse<B>(D, Di)) {
+  if (!decoupling_factor<B>(mode, D, Dm, Ai)) {
     atomicExch(err, 1);
     return;
   }
 #pragma unroll
-  for (int e = 0; e < BB; e++) dinv[(int64_t)e * n + i] = Di[e];
+  for (int e = 0; e < BB; e++) dinv[(int64_t)e * n + i] = Dm[e];
   if (cell) {
     const unsigned m = A.emask[i];
     for (int s = 0; s < kSlots; s++) {
       if (!((m >> s) & 1u)) continue;
-      if (s == kSelf) {
+      if (s == kSelf && unit) {
 #pragma unroll
         for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = (e % (B + 1) == 0) ? 1.0 : 0.0;
         ap_ell[(int64_t)s * nc + i] = 1.0;
@@ -324,14 +379,14 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_e
       }
 #pragma unroll
       for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
-      bmul<B>(Di, blk, out);
+      decouple_block<B>(mode, Dm, Ai, blk, out);
 #pragma unroll
       for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = out[e];
       ap_ell[(int64_t)s * nc + i] = out[0];
     }
   }
   for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
-    if (t == dtail) {
+    if (t == dtail && unit) {
 #pragma unroll
       for (int e = 0; e < BB; e++) at_tval[t * BB + e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
       ap_tval[t] = 1.0;
@@ -339,7 +394,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_e
     }
 #pragma unroll
     for (int e = 0; e < BB; e++) blk[e] = A.tval[t * BB + e];
-    bmul<B>(Di, blk, out);
+    decouple_block<B>(mode, Dm, Ai, blk, out);
 #pragma unroll
     for (int e = 0; e < BB; e++) at_tval[t * BB + e] = out[e];
     ap_tval[t] = out[0];
@@ -348,18 +403,20 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, double *at_e
 
 // The same decoupling for the FP32 preconditioner: D_i^-1 and the pressure
 // entries (Ã_ij)_00 are formed in FP64 exactly as above (they decide the
-// aggregates); the blocks Ã_ij = D_i^-1 A_ij and D_i^-1 are stored in FP32,
-// the product taken in FP32.
+// aggregates); the blocks Ã_ij and D_i^-1 are stored in FP32, the product
+// taken in FP32 (for FRS+ABF: Ai in FP32 times R A_ij formed in FP64).
 template <int B>
-__global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, float *at_ell, float *at_tval,
+__global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mode, float *at_ell, float *at_tval,
                                  float *dinv, double *ap_ell, double *ap_tval, int *err) {
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t nc = A.g.nc, n = A.g.n_rows;
   if (i >= n) return;
-  double D[BB], Di[BB];
-  float Df[BB], bf[BB], of[BB];
+  double D[BB], Dm[BB], Ai[BB], L[BB], blk[BB];
+  float Lf[BB], bf[BB], of[BB];
   const bool cell = i < nc;
+  const bool unit = unit_diagonal(mode);
+  const bool two_stage = mode == TRS_DEC_FRS_ABF;
   const int64_t dtail = cell ? -1 : tdiag[i - nc];
   if (cell) {
 #pragma unroll
@@ -368,55 +425,63 @@ __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, float 
 #pragma unroll
     for (int e = 0; e < BB; e++) D[e] = A.tval[dtail * BB + e];
   }
-  if (!gj_inverse<B>(D, Di)) {
+  if (!decoupling_factor<B>(mode, D, Dm, Ai)) {
     atomicExch(err, 1);
     return;
   }
 #pragma unroll
   for (int e = 0; e < BB; e++) {
-    Df[e] = (float)Di[e];
-    dinv[(int64_t)e * n + i] = Df[e];
+    dinv[(int64_t)e * n + i] = (float)Dm[e];
+    L[e] = two_stage ? Ai[e] : Dm[e];
+    Lf[e] = (float)L[e];
   }
-  // (D^-1 A)_00: first product then running sum over the inner index
-  auto p00 = [&](const double *blk, int64_t stride) {
-    double acc = Di[0] * blk[0];
+  // (Ã_ij)_00 in FP64 (first product, then a running sum over the inner
+  // index) and the FP32 block
+  auto one = [&](float *dst, int64_t dstride, double *pdst) {
+    double src[BB];
+    if (two_stage) {
+      double R[BB];
+      frs_matrix<B>(R);
+      bmul<B>(R, blk, src);
+    } else {
 #pragma unroll
-    for (int t = 1; t < B; t++) acc = acc + Di[t] * blk[(int64_t)(t * B) * stride];
-    return acc;
+      for (int e = 0; e < BB; e++) src[e] = blk[e];
+    }
+    double acc = L[0] * src[0];
+#pragma unroll
+    for (int t = 1; t < B; t++) acc = acc + L[t] * src[t * B];
+    *pdst = acc;
+#pragma unroll
+    for (int e = 0; e < BB; e++) bf[e] = (float)src[e];
+    bmul<B, float>(Lf, bf, of);
+#pragma unroll
+    for (int e = 0; e < BB; e++) dst[(int64_t)e * dstride] = of[e];
   };
   if (cell) {
     const unsigned m = A.emask[i];
     for (int s = 0; s < kSlots; s++) {
       if (!((m >> s) & 1u)) continue;
-      if (s == kSelf) {
+      if (s == kSelf && unit) {
 #pragma unroll
         for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = (e % (B + 1) == 0) ? 1.f : 0.f;
         ap_ell[(int64_t)s * nc + i] = 1.0;
         continue;
       }
-      const double *blk = A.ell + ((int64_t)s * BB) * nc + i;
-      ap_ell[(int64_t)s * nc + i] = p00(blk, nc);
 #pragma unroll
-      for (int e = 0; e < BB; e++) bf[e] = (float)blk[(int64_t)e * nc];
-      bmul<B, float>(Df, bf, of);
-#pragma unroll
-      for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = of[e];
+      for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
+      one(at_ell + ((int64_t)s * BB) * nc + i, nc, ap_ell + (int64_t)s * nc + i);
     }
   }
   for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
-    if (t == dtail) {
+    if (t == dtail && unit) {
 #pragma unroll
       for (int e = 0; e < BB; e++) at_tval[t * BB + e] = (e % (B + 1) == 0) ? 1.f : 0.f;
       ap_tval[t] = 1.0;
       continue;
     }
-    const double *blk = A.tval + t * BB;
-    ap_tval[t] = p00(blk, 1);
 #pragma unroll
-    for (int e = 0; e < BB; e++) bf[e] = (float)blk[e];
-    bmul<B, float>(Df, bf, of);
-#pragma unroll
-    for (int e = 0; e < BB; e++) at_tval[t * BB + e] = of[e];
+    for (int e = 0; e < BB; e++) blk[e] = A.tval[t * BB + e];
+    one(at_tval + t * BB, 1, ap_tval + t);
   }
 }
 
@@ -502,35 +567,50 @@ __global__ void k_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state) {
   state[i] = sdeg[i] > 0 ? kUndecided : kOut;
 }
 
-// out_i = max over {i} U strong(i) of the tuple (state, key); in_k == nullptr
-// means key = node_key(index)
-__global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
-                             const int8_t *in_s, const uint64_t *in_k, uint32_t seed, int8_t *out_s,
-                             uint64_t *out_k) {
-  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  if (i >= n) return;
-  int8_t ms = in_s[i];
-  uint64_t mk = in_k ? in_k[i] : node_key(i, seed);
-  for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
-    if (!sflag[p]) continue;
-    const int64_t j = col[p];
-    const int8_t s = in_s[j];
-    const uint64_t k = in_k ? in_k[j] : node_key(j, seed);
-    if (s > ms || (s == ms && k > mk)) { ms = s; mk = k; }
-  }
-  out_s[i] = ms;
-  out_k[i] = mk;
+// The tuple (state, key) with key = fmix32(i ^ seed) << 32 | i, packed into
+// one word as state << 62 | fmix32(i ^ seed) << 30 | i (i < 2^30): word order
+// is the tuple order, so one 64-bit maximum replaces the tuple comparison.
+__device__ __forceinline__ uint64_t mis2_word(int8_t state, int64_t i, uint32_t seed) {
+  return ((uint64_t)(uint8_t)state << 62) | ((uint64_t)fmix32((uint32_t)i ^ seed) << 30) | (uint64_t)i;
 }
 
-__global__ void k_mis2_decide(int64_t n, uint32_t seed, const int8_t *t2s, const uint64_t *t2k, int8_t *state,
+// out_i = max over {i} U strong(i) of the packed tuple; the first sweep
+// forms the words from the states (in_w == nullptr), the second reads the
+// first sweep's words.  Entries are read eight at a time so that their
+// gathers are in flight together (the maximum does not depend on order).
+__global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
+                             const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  uint64_t best = in_w ? in_w[i] : mis2_word(state[i], i, seed);
+  const int64_t e = rp[i + 1];
+  for (int64_t p0 = rp[i]; p0 < e; p0 += 8) {
+    int32_t jj[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int64_t p = p0 + u;
+      jj[u] = (p < e && sflag[p]) ? col[p] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      if (jj[u] < 0) continue;
+      const uint64_t w = in_w ? in_w[jj[u]] : mis2_word(state[jj[u]], jj[u], seed);
+      best = w > best ? w : best;
+    }
+  }
+  out_w[i] = best;
+}
+
+__global__ void k_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state,
                               unsigned long long *undecided) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   const int8_t s = state[i];
   if (s != kUndecided) return;
-  if (t2s[i] == s && t2k[i] == node_key(i, seed)) {
+  const uint64_t w = t2w[i];
+  if (w == mis2_word(kUndecided, i, seed)) {
     state[i] = kIn;
-  } else if (t2s[i] == kIn) {
+  } else if ((int8_t)(w >> 62) == kIn) {
     state[i] = kOut;
   } else {
     atomicAdd(undecided, 1ull);
@@ -633,18 +713,44 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
   const int64_t I = blockIdx.x * (int64_t)kWarps + wid;
   if (I >= na) return;
   const int64_t m0 = mptr[I], m1 = mptr[I + 1];
-  // stage
+  // stage, 32 members at a time: the lanes read the members' row extents
+  // together, a warp scan gives each member's offset, and every lane then
+  // fills the pairs q = lane, lane + 32, ... of the flattened (member,
+  // entry) order, so the loads of all members are in flight at once
   int total = 0;
   bool staged = true;
-  for (int64_t t = m0; t < m1; t++) {
-    const int64_t i = midx[t];
-    const int64_t p0 = rp[i], len = rp[i + 1] - p0;
-    if (total + len > kGalCap) { staged = false; break; }
-    for (int64_t k = lane; k < len; k += 32) {
-      sJ[wid][total + k] = agg[col[p0 + k]];
-      sV[wid][total + k] = val[p0 + k];
+  for (int64_t t0 = m0; t0 < m1; t0 += 32) {
+    const int nm = (int)(m1 - t0 < 32 ? m1 - t0 : 32);
+    int64_t p0 = 0;
+    int len = 0;
+    if (lane < nm) {
+      const int64_t i = midx[t0 + lane];
+      p0 = rp[i];
+      len = (int)(rp[i + 1] - p0);
     }
-    total += (int)len;
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int ctot = __shfl_sync(0xffffffffu, inc, 31);
+    if (total + ctot > kGalCap) { staged = false; break; }
+    const int excl = inc - len;
+    for (int q0 = 0; q0 < ctot; q0 += 32) {
+      const int q = q0 + lane;
+      int m = 0;
+      for (int mm = 1; mm < nm; mm++)
+        if (__shfl_sync(0xffffffffu, excl, mm) <= q) m = mm;
+      const int64_t pm = __shfl_sync(0xffffffffu, p0, m);
+      const int em = __shfl_sync(0xffffffffu, excl, m);
+      if (q < ctot) {
+        const int64_t p = pm + (q - em);
+        sJ[wid][total + q] = agg[col[p]];
+        sV[wid][total + q] = val[p];
+      }
+    }
+    total += ctot;
   }
   __syncwarp();
   if (!staged) {  // handled by k_galerkin_long
@@ -819,16 +925,34 @@ __global__ void __launch_bounds__(kThreads) k_galerkin_long(const int64_t *rp, c
 }
 
 // ----------------------------------------------------- smoother set-up
+// The maximum is taken on the bit patterns of the non-negative q_i (the
+// same order as their values), first within the block, then with one
+// atomic per block.
 __global__ void k_gershgorin(int64_t n, const int64_t *rp, const double *val, const int64_t *dpos,
                              double *dinv, unsigned long long *lam_bits) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = s + fabs(val[p]);
-  const double d = dpos[i] < 0 ? 0.0 : val[dpos[i]];
-  const double q = s / fabs(d);
-  dinv[i] = 1.0 / d;
-  atomicMax(lam_bits, (unsigned long long)__double_as_longlong(q));
+  unsigned long long qb = 0ull;
+  if (i < n) {
+    double s = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = s + fabs(val[p]);
+    const double d = dpos[i] < 0 ? 0.0 : val[dpos[i]];
+    const double q = s / fabs(d);
+    dinv[i] = 1.0 / d;
+    qb = (unsigned long long)__double_as_longlong(q);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, qb, o);
+    qb = other > qb ? other : qb;
+  }
+  __shared__ unsigned long long sm[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = qb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = sm[0];
+    for (int w = 1; w < kThreads / 32; w++) m = sm[w] > m ? sm[w] : m;
+    atomicMax(lam_bits, m);
+  }
 }
 
 // ------------------------------------------------- coarsest dense solve
@@ -1131,8 +1255,7 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
 #pragma unroll
       for (int e = 0; e < BB; e++) {
         T v = T(0);
-        if (s == kSelf) v = (e % (B + 1) == 0) ? T(1) : T(0);
-        else if ((m >> s) & 1u) v = at_ell[((int64_t)s * BB + e) * g.nc + i];
+        if ((m >> s) & 1u) v = at_ell[((int64_t)s * BB + e) * g.nc + i];
         fell[((int64_t)s * BB + e) * np + q] = v;
       }
     }
@@ -1456,19 +1579,19 @@ void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, dou
   TRS_LAUNCHED();
 }
 
-void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, double *at_ell, double *at_tval,
-                     double *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
+void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, int mode, double *at_ell,
+                     double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
   if (!A.g.n_rows) return;
-  TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, at_ell, at_tval, dinv,
+  TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_tval, dinv,
                                                                            ap_ell, ap_tval, err));
   TRS_LAUNCHED();
 }
 
-void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, float *at_ell, float *at_tval,
-                           float *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
+void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, int mode, float *at_ell,
+                           float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
   if (!A.g.n_rows) return;
-  TRS_DISPATCH_B(b, k_decouple_mixed<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, at_ell, at_tval, dinv,
-                                                                                 ap_ell, ap_tval, err));
+  TRS_DISPATCH_B(b, k_decouple_mixed<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_tval,
+                                                                                 dinv, ap_ell, ap_tval, err));
   TRS_LAUNCHED();
 }
 
@@ -1502,15 +1625,16 @@ void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_
   TRS_LAUNCHED();
 }
 
-void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int8_t *in_s,
-                       const uint64_t *in_k, uint32_t seed, int8_t *out_s, uint64_t *out_k, cudaStream_t s) {
-  k_mis2_sweep<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, sflag, in_s, in_k, seed, out_s, out_k);
+void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int8_t *state,
+                       const uint64_t *in_w, uint32_t seed, uint64_t *out_w, cudaStream_t s) {
+  if (n >= (int64_t(1) << 30)) throw Error(TRS_ERR_UNSUPPORTED, "AMG levels are limited to 2^30 rows");
+  k_mis2_sweep<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, sflag, state, in_w, seed, out_w);
   TRS_LAUNCHED();
 }
 
-void launch_mis2_decide(int64_t n, uint32_t seed, const int8_t *t2s, const uint64_t *t2k, int8_t *state,
-                        unsigned long long *undecided, cudaStream_t s) {
-  k_mis2_decide<<<grid_of(n), kThreads, 0, s>>>(n, seed, t2s, t2k, state, undecided);
+void launch_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state, unsigned long long *undecided,
+                        cudaStream_t s) {
+  k_mis2_decide<<<grid_of(n), kThreads, 0, s>>>(n, seed, t2w, state, undecided);
   TRS_LAUNCHED();
 }
 

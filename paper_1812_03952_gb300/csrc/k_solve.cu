@@ -58,6 +58,18 @@ __device__ __forceinline__ void store_blk(T *p, const T (&v)[B]) {
   }
 }
 
+// y2_j = y1_j + Pi_p e0_j (y1 = NULL: zero)
+template <int B, class T>
+__device__ __forceinline__ void load_y2(const T *__restrict__ y1, const T *__restrict__ e0, int64_t j, T (&v)[B]) {
+  if (y1) {
+    load_blk<B>(y1 + j * B, v);
+  } else {
+#pragma unroll
+    for (int c = 0; c < B; c++) v[c] = T(0);
+  }
+  v[0] = v[0] + e0[j];
+}
+
 // ------------------------------------------------------------ block SpMV
 template <int B, class TA, class TX>
 __device__ __forceinline__ void cell_row_apply(const MatView<TA> &A, int64_t i, const TX *__restrict__ x,
@@ -384,8 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
   store_blk<B>(y + i * B, xv);
   if (zout) {
     T zb[B];
-    load_blk<B>(y1 + i * B, zb);
-    zb[0] = zb[0] + e0[i];
+    load_y2<B>(y1, e0, i, zb);
     TZ zo[B];
 #pragma unroll
     for (int r = 0; r < B; r++) zo[r] = static_cast<TZ>(zb[r] + xv[r]);
@@ -398,14 +409,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__restrict__ f,
                                                       const T *__restrict__ y, T *__restrict__ rp,
-                                                      int64_t cell_blocks) {
+                                                      int64_t cell_blocks, int unit) {
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
     if (i >= At.g.nc) return;
     const int64_t nc = At.g.nc;
-    T acc = y[i * B];
-    const unsigned m = At.emask[i] & ~(1u << kSelf);
+    T acc = unit ? y[i * B] : T(0);
+    const unsigned m = At.emask[i] & (unit ? ~(1u << kSelf) : ~0u);
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (!((m >> s) & 1u)) continue;
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
     }
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];
-      if (j == i) continue;
+      if (unit && j == i) continue;
       const T *blk = At.tval + t * BB;
 #pragma unroll
       for (int c = 0; c < B; c++) acc = fma(blk[c], y[j * B + c], acc);
@@ -429,13 +440,13 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
     double acc = 0.0;
     for (int64_t t = At.tptr[i] + lane; t < At.tptr[i + 1]; t += 32) {
       const int64_t j = At.tcol[t];
-      if (j == i) continue;
+      if (unit && j == i) continue;
       const T *blk = At.tval + t * BB;
 #pragma unroll
       for (int c = 0; c < B; c++) acc = fma(to_d(blk[c]), to_d(y[j * B + c]), acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) rp[i] = static_cast<T>(to_d(f[i * B]) - (to_d(y[i * B]) + acc));
+    if (lane == 0) rp[i] = static_cast<T>(to_d(f[i * B]) - ((unit ? to_d(y[i * B]) : 0.0) + acc));
   }
 }
 
@@ -443,23 +454,26 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T *__restrict__ f,
                                                          const T *__restrict__ y1, const T *__restrict__ e0,
-                                                         T *__restrict__ r, int64_t cell_blocks) {
+                                                         T *__restrict__ r, int64_t cell_blocks, int unit) {
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
     if (i >= At.g.nc) return;
     const int64_t nc = At.g.nc;
     T acc[B];
-    load_blk<B>(y1 + i * B, acc);
-    acc[0] = acc[0] + e0[i];
-    const unsigned m = At.emask[i] & ~(1u << kSelf);
+    if (unit) {
+      load_y2<B>(y1, e0, i, acc);
+    } else {
+#pragma unroll
+      for (int c = 0; c < B; c++) acc[c] = T(0);
+    }
+    const unsigned m = At.emask[i] & (unit ? ~(1u << kSelf) : ~0u);
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (!((m >> s) & 1u)) continue;
       const int64_t j = i + At.g.off[s];
       T yj[B];
-      load_blk<B>(y1 + j * B, yj);
-      yj[0] = yj[0] + e0[j];
+      load_y2<B>(y1, e0, j, yj);
       const T *blk = At.ell + (int64_t)s * BB * nc + i;
 #pragma unroll
       for (int rr = 0; rr < B; rr++)
@@ -468,10 +482,10 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
     }
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];
-      if (j == i) continue;
+      if (unit && j == i) continue;
       T yj[B];
 #pragma unroll
-      for (int c = 0; c < B; c++) yj[c] = y1[j * B + c];
+      for (int c = 0; c < B; c++) yj[c] = y1 ? y1[j * B + c] : T(0);
       yj[0] = yj[0] + e0[j];
       const T *blk = At.tval + t * BB;
 #pragma unroll
@@ -491,11 +505,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
     double acc[B] = {};
     for (int64_t t = At.tptr[i] + lane; t < At.tptr[i + 1]; t += 32) {
       const int64_t j = At.tcol[t];
-      if (j == i) continue;
+      if (unit && j == i) continue;
       const T *blk = At.tval + t * BB;
 #pragma unroll
       for (int c = 0; c < B; c++) {
-        double yj = to_d(y1[j * B + c]);
+        double yj = y1 ? to_d(y1[j * B + c]) : 0.0;
         if (c == 0) yj += to_d(e0[j]);
 #pragma unroll
         for (int rr = 0; rr < B; rr++) acc[rr] = fma(to_d(blk[rr * B + c]), yj, acc[rr]);
@@ -506,8 +520,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
     if (lane == 0)
 #pragma unroll
       for (int rr = 0; rr < B; rr++) {
-        double own = to_d(y1[i * B + rr]);
-        if (rr == 0) own += to_d(e0[i]);
+        double own = 0.0;
+        if (unit) {
+          own = y1 ? to_d(y1[i * B + rr]) : 0.0;
+          if (rr == 0) own += to_d(e0[i]);
+        }
         r[i * B + rr] = static_cast<T>(to_d(f[i * B + rr]) - (own + acc[rr]));
       }
   }
@@ -876,6 +893,243 @@ __global__ void k_cast(const TS *__restrict__ a, TD *__restrict__ b, int64_t n) 
     b[i] = static_cast<TD>(a[i]);
 }
 
+// ----------------------------------------- CPR-FP / CPR-PF pieces
+// z = y1 + Pi_p e0 in FP64 (the last step of CPR-FP)
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_cpr_combine(int64_t n, const T *__restrict__ y1,
+                                                          const T *__restrict__ e0, double *__restrict__ z) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  T v[B];
+  load_y2<B>(y1, e0, i, v);
+  double o[B];
+#pragma unroll
+  for (int c = 0; c < B; c++) o[c] = to_d(v[c]);
+  store_blk<B>(z + i * B, o);
+}
+
+// rp = Pi_r f, the pressure entries (the first step of CPR-PF)
+template <class T>
+__global__ void k_pressure_of(int64_t n, int b, const T *__restrict__ f, T *__restrict__ rp) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i < n) rp[i] = f[i * b];
+}
+
+// ------------------------------------------------------------- BiCGSTAB
+// The recurrences of van der Vorst's BiCGSTAB, right-preconditioned: the
+// scalars (rho, alpha, omega, ...) stay in device memory, written by the
+// last block of each reduction and read by the next kernel, so an iteration
+// synchronises with the host once.
+
+// Sums K partials per block in block order; true in the last block to
+// arrive, where every thread holds the K sums.
+template <int K>
+__device__ __forceinline__ bool last_block_sums(const double *partial, unsigned int *counter, double (&sum)[K]) {
+  __shared__ bool is_last;
+  __shared__ double sm[kWarps];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  for (int k = 0; k < K; k++) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) s += __ldcg(partial + (int64_t)b * kRedStride + k);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kWarps; w++) t += sm[w];
+    sum[k] = t;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// (Re)start from the true residual r (r^ = r): rho = <r^, r> = ||r||^2.
+__global__ void k_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double rtol) {
+  sc->rho = rr[0];
+  sc->rho_old = 1.0;
+  sc->alpha = 1.0;
+  sc->omega = 1.0;
+  sc->rr = rr[0];
+  sc->half = 0.0;
+  sc->bnorm = bnorm;
+  sc->rtol = rtol;
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_old)(alpha / omega), or p = r
+// on the first step of a cycle; then f = D^-1 p, the input of CPR.
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_bicg_dir(int64_t n, const double *__restrict__ r,
+                                                       const double *__restrict__ v, double *__restrict__ p,
+                                                       const BicgScalars *__restrict__ sc, int first,
+                                                       const T *__restrict__ dinv, T *__restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= n) return;
+  double rv[B], pv[B];
+  load_blk<B>(r + i * B, rv);
+  if (first) {
+#pragma unroll
+    for (int c = 0; c < B; c++) pv[c] = rv[c];
+  } else {
+    const double beta = (sc->rho / sc->rho_old) * (sc->alpha / sc->omega), om = sc->omega;
+    double vv[B];
+    load_blk<B>(v + i * B, vv);
+    load_blk<B>(p + i * B, pv);
+#pragma unroll
+    for (int c = 0; c < B; c++) pv[c] = rv[c] + beta * (pv[c] - om * vv[c]);
+  }
+  store_blk<B>(p + i * B, pv);
+#pragma unroll
+  for (int rr = 0; rr < B; rr++) {
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) acc = fma(dinv[(int64_t)(rr * B + c) * n + i], static_cast<T>(pv[c]), acc);
+    f[i * B + rr] = acc;
+  }
+}
+
+// y = A x with <w, y> (ND = 1) or <w, y>, <y, y> (ND = 2), one thread per
+// cell row (blocks [0, cell_blocks)) and one warp per long row (the rest),
+// as k_spmv.  Each block stores its ND partial sums at part[block * ND]; the
+// last block sums them in block order and sets alpha = rho / <r^, v> (ND = 1:
+// x = p^, y = v, w = r^) or omega = <t, s> / <t, t> (ND = 2: x = s^, y = t,
+// w = s).
+template <int B, int ND>
+__global__ void __launch_bounds__(kThreads) k_bicg_spmv(MatView<double> A, const double *__restrict__ x,
+                                                        double *__restrict__ y, const double *__restrict__ w,
+                                                        int64_t cell_blocks, double *part, unsigned int *counter,
+                                                        BicgScalars *sc) {
+  double acc2[ND] = {};
+  if (blockIdx.x < cell_blocks) {
+    const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (i < A.g.nc) {
+      double acc[B] = {};
+      cell_row_apply<B>(A, i, x, acc);
+      store_blk<B>(y + i * B, acc);
+      double wv[B];
+      load_blk<B>(w + i * B, wv);
+#pragma unroll
+      for (int r = 0; r < B; r++) {
+        acc2[0] = fma(wv[r], acc[r], acc2[0]);
+        if constexpr (ND == 2) acc2[1] = fma(acc[r], acc[r], acc2[1]);
+      }
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = A.g.nc + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
+    if (i < A.g.n_rows) {
+      double acc[B] = {};
+      long_row_apply<B>(A, i, x, acc, lane);
+      if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < B; r++) {
+          y[i * B + r] = acc[r];
+          acc2[0] = fma(w[i * B + r], acc[r], acc2[0]);
+          if constexpr (ND == 2) acc2[1] = fma(acc[r], acc[r], acc2[1]);
+        }
+    }
+  }
+  // block sums (fixed shuffle pattern, warps in order)
+  __shared__ double sm[kWarps][ND];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < ND; k++) {
+    const double v = warp_sum(acc2[k]);
+    if (lane == 0) sm[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ND) {
+    double t = 0.0;
+    for (int q = 0; q < kWarps; q++) t += sm[q][threadIdx.x];
+    part[(int64_t)blockIdx.x * ND + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  __shared__ double tot[kWarps][ND];
+  double t[ND] = {};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads)
+#pragma unroll
+    for (int k = 0; k < ND; k++) t[k] += __ldcg(part + (int64_t)b * ND + k);
+#pragma unroll
+  for (int k = 0; k < ND; k++) {
+    const double v = warp_sum(t[k]);
+    if (lane == 0) tot[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum[ND];
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      sum[k] = 0.0;
+      for (int q = 0; q < kWarps; q++) sum[k] += tot[q][k];
+    }
+    if constexpr (ND == 1) {
+      sc->rv = sum[0];
+      sc->alpha = sc->rho / sum[0];
+    } else {
+      sc->ts = sum[0];
+      sc->tt = sum[1];
+      sc->omega = sum[1] > 0.0 ? sum[0] / sum[1] : 0.0;
+    }
+    *counter = 0u;
+  }
+}
+
+// s = r - alpha v and ||s||^2; the last block flags ||s|| <= rtol ||b||.
+__global__ void __launch_bounds__(kThreads) k_bicg_s(int64_t N, const double *__restrict__ r,
+                                                     const double *__restrict__ v, double *__restrict__ s,
+                                                     double *partial, unsigned int *counter, BicgScalars *sc) {
+  const double alpha = sc->alpha;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+    const double si = r[i] - alpha * v[i];
+    s[i] = si;
+    acc[0] = fma(si, si, acc[0]);
+  }
+  block_partial<1>(acc, partial + (int64_t)blockIdx.x * kRedStride);
+  double sum[1];
+  if (!last_block_sums<1>(partial, counter, sum)) return;
+  if (threadIdx.x == 0) {
+    sc->ss = sum[0];
+    sc->half = (sqrt(sum[0]) / sc->bnorm <= sc->rtol) ? 1.0 : 0.0;
+  }
+}
+
+// x += alpha p^ + omega s^, r = s - omega t (omega taken as 0 when ||s|| met
+// the tolerance); ||r||^2 and the next rho = <r^, r>.
+__global__ void __launch_bounds__(kThreads) k_bicg_xr(int64_t N, const double *__restrict__ ph,
+                                                      const double *__restrict__ sh, const double *__restrict__ s,
+                                                      const double *__restrict__ t, const double *__restrict__ rh,
+                                                      double *__restrict__ x, double *__restrict__ r,
+                                                      double *partial, unsigned int *counter, BicgScalars *sc) {
+  const double alpha = sc->alpha, omega = sc->half != 0.0 ? 0.0 : sc->omega;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+    x[i] = x[i] + alpha * ph[i] + omega * sh[i];
+    const double ri = s[i] - omega * t[i];
+    r[i] = ri;
+    acc[0] = fma(ri, ri, acc[0]);
+    acc[1] = fma(rh[i], ri, acc[1]);
+  }
+  block_partial<2>(acc, partial + (int64_t)blockIdx.x * kRedStride);
+  double sum[2];
+  if (!last_block_sums<2>(partial, counter, sum)) return;
+  if (threadIdx.x == 0) {
+    sc->rr = sum[0];
+    sc->rho_old = sc->rho;
+    sc->rho = sum[1];
+  }
+}
+
 inline unsigned grid_of(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -934,19 +1188,33 @@ void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, in
 }
 
 template <class T>
-void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, cudaStream_t s) {
+void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, int unit, cudaStream_t s) {
   const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_resid_p<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y, rp, cb));
+  TRS_DISPATCH_B(b, k_resid_p<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y, rp, cb, unit));
   TRS_LAUNCHED();
 }
 
 template <class T>
-void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r,
+void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r, int unit,
                        cudaStream_t s) {
   const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_resid_full<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y1, e0, r, cb));
+  TRS_DISPATCH_B(b, k_resid_full<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y1, e0, r, cb, unit));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_cpr_combine(int b, int64_t n, const T *y1, const T *e0, double *z, cudaStream_t s) {
+  if (!n) return;
+  TRS_DISPATCH_B(b, k_cpr_combine<B, T><<<grid_of(n), kThreads, 0, s>>>(n, y1, e0, z));
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_pressure_of(int b, int64_t n, const T *f, T *rp, cudaStream_t s) {
+  if (!n) return;
+  k_pressure_of<T><<<grid_of(n), kThreads, 0, s>>>(n, b, f, rp);
   TRS_LAUNCHED();
 }
 
@@ -1060,6 +1328,49 @@ void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
   TRS_LAUNCHED();
 }
 
+void launch_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double rtol, cudaStream_t s) {
+  k_bicg_start<<<1, 1, 0, s>>>(sc, rr, bnorm, rtol);
+  TRS_LAUNCHED();
+}
+
+template <class T>
+void launch_bicg_dir(int b, int64_t n, const double *r, const double *v, double *p, const BicgScalars *sc,
+                     int first, const T *dinv, T *f, cudaStream_t s) {
+  if (!n) return;
+  TRS_DISPATCH_B(b, k_bicg_dir<B, T><<<grid_of(n), kThreads, 0, s>>>(n, r, v, p, sc, first, dinv, f));
+  TRS_LAUNCHED();
+}
+template void launch_bicg_dir<double>(int, int64_t, const double *, const double *, double *, const BicgScalars *,
+                                      int, const double *, double *, cudaStream_t);
+template void launch_bicg_dir<float>(int, int64_t, const double *, const double *, double *, const BicgScalars *,
+                                     int, const float *, float *, cudaStream_t);
+
+int64_t bicg_spmv_blocks(const Geom &g) { return cell_blocks_of(g.nc) + long_blocks_of(g.n_rows - g.nc); }
+
+void launch_bicg_spmv(int b, const MatView<double> &A, const double *x, double *y, const double *w, int nd,
+                      double *part, unsigned int *counter, BicgScalars *sc, cudaStream_t s) {
+  const int64_t cb = cell_blocks_of(A.g.nc), nb = bicg_spmv_blocks(A.g);
+  if (nd == 1) {
+    TRS_DISPATCH_B(b, k_bicg_spmv<B, 1><<<(unsigned)nb, kThreads, 0, s>>>(A, x, y, w, cb, part, counter, sc));
+  } else {
+    TRS_DISPATCH_B(b, k_bicg_spmv<B, 2><<<(unsigned)nb, kThreads, 0, s>>>(A, x, y, w, cb, part, counter, sc));
+  }
+  TRS_LAUNCHED();
+}
+
+void launch_bicg_s(int64_t N, const double *r, const double *v, double *sv, const RedScratch &red,
+                   BicgScalars *sc, cudaStream_t s) {
+  k_bicg_s<<<red.grid, kThreads, 0, s>>>(N, r, v, sv, red.partial, red.counter, sc);
+  TRS_LAUNCHED();
+}
+
+void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double *sv, const double *t,
+                    const double *rh, double *x, double *r, const RedScratch &red, BicgScalars *sc,
+                    cudaStream_t s) {
+  k_bicg_xr<<<red.grid, kThreads, 0, s>>>(N, ph, sh, sv, t, rh, x, r, red.partial, red.counter, sc);
+  TRS_LAUNCHED();
+}
+
 #define TRS_INST_T(T)                                                                                       \
   template void launch_dscale<T>(int, int64_t, const double *, const double *, double *, const T *, T *,     \
                                  cudaStream_t);                                                             \
@@ -1067,9 +1378,11 @@ void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
                                   cudaStream_t);                                                            \
   template void launch_ilu_bwd<T, double>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,\
                                           const T *, double *, cudaStream_t);                               \
-  template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, T *, cudaStream_t);        \
-  template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *,         \
+  template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, T *, int, cudaStream_t);   \
+  template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,    \
                                      cudaStream_t);                                                         \
+  template void launch_cpr_combine<T>(int, int64_t, const T *, const T *, double *, cudaStream_t);          \
+  template void launch_pressure_of<T>(int, int64_t, const T *, T *, cudaStream_t);                          \
   template void launch_cheb_init<T>(int64_t, const T *, const T *, double, T *, T *, cudaStream_t);         \
   template void launch_cheb_resid_init<T>(const ScalarOp<T> &, const T *, const T *, const T *, double, T *, \
                                           T *, cudaStream_t);                                               \

@@ -91,6 +91,7 @@ struct trs_cpr {
   int ws_m = 0;
   trs::DBuf<double> V, w, r, H, cs, sn, gv, h1, h2, hn2, hnorm, status, yv, norms;
   trs::DBuf<char> Z;
+  trs::DBuf<double> bw, bsc, bpart;   // BiCGSTAB vectors (r^, p, v, p^, s, s^, t), scalars, SpMV partials
   trs::DBuf<double> partial;
   trs::DBuf<unsigned int> counter;
   int red_grid = 0;

@@ -74,16 +74,16 @@ void build_hierarchy(trs_cpr *M, cudaStream_t s) {
     // MIS-2 rounds; the undecided count is read every second round (an extra
     // round after completion changes nothing)
     const uint32_t seed = o.seed ^ (kLevelSeedMul * (uint32_t)(l + 1));
-    TBuf<int8_t> state(n, s), s1(n, s), s2(n, s);
-    TBuf<uint64_t> k1(n, s), k2(n, s);
+    TBuf<int8_t> state(n, s);
+    TBuf<uint64_t> w1(n, s), w2(n, s);
     TBuf<unsigned long long> und(1, s);
     launch_mis2_init(n, sdeg.p, state.p, s);
     for (int round = 0;; round++) {
       TRS_REQUIRE(round < 10000, TRS_ERR_COARSENING, "MIS-2 did not terminate");
       und.zero();
-      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, nullptr, seed, s1.p, k1.p, s);
-      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, s1.p, k1.p, seed, s2.p, k2.p, s);
-      launch_mis2_decide(n, seed, s2.p, k2.p, state.p, und.p, s);
+      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, nullptr, seed, w1.p, s);
+      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, w1.p, seed, w2.p, s);
+      launch_mis2_decide(n, seed, w2.p, state.p, und.p, s);
       if (round % 2 == 0) continue;
       unsigned long long left = 0;
       TRS_CUDA(cudaMemcpyAsync(&left, und.p, sizeof(left), cudaMemcpyDeviceToHost, s));
@@ -140,11 +140,12 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   TBuf<int> err(1, s);
   err.zero();
   const bool mixed = M->prec == TRS_FP32_PREC;
+  const int mode = M->opts.decoupling;
   if (mixed)
-    launch_decouple_mixed(b, A->view(), A->tdiag.p, M->at_ell32.p, M->at_tval32.p, M->dinv32.p, M->ap_ell64.p,
-                          M->ap_tval64.p, err.p, s);
+    launch_decouple_mixed(b, A->view(), A->tdiag.p, mode, M->at_ell32.p, M->at_tval32.p, M->dinv32.p,
+                          M->ap_ell64.p, M->ap_tval64.p, err.p, s);
   else
-    launch_decouple(b, A->view(), A->tdiag.p, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
+    launch_decouple(b, A->view(), A->tdiag.p, mode, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
                     M->ap_tval64.p, err.p, s);
   if (rebuild_amg) {
     if (M->lev.empty()) M->lev.emplace_back();
@@ -439,15 +440,31 @@ void ilu_solve(const trs_cpr *M, const T *rhs, T *y, const T *y1, const T *e0, T
     launch_ilu_bwd<T, TZ>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout, s);
 }
 
-// z = CPR(Ã)^-1 f (f already scaled by D^-1), written to z in FP64
+// z = CPR(Ã)^-1 f (f already scaled by D^-1), written to z in FP64.  With F
+// the block ILU(0) of Ã and P one AMG V-cycle on the pressure entries:
+//   FPF: y = F^-1 f; e = P (f - Ã y)_p; z = y + Pi e + F^-1 (f - Ã (y + Pi e));
+//   FP:  z = y + Pi e (the first two stages);
+//   PF:  e = P f_p; z = Pi e + F^-1 (f - Ã Pi e).
 template <class T>
 void cpr_apply_scaled(const trs_cpr *M, double *z, cudaStream_t s) {
   T *f = tp<T>(M->wf), *y = tp<T>(M->wy), *r = tp<T>(M->wr), *x = tp<T>(M->wx);
   const Level &L0 = M->lev[0];
+  const int unit = M->opts.decoupling == TRS_DEC_ABF || M->opts.decoupling == TRS_DEC_FRS_ABF;
+  if (M->opts.stages == TRS_CPR_PF) {
+    launch_pressure_of<T>(M->b, M->n, f, tp<T>(L0.r), s);
+    vcycle<T>(M, 0, tp<T>(L0.r), tp<T>(L0.e), s);
+    launch_resid_full<T>(M->b, at_view<T>(M), f, nullptr, tp<T>(L0.e), r, unit, s);
+    ilu_solve<T, double>(M, r, x, nullptr, tp<T>(L0.e), z, s);
+    return;
+  }
   ilu_solve<T, T>(M, f, y, nullptr, nullptr, (T *)nullptr, s);
-  launch_resid_p<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.r), s);
+  launch_resid_p<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.r), unit, s);
   vcycle<T>(M, 0, tp<T>(L0.r), tp<T>(L0.e), s);
-  launch_resid_full<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.e), r, s);
+  if (M->opts.stages == TRS_CPR_FP) {
+    launch_cpr_combine<T>(M->b, M->n, y, tp<T>(L0.e), z, s);
+    return;
+  }
+  launch_resid_full<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.e), r, unit, s);
   ilu_solve<T, double>(M, r, x, y, tp<T>(L0.e), z, s);
 }
 
@@ -457,14 +474,28 @@ void cpr_apply_full(const trs_cpr *M, const double *v, const double *div, double
   cpr_apply_scaled<T>(M, z, s);
 }
 
+// Reduction scratch and norms shared by the Krylov solvers.
+void ensure_reduction(trs_cpr *M) {
+  if (M->red_grid > 0) return;
+  const int64_t N = M->N;
+  M->r.alloc(N);
+  M->norms.alloc(4);
+  M->status.alloc(2);
+  M->red_grid = (int)std::min<int64_t>(kRedGridMax, std::max<int64_t>(1, (N + 255) / 256));
+  M->partial.alloc((size_t)M->red_grid * (kMaxRestart + 16));
+  M->counter.alloc(1);
+  M->counter.zero(0);
+  TRS_CUDA(cudaDeviceSynchronize());
+}
+
 // -------------------------------------------------------------- FGMRES
 void ensure_workspace(trs_cpr *M, int m) {
+  ensure_reduction(M);
   if (M->ws_m >= m) return;
   const int64_t N = M->N;
   M->V.alloc((size_t)(m + 1) * N);
   M->Z.alloc((size_t)m * N * sizeof(double));
   M->w.alloc(N);
-  M->r.alloc(N);
   M->H.alloc((size_t)(m + 1) * m);
   M->cs.alloc(m);
   M->sn.alloc(m);
@@ -473,13 +504,7 @@ void ensure_workspace(trs_cpr *M, int m) {
   M->h2.alloc(m + 2);
   M->hn2.alloc(2);
   M->hnorm.alloc(2);
-  M->status.alloc(2);
   M->yv.alloc(m);
-  M->norms.alloc(4);
-  M->red_grid = (int)std::min<int64_t>(kRedGridMax, std::max<int64_t>(1, (N + 255) / 256));
-  M->partial.alloc((size_t)M->red_grid * (kMaxRestart + 16));
-  M->counter.alloc(1);
-  M->counter.zero(0);
   TRS_CUDA(cudaDeviceSynchronize());
   M->ws_m = m;
 }
@@ -490,7 +515,7 @@ struct SpmvProfile {
   bool on = false;
   double ms = 0.0;
   int64_t launches = 0;
-  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr, c = nullptr, d = nullptr;
 };
 SpmvProfile g_spmv_prof;
 std::mutex g_prof_mutex;
@@ -591,6 +616,107 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
   return result;
 }
 
+// ------------------------------------------------------------ BiCGSTAB
+// Right-preconditioned BiCGSTAB (van der Vorst), the Krylov method of the
+// paper's runs, with M^-1 = CPR(Ã)^-1 D^-1:
+//   p = r + beta (p - omega v);  p^ = M^-1 p;  v = A p^;  alpha = rho / <r^, v>;
+//   s = r - alpha v;  s^ = M^-1 s;  t = A s^;  omega = <t, s> / <t, t>;
+//   x += alpha p^ + omega s^;  r = s - omega t;  rho' = <r^, r>.
+// When ||s|| already meets the tolerance the step ends with x += alpha p^.
+// A cycle ends when the recurrence residual meets the tolerance or on
+// breakdown (rho = 0 or omega = 0); the next cycle starts from the true FP64
+// residual, with r^ = r, and the solve stops only when that meets rtol.
+void ensure_bicg(trs_cpr *M) {
+  ensure_reduction(M);
+  if (M->bw.n) return;
+  M->bw.alloc((size_t)7 * M->N);
+  M->bsc.alloc(sizeof(BicgScalars) / sizeof(double));
+  M->bpart.alloc((size_t)2 * std::max<int64_t>(1, bicg_spmv_blocks(M->g)));
+  TRS_CUDA(cudaDeviceSynchronize());
+}
+
+template <class T>
+trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, const trs_solve_opts &o,
+                    cudaStream_t s, trs_solve_stats *st) {
+  const int64_t N = M->N;
+  ensure_bicg(M);
+  const RedScratch red{M->partial.p, M->counter.p, M->red_grid};
+  const MatView<double> Av = A->view();
+  double *r = M->r.p, *rh = M->bw.p, *p = rh + N, *v = p + N, *ph = v + N, *sv = ph + N, *sh = sv + N,
+         *t = sh + N;
+  BicgScalars *sc = reinterpret_cast<BicgScalars *>(M->bsc.p);
+  trs_solve_stats local{};
+  Timer timer(s);
+  launch_norm2(b, N, red, M->norms.p + 2, s);
+  double hb[2];
+  TRS_CUDA(cudaMemcpyAsync(hb, M->norms.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = hb[1];
+  TRS_REQUIRE(std::isfinite(bnorm), TRS_ERR_NAN, "the right-hand side holds NaN or Inf");
+  if (!o.use_x0 || bnorm == 0.0) TRS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+  trs_status result = TRS_ERR_NOT_CONVERGED;
+  int iters = 0, cycles = 0;
+  bool breakdown = false;
+  if (bnorm == 0.0) {
+    local.converged = 1;
+    result = TRS_OK;
+  }
+  while (result != TRS_OK) {
+    launch_true_residual(M->b, Av, x, b, r, red, M->norms.p, s);
+    double hn[2];
+    TRS_CUDA(cudaMemcpyAsync(hn, M->norms.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+    const double relres = hn[1] / bnorm;
+    local.true_relres = relres;
+    if (!std::isfinite(relres)) { result = TRS_ERR_NAN; break; }
+    if (relres <= o.rtol) { result = TRS_OK; local.converged = 1; break; }
+    if (iters >= o.maxit) break;
+    TRS_CUDA(cudaMemcpyAsync(rh, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_bicg_start(sc, M->norms.p, bnorm, o.rtol, s);
+    cycles++;
+    breakdown = false;
+    for (int k = 0; iters < o.maxit; k++) {
+      launch_bicg_dir<T>(M->b, M->n, r, v, p, sc, k == 0, dinv_of<T>(M), tp<T>(M->wf), s);
+      cpr_apply_scaled<T>(M, ph, s);
+      const bool prof = g_spmv_prof.on;
+      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.a, s));
+      launch_bicg_spmv(M->b, Av, ph, v, rh, 1, M->bpart.p, M->counter.p, sc, s);
+      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.b, s));
+      launch_bicg_s(N, r, v, sv, red, sc, s);
+      launch_dscale<T>(M->b, M->n, sv, nullptr, nullptr, dinv_of<T>(M), tp<T>(M->wf), s);
+      cpr_apply_scaled<T>(M, sh, s);
+      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.c, s));
+      launch_bicg_spmv(M->b, Av, sh, t, sv, 2, M->bpart.p, M->counter.p, sc, s);
+      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.d, s));
+      launch_bicg_xr(N, ph, sh, sv, t, rh, x, r, red, sc, s);
+      iters++;
+      BicgScalars h;
+      TRS_CUDA(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+      TRS_CUDA(cudaStreamSynchronize(s));
+      if (prof) {
+        float e1 = 0.f, e2 = 0.f;
+        TRS_CUDA(cudaEventElapsedTime(&e1, g_spmv_prof.a, g_spmv_prof.b));
+        TRS_CUDA(cudaEventElapsedTime(&e2, g_spmv_prof.c, g_spmv_prof.d));
+        g_spmv_prof.ms += (double)e1 + (double)e2;
+        g_spmv_prof.launches += 2;
+      }
+      const double est = std::sqrt(h.rr) / bnorm;
+      local.est_relres = est;
+      if (!std::isfinite(est) || !std::isfinite(h.rho)) { breakdown = true; break; }
+      if (est <= o.rtol) break;
+      if (h.omega == 0.0 || h.rho == 0.0) { breakdown = true; break; }
+    }
+  }
+  local.iters = iters;
+  local.restarts = cycles > 0 ? cycles - 1 : 0;
+  local.amg_levels = M->nlev;
+  local.n_colours = M->ncol;
+  local.ms_setup = M->ms_setup;
+  local.ms_solve = timer.stop();
+  if (st) *st = local;
+  return result;
+}
+
 trs_status run_solve(const trs_bsr *A, trs_cpr *M, const double *b, double *x, const trs_solve_opts *opts,
                      cudaStream_t s, trs_solve_stats *st) {
   trs_solve_opts o;
@@ -602,8 +728,49 @@ trs_status run_solve(const trs_bsr *A, trs_cpr *M, const double *b, double *x, c
   require_aligned(x, "x");
   TRS_REQUIRE(o.restart >= 1 && o.restart <= kMaxRestart, TRS_ERR_INVALID, "restart must be 1..64");
   TRS_REQUIRE(o.maxit >= 1 && o.rtol > 0.0, TRS_ERR_INVALID, "maxit must be >= 1 and rtol > 0");
+  TRS_REQUIRE(o.method == TRS_FGMRES || o.method == TRS_BICGSTAB, TRS_ERR_INVALID,
+              "method must be TRS_FGMRES or TRS_BICGSTAB");
+  if (o.method == TRS_BICGSTAB) {
+    if (M->prec == TRS_FP32_PREC) return bicgstab<float>(A, M, b, x, o, s, st);
+    return bicgstab<double>(A, M, b, x, o, s, st);
+  }
   if (M->prec == TRS_FP32_PREC) return fgmres<float>(A, M, b, x, o, s, st);
   return fgmres<double>(A, M, b, x, o, s, st);
+}
+
+trs_status solve_entry(const trs_bsr *A, const trs_cpr *M, const double *b, double *x, const trs_solve_opts *opts,
+                       int method, cudaStream_t s, trs_solve_stats *stats) {
+  trs_status st = TRS_OK;
+  trs_status g = guarded([&] {
+    trs_solve_opts o;
+    trs_solve_default_opts(&o);
+    if (opts) o = *opts;
+    if (method >= 0) o.method = method;
+    st = run_solve(A, const_cast<trs_cpr *>(M), b, x, &o, s, stats);
+  });
+  if (g != TRS_OK) return g;
+  if (st == TRS_ERR_NOT_CONVERGED) set_last_error("iteration limit reached before the tolerance");
+  if (st == TRS_ERR_NAN) set_last_error("NaN or Inf in a residual norm");
+  return st;
+}
+
+trs_status solve_host_entry(const trs_bsr *A, const trs_cpr *M, const double *b_host, double *x_host,
+                            const trs_solve_opts *opts, int method, cudaStream_t s, trs_solve_stats *stats) {
+  trs_status st = TRS_OK;
+  trs_status g = guarded([&] {
+    TRS_REQUIRE(A && M && b_host && x_host, TRS_ERR_INVALID, "NULL argument");
+    DBuf<double> db(M->N), dx(M->N);
+    db.upload(b_host, M->N, s);
+    trs_solve_opts o;
+    trs_solve_default_opts(&o);
+    if (opts) o = *opts;
+    if (method >= 0) o.method = method;
+    if (o.use_x0) dx.upload(x_host, M->N, s);
+    st = run_solve(A, const_cast<trs_cpr *>(M), db.p, dx.p, &o, s, stats);
+    TRS_CUDA(cudaMemcpyAsync(x_host, dx.p, M->N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRS_CUDA(cudaStreamSynchronize(s));
+  });
+  return g != TRS_OK ? g : st;
 }
 
 }  // namespace
@@ -629,6 +796,8 @@ void trs_cpr_default_opts(trs_cpr_opts *o) {
   o->max_levels = 12;
   o->cheb_degree = 2;
   o->seed = 0x5EED1812u;
+  o->stages = TRS_CPR_FPF;
+  o->decoupling = TRS_DEC_ABF;
 }
 
 void trs_solve_default_opts(trs_solve_opts *o) {
@@ -637,6 +806,7 @@ void trs_solve_default_opts(trs_solve_opts *o) {
   o->restart = 30;
   o->maxit = 1000;
   o->use_x0 = 0;
+  o->method = TRS_FGMRES;
 }
 
 trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *stream, trs_cpr **out) {
@@ -650,6 +820,10 @@ trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *strea
     TRS_REQUIRE(o.cheb_degree >= 2 && o.cheb_degree <= 8, TRS_ERR_UNSUPPORTED, "Chebyshev degree must be 2..8");
     TRS_REQUIRE(o.max_levels >= 1 && o.max_levels <= kMaxLevels, TRS_ERR_INVALID, "max_levels must be 1..16");
     TRS_REQUIRE(o.coarse_max >= 1 && o.coarse_max <= kDenseMax, TRS_ERR_INVALID, "coarse_max must be 1..4096");
+    TRS_REQUIRE(o.stages >= TRS_CPR_FPF && o.stages <= TRS_CPR_PF, TRS_ERR_INVALID,
+                "stages must be TRS_CPR_FPF, TRS_CPR_FP or TRS_CPR_PF");
+    TRS_REQUIRE(o.decoupling >= TRS_DEC_ABF && o.decoupling <= TRS_DEC_FRS_ABF, TRS_ERR_INVALID,
+                "decoupling must be TRS_DEC_ABF, TRS_DEC_NONE, TRS_DEC_FRS or TRS_DEC_FRS_ABF");
     cudaStream_t s = (cudaStream_t)stream;
     auto M = std::make_unique<trs_cpr>();
     M->opts = o;
@@ -788,31 +962,22 @@ void trs_cpr_destroy(trs_cpr *M) { delete M; }
 
 trs_status trs_fgmres_solve(const trs_bsr *A, const trs_cpr *M, const double *b, double *x,
                             const trs_solve_opts *opts, void *stream, trs_solve_stats *stats) {
-  trs_status st = TRS_OK;
-  trs_status g = guarded([&] { st = run_solve(A, const_cast<trs_cpr *>(M), b, x, opts, (cudaStream_t)stream, stats); });
-  if (g != TRS_OK) return g;
-  if (st == TRS_ERR_NOT_CONVERGED) set_last_error("iteration limit reached before the tolerance");
-  if (st == TRS_ERR_NAN) set_last_error("NaN or Inf in a residual norm");
-  return st;
+  return solve_entry(A, M, b, x, opts, TRS_FGMRES, (cudaStream_t)stream, stats);
 }
 
 trs_status trs_fgmres_solve_host(const trs_bsr *A, const trs_cpr *M, const double *b_host, double *x_host,
                                  const trs_solve_opts *opts, void *stream, trs_solve_stats *stats) {
-  trs_status st = TRS_OK;
-  trs_status g = guarded([&] {
-    TRS_REQUIRE(A && M && b_host && x_host, TRS_ERR_INVALID, "NULL argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    DBuf<double> db(M->N), dx(M->N);
-    db.upload(b_host, M->N, s);
-    trs_solve_opts o;
-    trs_solve_default_opts(&o);
-    if (opts) o = *opts;
-    if (o.use_x0) dx.upload(x_host, M->N, s);
-    st = run_solve(A, const_cast<trs_cpr *>(M), db.p, dx.p, &o, s, stats);
-    TRS_CUDA(cudaMemcpyAsync(x_host, dx.p, M->N * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TRS_CUDA(cudaStreamSynchronize(s));
-  });
-  return g != TRS_OK ? g : st;
+  return solve_host_entry(A, M, b_host, x_host, opts, TRS_FGMRES, (cudaStream_t)stream, stats);
+}
+
+trs_status trs_bicgstab_solve(const trs_bsr *A, const trs_cpr *M, const double *b, double *x,
+                              const trs_solve_opts *opts, void *stream, trs_solve_stats *stats) {
+  return solve_entry(A, M, b, x, opts, TRS_BICGSTAB, (cudaStream_t)stream, stats);
+}
+
+trs_status trs_bicgstab_solve_host(const trs_bsr *A, const trs_cpr *M, const double *b_host, double *x_host,
+                                   const trs_solve_opts *opts, void *stream, trs_solve_stats *stats) {
+  return solve_host_entry(A, M, b_host, x_host, opts, TRS_BICGSTAB, (cudaStream_t)stream, stats);
 }
 
 trs_status trs_solve_adjoint(const trs_bsr *A, const trs_bsr *AT, const trs_cpr *M_T, const double *g,
@@ -860,6 +1025,8 @@ trs_status trs_profile_spmv(int32_t enable, double *total_ms, int64_t *launches)
     if (!g_spmv_prof.a) {
       TRS_CUDA(cudaEventCreate(&g_spmv_prof.a));
       TRS_CUDA(cudaEventCreate(&g_spmv_prof.b));
+      TRS_CUDA(cudaEventCreate(&g_spmv_prof.c));
+      TRS_CUDA(cudaEventCreate(&g_spmv_prof.d));
     }
     if (total_ms) *total_ms = g_spmv_prof.ms;
     if (launches) *launches = g_spmv_prof.launches;

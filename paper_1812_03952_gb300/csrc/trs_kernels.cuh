@@ -101,11 +101,18 @@ void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, 
 template <class T, class TZ>
 void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2,
                     const T *y1, const T *e0, TZ *zout, cudaStream_t s);
+// CPR residuals on Ã; unit = 1 when every diagonal block of Ã is I (ABF,
+// FRS+ABF), so that y_i is added instead of multiplied; y1 may be NULL (zero).
 template <class T>
-void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, cudaStream_t s);
+void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, int unit, cudaStream_t s);
 template <class T>
 void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r,
-                       cudaStream_t s);
+                       int unit, cudaStream_t s);
+// z = y1 + Pi_p e0 (FP64 out) and rp = Pi_r f, for the CPR-FP and CPR-PF orderings
+template <class T>
+void launch_cpr_combine(int b, int64_t n, const T *y1, const T *e0, double *z, cudaStream_t s);
+template <class T>
+void launch_pressure_of(int b, int64_t n, const T *f, T *rp, cudaStream_t s);
 
 template <class T>
 void launch_cheb_init(int64_t n, const T *r, const T *dinv, double inv_theta, T *d, T *e,
@@ -145,6 +152,27 @@ void launch_scale_copy(const double *r, const double *norm2, double *v, int64_t 
 template <class TS, class TD>
 void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s);
 
+// BiCGSTAB scalars, kept on the device between the kernels of one iteration.
+struct BicgScalars {
+  double rho, rho_old, alpha, omega;   // recurrence coefficients
+  double rv, ss, ts, tt, rr;           // <r^,v>, ||s||^2, <t,s>, <t,t>, ||r||^2
+  double half;                         // 1: ||s|| met the tolerance (x += alpha p^ only)
+  double bnorm, rtol;
+};
+void launch_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double rtol, cudaStream_t s);
+template <class T>
+void launch_bicg_dir(int b, int64_t n, const double *r, const double *v, double *p, const BicgScalars *sc,
+                     int first, const T *dinv, T *f, cudaStream_t s);
+// blocks of one k_bicg_spmv launch (its partial sums take 2 doubles each)
+int64_t bicg_spmv_blocks(const Geom &g);
+void launch_bicg_spmv(int b, const MatView<double> &A, const double *x, double *y, const double *w, int nd,
+                      double *part, unsigned int *counter, BicgScalars *sc, cudaStream_t s);
+void launch_bicg_s(int64_t N, const double *r, const double *v, double *sv, const RedScratch &red,
+                   BicgScalars *sc, cudaStream_t s);
+void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double *sv, const double *t,
+                    const double *rh, double *x, double *r, const RedScratch &red, BicgScalars *sc,
+                    cudaStream_t s);
+
 // ---------------------------------------------------------------- k_setup
 void launch_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval,
                            int64_t nc, double *ell, double *tval, cudaStream_t s);
@@ -154,7 +182,7 @@ void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, dou
                      double c_t, const double *M, const double *acc, const double *wi,
                      const double *lam, cudaStream_t s);
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s);
-void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, double *at_ell,
+void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, int mode, double *at_ell,
                      double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err,
                      cudaStream_t s);
 
@@ -183,9 +211,9 @@ void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const dou
                      const int64_t *dpos, double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s);
 void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_t s);
 void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
-                       const int8_t *in_s, const uint64_t *in_k, uint32_t seed, int8_t *out_s,
-                       uint64_t *out_k, cudaStream_t s);
-void launch_mis2_decide(int64_t n, uint32_t seed, const int8_t *t2s, const uint64_t *t2k, int8_t *state,
+                       const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w,
+                       cudaStream_t s);
+void launch_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state,
                         unsigned long long *undecided, cudaStream_t s);
 void launch_in_flag(int64_t n, const int8_t *state, int64_t *flag, cudaStream_t s);
 void launch_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
@@ -217,9 +245,9 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
                               const int64_t *pos, const int64_t *ftptr, const int32_t *ftcol,
                               const uint8_t *ftlow, T *fell, T *ftval, int64_t q0, int64_t q1,
                               int64_t q2, int *err, cudaStream_t s);
-void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, float *at_ell,
-                           float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err,
-                           cudaStream_t s);
+void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, int mode,
+                           float *at_ell, float *at_tval, float *dinv, double *ap_ell, double *ap_tval,
+                           int *err, cudaStream_t s);
 
 // ------------------------------------------------------------- k_adjoint
 void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double alpha, double beta,

@@ -29,6 +29,12 @@ TRS_ERR_UNSUPPORTED = -9
 
 TRS_FP64 = 0
 TRS_FP32_PREC = 1
+TRS_FGMRES = 0
+TRS_BICGSTAB = 1
+METHODS = {"fgmres": TRS_FGMRES, "bicgstab": TRS_BICGSTAB}
+#: CPR stage orderings and decoupling methods by name
+STAGES = {"fpf": 0, "fp": 1, "pf": 2}
+DECOUPLINGS = {"abf": 0, "none": 1, "frs": 2, "frs+abf": 3}
 
 #: every entry point declared in include/trs.h
 EXPORTS = (
@@ -38,7 +44,7 @@ EXPORTS = (
     "trs_cpr_update", "trs_cpr_apply", "trs_cpr_get_info", "trs_cpr_get_aggregates",
     "trs_cpr_get_colours", "trs_cpr_get_decoupled", "trs_cpr_get_level", "trs_cpr_vcycle",
     "trs_cpr_destroy", "trs_solve_default_opts", "trs_fgmres_solve", "trs_fgmres_solve_host",
-    "trs_solve_adjoint", "trs_outer_product", "trs_chain_theta", "trs_last_error", "trs_version",
+    "trs_bicgstab_solve", "trs_bicgstab_solve_host", "trs_solve_adjoint", "trs_outer_product", "trs_chain_theta", "trs_last_error", "trs_version",
     "trs_kernel_launches", "trs_residual_norm_noalloc", "trs_profile_spmv",
 )
 
@@ -51,12 +57,13 @@ class TrsError(RuntimeError):
 
 class CprOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("theta", C.c_double), ("coarse_max", C.c_int32),
-                ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("seed", C.c_uint32)]
+                ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("seed", C.c_uint32),
+                ("stages", C.c_int32), ("decoupling", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
-                ("use_x0", C.c_int32)]
+                ("use_x0", C.c_int32), ("method", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -120,6 +127,9 @@ def load(path: str = LIB_PATH):
         "trs_fgmres_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveStats)]),
         "trs_fgmres_solve_host": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), vp,
                                         C.POINTER(SolveStats)]),
+        "trs_bicgstab_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveStats)]),
+        "trs_bicgstab_solve_host": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), vp,
+                                          C.POINTER(SolveStats)]),
         "trs_solve_adjoint": (i32, [vp, vp, vp, vp, vp, vp, vp, C.POINTER(SolveOpts), vp,
                                     C.POINTER(SolveStats)]),
         "trs_outer_product": (i32, [vp, vp, vp, vp, vp]),
@@ -271,6 +281,10 @@ def default_cpr_opts(**kw):
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": TRS_FP64, "fp32": TRS_FP32_PREC}[v]
+        elif k == "stages" and isinstance(v, str):
+            v = STAGES[v]
+        elif k == "decoupling" and isinstance(v, str):
+            v = DECOUPLINGS[v]
         setattr(o, k, v)
     return o
 
@@ -352,35 +366,63 @@ class Result:
     stats: dict
 
 
-def fgmres_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, restart=30, maxit=1000, use_x0=False):
-    """Solves A x = b (device tensors); returns (x, Result)."""
+def _device_solve(fn, A: Matrix, M: CPR, b, x, rtol, restart, maxit, use_x0):
     if x is None:
         x = _empty(A.N, device=b.device)
         use_x0 = False
     o = default_solve_opts(rtol=rtol, restart=restart, maxit=maxit, use_x0=int(use_x0))
     st = SolveStats()
-    code = load().trs_fgmres_solve(A.h, M.h, _dptr(b), _dptr(x), C.byref(o), _stream(), C.byref(st))
+    code = fn(A.h, M.h, _dptr(b), _dptr(x), C.byref(o), _stream(), C.byref(st))
     _check(code, allow=(TRS_ERR_NOT_CONVERGED,))
     return x, Result(code, st.as_dict())
 
 
-def fgmres_solve_host(A: Matrix, M: CPR, b: np.ndarray, rtol=1e-6, restart=30, maxit=1000):
-    """The same solve with host (numpy) vectors; the copies are part of the call."""
+def _host_solve(fn, A: Matrix, M: CPR, b, rtol, restart, maxit):
     bb = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros_like(bb)
     o = default_solve_opts(rtol=rtol, restart=restart, maxit=maxit, use_x0=0)
     st = SolveStats()
-    code = load().trs_fgmres_solve_host(A.h, M.h, _hptr(bb), _hptr(x), C.byref(o), _stream(),
-                                        C.byref(st))
+    code = fn(A.h, M.h, _hptr(bb), _hptr(x), C.byref(o), _stream(), C.byref(st))
     _check(code, allow=(TRS_ERR_NOT_CONVERGED,))
     return x, Result(code, st.as_dict())
 
 
+def fgmres_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, restart=30, maxit=1000, use_x0=False):
+    """Solves A x = b by FGMRES (device tensors); returns (x, Result)."""
+    return _device_solve(load().trs_fgmres_solve, A, M, b, x, rtol, restart, maxit, use_x0)
+
+
+def fgmres_solve_host(A: Matrix, M: CPR, b: np.ndarray, rtol=1e-6, restart=30, maxit=1000):
+    """The same solve with host (numpy) vectors; the copies are part of the call."""
+    return _host_solve(load().trs_fgmres_solve_host, A, M, b, rtol, restart, maxit)
+
+
+def bicgstab_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, maxit=1000, use_x0=False):
+    """Solves A x = b by BiCGSTAB (device tensors); returns (x, Result)."""
+    return _device_solve(load().trs_bicgstab_solve, A, M, b, x, rtol, 30, maxit, use_x0)
+
+
+def bicgstab_solve_host(A: Matrix, M: CPR, b: np.ndarray, rtol=1e-6, maxit=1000):
+    """BiCGSTAB with host (numpy) vectors; the copies are part of the call."""
+    return _host_solve(load().trs_bicgstab_solve_host, A, M, b, rtol, 30, maxit)
+
+
+def krylov_solve(method: str, A: Matrix, M: CPR, b, x=None, rtol=1e-6, restart=30, maxit=1000,
+                 use_x0=False):
+    """FGMRES or BiCGSTAB by name ("fgmres" | "bicgstab")."""
+    if method == "fgmres":
+        return fgmres_solve(A, M, b, x, rtol=rtol, restart=restart, maxit=maxit, use_x0=use_x0)
+    if method == "bicgstab":
+        return bicgstab_solve(A, M, b, x, rtol=rtol, maxit=maxit, use_x0=use_x0)
+    raise ValueError(f"unknown Krylov method {method!r}")
+
+
 def solve_adjoint(A: Matrix, AT: Matrix, MT: CPR, g, x=None, want_dA=False, rtol=1e-6, restart=30,
-                  maxit=1000):
+                  maxit=1000, method="fgmres"):
     lam = _empty(A.N, device=g.device)
     dA = _empty(A.nnzb * A.b * A.b, device=g.device) if want_dA else None
     o = default_solve_opts(rtol=rtol, restart=restart, maxit=maxit, use_x0=0)
+    o.method = METHODS[method]
     st = SolveStats()
     code = load().trs_solve_adjoint(A.h, AT.h, MT.h, _dptr(g), _dptr(x), _dptr(lam), _dptr(dA),
                                     C.byref(o), _stream(), C.byref(st))

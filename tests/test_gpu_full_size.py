@@ -1,0 +1,82 @@
+"""Checks at the full benchmark size: 128x128x64 cells, b = 4, 8 wells
+(4.19M unknowns), in the configuration the benchmark times (FP32 CPR inside
+FP64 Krylov, rtol 1e-6, default CPR options).
+
+The oracle still finishes the pieces that decide integers at this size
+(assembly 0.2 s, CPR setup 2 s, one application 1 s), so those are compared
+whole: assembled values, decoupled blocks and D^-1, every aggregate, every
+colour, bit for bit.  The solves are checked by a property that holds at any
+size: the true FP64 residual of the returned x, recomputed by the oracle on
+the host, meets rtol.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def trs():
+    from paper_1812_03952_gb300 import build as B
+    B.build()
+    from paper_1812_03952_gb300 import trs as T
+    T.load()
+    return T
+
+
+@pytest.fixture(scope="module")
+def full(trs, oracle, synth):
+    sysm = synth.config(1)
+    ds = trs.DeviceSystem(sysm)
+    A = ds.assemble()
+    Ao = oracle.assemble(sysm)
+    return sysm, ds, A, Ao
+
+
+def _relres(oracle, Ao, rhs, x):
+    return np.linalg.norm(rhs - oracle.spmv(Ao, x)) / np.linalg.norm(rhs)
+
+
+def test_full_size_assembly_and_setup_bit_exact(trs, oracle, full):
+    sysm, ds, A, Ao = full
+    rp, col = A.pattern()
+    np.testing.assert_array_equal(rp, Ao.rp)
+    np.testing.assert_array_equal(col, Ao.col)
+    np.testing.assert_array_equal(A.values(), Ao.val)
+    Mo = oracle.CPR(Ao)
+    for precision in ("fp64", "fp32"):
+        M = trs.CPR(A, precision=precision)
+        info = M.info()
+        assert info["level_rows"] == Mo.amg.sizes()
+        for l in range(Mo.amg.n_levels - 1):
+            np.testing.assert_array_equal(M.aggregates(l), Mo.amg.agg(l))
+        np.testing.assert_array_equal(M.colours(), Mo.colours())
+        if precision == "fp64":
+            vt, dinv = M.decoupled(Ao.nnzb)
+            vto, dinvo = Mo.decoupled()
+            np.testing.assert_array_equal(dinv, dinvo)
+            np.testing.assert_array_equal(vt, vto)
+            # one CPR application on a seeded vector, against the oracle's
+            v = np.random.default_rng(7).standard_normal(Ao.n * Ao.b)
+            z = M.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+            zo = Mo.apply(v)
+            assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-11
+
+
+@pytest.mark.parametrize("method", ["fgmres", "bicgstab"])
+def test_full_size_solve_meets_tolerance(trs, oracle, full, method):
+    sysm, ds, A, Ao = full
+    M = trs.CPR(A, precision="fp32")
+    x = torch.empty_like(ds.rhs)
+    # the benchmark's step: refresh the values, rebuild CPR, solve
+    ds.assemble()
+    M.update(A, reuse_amg=False)
+    x, res = trs.krylov_solve(method, A, M, ds.rhs, x, rtol=1e-6)
+    assert res.status == trs.TRS_OK and res.stats["converged"]
+    tr = _relres(oracle, Ao, sysm.rhs, x.cpu().numpy())
+    assert tr <= 1.01e-6
+    assert abs(tr - res.stats["true_relres"]) <= 1e-12
