@@ -321,8 +321,9 @@ int orc_pattern_symmetric(int64_t n, const int64_t *rp, const int32_t *col) {
  *
  * Gauss-Jordan elimination on [D | I] with row pivoting only (GJE): at
  * column c the pivot row is the one of largest |D(r,c)|, r >= c, the first
- * such row on ties; the pivot row is divided by the pivot, then the
- * multiple D(r,c) of it is subtracted from every other row.  The right half
+ * such row on ties; the pivot row is scaled by the reciprocal of the pivot
+ * (one division per column), then the multiple D(r,c) of it is subtracted
+ * from every other row.  The right half
  * becomes D^-1.  ABF (Eq. decoupled-abf) uses D_i = A_ii; the decoupled
  * blocks are  Ã_ij = D_i^-1 A_ij, with Ã_ii set to the identity.  The
  * products sum over the inner index in ascending order.
@@ -343,8 +344,8 @@ int orc_gj_inverse(int b, const double *D, double *inv) {
         double t = a[c * b + s]; a[c * b + s] = a[p * b + s]; a[p * b + s] = t;
         t = m[c * b + s]; m[c * b + s] = m[p * b + s]; m[p * b + s] = t;
       }
-    double piv = a[c * b + c];
-    for (int s = 0; s < b; s++) { a[c * b + s] = a[c * b + s] / piv; m[c * b + s] = m[c * b + s] / piv; }
+    const double rpiv = 1.0 / a[c * b + c];
+    for (int s = 0; s < b; s++) { a[c * b + s] = a[c * b + s] * rpiv; m[c * b + s] = m[c * b + s] * rpiv; }
     for (int r = 0; r < b; r++) {
       if (r == c) continue;
       double f = a[r * b + c];
