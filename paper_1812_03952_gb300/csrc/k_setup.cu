@@ -226,8 +226,8 @@ __global__ void k_scale_diag(Geom g, double *ell, double *tval, const int64_t *t
 // ------------------------------------------------------------ decoupling
 // Gauss-Jordan inversion with row pivoting (GJE of Sec. "Decoupling
 // Methods"): pivot = first row of largest |a| in the column at or below the
-// diagonal; pivot row divided by the pivot; its multiple a(r,c) subtracted
-// from every other row.
+// diagonal; pivot row scaled by the reciprocal of the pivot (one division
+// per column); its multiple a(r,c) subtracted from every other row.
 template <int B, class T = double>
 __device__ bool gj_inverse(const T (&D)[B * B], T (&inv)[B * B]) {
   T a[B * B];
@@ -255,11 +255,11 @@ __device__ bool gj_inverse(const T (&D)[B * B], T (&inv)[B * B]) {
         }
       }
     }
-    const T piv = a[c * B + c];
+    const T rpiv = T(1) / a[c * B + c];
 #pragma unroll
     for (int s = 0; s < B; s++) {
-      a[c * B + s] = a[c * B + s] / piv;
-      inv[c * B + s] = inv[c * B + s] / piv;
+      a[c * B + s] = a[c * B + s] * rpiv;
+      inv[c * B + s] = inv[c * B + s] * rpiv;
     }
 #pragma unroll
     for (int r = 0; r < B; r++) {
@@ -301,41 +301,53 @@ __device__ __forceinline__ void frs_matrix(double (&R)[B * B]) {
     for (int c = 0; c < B; c++) R[r * B + c] = (r == 0 || r == c) ? 1.0 : 0.0;
 }
 
+// The factor applied to the blocks of the row, Ai (ABF: A_ii^-1; FRS+ABF:
+// (R A_ii)^-1, the blocks then pre-multiplied by R; NONE: I; FRS: R), and the
+// stored D_i^-1 (Ai, or Ai R for FRS+ABF).  D is replaced by R D for FRS+ABF.
 template <int B>
-__device__ bool decoupling_factor(int mode, const double (&D)[B * B], double (&Dm)[B * B], double (&Ai)[B * B]) {
+__device__ bool decoupling_factor(int mode, double (&D)[B * B], double (&Ai)[B * B], double (&Dm)[B * B]) {
   constexpr int BB = B * B;
   if (mode == TRS_DEC_NONE) {
 #pragma unroll
-    for (int e = 0; e < BB; e++) Dm[e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+    for (int e = 0; e < BB; e++) Ai[e] = Dm[e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
     return true;
   }
   if (mode == TRS_DEC_FRS) {
-    frs_matrix<B>(Dm);
+    frs_matrix<B>(Ai);
+#pragma unroll
+    for (int e = 0; e < BB; e++) Dm[e] = Ai[e];
     return true;
   }
+  double R[BB];
   if (mode == TRS_DEC_FRS_ABF) {
-    double R[BB], Rd[BB];
+    double T[BB];
     frs_matrix<B>(R);
-    bmul<B>(R, D, Rd);
-    if (!gj_inverse<B>(Rd, Ai)) return false;
-    bmul<B>(Ai, R, Dm);
-    return true;
+    bmul<B>(R, D, T);
+#pragma unroll
+    for (int e = 0; e < BB; e++) D[e] = T[e];
   }
-  return gj_inverse<B>(D, Dm);
+  if (!gj_inverse<B>(D, Ai)) return false;
+  if (mode == TRS_DEC_FRS_ABF) {
+    bmul<B>(Ai, R, Dm);
+  } else {
+#pragma unroll
+    for (int e = 0; e < BB; e++) Dm[e] = Ai[e];
+  }
+  return true;
 }
 
 // Ã_ij = D_i^-1 A_ij; for FRS+ABF in the order of the two stages, Ai (R A_ij).
 template <int B>
-__device__ __forceinline__ void decouple_block(int mode, const double (&Dm)[B * B], const double (&Ai)[B * B],
-                                               const double (&blk)[B * B], double (&out)[B * B]) {
+__device__ __forceinline__ void decouple_block(int mode, const double (&Ai)[B * B], double (&blk)[B * B],
+                                               double (&out)[B * B]) {
   if (mode == TRS_DEC_FRS_ABF) {
     double R[B * B], Rb[B * B];
     frs_matrix<B>(R);
     bmul<B>(R, blk, Rb);
-    bmul<B>(Ai, Rb, out);
-  } else {
-    bmul<B>(Dm, blk, out);
+#pragma unroll
+    for (int e = 0; e < B * B; e++) blk[e] = Rb[e];
   }
+  bmul<B>(Ai, blk, out);
 }
 
 __device__ __forceinline__ bool unit_diagonal(int mode) { return mode == TRS_DEC_ABF || mode == TRS_DEC_FRS_ABF; }
@@ -361,7 +373,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
 #pragma unroll
     for (int e = 0; e < BB; e++) D[e] = A.tval[dtail * BB + e];
   }
-  if (!decoupling_factor<B>(mode, D, Dm, Ai)) {
+  if (!decoupling_factor<B>(mode, D, Ai, Dm)) {
     atomicExch(err, 1);
     return;
   }
@@ -379,7 +391,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
       }
 #pragma unroll
       for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
-      decouple_block<B>(mode, Dm, Ai, blk, out);
+      decouple_block<B>(mode, Ai, blk, out);
 #pragma unroll
       for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = out[e];
       ap_ell[(int64_t)s * nc + i] = out[0];
@@ -394,7 +406,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
     }
 #pragma unroll
     for (int e = 0; e < BB; e++) blk[e] = A.tval[t * BB + e];
-    decouple_block<B>(mode, Dm, Ai, blk, out);
+    decouple_block<B>(mode, Ai, blk, out);
 #pragma unroll
     for (int e = 0; e < BB; e++) at_tval[t * BB + e] = out[e];
     ap_tval[t] = out[0];
@@ -425,14 +437,14 @@ __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mo
 #pragma unroll
     for (int e = 0; e < BB; e++) D[e] = A.tval[dtail * BB + e];
   }
-  if (!decoupling_factor<B>(mode, D, Dm, Ai)) {
+  if (!decoupling_factor<B>(mode, D, Ai, Dm)) {
     atomicExch(err, 1);
     return;
   }
 #pragma unroll
   for (int e = 0; e < BB; e++) {
     dinv[(int64_t)e * n + i] = (float)Dm[e];
-    L[e] = two_stage ? Ai[e] : Dm[e];
+    L[e] = Ai[e];
     Lf[e] = (float)L[e];
   }
   // (Ã_ij)_00 in FP64 (first product, then a running sum over the inner
@@ -527,35 +539,48 @@ __device__ __forceinline__ int64_t bsearch_col(const int64_t *rp, const int32_t 
   return -1;
 }
 
-__global__ void k_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, int64_t *dpos) {
+__global__ void k_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int64_t *dpos,
+                           double *dval) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
-  dpos[i] = bsearch_col(rp, col, i, i);
+  const int64_t d = bsearch_col(rp, col, i, i);
+  dpos[i] = d;
+  dval[i] = d < 0 ? 0.0 : val[d];
 }
 
 // ------------------------------------------------------------- strength
-// j != i is strong if s = max(|a_ij|, |a_ji|) > 0 and s >= theta*sqrt(|a_ii a_jj|)
+// j != i is strong if s = max(|a_ij|, |a_ji|) > 0 and s >= theta*sqrt(|a_ii a_jj|).
+// Eight lanes per row, each lane a share of the row's entries, so that the
+// searches for a_ji of one row are in flight together; dval holds a_ii.
+constexpr int kStrengthLanes = 8;
+
 __global__ void k_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
-                           const int64_t *dpos, double theta, uint8_t *sflag, int32_t *sdeg) {
-  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  if (i >= n) return;
-  const double aii = dpos[i] < 0 ? 0.0 : val[dpos[i]];
+                           const double *dval, double theta, uint8_t *sflag, int32_t *sdeg) {
+  const int64_t gid = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t i = gid / kStrengthLanes;
+  const int sub = (int)(gid % kStrengthLanes);
   int32_t deg = 0;
-  for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
-    const int64_t j = col[p];
-    uint8_t f = 0;
-    if (j != i) {
-      const double ajj = dpos[j] < 0 ? 0.0 : val[dpos[j]];
-      const int64_t pt = bsearch_col(rp, col, j, i);
-      const double aij = fabs(val[p]), aji = pt < 0 ? 0.0 : fabs(val[pt]);
-      const double sv = aij > aji ? aij : aji;
-      const double thr = theta * sqrt(fabs(aii * ajj));
-      f = (sv > 0.0 && sv >= thr) ? 1 : 0;
+  if (i < n) {
+    const double aii = dval[i];
+    const int64_t e = rp[i + 1];
+    for (int64_t p = rp[i] + sub; p < e; p += kStrengthLanes) {
+      const int64_t j = col[p];
+      uint8_t f = 0;
+      if (j != i) {
+        const double ajj = dval[j];
+        const int64_t pt = bsearch_col(rp, col, j, i);
+        const double aij = fabs(val[p]), aji = pt < 0 ? 0.0 : fabs(val[pt]);
+        const double sv = aij > aji ? aij : aji;
+        const double thr = theta * sqrt(fabs(aii * ajj));
+        f = (sv > 0.0 && sv >= thr) ? 1 : 0;
+      }
+      sflag[p] = f;
+      deg += f;
     }
-    sflag[p] = f;
-    deg += f;
   }
-  sdeg[i] = deg;
+#pragma unroll
+  for (int o = kStrengthLanes / 2; o > 0; o >>= 1) deg += __shfl_xor_sync(0xffffffffu, deg, o);
+  if (i < n && sub == 0) sdeg[i] = deg;
 }
 
 // ----------------------------------------------------------------- MIS-2
@@ -1310,7 +1335,11 @@ __device__ BRef<T> ilu_find(const Geom &g, const uint8_t *emask, const int64_t *
 // IKJ ILU(0) of the rows at positions [q0, q1) (one colour): for every
 // earlier-ordered k of row i in ascending order, L_ik = W_ik U_kk^-1 and
 // W_ij -= L_ik U_kj for later-ordered j of row i with (k, j) stored; then
-// U_ii^-1 replaces W_ii in slot 3.
+// U_ii^-1 replaces W_ii in slot 3.  The pairs (k, j) are found by walking
+// row k (its slots, then its tail) and locating each j in row i: by offset
+// for a slot neighbour, directly for j = i, by a search of row i's (short)
+// tail otherwise; the positions of row i's slot neighbours stay in
+// registers.
 template <int B, class T>
 __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, T *fell,
@@ -1322,46 +1351,86 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
   const bool cell = i < g.nc;
   const unsigned m = cell ? emask[i] : 0u;
   const int64_t u0 = ftptr[q], u1 = ftptr[q + 1];
-  // the row's entries: slots 0..6 (cells) then tail entries u0..u1-1
-  const int n_ent = kSlots + (int)(u1 - u0);
-  auto ent_col = [&](int k) -> int64_t {
-    if (k < kSlots) return ((m >> k) & 1u) ? i + g.off[k] : -1;
-    return ftcol[u0 + (k - kSlots)];
-  };
-  auto ent_ref = [&](int k) -> BRef<T> {
-    if (k < kSlots) return BRef<T>{fell + ((int64_t)k * BB) * np + q, np};
-    return BRef<T>{ftval + (u0 + (k - kSlots)) * BB, 1};
+  int64_t spos[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; s++) spos[s] = (s != kSelf && ((m >> s) & 1u)) ? pos[i + g.off[s]] : -1;
+  // reference to the entry of row i in column j with its position, or p = nullptr
+  auto target = [&](int64_t j, int64_t &pj) -> BRef<T> {
+    if (j == i) {
+      pj = q;
+      if (cell) return BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np};
+    } else if (cell && j < g.nc) {
+      const int64_t d = j - i;
+#pragma unroll
+      for (int s = 0; s < kSlots; s++)
+        if (s != kSelf && ((m >> s) & 1u) && g.off[s] == d) {
+          pj = spos[s];
+          return BRef<T>{fell + ((int64_t)s * BB) * np + q, np};
+        }
+    }
+    for (int64_t u = u0; u < u1; u++)
+      if (ftcol[u] == j) {
+        pj = j == i ? q : pos[j];
+        return BRef<T>{ftval + u * BB, 1};
+      }
+    return BRef<T>{nullptr, 0};
   };
   int64_t cur = -1;
   for (;;) {
     // next lower entry in ascending position
-    int kbest = -1;
-    int64_t pbest = q;
-    for (int k = 0; k < n_ent; k++) {
-      const int64_t c = ent_col(k);
-      if (c < 0 || c == i) continue;
-      const int64_t pc = pos[c];
-      if (pc > cur && pc < pbest) { pbest = pc; kbest = k; }
+    int64_t pbest = q, kr = -1;
+    BRef<T> wref{nullptr, 0};
+#pragma unroll
+    for (int s = 0; s < kSlots; s++) {
+      const int64_t pc = spos[s];
+      if (pc > cur && pc < pbest) {
+        pbest = pc;
+        kr = i + g.off[s];
+        wref = BRef<T>{fell + ((int64_t)s * BB) * np + q, np};
+      }
     }
-    if (kbest < 0) break;
+    for (int64_t u = u0; u < u1; u++) {
+      const int64_t c = ftcol[u];
+      if (c == i) continue;
+      const int64_t pc = pos[c];
+      if (pc > cur && pc < pbest) {
+        pbest = pc;
+        kr = c;
+        wref = BRef<T>{ftval + u * BB, 1};
+      }
+    }
+    if (kr < 0) break;
     cur = pbest;
-    const int64_t kr = ent_col(kbest);
     T W[BB], Uinv[BB], L[BB];
-    bload<B, T>(ent_ref(kbest), W);
+    bload<B, T>(wref, W);
     bload<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + pbest, np}, Uinv);
     bmul<B, T>(W, Uinv, L);
-    bstore<B, T>(ent_ref(kbest), L);
-    for (int k = 0; k < n_ent; k++) {
-      const int64_t j = ent_col(k);
-      if (j < 0 || pos[j] <= pbest) continue;
-      BRef<T> ukj;
-      if (j == kr) continue;
-      ukj = ilu_find<B, T>(g, emask, pos, ftptr, ftcol, fell, ftval, kr, j);
-      if (!ukj.p) continue;
+    bstore<B, T>(wref, L);
+    // row k: its slots, then its tail
+    const unsigned mk = kr < g.nc ? emask[kr] : 0u;
+    for (int s2 = 0; s2 < kSlots; s2++) {
+      if (s2 == kSelf || !((mk >> s2) & 1u)) continue;
+      int64_t pj = -1;
+      const BRef<T> wr = target(kr + g.off[s2], pj);
+      if (!wr.p || pj <= pbest) continue;
       T U[BB], P[BB], Wij[BB];
-      bload<B, T>(ukj, U);
+      bload<B, T>(BRef<T>{fell + ((int64_t)s2 * BB) * np + pbest, np}, U);
       bmul<B, T>(L, U, P);
-      BRef<T> wr = (j == i && cell) ? BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np} : ent_ref(k);
+      bload<B, T>(wr, Wij);
+#pragma unroll
+      for (int e = 0; e < BB; e++) Wij[e] = Wij[e] - P[e];
+      bstore<B, T>(wr, Wij);
+    }
+    const int64_t k0 = ftptr[pbest], k1 = ftptr[pbest + 1];
+    for (int64_t uk = k0; uk < k1; uk++) {
+      const int64_t j = ftcol[uk];
+      if (j == kr) continue;
+      int64_t pj = -1;
+      const BRef<T> wr = target(j, pj);
+      if (!wr.p || pj <= pbest) continue;
+      T U[BB], P[BB], Wij[BB];
+      bload<B, T>(BRef<T>{ftval + uk * BB, 1}, U);
+      bmul<B, T>(L, U, P);
       bload<B, T>(wr, Wij);
 #pragma unroll
       for (int e = 0; e < BB; e++) Wij[e] = Wij[e] - P[e];
@@ -1372,8 +1441,8 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
   T Wd[BB], inv[BB];
   BRef<T> dref{fell + ((int64_t)kSelf * BB) * np + q, np};
   if (!cell) {
-    for (int k = kSlots; k < n_ent; k++)
-      if (ent_col(k) == i) { dref = ent_ref(k); break; }
+    for (int64_t u = u0; u < u1; u++)
+      if (ftcol[u] == i) { dref = BRef<T>{ftval + u * BB, 1}; break; }
   }
   bload<B, T>(dref, Wd);
   if (!gj_inverse<B, T>(Wd, inv)) {
@@ -1381,6 +1450,7 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
     return;
   }
   bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+  (void)ftlow;
 }
 
 // The same factorisation for rows held entirely in the tail (wells, general
@@ -1520,6 +1590,84 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
   bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
 }
 
+// Long rows with a precomputed plan, one block per row: the row's blocks,
+// the U_kk^-1 of its earlier-ordered entries and (when they fit) the U_kj
+// blocks of the plan's pairs are staged in shared memory; the IKJ steps run
+// in ascending position of k, each step forming L_ik = W_ik U_kk^-1 with
+// BB threads and then W_ij -= L_ik U_kj with one thread per (pair,
+// element), the same products in the same order as the other kernels.
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_ilu_factor_planned(
+    int64_t np, const int64_t *ftptr, LongRowPlan plan, int64_t first, int64_t q1, int ub_in_smem, T *fell,
+    T *ftval, int *err) {
+  constexpr int BB = B * B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t r = first + blockIdx.x, q = q1 + blockIdx.x;
+  const int64_t u0 = ftptr[q], ne = ftptr[q + 1] - u0;
+  const int64_t l0 = plan.Lptr[r], nl = plan.Lptr[r + 1] - l0;
+  const int64_t p0 = plan.Pptr[l0], npair = plan.Pptr[l0 + nl] - p0;
+  T *W = reinterpret_cast<T *>(smem_raw);
+  T *Ui = W + ne * BB;
+  T *Ub = Ui + nl * BB;
+  __shared__ T Lsh[BB];
+  for (int64_t x = threadIdx.x; x < ne * BB; x += kThreads) W[x] = ftval[u0 * BB + x];
+  for (int64_t x = threadIdx.x; x < nl * BB; x += kThreads) {
+    const int64_t t = x / BB, e = x % BB;
+    Ui[x] = fell[((int64_t)kSelf * BB + e) * np + plan.Lpk[l0 + t]];
+  }
+  auto ublk = [&](int64_t pidx, int e) -> T {
+    const int64_t src = plan.Psrc[pidx];
+    return src >= 0 ? ftval[src + e] : fell[~src + (int64_t)e * np];
+  };
+  if (ub_in_smem)
+    for (int64_t x = threadIdx.x; x < npair * BB; x += kThreads) Ub[x] = ublk(p0 + x / BB, (int)(x % BB));
+  __syncthreads();
+  for (int64_t t = 0; t < nl; t++) {
+    const int64_t ut = plan.Lu[l0 + t];
+    if (threadIdx.x < BB) {
+      const int rr = threadIdx.x / B, c = threadIdx.x % B;
+      const T *Wt = W + ut * BB, *U = Ui + t * BB;
+      T acc = Wt[rr * B] * U[c];
+#pragma unroll
+      for (int tt = 1; tt < B; tt++) acc = acc + Wt[rr * B + tt] * U[tt * B + c];
+      Lsh[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < BB) W[ut * BB + threadIdx.x] = Lsh[threadIdx.x];
+    const int64_t pa = plan.Pptr[l0 + t], pb = plan.Pptr[l0 + t + 1];
+    for (int64_t task = threadIdx.x; task < (pb - pa) * BB; task += kThreads) {
+      const int64_t pidx = pa + task / BB;
+      const int el = (int)(task % BB), rr = el / B, c = el % B;
+      T acc;
+      if (ub_in_smem) {
+        const T *U = Ub + (pidx - p0) * BB;
+        acc = Lsh[rr * B] * U[c];
+#pragma unroll
+        for (int tt = 1; tt < B; tt++) acc = acc + Lsh[rr * B + tt] * U[tt * B + c];
+      } else {
+        acc = Lsh[rr * B] * ublk(pidx, c);
+#pragma unroll
+        for (int tt = 1; tt < B; tt++) acc = acc + Lsh[rr * B + tt] * ublk(pidx, tt * B + c);
+      }
+      T *Wd = W + (int64_t)plan.Pdst[pidx] * BB + el;
+      *Wd = *Wd - acc;
+    }
+    __syncthreads();
+  }
+  for (int64_t x = threadIdx.x; x < ne * BB; x += kThreads) ftval[u0 * BB + x] = W[x];
+  if (threadIdx.x != 0) return;
+  const int32_t dg = plan.diag[r];
+  T Wd[BB], inv[BB];
+  if (dg < 0) { atomicExch(err, 1); return; }
+#pragma unroll
+  for (int e = 0; e < BB; e++) Wd[e] = W[(int64_t)dg * BB + e];
+  if (!gj_inverse<B, T>(Wd, inv)) {
+    atomicExch(err, 1);
+    return;
+  }
+  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+}
+
 }  // namespace
 
 // =============================================================== launchers
@@ -1607,16 +1755,17 @@ void launch_ap_csr_fill(const Geom &g, const uint8_t *emask, const int64_t *tptr
   TRS_LAUNCHED();
 }
 
-void launch_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, int64_t *dpos, cudaStream_t s) {
+void launch_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int64_t *dpos,
+                     double *dval, cudaStream_t s) {
   if (!n) return;
-  k_diag_pos<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, dpos);
+  k_diag_pos<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, val, dpos, dval);
   TRS_LAUNCHED();
 }
 
-void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const int64_t *dpos,
+void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *dval,
                      double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s) {
   if (!n) return;
-  k_strength<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, val, dpos, theta, sflag, sdeg);
+  k_strength<<<grid_of(n * kStrengthLanes), kThreads, 0, s>>>(n, rp, col, val, dval, theta, sflag, sdeg);
   TRS_LAUNCHED();
 }
 
@@ -1848,11 +1997,30 @@ template void launch_ilu_init<float>(int, const Geom &, const uint8_t *, const i
 template <class T>
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
                               const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, T *fell, T *ftval,
-                              int64_t q0, int64_t q1, int64_t q2, int *err, cudaStream_t s) {
+                              int64_t q0, int64_t q1, int64_t q2, const LongRowPlan *plan, const LongRowColour *pc,
+                              int *err, cudaStream_t s) {
   if (q1 > q0) {
     TRS_DISPATCH_B(b, k_ilu_factor<B, T><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
                                                                                ftlow, fell, ftval, q0, q1, err));
     TRS_LAUNCHED();
+  }
+  if (q2 > q1 && plan && pc) {
+    // shared memory: the rows' blocks, the U_kk^-1 and, if they fit, the U_kj
+    const size_t bbs = (size_t)b * b * sizeof(T);
+    const size_t base = (size_t)(pc->max_ne + pc->max_nl) * bbs, full = base + (size_t)pc->max_np * bbs;
+    constexpr size_t kSmemMax = 200 * 1024;
+    if (base <= kSmemMax) {
+      const int ub = full <= kSmemMax;
+      const size_t bytes = ub ? full : base;
+      TRS_DISPATCH_B(b, {
+        auto kfn = k_ilu_factor_planned<B, T>;
+        TRS_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        kfn<<<(unsigned)(q2 - q1), kThreads, bytes, s>>>(g.n_rows, ftptr, *plan, pc->first, q1, ub, fell, ftval,
+                                                         err);
+      });
+      TRS_LAUNCHED();
+      return;
+    }
   }
   if (q2 > q1) {
     const unsigned grid = (unsigned)((q2 - q1 + kWarps - 1) / kWarps);
@@ -1863,10 +2031,12 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
 }
 template void launch_ilu_factor_colour<double>(int, const Geom &, const uint8_t *, const int32_t *, const int64_t *,
                                                const int64_t *, const int32_t *, const uint8_t *, double *,
-                                               double *, int64_t, int64_t, int64_t, int *, cudaStream_t);
+                                               double *, int64_t, int64_t, int64_t, const LongRowPlan *,
+                                               const LongRowColour *, int *, cudaStream_t);
 template void launch_ilu_factor_colour<float>(int, const Geom &, const uint8_t *, const int32_t *, const int64_t *,
                                               const int64_t *, const int32_t *, const uint8_t *, float *, float *,
-                                              int64_t, int64_t, int64_t, int *, cudaStream_t);
+                                              int64_t, int64_t, int64_t, const LongRowPlan *, const LongRowColour *,
+                                              int *, cudaStream_t);
 
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s) {
   if (!A->n) return;

@@ -44,6 +44,7 @@ struct Level {
   Csr A;                       // FP64 operator (level 0: CSR copy used by the setup only)
   DBuf<float> val32;           // FP32 values of A (levels >= 1, mixed precision)
   DBuf<int64_t> dpos;
+  DBuf<double> dval;           // diagonal values (for the strength test)
   DBuf<int32_t> agg;           // aggregate of each row in the next level (not on the coarsest)
   int64_t n_agg = 0;
   DBuf<int64_t> mptr;          // members of each next-level aggregate, ascending
@@ -85,6 +86,10 @@ struct trs_cpr {
   int64_t nft = 0;
   trs::DBuf<double> fell64, ftval64;
   trs::DBuf<float> fell32, ftval32;
+  // symbolic IKJ plan of the long rows (see trs::LongRowPlan)
+  trs::DBuf<int64_t> lr_Lptr, lr_Lpk, lr_Pptr, lr_Psrc;
+  trs::DBuf<int32_t> lr_diag, lr_Lu, lr_Pdst;
+  std::vector<trs::LongRowColour> lr_col;
   // preconditioner work vectors (precision of the preconditioner)
   trs::DBuf<char> wf, wy, wr, wx, wz;
   // Krylov workspace, sized on first use

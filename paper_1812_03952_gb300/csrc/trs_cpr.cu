@@ -6,6 +6,7 @@
 // Application, with f = D^-1 v (Algorithm pc-fpf read from its prose):
 //   y1 = F^-1 f; r1_p = (f - Ã y1)_0; e = V-cycle(r1_p);
 //   r2 = f - Ã (y1 + Pi_p e); z = y1 + Pi_p e + F^-1 r2.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <chrono>
@@ -63,14 +64,15 @@ void build_hierarchy(trs_cpr *M, cudaStream_t s) {
     Level &F = lev[l];
     const int64_t n = F.A.n;
     reserve(F.dpos, n);
-    launch_diag_pos(n, F.A.rp.p, F.A.col.p, F.dpos.p, s);
+    reserve(F.dval, n);
+    launch_diag_pos(n, F.A.rp.p, F.A.col.p, F.A.val.p, F.dpos.p, F.dval.p, s);
     reserve(F.dinv64, n);
     launch_gershgorin_dinv(F.A, F.dpos.p, F.dinv64.p, M->lam_bits.p + l, s);
     if (n <= o.coarse_max || l + 1 >= o.max_levels) break;
     const int64_t nnz = F.A.nnz;
     TBuf<uint8_t> sflag(std::max<int64_t>(nnz, 1), s);
     TBuf<int32_t> sdeg(n, s);
-    launch_strength(n, F.A.rp.p, F.A.col.p, F.A.val.p, F.dpos.p, o.theta, sflag.p, sdeg.p, s);
+    launch_strength(n, F.A.rp.p, F.A.col.p, F.A.val.p, F.dval.p, o.theta, sflag.p, sdeg.p, s);
     // MIS-2 rounds; the undecided count is read every second round (an extra
     // round after completion changes nothing)
     const uint32_t seed = o.seed ^ (kLevelSeedMul * (uint32_t)(l + 1));
@@ -133,6 +135,101 @@ void alloc_level_vectors(trs_cpr *M) {
   }
 }
 
+// ------------------------------------------------- long-row ILU plan
+// Built once per pattern on the host from the colour-major structure: for
+// every long row, its earlier-ordered entries in ascending position and the
+// (k, j) pairs that update it (the same sets the IKJ factorisation visits).
+void build_long_row_plan(trs_cpr *M, cudaStream_t s) {
+  const int64_t n = M->n, nc = M->g.nc;
+  const int bb = M->b * M->b;
+  M->lr_col.assign(M->ncol, LongRowColour{});
+  int64_t nlong = 0;
+  for (int c = 0; c < M->ncol; c++) nlong += M->cptr[c + 1] - M->cmid[c];
+  if (!nlong) return;
+  const auto hpos = download(M->pos.p, n, s);
+  const auto hft = download(M->ftptr.p, n + 1, s);
+  const auto hcol = download(M->ftcol.p, M->nft, s);
+  const auto hem = download(M->emask.p, nc, s);
+  const auto hcrow = download(M->crow.p, n, s);
+  std::vector<int64_t> Lptr{0}, Lpk, Pptr{0}, Psrc;
+  std::vector<int32_t> diag, Lu, Pdst;
+  std::vector<std::pair<int64_t, int32_t>> Ls;
+  for (int c = 0; c < M->ncol; c++) {
+    LongRowColour &pc = M->lr_col[c];
+    pc.first = (int64_t)diag.size();
+    for (int64_t q = M->cmid[c]; q < M->cptr[c + 1]; q++) {
+      const int64_t i = hcrow[q], u0 = hft[q], u1 = hft[q + 1];
+      auto local = [&](int64_t j) -> int32_t {
+        const auto b0 = hcol.begin() + u0, b1 = hcol.begin() + u1;
+        const auto it = std::lower_bound(b0, b1, (int32_t)j);
+        return (it != b1 && *it == j) ? (int32_t)(it - b0) : -1;
+      };
+      diag.push_back(local(i));
+      Ls.clear();
+      for (int64_t u = u0; u < u1; u++) {
+        const int64_t cj = hcol[u];
+        if (cj != i && hpos[cj] < q) Ls.push_back({hpos[cj], (int32_t)(u - u0)});
+      }
+      std::sort(Ls.begin(), Ls.end());
+      const int64_t pairs0 = (int64_t)Pdst.size();
+      for (const auto &L : Ls) {
+        const int64_t pk = L.first, kr = hcol[u0 + L.second];
+        Lu.push_back(L.second);
+        Lpk.push_back(pk);
+        if (kr < nc) {
+          const unsigned m = hem[kr];
+          for (int s2 = 0; s2 < kSlots; s2++) {
+            if (s2 == kSelf || !((m >> s2) & 1u)) continue;
+            const int64_t j = kr + M->g.off[s2];
+            if (hpos[j] <= pk) continue;
+            const int32_t d = local(j);
+            if (d < 0) continue;
+            Pdst.push_back(d);
+            Psrc.push_back(~((int64_t)s2 * bb * n + pk));
+          }
+        }
+        for (int64_t uk = hft[pk]; uk < hft[pk + 1]; uk++) {
+          const int64_t j = hcol[uk];
+          if (j == kr || hpos[j] <= pk) continue;
+          const int32_t d = local(j);
+          if (d < 0) continue;
+          Pdst.push_back(d);
+          Psrc.push_back(uk * bb);
+        }
+        Pptr.push_back((int64_t)Pdst.size());
+      }
+      Lptr.push_back((int64_t)Lu.size());
+      pc.max_ne = std::max<int64_t>(pc.max_ne, u1 - u0);
+      pc.max_nl = std::max<int64_t>(pc.max_nl, (int64_t)Ls.size());
+      pc.max_np = std::max<int64_t>(pc.max_np, (int64_t)Pdst.size() - pairs0);
+    }
+  }
+  auto up = [&](auto &dst, const auto &src) {
+    dst.alloc(std::max<size_t>(src.size(), 1));
+    dst.upload(src.data(), src.size(), s);
+  };
+  up(M->lr_Lptr, Lptr);
+  up(M->lr_diag, diag);
+  up(M->lr_Lu, Lu);
+  up(M->lr_Lpk, Lpk);
+  up(M->lr_Pptr, Pptr);
+  up(M->lr_Pdst, Pdst);
+  up(M->lr_Psrc, Psrc);
+  TRS_CUDA(cudaStreamSynchronize(s));
+}
+
+LongRowPlan long_row_plan(const trs_cpr *M) {
+  LongRowPlan p;
+  p.Lptr = M->lr_Lptr.p;
+  p.diag = M->lr_diag.p;
+  p.Lu = M->lr_Lu.p;
+  p.Lpk = M->lr_Lpk.p;
+  p.Pptr = M->lr_Pptr.p;
+  p.Pdst = M->lr_Pdst.p;
+  p.Psrc = M->lr_Psrc.p;
+  return p;
+}
+
 // --------------------------------------------------- decoupling + ILU
 void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s) {
   const int b = M->b, bb = b * b;
@@ -169,19 +266,22 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
     alloc_level_vectors(M);
   }
   // block ILU(0) on Ã, in the preconditioner's precision
+  const LongRowPlan plan = long_row_plan(M);
   if (mixed) {
     launch_ilu_init<float>(b, M->g, M->emask.p, M->crow.p, M->at_ell32.p, M->at_tval32.p, M->ftsrc.p, M->nft,
                            M->fell32.p, M->ftval32.p, s);
     for (int c = 0; c < M->ncol; c++)
       launch_ilu_factor_colour<float>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
-                                      M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], err.p, s);
+                                      M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], &plan,
+                                      M->lr_col.empty() ? nullptr : &M->lr_col[c], err.p, s);
   } else {
     launch_ilu_init<double>(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft,
                             M->fell64.p, M->ftval64.p, s);
     for (int c = 0; c < M->ncol; c++)
       launch_ilu_factor_colour<double>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p,
                                        M->ftlow.p, M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c],
-                                       M->cptr[c + 1], err.p, s);
+                                       M->cptr[c + 1], &plan, M->lr_col.empty() ? nullptr : &M->lr_col[c],
+                                       err.p, s);
   }
   if (mixed) {
     auto cast = [&](DBuf<double> &src, DBuf<float> &dst, int64_t cnt) {
@@ -254,6 +354,7 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   launch_ilu_structure(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->crow.p, M->pos.p, M->lmask.p, M->ftptr, M->ftcol,
                        M->ftlow, M->ftsrc, s);
   M->nft = M->ntail;
+  build_long_row_plan(M, s);
   if (M->prec == TRS_FP32_PREC) {
     M->fell32.alloc((size_t)kSlots * bb * n);
     M->ftval32.alloc(std::max<int64_t>(M->nft * bb, 1));

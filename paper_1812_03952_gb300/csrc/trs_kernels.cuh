@@ -206,9 +206,11 @@ void launch_ap_csr_rowlen(const Geom &g, const uint8_t *emask, const int64_t *tp
 void launch_ap_csr_fill(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
                         const double *ap_ell, const double *ap_tval, const int64_t *rp, int32_t *col,
                         double *val, cudaStream_t s);
-void launch_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, int64_t *dpos, cudaStream_t s);
+// position and value of each row's diagonal entry (-1 and 0.0 if absent)
+void launch_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int64_t *dpos,
+                     double *dval, cudaStream_t s);
 void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
-                     const int64_t *dpos, double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s);
+                     const double *dval, double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s);
 void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_t s);
 void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
                        const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w,
@@ -240,11 +242,33 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
 template <class T>
 void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
                      const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell, T *ftval, cudaStream_t s);
+// Symbolic IKJ plan of the long rows (rows held in the tail: wells, general
+// rows), built once per pattern: for long row r, its earlier-ordered
+// entries k in ascending position (L_u: index in the row, L_pk: position of
+// row k) and, for each, the pairs (k, j) of row k with j later than k and
+// stored in row r (P_dst: index in row r; P_src: the block of U_kj, as an
+// element offset into the tail values if >= 0, or ~offset into the slot
+// array, stride n_rows).  diag: index of the diagonal in the row.
+struct LongRowPlan {
+  const int64_t *Lptr = nullptr;   // [nlong + 1]
+  const int32_t *diag = nullptr;   // [nlong]
+  const int32_t *Lu = nullptr;
+  const int64_t *Lpk = nullptr;
+  const int64_t *Pptr = nullptr;   // [nL + 1]
+  const int32_t *Pdst = nullptr;
+  const int64_t *Psrc = nullptr;
+};
+// Per colour: the first long row of the colour in the plan and the largest
+// entry, L and pair counts of its rows (they size the shared memory).
+struct LongRowColour {
+  int64_t first = 0, max_ne = 0, max_nl = 0, max_np = 0;
+};
 template <class T>
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow,
                               const int64_t *pos, const int64_t *ftptr, const int32_t *ftcol,
                               const uint8_t *ftlow, T *fell, T *ftval, int64_t q0, int64_t q1,
-                              int64_t q2, int *err, cudaStream_t s);
+                              int64_t q2, const LongRowPlan *plan, const LongRowColour *pc, int *err,
+                              cudaStream_t s);
 void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, int mode,
                            float *at_ell, float *at_tval, float *dinv, double *ap_ell, double *ap_tval,
                            int *err, cudaStream_t s);
