@@ -113,13 +113,13 @@ __global__ void k_scatter_values(int64_t nnzb, int bb, const int64_t *map, const
 }
 
 __global__ void k_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell,
-                                const double *tval, int64_t nc, double *uval) {
+                                const double *tval, int64_t nc, int aos, double *uval) {
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (idx >= nnzb * bb) return;
   const int64_t p = idx / bb, e = idx % bb, loc = map[p];
   if (loc < kSlots * nc) {
     const int64_t s = loc / nc, row = loc % nc;
-    uval[idx] = ell[(s * bb + e) * nc + row];
+    uval[idx] = aos ? ell[(s * nc + row) * bb + e] : ell[(s * bb + e) * nc + row];
   } else {
     uval[idx] = tval[(loc - kSlots * nc) * bb + e];
   }
@@ -385,7 +385,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
       if (!((m >> s) & 1u)) continue;
       if (s == kSelf && unit) {
 #pragma unroll
-        for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+        for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
         ap_ell[(int64_t)s * nc + i] = 1.0;
         continue;
       }
@@ -393,7 +393,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
       for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
       decouple_block<B>(mode, Ai, blk, out);
 #pragma unroll
-      for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = out[e];
+      for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = out[e];
       ap_ell[(int64_t)s * nc + i] = out[0];
     }
   }
@@ -475,13 +475,13 @@ __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mo
       if (!((m >> s) & 1u)) continue;
       if (s == kSelf && unit) {
 #pragma unroll
-        for (int e = 0; e < BB; e++) at_ell[((int64_t)s * BB + e) * nc + i] = (e % (B + 1) == 0) ? 1.f : 0.f;
+        for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = (e % (B + 1) == 0) ? 1.f : 0.f;
         ap_ell[(int64_t)s * nc + i] = 1.0;
         continue;
       }
 #pragma unroll
       for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
-      one(at_ell + ((int64_t)s * BB) * nc + i, nc, ap_ell + (int64_t)s * nc + i);
+      one(at_ell + ((int64_t)s * nc + i) * BB, 1, ap_ell + (int64_t)s * nc + i);
     }
   }
   for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
@@ -1280,8 +1280,8 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
 #pragma unroll
       for (int e = 0; e < BB; e++) {
         T v = T(0);
-        if ((m >> s) & 1u) v = at_ell[((int64_t)s * BB + e) * g.nc + i];
-        fell[((int64_t)s * BB + e) * np + q] = v;
+        if ((m >> s) & 1u) v = at_ell[((int64_t)s * g.nc + i) * BB + e];
+        fell[((int64_t)s * np + q) * BB + e] = v;
       }
     }
   }
@@ -1298,15 +1298,52 @@ struct BRef {
   int64_t stride;
 };
 
+// Blocks with unit stride start at multiples of bb elements of a cudaMalloc
+// allocation, so they take 128-bit accesses when bb * sizeof(T) allows.
 template <int B, class T>
 __device__ __forceinline__ void bload(BRef<T> r, T (&v)[B * B]) {
+  constexpr int BB = B * B;
+  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
+    if (r.stride == 1) {
 #pragma unroll
-  for (int e = 0; e < B * B; e++) v[e] = r.p[e * r.stride];
+      for (int k = 0; k < BB / 4; k++) {
+        const float4 t = reinterpret_cast<const float4 *>(r.p)[k];
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+      }
+      return;
+    }
+  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
+    if (r.stride == 1) {
+#pragma unroll
+      for (int k = 0; k < BB / 2; k++) {
+        const double2 t = reinterpret_cast<const double2 *>(r.p)[k];
+        v[2 * k] = t.x; v[2 * k + 1] = t.y;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) v[e] = r.p[e * r.stride];
 }
 template <int B, class T>
 __device__ __forceinline__ void bstore(BRef<T> r, const T (&v)[B * B]) {
+  constexpr int BB = B * B;
+  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
+    if (r.stride == 1) {
 #pragma unroll
-  for (int e = 0; e < B * B; e++) r.p[e * r.stride] = v[e];
+      for (int k = 0; k < BB / 4; k++)
+        reinterpret_cast<float4 *>(r.p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      return;
+    }
+  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
+    if (r.stride == 1) {
+#pragma unroll
+      for (int k = 0; k < BB / 2; k++) reinterpret_cast<double2 *>(r.p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) r.p[e * r.stride] = v[e];
 }
 
 // entry k of row i (k != i) in factor storage, or p = nullptr
@@ -1320,7 +1357,7 @@ __device__ BRef<T> ilu_find(const Geom &g, const uint8_t *emask, const int64_t *
     const unsigned m = emask[i];
     for (int s = 0; s < kSlots; s++)
       if (s != kSelf && ((m >> s) & 1u) && g.off[s] == d)
-        return BRef<T>{fell + ((int64_t)s * BB) * np + qi, np};
+        return BRef<T>{fell + ((int64_t)s * np + qi) * BB, 1};
   }
   int64_t lo = ftptr[qi], hi = ftptr[qi + 1] - 1;
   while (lo <= hi) {
@@ -1358,14 +1395,14 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
   auto target = [&](int64_t j, int64_t &pj) -> BRef<T> {
     if (j == i) {
       pj = q;
-      if (cell) return BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np};
+      if (cell) return BRef<T>{fell + ((int64_t)kSelf * np + q) * BB, 1};
     } else if (cell && j < g.nc) {
       const int64_t d = j - i;
 #pragma unroll
       for (int s = 0; s < kSlots; s++)
         if (s != kSelf && ((m >> s) & 1u) && g.off[s] == d) {
           pj = spos[s];
-          return BRef<T>{fell + ((int64_t)s * BB) * np + q, np};
+          return BRef<T>{fell + ((int64_t)s * np + q) * BB, 1};
         }
     }
     for (int64_t u = u0; u < u1; u++)
@@ -1386,7 +1423,7 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
       if (pc > cur && pc < pbest) {
         pbest = pc;
         kr = i + g.off[s];
-        wref = BRef<T>{fell + ((int64_t)s * BB) * np + q, np};
+        wref = BRef<T>{fell + ((int64_t)s * np + q) * BB, 1};
       }
     }
     for (int64_t u = u0; u < u1; u++) {
@@ -1403,7 +1440,7 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
     cur = pbest;
     T W[BB], Uinv[BB], L[BB];
     bload<B, T>(wref, W);
-    bload<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + pbest, np}, Uinv);
+    bload<B, T>(BRef<T>{fell + ((int64_t)kSelf * np + pbest) * BB, 1}, Uinv);
     bmul<B, T>(W, Uinv, L);
     bstore<B, T>(wref, L);
     // row k: its slots, then its tail
@@ -1414,7 +1451,7 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
       const BRef<T> wr = target(kr + g.off[s2], pj);
       if (!wr.p || pj <= pbest) continue;
       T U[BB], P[BB], Wij[BB];
-      bload<B, T>(BRef<T>{fell + ((int64_t)s2 * BB) * np + pbest, np}, U);
+      bload<B, T>(BRef<T>{fell + ((int64_t)s2 * np + pbest) * BB, 1}, U);
       bmul<B, T>(L, U, P);
       bload<B, T>(wr, Wij);
 #pragma unroll
@@ -1439,7 +1476,7 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
   }
   // diagonal: slot 3 for cells, the tail entry for other rows
   T Wd[BB], inv[BB];
-  BRef<T> dref{fell + ((int64_t)kSelf * BB) * np + q, np};
+  BRef<T> dref{fell + ((int64_t)kSelf * np + q) * BB, 1};
   if (!cell) {
     for (int64_t u = u0; u < u1; u++)
       if (ftcol[u] == i) { dref = BRef<T>{ftval + u * BB, 1}; break; }
@@ -1449,7 +1486,7 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
     atomicExch(err, 1);
     return;
   }
-  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * np + q) * BB, 1}, inv);
   (void)ftlow;
 }
 
@@ -1510,10 +1547,10 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
     if (lane < BB) {
       const int r = lane / B, c = lane % B;
       const T *W = ftval + ub * BB;
-      const T *U = fell + ((int64_t)kSelf * BB) * np + pb;
-      T acc = W[r * B] * U[(int64_t)c * np];
+      const T *U = fell + ((int64_t)kSelf * np + pb) * BB;
+      T acc = W[r * B] * U[c];
 #pragma unroll
-      for (int t = 1; t < B; t++) acc = acc + W[r * B + t] * U[(int64_t)(t * B + c) * np];
+      for (int t = 1; t < B; t++) acc = acc + W[r * B + t] * U[t * B + c];
       s_L[wid][lane] = acc;
     }
     __syncwarp();
@@ -1530,8 +1567,8 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
         if (e < kSlots) {
           if (e != kSelf && ((mk >> e) & 1u)) {
             j = kr + g.off[e];
-            src = ((int64_t)e * BB) * np + pb;  // into fell
-            srcs = -np;                          // negative stride marks fell
+            src = ((int64_t)e * np + pb) * BB;  // into fell
+            srcs = -1;                          // negative marks fell
           }
         } else {
           const int64_t uk = ku0 + (e - kSlots);
@@ -1562,7 +1599,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
         const int r = el / B, c = el % B;
         const int64_t sb = s_src[wid][ent], ss = s_srcs[wid][ent];
         const T *U = ss < 0 ? fell + sb : ftval + sb;
-        const int64_t st = ss < 0 ? np : 1;
+        const int64_t st = 1;
         T acc = s_L[wid][r * B] * U[(int64_t)c * st];
 #pragma unroll
         for (int t = 1; t < B; t++) acc = acc + s_L[wid][r * B + t] * U[(int64_t)(t * B + c) * st];
@@ -1587,7 +1624,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
     atomicExch(err, 1);
     return;
   }
-  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * np + q) * BB, 1}, inv);
 }
 
 // Long rows with a precomputed plan, one block per row: the row's blocks,
@@ -1613,11 +1650,11 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_planned(
   for (int64_t x = threadIdx.x; x < ne * BB; x += kThreads) W[x] = ftval[u0 * BB + x];
   for (int64_t x = threadIdx.x; x < nl * BB; x += kThreads) {
     const int64_t t = x / BB, e = x % BB;
-    Ui[x] = fell[((int64_t)kSelf * BB + e) * np + plan.Lpk[l0 + t]];
+    Ui[x] = fell[((int64_t)kSelf * np + plan.Lpk[l0 + t]) * BB + e];
   }
   auto ublk = [&](int64_t pidx, int e) -> T {
     const int64_t src = plan.Psrc[pidx];
-    return src >= 0 ? ftval[src + e] : fell[~src + (int64_t)e * np];
+    return src >= 0 ? ftval[src + e] : fell[~src + e];
   };
   if (ub_in_smem)
     for (int64_t x = threadIdx.x; x < npair * BB; x += kThreads) Ub[x] = ublk(p0 + x / BB, (int)(x % BB));
@@ -1665,7 +1702,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_planned(
     atomicExch(err, 1);
     return;
   }
-  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * BB) * np + q, np}, inv);
+  bstore<B, T>(BRef<T>{fell + ((int64_t)kSelf * np + q) * BB, 1}, inv);
 }
 
 }  // namespace
@@ -1703,9 +1740,9 @@ void launch_scatter_values(int64_t nnzb, int bb, const int64_t *map, const doubl
 }
 
 void launch_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell, const double *tval,
-                          int64_t nc, double *uval, cudaStream_t s) {
+                          int64_t nc, double *uval, cudaStream_t s, int aos) {
   if (!nnzb) return;
-  k_gather_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(nnzb, bb, map, ell, tval, nc, uval);
+  k_gather_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(nnzb, bb, map, ell, tval, nc, aos, uval);
   TRS_LAUNCHED();
 }
 

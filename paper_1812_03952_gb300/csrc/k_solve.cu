@@ -58,6 +58,31 @@ __device__ __forceinline__ void store_blk(T *p, const T (&v)[B]) {
   }
 }
 
+// One b x b block stored contiguously (the per-slot layout [7][rows][bb] of
+// the decoupled matrix and of the ILU factors), with 128-bit loads where the
+// block size allows (block starts are multiples of bb elements from a
+// cudaMalloc base, so 16-byte aligned when bb * sizeof(T) is).
+template <int B, class T>
+__device__ __forceinline__ void load_block(const T *__restrict__ p, T (&v)[B * B]) {
+  constexpr int BB = B * B;
+  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < BB / 4; k++) {
+      const float4 t = reinterpret_cast<const float4 *>(p)[k];
+      v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < BB / 2; k++) {
+      const double2 t = reinterpret_cast<const double2 *>(p)[k];
+      v[2 * k] = t.x; v[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < BB; e++) v[e] = p[e];
+  }
+}
+
 // y2_j = y1_j + Pi_p e0_j (y1 = NULL: zero)
 template <int B, class T>
 __device__ __forceinline__ void load_y2(const T *__restrict__ y1, const T *__restrict__ e0, int64_t j, T (&v)[B]) {
@@ -286,11 +311,12 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
       const int64_t j = i + F.g.off[s];
       T yj[B];
       load_blk<B>(y + j * B, yj);
-      const T *blk = F.fell + (int64_t)s * BB * np + q;
+      T bv[BB];
+      load_block<B>(F.fell + ((int64_t)s * np + q) * BB, bv);
 #pragma unroll
       for (int r = 0; r < B; r++)
 #pragma unroll
-        for (int c = 0; c < B; c++) t[r] = fma(-blk[(int64_t)(r * B + c) * np], yj[c], t[r]);
+        for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
     }
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       if (!F.ftlow[u]) continue;
@@ -347,11 +373,12 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
       const int64_t j = i + F.g.off[s];
       T yj[B];
       load_blk<B>(y + j * B, yj);
-      const T *blk = F.fell + (int64_t)s * BB * np + q;
+      T bv[BB];
+      load_block<B>(F.fell + ((int64_t)s * np + q) * BB, bv);
 #pragma unroll
       for (int r = 0; r < B; r++)
 #pragma unroll
-        for (int c = 0; c < B; c++) t[r] = fma(-blk[(int64_t)(r * B + c) * np], yj[c], t[r]);
+        for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
     }
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       const int64_t j = F.ftcol[u];
@@ -384,13 +411,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     for (int r = 0; r < B; r++) t[r] = static_cast<T>(to_d(y[i * B + r]) - acc[r]);
   }
   // x_i = U_ii^-1 t
-  const T *dg = F.fell + (int64_t)kSelf * BB * np + q;
+  T dg[BB];
+  load_block<B>(F.fell + ((int64_t)kSelf * np + q) * BB, dg);
   T xv[B];
 #pragma unroll
   for (int r = 0; r < B; r++) {
     T a = T(0);
 #pragma unroll
-    for (int c = 0; c < B; c++) a = fma(dg[(int64_t)(r * B + c) * np], t[c], a);
+    for (int c = 0; c < B; c++) a = fma(dg[r * B + c], t[c], a);
     xv[r] = a;
   }
   store_blk<B>(y + i * B, xv);
@@ -421,9 +449,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
     for (int s = 0; s < kSlots; s++) {
       if (!((m >> s) & 1u)) continue;
       const int64_t j = i + At.g.off[s];
-      const T *blk = At.ell + (int64_t)s * BB * nc + i;
+      const T *blk = At.ell + ((int64_t)s * nc + i) * BB;
 #pragma unroll
-      for (int c = 0; c < B; c++) acc = fma(blk[(int64_t)c * nc], y[j * B + c], acc);
+      for (int c = 0; c < B; c++) acc = fma(blk[c], y[j * B + c], acc);
     }
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];
@@ -474,11 +502,12 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
       const int64_t j = i + At.g.off[s];
       T yj[B];
       load_y2<B>(y1, e0, j, yj);
-      const T *blk = At.ell + (int64_t)s * BB * nc + i;
+      T bv[BB];
+      load_block<B>(At.ell + ((int64_t)s * nc + i) * BB, bv);
 #pragma unroll
       for (int rr = 0; rr < B; rr++)
 #pragma unroll
-        for (int c = 0; c < B; c++) acc[rr] = fma(blk[(int64_t)(rr * B + c) * nc], yj[c], acc[rr]);
+        for (int c = 0; c < B; c++) acc[rr] = fma(bv[rr * B + c], yj[c], acc[rr]);
     }
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];

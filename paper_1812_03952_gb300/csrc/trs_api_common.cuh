@@ -68,7 +68,8 @@ struct trs_cpr {
   trs::DBuf<uint8_t> emask;
   trs::DBuf<int64_t> tptr, tdiag, map;
   trs::DBuf<int32_t> tcol;
-  // decoupled matrix, D^-1 ([bb][n]) and the level-0 pressure matrix
+  // decoupled matrix (ELL part [7][nc][bb], blocks contiguous), D^-1 ([bb][n]) and the
+  // level-0 pressure matrix
   trs::DBuf<double> at_ell64, at_tval64, dinv64, ap_ell64, ap_tval64;
   trs::DBuf<float> at_ell32, at_tval32, dinv32, ap_ell32, ap_tval32;
   // pressure AMG

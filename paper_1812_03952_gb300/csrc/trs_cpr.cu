@@ -185,7 +185,7 @@ void build_long_row_plan(trs_cpr *M, cudaStream_t s) {
             const int32_t d = local(j);
             if (d < 0) continue;
             Pdst.push_back(d);
-            Psrc.push_back(~((int64_t)s2 * bb * n + pk));
+            Psrc.push_back(~(((int64_t)s2 * n + pk) * bb));
           }
         }
         for (int64_t uk = hft[pk]; uk < hft[pk + 1]; uk++) {
@@ -1033,7 +1033,7 @@ trs_status trs_cpr_get_decoupled(const trs_cpr *M, double *vt, double *dinv) {
     }
     if (vt) {
       DBuf<double> stage(std::max<int64_t>(M->nnzb * bb, 1));
-      launch_gather_values(M->nnzb, bb, M->map.p, ellp, tvalp, M->g.nc, stage.p, 0);
+      launch_gather_values(M->nnzb, bb, M->map.p, ellp, tvalp, M->g.nc, stage.p, 0, /*aos=*/1);
       auto h = download(stage.p, M->nnzb * bb, 0);
       std::copy(h.begin(), h.end(), vt);
     }

@@ -151,7 +151,7 @@ struct MatView {
   const uint8_t *emask;   // [nc]
   const int64_t *tptr;    // [n_rows + 1]
   const int32_t *tcol;    // [ntail]
-  const T *ell;           // [7][bb][nc]
+  const T *ell;           // [7][bb][nc] (the decoupled matrix Ã: [7][nc][bb], blocks contiguous)
   const T *tval;          // [ntail][bb]
 };
 

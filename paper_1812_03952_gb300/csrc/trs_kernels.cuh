@@ -25,7 +25,7 @@ struct IluView {
   const int64_t *ftptr;   // [n_rows+1] tail by position
   const int32_t *ftcol;   // natural column
   const uint8_t *ftlow;   // 1: L block, 0: U block
-  const T *fell;          // [7][bb][n_rows] by position; slot 3 = U_ii^-1
+  const T *fell;          // [7][n_rows][bb] by position (blocks contiguous); slot 3 = U_ii^-1
   const T *ftval;         // [nft][bb]
 };
 
@@ -176,8 +176,10 @@ void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double 
 // ---------------------------------------------------------------- k_setup
 void launch_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval,
                            int64_t nc, double *ell, double *tval, cudaStream_t s);
+// values in canonical BSR order from the ELL/tail storage; aos = 1 for the
+// per-slot block-contiguous layout [7][nc][bb] of the decoupled matrix
 void launch_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell,
-                          const double *tval, int64_t nc, double *uval, cudaStream_t s);
+                          const double *tval, int64_t nc, double *uval, cudaStream_t s, int aos = 0);
 void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, double kvkh,
                      double c_t, const double *M, const double *acc, const double *wi,
                      const double *lam, cudaStream_t s);
