@@ -356,8 +356,8 @@ __device__ __forceinline__ bool unit_diagonal(int mode) { return mode == TRS_DEC
 // the ELL/tail layout of A (diagonal exactly I for ABF and FRS+ABF), and
 // the pressure entries (Ã_ij)_00.
 template <int B>
-__global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, double *at_ell, double *at_tval,
-                           double *dinv, double *ap_ell, double *ap_tval, int *err) {
+__global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, double *at_ell, double *at_p,
+                           double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err) {
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t nc = A.g.nc, n = A.g.n_rows;
@@ -386,6 +386,8 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
       if (s == kSelf && unit) {
 #pragma unroll
         for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = (e % (B + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+        for (int c = 0; c < B; c++) at_p[((int64_t)s * B + c) * nc + i] = c == 0 ? 1.0 : 0.0;
         ap_ell[(int64_t)s * nc + i] = 1.0;
         continue;
       }
@@ -394,6 +396,8 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
       decouple_block<B>(mode, Ai, blk, out);
 #pragma unroll
       for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = out[e];
+#pragma unroll
+      for (int c = 0; c < B; c++) at_p[((int64_t)s * B + c) * nc + i] = out[c];
       ap_ell[(int64_t)s * nc + i] = out[0];
     }
   }
@@ -418,8 +422,8 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
 // aggregates); the blocks Ã_ij and D_i^-1 are stored in FP32, the product
 // taken in FP32 (for FRS+ABF: Ai in FP32 times R A_ij formed in FP64).
 template <int B>
-__global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mode, float *at_ell, float *at_tval,
-                                 float *dinv, double *ap_ell, double *ap_tval, int *err) {
+__global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mode, float *at_ell, float *at_p,
+                                 float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err) {
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t nc = A.g.nc, n = A.g.n_rows;
@@ -476,12 +480,16 @@ __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mo
       if (s == kSelf && unit) {
 #pragma unroll
         for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = (e % (B + 1) == 0) ? 1.f : 0.f;
+#pragma unroll
+        for (int c = 0; c < B; c++) at_p[((int64_t)s * B + c) * nc + i] = c == 0 ? 1.f : 0.f;
         ap_ell[(int64_t)s * nc + i] = 1.0;
         continue;
       }
 #pragma unroll
       for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
       one(at_ell + ((int64_t)s * nc + i) * BB, 1, ap_ell + (int64_t)s * nc + i);
+#pragma unroll
+      for (int c = 0; c < B; c++) at_p[((int64_t)s * B + c) * nc + i] = of[c];
     }
   }
   for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
@@ -1266,31 +1274,6 @@ __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol
   }
 }
 
-template <int B, class T>
-__global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
-                           const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell,
-                           T *ftval) {
-  constexpr int BB = B * B;
-  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  const int64_t np = g.n_rows;
-  if (idx < np) {
-    const int64_t q = idx, i = crow[q];
-    const unsigned m = i < g.nc ? emask[i] : 0u;
-    for (int s = 0; s < kSlots; s++) {
-#pragma unroll
-      for (int e = 0; e < BB; e++) {
-        T v = T(0);
-        if ((m >> s) & 1u) v = at_ell[((int64_t)s * g.nc + i) * BB + e];
-        fell[((int64_t)s * np + q) * BB + e] = v;
-      }
-    }
-  }
-  if (idx < nft) {
-#pragma unroll
-    for (int e = 0; e < BB; e++) ftval[idx * BB + e] = at_tval[ftsrc[idx] * BB + e];
-  }
-}
-
 // Reference to one stored block of the factor: base pointer and stride.
 template <class T>
 struct BRef {
@@ -1344,6 +1327,33 @@ __device__ __forceinline__ void bstore(BRef<T> r, const T (&v)[B * B]) {
   }
 #pragma unroll
   for (int e = 0; e < BB; e++) r.p[e * r.stride] = v[e];
+}
+
+template <int B, class T>
+__global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
+                           const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell,
+                           T *ftval) {
+  constexpr int BB = B * B;
+  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  const int64_t np = g.n_rows;
+  if (idx < np) {
+    const int64_t q = idx, i = crow[q];
+    const unsigned m = i < g.nc ? emask[i] : 0u;
+    for (int s = 0; s < kSlots; s++) {
+      T v[BB];
+      if ((m >> s) & 1u) {
+        bload<B, T>(BRef<T>{const_cast<T *>(at_ell) + ((int64_t)s * g.nc + i) * BB, 1}, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < BB; e++) v[e] = T(0);
+      }
+      bstore<B, T>(BRef<T>{fell + ((int64_t)s * np + q) * BB, 1}, v);
+    }
+  }
+  if (idx < nft) {
+#pragma unroll
+    for (int e = 0; e < BB; e++) ftval[idx * BB + e] = at_tval[ftsrc[idx] * BB + e];
+  }
 }
 
 // entry k of row i (k != i) in factor storage, or p = nullptr
@@ -1765,18 +1775,21 @@ void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, dou
 }
 
 void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, int mode, double *at_ell,
-                     double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
+                     double *at_p, double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err,
+                     cudaStream_t s) {
   if (!A.g.n_rows) return;
-  TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_tval, dinv,
-                                                                           ap_ell, ap_tval, err));
+  TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_p, at_tval,
+                                                                           dinv, ap_ell, ap_tval, err));
   TRS_LAUNCHED();
 }
 
 void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, int mode, float *at_ell,
-                           float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err, cudaStream_t s) {
+                           float *at_p, float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err,
+                           cudaStream_t s) {
   if (!A.g.n_rows) return;
-  TRS_DISPATCH_B(b, k_decouple_mixed<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_tval,
-                                                                                 dinv, ap_ell, ap_tval, err));
+  TRS_DISPATCH_B(b, k_decouple_mixed<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_p,
+                                                                                 at_tval, dinv, ap_ell, ap_tval,
+                                                                                 err));
   TRS_LAUNCHED();
 }
 

@@ -435,9 +435,9 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
 // --------------------------------------------------- CPR residuals on Ã
 // rp_i = f_i0 - (Ã y)_i0, Ã_ii = I
 template <int B, class T>
-__global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__restrict__ f,
-                                                      const T *__restrict__ y, T *__restrict__ rp,
-                                                      int64_t cell_blocks, int unit) {
+__global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__restrict__ atp,
+                                                      const T *__restrict__ f, const T *__restrict__ y,
+                                                      T *__restrict__ rp, int64_t cell_blocks, int unit) {
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -449,9 +449,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
     for (int s = 0; s < kSlots; s++) {
       if (!((m >> s) & 1u)) continue;
       const int64_t j = i + At.g.off[s];
-      const T *blk = At.ell + ((int64_t)s * nc + i) * BB;
 #pragma unroll
-      for (int c = 0; c < B; c++) acc = fma(blk[c], y[j * B + c], acc);
+      for (int c = 0; c < B; c++) acc = fma(atp[((int64_t)s * B + c) * nc + i], y[j * B + c], acc);
     }
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];
@@ -1217,10 +1216,11 @@ void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, in
 }
 
 template <class T>
-void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, int unit, cudaStream_t s) {
+void launch_resid_p(int b, const MatView<T> &At, const T *atp, const T *f, const T *y, T *rp, int unit,
+                    cudaStream_t s) {
   const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_resid_p<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y, rp, cb, unit));
+  TRS_DISPATCH_B(b, k_resid_p<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, atp, f, y, rp, cb, unit));
   TRS_LAUNCHED();
 }
 
@@ -1407,7 +1407,8 @@ void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double 
                                   cudaStream_t);                                                            \
   template void launch_ilu_bwd<T, double>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,\
                                           const T *, double *, cudaStream_t);                               \
-  template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, T *, int, cudaStream_t);   \
+  template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,      \
+                                  cudaStream_t);                                                            \
   template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,    \
                                      cudaStream_t);                                                         \
   template void launch_cpr_combine<T>(int, int64_t, const T *, const T *, double *, cudaStream_t);          \

@@ -72,6 +72,8 @@ struct trs_cpr {
   // level-0 pressure matrix
   trs::DBuf<double> at_ell64, at_tval64, dinv64, ap_ell64, ap_tval64;
   trs::DBuf<float> at_ell32, at_tval32, dinv32, ap_ell32, ap_tval32;
+  trs::DBuf<double> at_p64;    // pressure rows of Ã's ELL part, [7][b][nc] (the first-stage residual)
+  trs::DBuf<float> at_p32;
   // pressure AMG
   std::vector<trs::Level> lev;   // lev[0 .. nlev-1] active; extra entries keep their buffers
   int nlev = 0;

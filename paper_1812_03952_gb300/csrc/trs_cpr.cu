@@ -239,11 +239,11 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   const bool mixed = M->prec == TRS_FP32_PREC;
   const int mode = M->opts.decoupling;
   if (mixed)
-    launch_decouple_mixed(b, A->view(), A->tdiag.p, mode, M->at_ell32.p, M->at_tval32.p, M->dinv32.p,
+    launch_decouple_mixed(b, A->view(), A->tdiag.p, mode, M->at_ell32.p, M->at_p32.p, M->at_tval32.p, M->dinv32.p,
                           M->ap_ell64.p, M->ap_tval64.p, err.p, s);
   else
-    launch_decouple(b, A->view(), A->tdiag.p, mode, M->at_ell64.p, M->at_tval64.p, M->dinv64.p, M->ap_ell64.p,
-                    M->ap_tval64.p, err.p, s);
+    launch_decouple(b, A->view(), A->tdiag.p, mode, M->at_ell64.p, M->at_p64.p, M->at_tval64.p, M->dinv64.p,
+                    M->ap_ell64.p, M->ap_tval64.p, err.p, s);
   if (rebuild_amg) {
     if (M->lev.empty()) M->lev.emplace_back();
     Csr &C0 = M->lev[0].A;
@@ -325,11 +325,15 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   if (M->prec == TRS_FP32_PREC) {
     M->at_ell32.alloc(std::max<int64_t>((int64_t)kSlots * bb * nc, 1));
     M->at_ell32.zero(s);
+    M->at_p32.alloc(std::max<int64_t>((int64_t)kSlots * b * nc, 1));
+    M->at_p32.zero(s);
     M->at_tval32.alloc(std::max<int64_t>(A->ntail * bb, 1));
     M->dinv32.alloc((size_t)bb * n);
   } else {
     M->at_ell64.alloc(std::max<int64_t>((int64_t)kSlots * bb * nc, 1));
     M->at_ell64.zero(s);
+    M->at_p64.alloc(std::max<int64_t>((int64_t)kSlots * b * nc, 1));
+    M->at_p64.zero(s);
     M->at_tval64.alloc(std::max<int64_t>(A->ntail * bb, 1));
     M->dinv64.alloc((size_t)bb * n);
   }
@@ -377,6 +381,12 @@ template <class T>
 struct Prec {
   static const T *dinv(const trs_cpr *M);
 };
+
+template <class T>
+const T *atp_of(const trs_cpr *M) {
+  if constexpr (std::is_same<T, float>::value) return M->at_p32.p;
+  else return M->at_p64.p;
+}
 
 template <class T>
 MatView<T> at_view(const trs_cpr *M) {
@@ -559,7 +569,7 @@ void cpr_apply_scaled(const trs_cpr *M, double *z, cudaStream_t s) {
     return;
   }
   ilu_solve<T, T>(M, f, y, nullptr, nullptr, (T *)nullptr, s);
-  launch_resid_p<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.r), unit, s);
+  launch_resid_p<T>(M->b, at_view<T>(M), atp_of<T>(M), f, y, tp<T>(L0.r), unit, s);
   vcycle<T>(M, 0, tp<T>(L0.r), tp<T>(L0.e), s);
   if (M->opts.stages == TRS_CPR_FP) {
     launch_cpr_combine<T>(M->b, M->n, y, tp<T>(L0.e), z, s);

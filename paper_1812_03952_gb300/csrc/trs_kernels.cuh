@@ -104,7 +104,8 @@ void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, in
 // CPR residuals on Ã; unit = 1 when every diagonal block of Ã is I (ABF,
 // FRS+ABF), so that y_i is added instead of multiplied; y1 may be NULL (zero).
 template <class T>
-void launch_resid_p(int b, const MatView<T> &At, const T *f, const T *y, T *rp, int unit, cudaStream_t s);
+void launch_resid_p(int b, const MatView<T> &At, const T *atp, const T *f, const T *y, T *rp, int unit,
+                    cudaStream_t s);
 template <class T>
 void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r,
                        int unit, cudaStream_t s);
@@ -184,8 +185,9 @@ void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, dou
                      double c_t, const double *M, const double *acc, const double *wi,
                      const double *lam, cudaStream_t s);
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s);
+// at_ell: Ã's ELL part [7][nc][bb]; at_p: its pressure rows (row 0 of every block) [7][b][nc]
 void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, int mode, double *at_ell,
-                     double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err,
+                     double *at_p, double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err,
                      cudaStream_t s);
 
 // exclusive scan of n int64 values (in place allowed), total written to *total (device)
@@ -272,8 +274,8 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
                               int64_t q2, const LongRowPlan *plan, const LongRowColour *pc, int *err,
                               cudaStream_t s);
 void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, int mode,
-                           float *at_ell, float *at_tval, float *dinv, double *ap_ell, double *ap_tval,
-                           int *err, cudaStream_t s);
+                           float *at_ell, float *at_p, float *at_tval, float *dinv, double *ap_ell,
+                           double *ap_tval, int *err, cudaStream_t s);
 
 // ------------------------------------------------------------- k_adjoint
 void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double alpha, double beta,
