@@ -449,11 +449,12 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, detail = oracle_sample(sysm, 1, last["iters"] if args.precision == "fp64" else
-                                    (fp64["iters"] if fp64 else FULL_ITERS[args.workload]))
+        est, detail = oracle_sample(sysm, 1, last["iters"] if args.precision == "fp64" or fp64 is None else
+                                    fp64["iters"])
         cpu = {"value": est, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": "assembly + CPR setup + 1 FGMRES iteration of the FP64 oracle on the full system, "
-                         "scaled to the FP64 path's iteration count", "detail": detail}
+                         "scaled to the iteration count of the FP64 path (of this run's path if the FP64 path "
+                         "was not run)", "detail": detail}
 
     if rank == 0:
         kname = ("k_spmv<4,double,double> (FGMRES operator block SpMV)" if args.krylov == "fgmres" else

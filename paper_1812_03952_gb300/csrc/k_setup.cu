@@ -125,6 +125,61 @@ __global__ void k_gather_values(int64_t nnzb, int bb, const int64_t *map, const 
   }
 }
 
+// Reference to one stored block of the factor: base pointer and stride.
+template <class T>
+struct BRef {
+  T *p;
+  int64_t stride;
+};
+
+// Blocks with unit stride start at multiples of bb elements of a cudaMalloc
+// allocation, so they take 128-bit accesses when bb * sizeof(T) allows.
+template <int B, class T>
+__device__ __forceinline__ void bload(BRef<T> r, T (&v)[B * B]) {
+  constexpr int BB = B * B;
+  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
+    if (r.stride == 1) {
+#pragma unroll
+      for (int k = 0; k < BB / 4; k++) {
+        const float4 t = reinterpret_cast<const float4 *>(r.p)[k];
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+      }
+      return;
+    }
+  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
+    if (r.stride == 1) {
+#pragma unroll
+      for (int k = 0; k < BB / 2; k++) {
+        const double2 t = reinterpret_cast<const double2 *>(r.p)[k];
+        v[2 * k] = t.x; v[2 * k + 1] = t.y;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) v[e] = r.p[e * r.stride];
+}
+template <int B, class T>
+__device__ __forceinline__ void bstore(BRef<T> r, const T (&v)[B * B]) {
+  constexpr int BB = B * B;
+  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
+    if (r.stride == 1) {
+#pragma unroll
+      for (int k = 0; k < BB / 4; k++)
+        reinterpret_cast<float4 *>(r.p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      return;
+    }
+  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
+    if (r.stride == 1) {
+#pragma unroll
+      for (int k = 0; k < BB / 2; k++) reinterpret_cast<double2 *>(r.p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < BB; e++) r.p[e * r.stride] = v[e];
+}
+
 // ------------------------------------------------------------ assembly
 // Harmonic-mean geometric transmissibility of one face (unit cell, unit
 // face), zero when both permeabilities vanish.
@@ -150,8 +205,7 @@ __global__ void k_assemble_cells(Geom g, const uint8_t *emask, double *ell, doub
   if (c >= g.nc) return;
   const int64_t nc = g.nc;
   double dg[BB];
-#pragma unroll
-  for (int e = 0; e < BB; e++) dg[e] = acc[c * BB + e];
+  bload<B, double>(BRef<double>{const_cast<double *>(acc) + c * BB, 1}, dg);
   const double kc = perm_of(perm, is_log, c);
   const unsigned m = emask[c];
   for (int d = 0; d < 6; d++) {
@@ -159,7 +213,8 @@ __global__ void k_assemble_cells(Geom g, const uint8_t *emask, double *ell, doub
     if (!((m >> s) & 1u)) continue;
     const int64_t j = c + g.off[s];
     const double T = face_T(kc, perm_of(perm, is_log, j), d == 0 || d == 5, kvkh, c_t);
-    const double *Mij = M + (c * 6 + d) * BB;
+    double Mij[BB];
+    bload<B, double>(BRef<double>{const_cast<double *>(M) + (c * 6 + d) * BB, 1}, Mij);
 #pragma unroll
     for (int e = 0; e < BB; e++) {
       const double flux = T * Mij[e];
@@ -394,8 +449,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
 #pragma unroll
       for (int e = 0; e < BB; e++) blk[e] = A.ell[((int64_t)s * BB + e) * nc + i];
       decouple_block<B>(mode, Ai, blk, out);
-#pragma unroll
-      for (int e = 0; e < BB; e++) at_ell[((int64_t)s * nc + i) * BB + e] = out[e];
+      bstore<B, double>(BRef<double>{at_ell + ((int64_t)s * nc + i) * BB, 1}, out);
 #pragma unroll
       for (int c = 0; c < B; c++) at_p[((int64_t)s * B + c) * nc + i] = out[c];
       ap_ell[(int64_t)s * nc + i] = out[0];
@@ -470,8 +524,7 @@ __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mo
 #pragma unroll
     for (int e = 0; e < BB; e++) bf[e] = (float)src[e];
     bmul<B, float>(Lf, bf, of);
-#pragma unroll
-    for (int e = 0; e < BB; e++) dst[(int64_t)e * dstride] = of[e];
+    bstore<B, float>(BRef<float>{dst, dstride}, of);
   };
   if (cell) {
     const unsigned m = A.emask[i];
@@ -722,25 +775,20 @@ __global__ void k_member_sort(int64_t na, const int64_t *mptr, int32_t *midx) {
 
 // ------------------------------------------------------------- Galerkin
 // One warp per coarse row I.  The (J, a) pairs of the members of I (members
-// ascending, entries in column order) are staged in shared memory; the
-// distinct coarse columns are taken in ascending order by repeated minimum
-// search, and each value is the running sum, from 0.0, of the matching
-// pairs in staging order.  Rows longer than the staging area read the pairs
-// from global memory in the same order.  fill == 0 counts, fill == 1 writes.
+// ascending, entries in column order) are staged in shared memory in that
+// order, with keys J << 32 | staging index; a warp bitonic sort of the keys
+// puts equal J together in staging order, and the first lane of each run
+// sums its run's values from 0.0 in that order (the definition's order).
+// Rows with more pairs than the staging area go to k_galerkin_long.
+// fill == 0 counts the distinct J, fill == 1 writes them.
 constexpr int kGalCap = 256;
-
-__device__ __forceinline__ int32_t warp_min_i32(int32_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
 __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t *rp, const int32_t *col,
                                                        const double *val, const int32_t *agg, const int64_t *mptr,
                                                        const int32_t *midx, int fill, int64_t *ccount,
                                                        const int64_t *crp, int32_t *ccol, double *cval,
                                                        int32_t *long_rows, int *n_long) {
-  __shared__ int32_t sJ[kWarps][kGalCap];
+  __shared__ uint64_t sK[kWarps][kGalCap];
   __shared__ double sV[kWarps][kGalCap];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t I = blockIdx.x * (int64_t)kWarps + wid;
@@ -779,75 +827,55 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
       const int em = __shfl_sync(0xffffffffu, excl, m);
       if (q < ctot) {
         const int64_t p = pm + (q - em);
-        sJ[wid][total + q] = agg[col[p]];
+        sK[wid][total + q] = ((uint64_t)(uint32_t)agg[col[p]] << 32) | (uint64_t)(total + q);
         sV[wid][total + q] = val[p];
       }
     }
     total += ctot;
   }
-  __syncwarp();
-  if (!staged) {  // handled by k_galerkin_long
+  if (!staged) {
     if (!fill && lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)I;
     return;
   }
-  int32_t cur = -1;
+  // bitonic sort of the keys, padded with the largest key to a power of two
+  int P = 1;
+  while (P < total) P <<= 1;
+  for (int t = total + lane; t < P; t += 32) sK[wid][t] = ~0ull;
+  __syncwarp();
+  for (int k2 = 2; k2 <= P; k2 <<= 1)
+    for (int j = k2 >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < P; t += 32) {
+        const int u = t ^ j;
+        if (u > t) {
+          const uint64_t a = sK[wid][t], b = sK[wid][u];
+          if ((a > b) == ((t & k2) == 0)) {
+            sK[wid][t] = b;
+            sK[wid][u] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  // runs of equal J: count them, or write each with its sum
   int64_t count = 0;
-  for (;;) {
-    int32_t mn = 0x7fffffff;
-    if (staged) {
-      for (int k = lane; k < total; k += 32) {
-        const int32_t J = sJ[wid][k];
-        if (J > cur && J < mn) mn = J;
-      }
-    } else {
-      for (int64_t t = m0; t < m1; t++) {
-        const int64_t i = midx[t];
-        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
-          const int32_t J = agg[col[p]];
-          if (J > cur && J < mn) mn = J;
-        }
-      }
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int t = t0 + lane;
+    bool head = false;
+    uint32_t J = 0;
+    if (t < total) {
+      J = (uint32_t)(sK[wid][t] >> 32);
+      head = t == 0 || (uint32_t)(sK[wid][t - 1] >> 32) != J;
     }
-    mn = warp_min_i32(mn);
-    if (mn == 0x7fffffff) break;
-    if (fill) {
-      double s = 0.0;
-      if (staged) {
-        for (int base = 0; base < total; base += 32) {
-          const int k = base + lane;
-          const bool hit = k < total && sJ[wid][k] == mn;
-          const double v = k < total ? sV[wid][k] : 0.0;
-          unsigned mask = __ballot_sync(0xffffffffu, hit);
-          while (mask) {
-            const int src = __ffs(mask) - 1;
-            s = s + __shfl_sync(0xffffffffu, v, src);
-            mask &= mask - 1;
-          }
-        }
-      } else {
-        for (int64_t t = m0; t < m1; t++) {
-          const int64_t i = midx[t];
-          const int64_t e = rp[i + 1];
-          for (int64_t base = rp[i]; base < e; base += 32) {
-            const int64_t p = base + lane;
-            const bool hit = p < e && agg[col[p]] == mn;
-            const double v = p < e ? val[p] : 0.0;
-            unsigned mask = __ballot_sync(0xffffffffu, hit);
-            while (mask) {
-              const int src = __ffs(mask) - 1;
-              s = s + __shfl_sync(0xffffffffu, v, src);
-              mask &= mask - 1;
-            }
-          }
-        }
-      }
-      if (lane == 0) {
-        ccol[crp[I] + count] = mn;
-        cval[crp[I] + count] = s;
-      }
+    const unsigned hm = __ballot_sync(0xffffffffu, head);
+    if (fill && head) {
+      double sum = 0.0;
+      for (int u = t; u < total && (uint32_t)(sK[wid][u] >> 32) == J; u++)
+        sum = sum + sV[wid][(int)(sK[wid][u] & 0xffffffffu)];
+      const int64_t at = crp[I] + count + __popc(hm & ((1u << lane) - 1u));
+      ccol[at] = (int32_t)J;
+      cval[at] = sum;
     }
-    count++;
-    cur = mn;
+    count += __popc(hm);
   }
   if (!fill && lane == 0) ccount[I] = count;
 }
@@ -1272,61 +1300,6 @@ __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol
     ftlow[u] = pos[tcol[t]] < q ? 1 : 0;
     ftsrc[u] = t;
   }
-}
-
-// Reference to one stored block of the factor: base pointer and stride.
-template <class T>
-struct BRef {
-  T *p;
-  int64_t stride;
-};
-
-// Blocks with unit stride start at multiples of bb elements of a cudaMalloc
-// allocation, so they take 128-bit accesses when bb * sizeof(T) allows.
-template <int B, class T>
-__device__ __forceinline__ void bload(BRef<T> r, T (&v)[B * B]) {
-  constexpr int BB = B * B;
-  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
-    if (r.stride == 1) {
-#pragma unroll
-      for (int k = 0; k < BB / 4; k++) {
-        const float4 t = reinterpret_cast<const float4 *>(r.p)[k];
-        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
-      }
-      return;
-    }
-  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
-    if (r.stride == 1) {
-#pragma unroll
-      for (int k = 0; k < BB / 2; k++) {
-        const double2 t = reinterpret_cast<const double2 *>(r.p)[k];
-        v[2 * k] = t.x; v[2 * k + 1] = t.y;
-      }
-      return;
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < BB; e++) v[e] = r.p[e * r.stride];
-}
-template <int B, class T>
-__device__ __forceinline__ void bstore(BRef<T> r, const T (&v)[B * B]) {
-  constexpr int BB = B * B;
-  if constexpr (sizeof(T) == 4 && BB % 4 == 0) {
-    if (r.stride == 1) {
-#pragma unroll
-      for (int k = 0; k < BB / 4; k++)
-        reinterpret_cast<float4 *>(r.p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-      return;
-    }
-  } else if constexpr (sizeof(T) == 8 && BB % 2 == 0) {
-    if (r.stride == 1) {
-#pragma unroll
-      for (int k = 0; k < BB / 2; k++) reinterpret_cast<double2 *>(r.p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
-      return;
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < BB; e++) r.p[e * r.stride] = v[e];
 }
 
 template <int B, class T>

@@ -49,7 +49,10 @@ struct ScalarOp {
 
 // Coarse part of the AMG hierarchy run by one block (levels with few rows).
 constexpr int kMaxCheb = 8;
-constexpr int kCoarseFuseRows = 4096;
+#ifndef TRS_COARSE_FUSE_ROWS
+#define TRS_COARSE_FUSE_ROWS 4096
+#endif
+constexpr int kCoarseFuseRows = TRS_COARSE_FUSE_ROWS;
 
 template <class T>
 struct CoarseLevel {
