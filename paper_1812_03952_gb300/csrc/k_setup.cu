@@ -827,7 +827,10 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
       const int em = __shfl_sync(0xffffffffu, excl, m);
       if (q < ctot) {
         const int64_t p = pm + (q - em);
-        sK[wid][total + q] = ((uint64_t)(uint32_t)agg[col[p]] << 32) | (uint64_t)(total + q);
+        // columns outside the coarse space (agg < 0, a zero row of P) take the
+        // largest key: they sort last and start no run
+        const int32_t a = agg[col[p]];
+        sK[wid][total + q] = a < 0 ? ~0ull : (((uint64_t)(uint32_t)a << 32) | (uint64_t)(total + q));
         sV[wid][total + q] = val[p];
       }
     }
@@ -864,7 +867,7 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
     uint32_t J = 0;
     if (t < total) {
       J = (uint32_t)(sK[wid][t] >> 32);
-      head = t == 0 || (uint32_t)(sK[wid][t - 1] >> 32) != J;
+      head = J != 0xffffffffu && (t == 0 || (uint32_t)(sK[wid][t - 1] >> 32) != J);
     }
     const unsigned hm = __ballot_sync(0xffffffffu, head);
     if (fill && head) {
