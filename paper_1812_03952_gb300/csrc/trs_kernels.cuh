@@ -50,7 +50,7 @@ struct ScalarOp {
 // Coarse part of the AMG hierarchy run by one block (levels with few rows).
 constexpr int kMaxCheb = 8;
 #ifndef TRS_COARSE_FUSE_ROWS
-#define TRS_COARSE_FUSE_ROWS 4096
+#define TRS_COARSE_FUSE_ROWS 1024
 #endif
 constexpr int kCoarseFuseRows = TRS_COARSE_FUSE_ROWS;
 
