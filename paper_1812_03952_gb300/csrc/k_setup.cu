@@ -563,7 +563,7 @@ __global__ void k_ap_rowlen(Geom g, const uint8_t *emask, const int64_t *tptr, i
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.n_rows) return;
   int64_t l = tptr[i + 1] - tptr[i];
-  if (i < g.nc) l += __popc((unsigned)emask[i]);
+  if (i < g.nc) l += __popc((unsigned)emask[i] & ~kTailBit);
   len[i] = l;
 }
 
@@ -1287,8 +1287,9 @@ __global__ void k_ilu_lmask_len(Geom g, const uint8_t *emask, const int64_t *tpt
     for (int s = 0; s < kSlots; s++)
       if (s != kSelf && ((m >> s) & 1u) && pos[i + g.off[s]] < q) lm |= 1u << s;
   }
-  lmask[q] = (uint8_t)lm;
   len[q] = tptr[i + 1] - tptr[i];
+  if (len[q] > 0) lm |= kTailBit;
+  lmask[q] = (uint8_t)lm;
 }
 
 __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol, const int32_t *crow,

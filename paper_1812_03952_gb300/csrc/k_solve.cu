@@ -117,6 +117,7 @@ __device__ __forceinline__ void cell_row_apply(const MatView<TA> &A, int64_t i, 
 #pragma unroll
       for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[(int64_t)(r * B + c) * nc]), xj[c], acc[r]);
   }
+  if (!(m & kTailBit)) return;
   for (int64_t t = A.tptr[i]; t < A.tptr[i + 1]; t++) {
     const int64_t j = A.tcol[t];
     const TA *blk = A.tval + t * BB;
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
 #pragma unroll
         for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
     }
+    if (lm & kTailBit)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       if (!F.ftlow[u]) continue;
       const int64_t j = F.ftcol[u];
@@ -366,7 +368,8 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     if (!active) return;
     i = F.crow[q];
     load_blk<B>(y + i * B, t);
-    const unsigned um = F.emask[i] & ~(unsigned)F.lmask[q] & ~(1u << kSelf);
+    const unsigned lmq = F.lmask[q];
+    const unsigned um = F.emask[i] & ~lmq & ~(1u << kSelf);
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (!((um >> s) & 1u)) continue;
@@ -380,6 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
 #pragma unroll
         for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
     }
+    if (lmq & kTailBit)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       const int64_t j = F.ftcol[u];
       if (F.ftlow[u] || j == i) continue;
@@ -452,6 +456,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
 #pragma unroll
       for (int c = 0; c < B; c++) acc = fma(atp[((int64_t)s * B + c) * nc + i], y[j * B + c], acc);
     }
+    if (m & kTailBit)
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];
       if (unit && j == i) continue;
@@ -508,6 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
 #pragma unroll
         for (int c = 0; c < B; c++) acc[rr] = fma(bv[rr * B + c], yj[c], acc[rr]);
     }
+    if (m & kTailBit)
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
       const int64_t j = At.tcol[t];
       if (unit && j == i) continue;
@@ -568,6 +574,7 @@ __device__ __forceinline__ T scalar_rowdot(const ScalarOp<T> &op, int64_t i, con
 #pragma unroll
       for (int s = 0; s < kSlots; s++)
         if ((m >> s) & 1u) acc = fma(op.ell[(int64_t)s * op.g.nc + i], x[i + op.g.off[s]], acc);
+      if (!(m & kTailBit)) return acc;
     }
     for (int64_t t = op.tptr[i]; t < op.tptr[i + 1]; t++) acc = fma(op.tval[t], x[op.tcol[t]], acc);
   } else {

@@ -28,6 +28,10 @@ namespace trs {
 constexpr int kMaxB = 5;
 constexpr int kSlots = 7;
 constexpr int kSelf = 3;
+// Bit 7 of a cell's slot mask (emask) and of a position's lower mask
+// (lmask): the row also has entries in the tail, so that rows without any
+// (almost all cells) never read their tail pointers.
+constexpr unsigned kTailBit = 0x80u;
 constexpr int kMaxLevels = 16;
 constexpr int kDenseMax = 4096;
 constexpr int kMaxColours = 64;

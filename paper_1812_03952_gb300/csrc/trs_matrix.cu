@@ -106,6 +106,8 @@ void build_layout(trs_bsr *A, int64_t n, int b, const int64_t *rp, const int32_t
       }
     }
   }
+  for (int64_t i = 0; i < nc; i++)
+    if (tptr[i + 1] > tptr[i]) emask[i] |= (uint8_t)kTailBit;
   // tail entries grouped by column, rows ascending
   std::vector<int64_t> tc_ptr(n + 1, 0), tc_src(std::max<int64_t>(ntail, 1));
   std::vector<int32_t> tc_row(std::max<int64_t>(ntail, 1));
