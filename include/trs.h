@@ -235,9 +235,11 @@ trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *strea
                          trs_cpr **out);
 
 /* Refreshes M for new values of A with the same pattern.  reuse_amg = 1
- * keeps the AMG hierarchy (aggregates and coarse operators) and rebuilds
- * the decoupling, the level-0 pressure matrix and the ILU(0) factors;
- * reuse_amg = 0 rebuilds everything. */
+ * keeps the AMG aggregates (the strength graph, MIS-2 and aggregation, so P
+ * and every coarse pattern) and recomputes all values: the decoupling, the
+ * pressure matrix, every Galerkin product, the smoother bounds, the
+ * coarsest inverse and the ILU(0) factors; reuse_amg = 0 rebuilds
+ * everything. */
 trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void *stream);
 
 /* z = M^-1 v = CPR(Ã)^-1 (D^-1 v): one application of the preconditioner

@@ -122,6 +122,29 @@ void build_hierarchy(trs_cpr *M, cudaStream_t s) {
   for (int l = 0; l < nlev; l++) std::memcpy(&lev[l].lam, &bits[l], sizeof(double));
 }
 
+// Values only, for a matrix with the same pattern: the aggregates (and so P
+// and every coarse pattern) are kept; the level-0 pressure matrix, every
+// Galerkin product, the Gershgorin bounds and D^-1 of every level and the
+// coarsest inverse are recomputed from the new values.
+void refresh_hierarchy(trs_cpr *M, cudaStream_t s) {
+  auto &lev = M->lev;
+  Csr &C0 = lev[0].A;
+  launch_ap_csr_fill(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->ap_ell64.p, M->ap_tval64.p, C0.rp.p, C0.col.p,
+                     C0.val.p, s);
+  for (int l = 0; l < M->nlev; l++) {
+    Level &F = lev[l];
+    launch_gershgorin_dinv(F.A, F.dpos.p, F.dinv64.p, M->lam_bits.p + l, s);
+    if (l + 1 < M->nlev)
+      launch_galerkin(F.A, F.agg.p, F.n_agg, F.mptr.p, F.midx.p, lev[l + 1].A, s);
+  }
+  Level &C = lev[M->nlev - 1];
+  TRS_REQUIRE(launch_dense_inverse(C.A, M->cinv, s) == 0, TRS_ERR_SINGULAR_BLOCK, "coarsest AMG matrix is singular");
+  unsigned long long bits[kMaxLevels];
+  TRS_CUDA(cudaMemcpyAsync(bits, M->lam_bits.p, M->nlev * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamSynchronize(s));
+  for (int l = 0; l < M->nlev; l++) std::memcpy(&lev[l].lam, &bits[l], sizeof(double));
+}
+
 void alloc_level_vectors(trs_cpr *M) {
   const size_t es = M->prec == TRS_FP32_PREC ? sizeof(float) : sizeof(double);
   for (int l = 0; l < M->nlev; l++) {
@@ -264,6 +287,8 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
                        C0.val.p, s);
     build_hierarchy(M, s);
     alloc_level_vectors(M);
+  } else {
+    refresh_hierarchy(M, s);
   }
   // block ILU(0) on Ã, in the preconditioner's precision
   const LongRowPlan plan = long_row_plan(M);

@@ -311,3 +311,20 @@ def test_update_reuse_amg(trs, oracle, synth):
         np.testing.assert_array_equal(ds.A.values(), Ao.val)
         xg = x.cpu().numpy()
         assert np.linalg.norm(s.rhs - oracle.spmv(Ao, xg)) / np.linalg.norm(s.rhs) <= 1.01e-8
+        # the aggregates are kept; the values of every level follow the new matrix: level 0 is
+        # the new pressure matrix and level 1 its Galerkin product over the kept aggregates
+        # (FP64 preconditioner, so the decoupled values are the oracle's bit for bit)
+        M64 = trs.CPR(ds.A, precision="fp64") if step == 0 else M64
+        if step > 0:
+            M64.update(ds.A, reuse_amg=True)
+            vt, _ = oracle.decouple(Ao)
+            ap = oracle.pressure_matrix(Ao, vt)
+            rp0, col0, val0 = M64.level(0)
+            np.testing.assert_array_equal(val0, ap)
+            agg0 = M64.aggregates(0)
+            n1 = M64.info()["level_rows"][1]
+            crp, ccol, cval = oracle.galerkin(Ao.n, rp0, col0, val0, agg0, n1)
+            rp1, col1, val1 = M64.level(1)
+            np.testing.assert_array_equal(rp1, crp)
+            np.testing.assert_array_equal(col1, ccol)
+            np.testing.assert_array_equal(val1, cval)
