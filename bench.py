@@ -62,6 +62,10 @@ def parse():
                         "seeded +-20%% factors, AMG hierarchy rebuilt every --reuse steps, forward and adjoint "
                         "solve per system) instead of single solves")
     p.add_argument("--reuse", type=int, default=5)
+    p.add_argument("--decoupling", default="abf", choices=["abf", "none", "frs", "frs+abf"],
+                   help="decoupling of the forward CPR")
+    p.add_argument("--adjoint-decoupling", default="none", choices=["abf", "none", "frs", "frs+abf"],
+                   help="decoupling of the CPR built on A^T for the adjoint solves")
     p.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoother degree")
     p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"],
@@ -238,9 +242,9 @@ def run_sequence(args):
     g = torch.zeros(sysm.n_unknowns, dtype=torch.float64, device=dev)
     g[torch.from_numpy(np.unique(sysm.perf_cell).astype(np.int64) * sysm.b).to(dev)] = 1.0
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree)
+    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling)
     AT = A.transpose()
-    MT = trs.CPR(AT, precision=args.precision, cheb_degree=args.cheb_degree)
+    MT = trs.CPR(AT, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.adjoint_decoupling)
     x = torch.zeros_like(ds.rhs)
     records = []
 
@@ -285,6 +289,8 @@ def run_sequence(args):
                 "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
                            "unknowns": sysm.n_unknowns, "systems": args.sequence, "amg_rebuild_every": args.reuse,
                            "rtol": args.rtol, "precision": args.precision,
+                           "decoupling": args.decoupling, "adjoint_decoupling": args.adjoint_decoupling,
+                           "restart": args.restart,
                            "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
                 "per_system": records, "clocks": clk.summary(), "gpu_launches": trs.kernel_launches() - l0}
         print(json.dumps(line), flush=True)

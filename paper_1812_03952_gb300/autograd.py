@@ -16,9 +16,13 @@ class SolveContext:
     """Holds a synthetic system on the GPU and the preconditioners reused
     across forward/backward calls."""
 
-    def __init__(self, sysm, device="cuda", precision="fp64", rtol=1e-10, restart=30, maxit=1000):
+    def __init__(self, sysm, device="cuda", precision="fp64", rtol=1e-10, restart=30, maxit=1000,
+                 adjoint_decoupling="none"):
         self.ds = trs.DeviceSystem(sysm, device)
         self.precision = precision
+        # the CPR on A^T works best undecoupled: ABF of A^T turns the dominant pressure column of A
+        # into a dominant row, which the pressure extraction then weights badly
+        self.adjoint_decoupling = adjoint_decoupling
         self.rtol = rtol
         self.restart = restart
         self.maxit = maxit
@@ -46,7 +50,7 @@ class SolveContext:
         A = self.assemble(theta)
         self.AT = A.transpose(into=self.AT)
         if self.MT is None:
-            self.MT = trs.CPR(self.AT, precision=self.precision)
+            self.MT = trs.CPR(self.AT, precision=self.precision, decoupling=self.adjoint_decoupling)
         else:
             self.MT.update(self.AT, reuse_amg=False)
         lam, _, res = trs.solve_adjoint(A, self.AT, self.MT, g.contiguous(), x, rtol=self.rtol,
