@@ -317,7 +317,7 @@ def main():
     sysm = make_workload(args.workload)
     ds = trs.DeviceSystem(sysm, dev)
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree)
+    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling)
     x = torch.zeros_like(ds.rhs)
     info = M.info()
 
@@ -475,6 +475,7 @@ def main():
                        "krylov": args.krylov,
                        "precision": "FP32 CPR inside FP64 Krylov" if args.precision == "fp32" else "FP64",
                        "rtol": args.rtol, "restart": args.restart, "cheb_degree": args.cheb_degree,
+                       "decoupling": args.decoupling,
                        "l2": "inputs larger than L2 (Jacobian inputs 0.9 GB, matrix 0.9 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters": last["iters"], "true_relres": last["true_relres"], "host_true_relres": host_relres,
