@@ -270,10 +270,27 @@ __global__ void __launch_bounds__(kThreads) k_norm2(const double *__restrict__ x
 }
 
 // ----------------------------------------------------------- D^-1 scale
+// f = D^-1 (w / *div) (and vout = w / *div); rows of colour 0, which have no
+// earlier-ordered neighbour, also get y0 = f: the first forward ILU(0) sweep
+// of f, done here (seed.colour == nullptr: no seeding).
+template <class T>
+struct Seed {
+  const int32_t *colour;
+  T *y0;
+};
+
+template <int B, class T>
+__device__ __forceinline__ void seed_row(const Seed<T> &sd, int64_t i, const T *row) {
+  if (sd.colour && sd.colour[i] == 0) {
+#pragma unroll
+    for (int c = 0; c < B; c++) sd.y0[i * B + c] = row[c];
+  }
+}
+
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__restrict__ w,
                                                      const double *__restrict__ div, double *__restrict__ vout,
-                                                     const T *__restrict__ dinv, T *__restrict__ f) {
+                                                     const T *__restrict__ dinv, T *__restrict__ f, Seed<T> sd) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   double v[B];
@@ -284,13 +301,16 @@ __global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__
     for (int c = 0; c < B; c++) v[c] = v[c] * rd;
   }
   if (vout) store_blk<B>(vout + i * B, v);
+  T fr[B];
 #pragma unroll
   for (int r = 0; r < B; r++) {
     T acc = T(0);
 #pragma unroll
     for (int c = 0; c < B; c++) acc = fma(dinv[(int64_t)(r * B + c) * n + i], static_cast<T>(v[c]), acc);
     f[i * B + r] = acc;
+    fr[r] = acc;
   }
+  seed_row<B>(sd, i, fr);
 }
 
 // ------------------------------------------------------------ ILU sweeps
@@ -486,7 +506,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T *__restrict__ f,
                                                          const T *__restrict__ y1, const T *__restrict__ e0,
-                                                         T *__restrict__ r, int64_t cell_blocks, int unit) {
+                                                         T *__restrict__ r, int64_t cell_blocks, int unit,
+                                                         Seed<T> sd) {
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -532,6 +553,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
 #pragma unroll
     for (int rr = 0; rr < B; rr++) fv[rr] = fv[rr] - acc[rr];
     store_blk<B>(r + i * B, fv);
+    seed_row<B>(sd, i, fv);
   } else {
     const int lane = threadIdx.x & 31;
     const int64_t i = At.g.nc + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
@@ -559,7 +581,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
           own = y1 ? to_d(y1[i * B + rr]) : 0.0;
           if (rr == 0) own += to_d(e0[i]);
         }
-        r[i * B + rr] = static_cast<T>(to_d(f[i * B + rr]) - (own + acc[rr]));
+        const T rv = static_cast<T>(to_d(f[i * B + rr]) - (own + acc[rr]));
+        r[i * B + rr] = rv;
+        if (sd.colour && sd.colour[i] == 0) sd.y0[i * B + rr] = rv;
       }
   }
 }
@@ -1001,7 +1025,8 @@ template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_bicg_dir(int64_t n, const double *__restrict__ r,
                                                        const double *__restrict__ v, double *__restrict__ p,
                                                        const BicgScalars *__restrict__ sc, int first,
-                                                       const T *__restrict__ dinv, T *__restrict__ f) {
+                                                       const T *__restrict__ dinv, T *__restrict__ f,
+                                                       Seed<T> sd) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   double rv[B], pv[B];
@@ -1018,13 +1043,16 @@ __global__ void __launch_bounds__(kThreads) k_bicg_dir(int64_t n, const double *
     for (int c = 0; c < B; c++) pv[c] = rv[c] + beta * (pv[c] - om * vv[c]);
   }
   store_blk<B>(p + i * B, pv);
+  T fr[B];
 #pragma unroll
   for (int rr = 0; rr < B; rr++) {
     T acc = T(0);
 #pragma unroll
     for (int c = 0; c < B; c++) acc = fma(dinv[(int64_t)(rr * B + c) * n + i], static_cast<T>(pv[c]), acc);
     f[i * B + rr] = acc;
+    fr[rr] = acc;
   }
+  seed_row<B>(sd, i, fr);
 }
 
 // y = A x with <w, y> (ND = 1) or <w, y>, <y, y> (ND = 2), one thread per
@@ -1197,9 +1225,10 @@ void launch_norm2(const double *x, int64_t n, const RedScratch &red, double *out
 
 template <class T>
 void launch_dscale(int b, int64_t n_rows, const double *w, const double *div, double *vout, const T *dinv, T *f,
-                   cudaStream_t s) {
+                   const int32_t *colour, T *y0, cudaStream_t s) {
   if (!n_rows) return;
-  TRS_DISPATCH_B(b, k_dscale<B, T><<<grid_of(n_rows), kThreads, 0, s>>>(n_rows, w, div, vout, dinv, f));
+  const Seed<T> sd{colour, y0};
+  TRS_DISPATCH_B(b, k_dscale<B, T><<<grid_of(n_rows), kThreads, 0, s>>>(n_rows, w, div, vout, dinv, f, sd));
   TRS_LAUNCHED();
 }
 
@@ -1233,10 +1262,11 @@ void launch_resid_p(int b, const MatView<T> &At, const T *atp, const T *f, const
 
 template <class T>
 void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r, int unit,
-                       cudaStream_t s) {
+                       const int32_t *colour, T *x0, cudaStream_t s) {
   const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_resid_full<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y1, e0, r, cb, unit));
+  const Seed<T> sd{colour, x0};
+  TRS_DISPATCH_B(b, k_resid_full<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y1, e0, r, cb, unit, sd));
   TRS_LAUNCHED();
 }
 
@@ -1371,15 +1401,16 @@ void launch_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double r
 
 template <class T>
 void launch_bicg_dir(int b, int64_t n, const double *r, const double *v, double *p, const BicgScalars *sc,
-                     int first, const T *dinv, T *f, cudaStream_t s) {
+                     int first, const T *dinv, T *f, const int32_t *colour, T *y0, cudaStream_t s) {
   if (!n) return;
-  TRS_DISPATCH_B(b, k_bicg_dir<B, T><<<grid_of(n), kThreads, 0, s>>>(n, r, v, p, sc, first, dinv, f));
+  const Seed<T> sd{colour, y0};
+  TRS_DISPATCH_B(b, k_bicg_dir<B, T><<<grid_of(n), kThreads, 0, s>>>(n, r, v, p, sc, first, dinv, f, sd));
   TRS_LAUNCHED();
 }
 template void launch_bicg_dir<double>(int, int64_t, const double *, const double *, double *, const BicgScalars *,
-                                      int, const double *, double *, cudaStream_t);
+                                      int, const double *, double *, const int32_t *, double *, cudaStream_t);
 template void launch_bicg_dir<float>(int, int64_t, const double *, const double *, double *, const BicgScalars *,
-                                     int, const float *, float *, cudaStream_t);
+                                     int, const float *, float *, const int32_t *, float *, cudaStream_t);
 
 int64_t bicg_spmv_blocks(const Geom &g) { return cell_blocks_of(g.nc) + long_blocks_of(g.n_rows - g.nc); }
 
@@ -1409,7 +1440,7 @@ void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double 
 
 #define TRS_INST_T(T)                                                                                       \
   template void launch_dscale<T>(int, int64_t, const double *, const double *, double *, const T *, T *,     \
-                                 cudaStream_t);                                                             \
+                                 const int32_t *, T *, cudaStream_t);                                       \
   template void launch_ilu_fwd<T>(int, const IluView<T> &, const T *, T *, int64_t, int64_t, int64_t,        \
                                   cudaStream_t);                                                            \
   template void launch_ilu_bwd<T, double>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,\
@@ -1417,7 +1448,7 @@ void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double 
   template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,      \
                                   cudaStream_t);                                                            \
   template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,    \
-                                     cudaStream_t);                                                         \
+                                     const int32_t *, T *, cudaStream_t);                                   \
   template void launch_cpr_combine<T>(int, int64_t, const T *, const T *, double *, cudaStream_t);          \
   template void launch_pressure_of<T>(int, int64_t, const T *, T *, cudaStream_t);                          \
   template void launch_cheb_init<T>(int64_t, const T *, const T *, double, T *, T *, cudaStream_t);         \

@@ -568,10 +568,13 @@ void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
   chebyshev<T>(M, l, r, e, false, s);
 }
 
+// The forward sweep starts at colour 1: the kernel that produced rhs also
+// wrote y = rhs on the rows of colour 0, which have no earlier-ordered
+// neighbour (the sweep of colour 0).
 template <class T, class TZ>
 void ilu_solve(const trs_cpr *M, const T *rhs, T *y, const T *y1, const T *e0, TZ *zout, cudaStream_t s) {
   const IluView<T> F = ilu_view<T>(M);
-  for (int c = 0; c < M->ncol; c++) launch_ilu_fwd<T>(M->b, F, rhs, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], s);
+  for (int c = 1; c < M->ncol; c++) launch_ilu_fwd<T>(M->b, F, rhs, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], s);
   for (int c = M->ncol - 1; c >= 0; c--)
     launch_ilu_bwd<T, TZ>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout, s);
 }
@@ -589,7 +592,7 @@ void cpr_apply_scaled(const trs_cpr *M, double *z, cudaStream_t s) {
   if (M->opts.stages == TRS_CPR_PF) {
     launch_pressure_of<T>(M->b, M->n, f, tp<T>(L0.r), s);
     vcycle<T>(M, 0, tp<T>(L0.r), tp<T>(L0.e), s);
-    launch_resid_full<T>(M->b, at_view<T>(M), f, nullptr, tp<T>(L0.e), r, unit, s);
+    launch_resid_full<T>(M->b, at_view<T>(M), f, nullptr, tp<T>(L0.e), r, unit, M->colour.p, x, s);
     ilu_solve<T, double>(M, r, x, nullptr, tp<T>(L0.e), z, s);
     return;
   }
@@ -600,13 +603,13 @@ void cpr_apply_scaled(const trs_cpr *M, double *z, cudaStream_t s) {
     launch_cpr_combine<T>(M->b, M->n, y, tp<T>(L0.e), z, s);
     return;
   }
-  launch_resid_full<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.e), r, unit, s);
+  launch_resid_full<T>(M->b, at_view<T>(M), f, y, tp<T>(L0.e), r, unit, M->colour.p, x, s);
   ilu_solve<T, double>(M, r, x, y, tp<T>(L0.e), z, s);
 }
 
 template <class T>
 void cpr_apply_full(const trs_cpr *M, const double *v, const double *div, double *vout, double *z, cudaStream_t s) {
-  launch_dscale<T>(M->b, M->n, v, div, vout, dinv_of<T>(M), tp<T>(M->wf), s);
+  launch_dscale<T>(M->b, M->n, v, div, vout, dinv_of<T>(M), tp<T>(M->wf), M->colour.p, tp<T>(M->wy), s);
   cpr_apply_scaled<T>(M, z, s);
 }
 
@@ -812,14 +815,14 @@ trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, co
     cycles++;
     breakdown = false;
     for (int k = 0; iters < o.maxit; k++) {
-      launch_bicg_dir<T>(M->b, M->n, r, v, p, sc, k == 0, dinv_of<T>(M), tp<T>(M->wf), s);
+      launch_bicg_dir<T>(M->b, M->n, r, v, p, sc, k == 0, dinv_of<T>(M), tp<T>(M->wf), M->colour.p, tp<T>(M->wy), s);
       cpr_apply_scaled<T>(M, ph, s);
       const bool prof = g_spmv_prof.on;
       if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.a, s));
       launch_bicg_spmv(M->b, Av, ph, v, rh, 1, M->bpart.p, M->counter.p, sc, s);
       if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.b, s));
       launch_bicg_s(N, r, v, sv, red, sc, s);
-      launch_dscale<T>(M->b, M->n, sv, nullptr, nullptr, dinv_of<T>(M), tp<T>(M->wf), s);
+      launch_dscale<T>(M->b, M->n, sv, nullptr, nullptr, dinv_of<T>(M), tp<T>(M->wf), M->colour.p, tp<T>(M->wy), s);
       cpr_apply_scaled<T>(M, sh, s);
       if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.c, s));
       launch_bicg_spmv(M->b, Av, sh, t, sv, 2, M->bpart.p, M->counter.p, sc, s);

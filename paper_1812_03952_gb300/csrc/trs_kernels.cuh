@@ -96,8 +96,9 @@ void launch_true_residual(int b, const MatView<double> &A, const double *x, cons
 void launch_norm2(const double *x, int64_t n, const RedScratch &red, double *out, cudaStream_t s);
 
 template <class T>
+// colour, y0: if not NULL, rows of colour 0 also get y0 = f (their forward ILU(0) sweep)
 void launch_dscale(int b, int64_t n_rows, const double *w, const double *hnorm2, double *vout,
-                   const T *dinv, T *f, cudaStream_t s);
+                   const T *dinv, T *f, const int32_t *colour, T *y0, cudaStream_t s);
 template <class T>
 void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, int64_t q1,
                     int64_t q2, cudaStream_t s);
@@ -111,7 +112,7 @@ void launch_resid_p(int b, const MatView<T> &At, const T *atp, const T *f, const
                     cudaStream_t s);
 template <class T>
 void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, const T *e0, T *r,
-                       int unit, cudaStream_t s);
+                       int unit, const int32_t *colour, T *x0, cudaStream_t s);
 // z = y1 + Pi_p e0 (FP64 out) and rp = Pi_r f, for the CPR-FP and CPR-PF orderings
 template <class T>
 void launch_cpr_combine(int b, int64_t n, const T *y1, const T *e0, double *z, cudaStream_t s);
@@ -166,7 +167,7 @@ struct BicgScalars {
 void launch_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double rtol, cudaStream_t s);
 template <class T>
 void launch_bicg_dir(int b, int64_t n, const double *r, const double *v, double *p, const BicgScalars *sc,
-                     int first, const T *dinv, T *f, cudaStream_t s);
+                     int first, const T *dinv, T *f, const int32_t *colour, T *y0, cudaStream_t s);
 // blocks of one k_bicg_spmv launch (its partial sums take 2 doubles each)
 int64_t bicg_spmv_blocks(const Geom &g);
 void launch_bicg_spmv(int b, const MatView<double> &A, const double *x, double *y, const double *w, int nd,
