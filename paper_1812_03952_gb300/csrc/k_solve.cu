@@ -373,10 +373,16 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
   }
 }
 
+// Backward sweep of one colour: x_i = U_ii^-1 (y_i - sum over upper j of
+// U_ij x_j), written over y (and z = y1 + Pi e0 + x to zout when given).
+// With rhs given (the last colour, whose rows have no upper neighbour), the
+// forward sweep of the colour is done in the same pass: t = rhs_i - sum over
+// lower j of L_ij y_j, the same operations as k_ilu_fwd, then x_i = U_ii^-1 t.
 template <int B, class T, class TZ>
 __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_t q0, int64_t q1, int64_t q2,
                                                       int64_t cell_blocks, const T *__restrict__ y1,
-                                                      const T *__restrict__ e0, TZ *__restrict__ zout) {
+                                                      const T *__restrict__ e0, TZ *__restrict__ zout,
+                                                      const T *__restrict__ rhs) {
   constexpr int BB = B * B;
   const int64_t np = F.g.n_rows;
   T t[B];
@@ -387,9 +393,9 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     active = q < q1;
     if (!active) return;
     i = F.crow[q];
-    load_blk<B>(y + i * B, t);
+    load_blk<B>((rhs ? rhs : y) + i * B, t);
     const unsigned lmq = F.lmask[q];
-    const unsigned um = F.emask[i] & ~lmq & ~(1u << kSelf);
+    const unsigned um = rhs ? lmq : F.emask[i] & ~lmq & ~(1u << kSelf);
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
       if (!((um >> s) & 1u)) continue;
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     if (lmq & kTailBit)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       const int64_t j = F.ftcol[u];
-      if (F.ftlow[u] || j == i) continue;
+      if (rhs ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
       const T *blk = F.ftval + u * BB;
 #pragma unroll
       for (int r = 0; r < B; r++)
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     double acc[B] = {};
     for (int64_t u = F.ftptr[q] + lane; u < F.ftptr[q + 1]; u += 32) {
       const int64_t j = F.ftcol[u];
-      if (F.ftlow[u] || j == i) continue;
+      if (rhs ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
       const T *blk = F.ftval + u * BB;
 #pragma unroll
       for (int r = 0; r < B; r++)
@@ -431,8 +437,9 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
 #pragma unroll
     for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
     if (lane != 0) return;
+    const T *src = rhs ? rhs : y;
 #pragma unroll
-    for (int r = 0; r < B; r++) t[r] = static_cast<T>(to_d(y[i * B + r]) - acc[r]);
+    for (int r = 0; r < B; r++) t[r] = static_cast<T>(to_d(src[i * B + r]) - acc[r]);
   }
   // x_i = U_ii^-1 t
   T dg[BB];
@@ -589,31 +596,29 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
 }
 
 // ------------------------------------------------------------- AMG pieces
-template <class T>
-__device__ __forceinline__ T scalar_rowdot(const ScalarOp<T> &op, int64_t i, const T *__restrict__ x) {
+// (A x)_i of a scalar level, with x_j = xv(j) (an array read, or a value
+// formed on the fly from the inputs of a fused step)
+template <class T, class XV>
+__device__ __forceinline__ T scalar_rowdot_fn(const ScalarOp<T> &op, int64_t i, XV xv) {
   T acc = T(0);
   if (op.is_ell) {
     if (i < op.g.nc) {
       const unsigned m = op.emask[i];
 #pragma unroll
       for (int s = 0; s < kSlots; s++)
-        if ((m >> s) & 1u) acc = fma(op.ell[(int64_t)s * op.g.nc + i], x[i + op.g.off[s]], acc);
+        if ((m >> s) & 1u) acc = fma(op.ell[(int64_t)s * op.g.nc + i], xv(i + op.g.off[s]), acc);
       if (!(m & kTailBit)) return acc;
     }
-    for (int64_t t = op.tptr[i]; t < op.tptr[i + 1]; t++) acc = fma(op.tval[t], x[op.tcol[t]], acc);
+    for (int64_t t = op.tptr[i]; t < op.tptr[i + 1]; t++) acc = fma(op.tval[t], xv((int64_t)op.tcol[t]), acc);
   } else {
-    for (int64_t p = op.rp[i]; p < op.rp[i + 1]; p++) acc = fma(op.val[p], x[op.col[p]], acc);
+    for (int64_t p = op.rp[i]; p < op.rp[i + 1]; p++) acc = fma(op.val[p], xv((int64_t)op.col[p]), acc);
   }
   return acc;
 }
 
 template <class T>
-__global__ void k_cheb_init(int64_t n, const T *__restrict__ r, const T *__restrict__ dinv, T inv_theta,
-                            T *__restrict__ d, T *__restrict__ e) {
-  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  if (i >= n) return;
-  d[i] = (dinv[i] * r[i]) * inv_theta;
-  e[i] = T(0);
+__device__ __forceinline__ T scalar_rowdot(const ScalarOp<T> &op, int64_t i, const T *__restrict__ x) {
+  return scalar_rowdot_fn(op, i, [x](int64_t j) { return x[j]; });
 }
 
 template <class T>
@@ -630,8 +635,7 @@ __global__ void k_cheb_resid_init(ScalarOp<T> op, const T *__restrict__ r, const
 // res -= A d; dn = c1 d + c2 D^-1 res; e = (e + d) [+ dn if last]
 template <class T>
 __global__ void k_cheb_step(ScalarOp<T> op, const T *res_in, T *res_out, const T *__restrict__ d,
-                            const T *__restrict__ dinv, T c1, T c2, T *__restrict__ dn, T *__restrict__ e,
-                            int last) {
+                            const T *__restrict__ dinv, T c1, T c2, T *__restrict__ dn, T *e, int last) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= op.n) return;
   const T rv = res_in[i] - scalar_rowdot(op, i, d);
@@ -647,22 +651,60 @@ __global__ void k_cheb_step(ScalarOp<T> op, const T *res_in, T *res_out, const T
   }
 }
 
+// The first Chebyshev step from e = 0 fused with its initialisation: with
+// d = D^-1 r / theta formed on the fly for the neighbours, res = r - A d,
+// dn = c1 d + c2 D^-1 res, e = d (+ dn on the last step): the same
+// operations as setting d = D^-1 r / theta, e = 0 and then k_cheb_step.
 template <class T>
-__global__ void k_scalar_resid(ScalarOp<T> op, const T *__restrict__ r, const T *__restrict__ e,
-                               T *__restrict__ res) {
+__global__ void k_cheb_first(ScalarOp<T> op, const T *__restrict__ r, const T *__restrict__ dinv, T inv_theta,
+                             T c1, T c2, T *__restrict__ res_out, T *__restrict__ d_out, T *__restrict__ dn,
+                             T *__restrict__ e, int last) {
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= op.n) return;
-  res[i] = r[i] - scalar_rowdot(op, i, e);
+  auto dval = [&](int64_t j) { return (dinv[j] * r[j]) * inv_theta; };
+  const T rv = r[i] - scalar_rowdot_fn(op, i, dval);
+  const T di = dval(i);
+  const T nv = fma(c1, di, c2 * (dinv[i] * rv));
+  const T ev = T(0) + di;
+  if (last) {
+    e[i] = ev + nv;
+  } else {
+    e[i] = ev;
+    dn[i] = nv;
+    res_out[i] = rv;
+    d_out[i] = di;
+  }
 }
 
+// Restriction fused with the fine residual: rc_I = sum over the members i of
+// I, ascending, of (r_i - (A e)_i).  A group of kGroup lanes serves one
+// aggregate: lane k forms the residual of members k, k + kGroup, ...; the
+// group then adds them in member order, so the sum is the sequential one.
+constexpr int kGroup = 8;
+
 template <class T>
-__global__ void k_restrict(int64_t nc, const int64_t *__restrict__ mptr, const int32_t *__restrict__ midx,
-                           const T *__restrict__ res, T *__restrict__ rc) {
-  const int64_t I = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  if (I >= nc) return;
+__global__ void k_restrict_resid(ScalarOp<T> op, int64_t nc, const int64_t *__restrict__ mptr,
+                                 const int32_t *__restrict__ midx, const T *__restrict__ r,
+                                 const T *__restrict__ e, T *__restrict__ rc) {
+  const int64_t I = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / kGroup;
+  if (I >= nc) return;  // the whole group leaves together
+  const int k = threadIdx.x & (kGroup - 1);
+  const unsigned gmask = ((1u << kGroup) - 1u) << ((threadIdx.x & 31) & ~(kGroup - 1));
+  const int64_t t1 = mptr[I + 1];
   T s = T(0);
-  for (int64_t t = mptr[I]; t < mptr[I + 1]; t++) s = s + res[midx[t]];
-  rc[I] = s;
+  for (int64_t t0 = mptr[I]; t0 < t1; t0 += kGroup) {
+    T v = T(0);
+    if (t0 + k < t1) {
+      const int64_t i = midx[t0 + k];
+      v = r[i] - scalar_rowdot(op, i, e);
+    }
+#pragma unroll
+    for (int q = 0; q < kGroup; q++) {
+      const T vq = __shfl_sync(gmask, v, q, kGroup);
+      if (t0 + q < t1) s = s + vq;
+    }
+  }
+  if (k == 0) rc[I] = s;
 }
 
 template <class T>
@@ -1243,11 +1285,11 @@ void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, 
 
 template <class T, class TZ>
 void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2, const T *y1,
-                    const T *e0, TZ *zout, cudaStream_t s) {
+                    const T *e0, TZ *zout, const T *rhs, cudaStream_t s) {
   const int64_t cb = cell_blocks_of(q1 - q0), lb = long_blocks_of(q2 - q1);
   if (cb + lb == 0) return;
   TRS_DISPATCH_B(b, k_ilu_bwd<B, T, TZ><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0,
-                                                                                 zout));
+                                                                                 zout, rhs));
   TRS_LAUNCHED();
 }
 
@@ -1285,12 +1327,6 @@ void launch_pressure_of(int b, int64_t n, const T *f, T *rp, cudaStream_t s) {
 }
 
 template <class T>
-void launch_cheb_init(int64_t n, const T *r, const T *dinv, double inv_theta, T *d, T *e, cudaStream_t s) {
-  if (!n) return;
-  k_cheb_init<T><<<grid_of(n), kThreads, 0, s>>>(n, r, dinv, static_cast<T>(inv_theta), d, e);
-  TRS_LAUNCHED();
-}
-template <class T>
 void launch_cheb_resid_init(const ScalarOp<T> &op, const T *r, const T *e, const T *dinv, double inv_theta,
                             T *res, T *d, cudaStream_t s) {
   if (!op.n) return;
@@ -1306,15 +1342,18 @@ void launch_cheb_step(const ScalarOp<T> &op, const T *res_in, T *res_out, const 
   TRS_LAUNCHED();
 }
 template <class T>
-void launch_scalar_resid(const ScalarOp<T> &op, const T *r, const T *e, T *res, cudaStream_t s) {
+void launch_cheb_first(const ScalarOp<T> &op, const T *r, const T *dinv, double inv_theta, double c1, double c2,
+                       T *res_out, T *d_out, T *dn, T *e, int last, cudaStream_t s) {
   if (!op.n) return;
-  k_scalar_resid<T><<<grid_of(op.n), kThreads, 0, s>>>(op, r, e, res);
+  k_cheb_first<T><<<grid_of(op.n), kThreads, 0, s>>>(op, r, dinv, static_cast<T>(inv_theta), static_cast<T>(c1),
+                                                     static_cast<T>(c2), res_out, d_out, dn, e, last);
   TRS_LAUNCHED();
 }
 template <class T>
-void launch_restrict(int64_t nc, const int64_t *mptr, const int32_t *midx, const T *res, T *rc, cudaStream_t s) {
+void launch_restrict_resid(const ScalarOp<T> &op, int64_t nc, const int64_t *mptr, const int32_t *midx, const T *r,
+                           const T *e, T *rc, cudaStream_t s) {
   if (!nc) return;
-  k_restrict<T><<<grid_of(nc), kThreads, 0, s>>>(nc, mptr, midx, res, rc);
+  k_restrict_resid<T><<<grid_of(nc * kGroup), kThreads, 0, s>>>(op, nc, mptr, midx, r, e, rc);
   TRS_LAUNCHED();
 }
 template <class T>
@@ -1444,20 +1483,21 @@ void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double 
   template void launch_ilu_fwd<T>(int, const IluView<T> &, const T *, T *, int64_t, int64_t, int64_t,        \
                                   cudaStream_t);                                                            \
   template void launch_ilu_bwd<T, double>(int, const IluView<T> &, T *, int64_t, int64_t, int64_t, const T *,\
-                                          const T *, double *, cudaStream_t);                               \
+                                          const T *, double *, const T *, cudaStream_t);                    \
   template void launch_resid_p<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,      \
                                   cudaStream_t);                                                            \
   template void launch_resid_full<T>(int, const MatView<T> &, const T *, const T *, const T *, T *, int,    \
                                      const int32_t *, T *, cudaStream_t);                                   \
   template void launch_cpr_combine<T>(int, int64_t, const T *, const T *, double *, cudaStream_t);          \
   template void launch_pressure_of<T>(int, int64_t, const T *, T *, cudaStream_t);                          \
-  template void launch_cheb_init<T>(int64_t, const T *, const T *, double, T *, T *, cudaStream_t);         \
   template void launch_cheb_resid_init<T>(const ScalarOp<T> &, const T *, const T *, const T *, double, T *, \
                                           T *, cudaStream_t);                                               \
   template void launch_cheb_step<T>(const ScalarOp<T> &, const T *, T *, const T *, const T *, double,      \
                                     double, T *, T *, int, cudaStream_t);                                   \
-  template void launch_scalar_resid<T>(const ScalarOp<T> &, const T *, const T *, T *, cudaStream_t);       \
-  template void launch_restrict<T>(int64_t, const int64_t *, const int32_t *, const T *, T *, cudaStream_t); \
+  template void launch_cheb_first<T>(const ScalarOp<T> &, const T *, const T *, double, double, double, T *, \
+                                     T *, T *, T *, int, cudaStream_t);                                     \
+  template void launch_restrict_resid<T>(const ScalarOp<T> &, int64_t, const int64_t *, const int32_t *,     \
+                                         const T *, const T *, T *, cudaStream_t);                          \
   template void launch_prolong<T>(int64_t, const int32_t *, const T *, T *, cudaStream_t);                  \
   template void launch_dense_gemv<T>(int64_t, const double *, const T *, T *, cudaStream_t);                \
   template void launch_xupdate<T>(const T *, int64_t, int, const double *, double *, cudaStream_t);
@@ -1465,7 +1505,7 @@ void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double 
 TRS_INST_T(double)
 TRS_INST_T(float)
 template void launch_ilu_bwd<float, float>(int, const IluView<float> &, float *, int64_t, int64_t, int64_t,
-                                           const float *, const float *, float *, cudaStream_t);
+                                           const float *, const float *, float *, const float *, cudaStream_t);
 template void launch_cast<double, float>(const double *, float *, int64_t, cudaStream_t);
 template void launch_cast<float, double>(const float *, double *, int64_t, cudaStream_t);
 template void launch_cast<double, double>(const double *, double *, int64_t, cudaStream_t);

@@ -465,7 +465,8 @@ const T *level_dinv(const Level &L) {
 }
 
 // Chebyshev smoothing of degree >= 2 (Saad, Alg. 12.1 on D^-1 A over
-// [0.3 lam, lam]); zero_init starts from e = 0.
+// [0.3 lam, lam]); zero_init starts from e = 0, with the first step fused
+// into its initialisation.
 template <class T>
 void chebyshev(const trs_cpr *M, int l, const T *r, T *e, bool zero_init, cudaStream_t s) {
   const Level &L = M->lev[l];
@@ -476,20 +477,23 @@ void chebyshev(const trs_cpr *M, int l, const T *r, T *e, bool zero_init, cudaSt
   double rho = 1.0 / sigma;
   T *res = tp<T>(L.res), *d = tp<T>(L.d), *dn = tp<T>(L.dn);
   const T *dinv = level_dinv<T>(L);
-  const T *res_in = res;
+  const int deg = M->opts.cheb_degree;
+  int k = 1;
   if (zero_init) {
-    launch_cheb_init<T>(L.A.n, r, dinv, 1.0 / theta, d, e, s);
-    res_in = r;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rho_new * rho, c2 = (2.0 * rho_new) / delta;
+    launch_cheb_first<T>(op, r, dinv, 1.0 / theta, c1, c2, res, d, dn, e, deg == 2, s);
+    std::swap(d, dn);
+    rho = rho_new;
+    k = 2;
   } else {
     launch_cheb_resid_init<T>(op, r, e, dinv, 1.0 / theta, res, d, s);
   }
-  const int deg = M->opts.cheb_degree;
-  for (int k = 1; k < deg; k++) {
+  for (; k < deg; k++) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double c1 = rho_new * rho, c2 = (2.0 * rho_new) / delta;
     const int last = (k == deg - 1);
-    launch_cheb_step<T>(op, res_in, res, d, dinv, c1, c2, dn, e, last, s);
-    res_in = res;
+    launch_cheb_step<T>(op, res, res, d, dinv, c1, c2, dn, e, last, s);
     std::swap(d, dn);
     rho = rho_new;
   }
@@ -560,9 +564,8 @@ void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
     return;
   }
   chebyshev<T>(M, l, r, e, true, s);
-  launch_scalar_resid<T>(level_op<T>(M, l), r, e, tp<T>(Lv.res), s);
   const Level &C = M->lev[l + 1];
-  launch_restrict<T>(C.A.n, Lv.mptr.p, Lv.midx.p, tp<T>(Lv.res), tp<T>(C.r), s);
+  launch_restrict_resid<T>(level_op<T>(M, l), C.A.n, Lv.mptr.p, Lv.midx.p, r, e, tp<T>(C.r), s);
   vcycle<T>(M, l + 1, tp<T>(C.r), tp<T>(C.e), s);
   launch_prolong<T>(Lv.A.n, Lv.agg.p, tp<T>(C.e), e, s);
   chebyshev<T>(M, l, r, e, false, s);
@@ -570,13 +573,16 @@ void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
 
 // The forward sweep starts at colour 1: the kernel that produced rhs also
 // wrote y = rhs on the rows of colour 0, which have no earlier-ordered
-// neighbour (the sweep of colour 0).
+// neighbour (the sweep of colour 0).  The rows of the last colour have no
+// later-ordered neighbour, so their forward and backward sweeps are one pass.
 template <class T, class TZ>
 void ilu_solve(const trs_cpr *M, const T *rhs, T *y, const T *y1, const T *e0, TZ *zout, cudaStream_t s) {
   const IluView<T> F = ilu_view<T>(M);
-  for (int c = 1; c < M->ncol; c++) launch_ilu_fwd<T>(M->b, F, rhs, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], s);
-  for (int c = M->ncol - 1; c >= 0; c--)
-    launch_ilu_bwd<T, TZ>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout, s);
+  const int last = M->ncol - 1;
+  for (int c = 1; c < last; c++) launch_ilu_fwd<T>(M->b, F, rhs, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], s);
+  for (int c = last; c >= 0; c--)
+    launch_ilu_bwd<T, TZ>(M->b, F, y, M->cptr[c], M->cmid[c], M->cptr[c + 1], y1, e0, zout,
+                          c == last ? rhs : nullptr, s);
 }
 
 // z = CPR(Ã)^-1 f (f already scaled by D^-1), written to z in FP64.  With F

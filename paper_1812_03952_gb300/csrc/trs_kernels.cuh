@@ -104,7 +104,7 @@ void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, 
                     int64_t q2, cudaStream_t s);
 template <class T, class TZ>
 void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2,
-                    const T *y1, const T *e0, TZ *zout, cudaStream_t s);
+                    const T *y1, const T *e0, TZ *zout, const T *rhs, cudaStream_t s);
 // CPR residuals on Ã; unit = 1 when every diagonal block of Ã is I (ABF,
 // FRS+ABF), so that y_i is added instead of multiplied; y1 may be NULL (zero).
 template <class T>
@@ -120,19 +120,19 @@ template <class T>
 void launch_pressure_of(int b, int64_t n, const T *f, T *rp, cudaStream_t s);
 
 template <class T>
-void launch_cheb_init(int64_t n, const T *r, const T *dinv, double inv_theta, T *d, T *e,
-                      cudaStream_t s);
-template <class T>
 void launch_cheb_resid_init(const ScalarOp<T> &op, const T *r, const T *e, const T *dinv,
                             double inv_theta, T *res, T *d, cudaStream_t s);
 template <class T>
 void launch_cheb_step(const ScalarOp<T> &op, const T *res_in, T *res_out, const T *d,
                       const T *dinv, double c1, double c2, T *dn, T *e, int last, cudaStream_t s);
+// fused forms: first step from e = 0 with its initialisation; restriction
+// of the fine residual r - A e
 template <class T>
-void launch_scalar_resid(const ScalarOp<T> &op, const T *r, const T *e, T *res, cudaStream_t s);
+void launch_cheb_first(const ScalarOp<T> &op, const T *r, const T *dinv, double inv_theta, double c1,
+                       double c2, T *res_out, T *d_out, T *dn, T *e, int last, cudaStream_t s);
 template <class T>
-void launch_restrict(int64_t nc, const int64_t *mptr, const int32_t *midx, const T *res, T *rc,
-                     cudaStream_t s);
+void launch_restrict_resid(const ScalarOp<T> &op, int64_t nc, const int64_t *mptr, const int32_t *midx,
+                           const T *r, const T *e, T *rc, cudaStream_t s);
 template <class T>
 void launch_prolong(int64_t n, const int32_t *agg, const T *ec, T *e, cudaStream_t s);
 template <class T>
