@@ -43,7 +43,7 @@ class _Stats(C.Structure):
 class _CprOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
                 ("cheb_degree", C.c_int), ("seed", C.c_uint32), ("stages", C.c_int),
-                ("decoupling", C.c_int)]
+                ("decoupling", C.c_int), ("ilu_fill", C.c_int), ("grid", C.c_int * 3)]
 
 
 #: CPR stage orderings and decoupling methods (Sec. "Preconditioners",
@@ -129,6 +129,19 @@ def lib():
         L.orc_bilu0_factors.argtypes = [C.c_void_p, f64p]
         L.orc_bilu0_free.restype = None
         L.orc_bilu0_free.argtypes = [C.c_void_p]
+        L.orc_colour_geo.restype = C.c_int
+        L.orc_colour_geo.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i32p, i32p]
+        L.orc_biluk_setup.restype = C.c_void_p
+        L.orc_biluk_setup.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, i32p, C.c_int,
+                                      C.POINTER(C.c_int)]
+        L.orc_bilu_nnz.restype = C.c_int64
+        L.orc_bilu_nnz.argtypes = [C.c_void_p]
+        L.orc_bilu_pattern.restype = None
+        L.orc_bilu_pattern.argtypes = [C.c_void_p, i64p, i32p]
+        L.orc_bilu_colours_independent.restype = C.c_int
+        L.orc_bilu_colours_independent.argtypes = [C.c_void_p, i32p]
+        L.orc_cpr_ilu.restype = C.c_void_p
+        L.orc_cpr_ilu.argtypes = [C.c_void_p]
         L.orc_cpr_setup.restype = C.c_void_p
         L.orc_cpr_setup.argtypes = [C.c_int64, C.c_int, i64p, i32p, f64p, C.POINTER(_CprOpts),
                                     C.POINTER(C.c_int)]
@@ -373,25 +386,52 @@ def colour_jp(A: BSR, seed):
     return colour, nc
 
 
+def colour_geo(A: BSR, grid):
+    """Distance-2 order of block ILU(1): cells (x + 2y + 3z) mod 7, the other
+    rows first-fit from colour 7 (Sec. "Preconditioners", block ILU(k))."""
+    colour = np.zeros(A.n, np.int32)
+    nc = lib().orc_colour_geo(int(grid[0]), int(grid[1]), int(grid[2]), A.n, A.rp, A.col, colour)
+    _check(nc, "colour_geo")
+    return colour, nc
+
+
+def _ilu_pattern(h, n):
+    nnz = lib().orc_bilu_nnz(h)
+    rp = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(nnz, 1), np.int32)
+    lib().orc_bilu_pattern(h, rp, col)
+    return rp, col[:nnz]
+
+
 class BILU0:
-    def __init__(self, A: BSR, vt, colour):
+    """Block ILU(level) in colour-major order; level 0 on the block pattern,
+    level 1 on the level-1 fill pattern (:meth:`pattern`)."""
+
+    def __init__(self, A: BSR, vt, colour, level=0):
         st = C.c_int(0)
         self.A = A
-        self.h = lib().orc_bilu0_setup(A.n, A.b, A.rp, A.col,
+        self.h = lib().orc_biluk_setup(A.n, A.b, A.rp, A.col,
                                        np.ascontiguousarray(vt, dtype=np.float64).reshape(-1),
-                                       np.ascontiguousarray(colour, dtype=np.int32), C.byref(st))
+                                       np.ascontiguousarray(colour, dtype=np.int32), level,
+                                       C.byref(st))
         if not self.h:
-            raise OracleError(f"bilu0 setup failed with status {st.value}")
+            raise OracleError(f"bilu setup failed with status {st.value}")
 
     def solve(self, r):
         y = np.zeros(self.A.n * self.A.b)
         lib().orc_bilu0_solve(self.h, np.ascontiguousarray(r, dtype=np.float64), y)
         return y
 
+    def pattern(self):
+        return _ilu_pattern(self.h, self.A.n)
+
     def factors(self):
-        F = np.zeros((self.A.nnzb, self.A.b, self.A.b))
+        F = np.zeros((max(lib().orc_bilu_nnz(self.h), 1), self.A.b, self.A.b))
         lib().orc_bilu0_factors(self.h, F.reshape(-1))
-        return F
+        return F[:lib().orc_bilu_nnz(self.h)]
+
+    def colours_independent(self, colour):
+        return bool(lib().orc_bilu_colours_independent(self.h, np.ascontiguousarray(colour, dtype=np.int32)))
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -401,7 +441,7 @@ class BILU0:
 
 #: default CPR options (the same defaults as the CUDA library)
 CPR_DEFAULTS = dict(theta=0.08, coarse_max=64, max_levels=12, cheb_degree=2, seed=0x5EED1812,
-                    stages="fpf", decoupling="abf")
+                    stages="fpf", decoupling="abf", ilu_fill=0, grid=(0, 0, 0))
 
 
 class CPR:
@@ -409,7 +449,8 @@ class CPR:
         o = dict(CPR_DEFAULTS)
         o.update(kw)
         self.opts = _CprOpts(o["theta"], o["coarse_max"], o["max_levels"], o["cheb_degree"],
-                             o["seed"], STAGES[o["stages"]], DECOUPLINGS[o["decoupling"]])
+                             o["seed"], STAGES[o["stages"]], DECOUPLINGS[o["decoupling"]],
+                             int(o["ilu_fill"]), (C.c_int * 3)(*[int(v) for v in o["grid"]]))
         st = C.c_int(0)
         self.A = A
         self.h = lib().orc_cpr_setup(A.n, A.b, A.rp, A.col, A.val.reshape(-1),
@@ -442,10 +483,14 @@ class CPR:
         lib().orc_cpr_decoupled(self.h, vt.reshape(-1), dinv.reshape(-1))
         return vt, dinv
 
+    def ilu_pattern(self):
+        return _ilu_pattern(lib().orc_cpr_ilu(self.h), self.A.n)
+
     def ilu_factors(self):
-        F = np.zeros_like(self.A.val)
+        nnz = lib().orc_bilu_nnz(lib().orc_cpr_ilu(self.h))
+        F = np.zeros((max(nnz, 1), self.A.b, self.A.b))
         lib().orc_cpr_ilu_factors(self.h, F.reshape(-1))
-        return F
+        return F[:nnz]
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -999,6 +999,149 @@ void orc_bilu0_factors(const void *hv, double *F) {
 }
 
 /* ======================================================================
+ * Block ILU(1).  The paper's subdomain solves may be block ILU(k), and the
+ * level it recommends is k = 1 (Sec. "Preconditioners", the RAS paragraph).
+ * Reading for a single-domain, multicolour form:
+ *   order: a distance-2 colouring, so that the rows of one colour are still
+ *     uncoupled once the level-1 fill is added: grid cell (x, y, z) takes
+ *     colour (x + 2y + 3z) mod 7 (the 7-point neighbours of a cell differ
+ *     from it by +-1, +-2, +-3 mod 7 and cells two steps apart by a nonzero
+ *     sum of two of those, |sum| <= 6); every other row (the wells), in
+ *     index order, takes the first colour 7, 8, ... not taken by an earlier
+ *     such row that is adjacent to it or shares a neighbour with it; rows
+ *     are sorted by (colour, index) as for ILU(0);
+ *   pattern: level of fill at most 1 (Saad, Iterative Methods for Sparse
+ *     Linear Systems, Sec. 10.3.3, lev_ij = min over k of lev_ik + lev_kj
+ *     + 1): the stored pattern plus every (i, j) with a neighbour k ordered
+ *     before both i and j and (i, k), (k, j) stored; an entry made from a
+ *     fill entry has level >= 2 and is dropped;
+ *   numeric: the IKJ factorisation of orc_bilu0_setup on that pattern, the
+ *     fill entries starting from zero.
+ * The parallel sweeps need the rows of one colour uncoupled in the factor
+ * pattern; orc_bilu_colours_independent checks it.
+ * ====================================================================== */
+int orc_colour_geo(int nx, int ny, int nz, int64_t n, const int64_t *rp, const int32_t *col,
+                   int32_t *colour) {
+  const int64_t nc = (int64_t)nx * ny * nz;
+  if (nx < 1 || ny < 1 || nz < 1 || nc > n) return ORC_INVALID;
+  for (int64_t i = 0; i < nc; i++) {
+    const int64_t x = i % nx, y = (i / nx) % ny, z = i / ((int64_t)nx * ny);
+    colour[i] = (int32_t)((x + 2 * y + 3 * z) % 7);
+  }
+  int ncol = 0;
+  for (int64_t i = 0; i < nc; i++) if (colour[i] + 1 > ncol) ncol = colour[i] + 1;
+  for (int64_t w = nc; w < n; w++) {
+    uint64_t used = 0;
+    for (int64_t p = rp[w]; p < rp[w + 1]; p++) {
+      const int64_t k = col[p];
+      if (k == w) continue;
+      if (k >= nc && k < w) used |= (uint64_t)1 << (colour[k] - 7);
+      for (int64_t q = rp[k]; q < rp[k + 1]; q++) {
+        const int64_t j = col[q];
+        if (j >= nc && j < w) used |= (uint64_t)1 << (colour[j] - 7);
+      }
+    }
+    int c = 0;
+    while (c < ORC_MAX_COLOURS - 7 && (used >> c) & 1) c++;
+    if (c >= ORC_MAX_COLOURS - 7) return ORC_COLOURS;
+    colour[w] = 7 + c;
+    if (colour[w] + 1 > ncol) ncol = colour[w] + 1;
+  }
+  return ncol;
+}
+
+/* The level-1 pattern of (rp, col) in the order pos: rows sorted by column. */
+static void ilu1_pattern(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *pos,
+                         int64_t **rp1_out, int32_t **col1_out) {
+  int64_t *stamp = malloc(sizeof(int64_t) * nz1(n));
+  for (int64_t i = 0; i < n; i++) stamp[i] = -1;
+  int64_t *rp1 = malloc(sizeof(int64_t) * (size_t)(n + 1));
+  rp1[0] = 0;
+  for (int pass = 0; pass < 2; pass++) {
+    int32_t *col1 = pass ? *col1_out : NULL;
+    for (int64_t i = 0; i < n; i++) stamp[i] = -1;
+    for (int64_t i = 0; i < n; i++) {
+      int64_t cnt = 0, base = pass ? rp1[i] : 0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+        stamp[col[p]] = i;
+        if (pass) col1[base + cnt] = col[p];
+        cnt++;
+      }
+      for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+        const int64_t k = col[p];
+        if (pos[k] >= pos[i]) continue;
+        for (int64_t q = rp[k]; q < rp[k + 1]; q++) {
+          const int64_t j = col[q];
+          if (pos[j] <= pos[k] || stamp[j] == i) continue;
+          stamp[j] = i;
+          if (pass) col1[base + cnt] = (int32_t)j;
+          cnt++;
+        }
+      }
+      if (!pass) rp1[i + 1] = rp1[i] + cnt;
+      else
+        for (int64_t a = base + 1; a < base + cnt; a++) {   /* insertion sort of the row */
+          int32_t v = col1[a];
+          int64_t b2 = a - 1;
+          while (b2 >= base && col1[b2] > v) { col1[b2 + 1] = col1[b2]; b2--; }
+          col1[b2 + 1] = v;
+        }
+    }
+    if (!pass) *col1_out = malloc(sizeof(int32_t) * nz1(rp1[n]));
+  }
+  free(stamp);
+  *rp1_out = rp1;
+}
+
+void *orc_biluk_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *vt,
+                      const int32_t *colour, int level, int *status) {
+  if (level == 0) return orc_bilu0_setup(n, b, rp, col, vt, colour, status);
+  if (level != 1) { *status = ORC_INVALID; return NULL; }
+  const int64_t bb = (int64_t)b * b;
+  /* positions of the colour-major order (the same stable sort as ILU(0)) */
+  int maxc = 0;
+  for (int64_t i = 0; i < n; i++) if (colour[i] + 1 > maxc) maxc = colour[i] + 1;
+  int64_t *cnt = calloc((size_t)maxc + 1, sizeof(int64_t));
+  int64_t *pos = malloc(sizeof(int64_t) * nz1(n));
+  for (int64_t i = 0; i < n; i++) cnt[colour[i] + 1]++;
+  for (int c = 0; c < maxc; c++) cnt[c + 1] += cnt[c];
+  for (int64_t i = 0; i < n; i++) pos[i] = cnt[colour[i]]++;
+  free(cnt);
+  int64_t *rp1;
+  int32_t *col1;
+  ilu1_pattern(n, rp, col, pos, &rp1, &col1);
+  free(pos);
+  double *vt1 = calloc(nz1(rp1[n] * bb), sizeof(double));
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t p = rp1[i]; p < rp1[i + 1]; p++) {
+      const int64_t src = find_entry(rp, col, i, col1[p]);
+      if (src >= 0) memcpy(vt1 + p * bb, vt + src * bb, sizeof(double) * (size_t)bb);
+    }
+  void *h = orc_bilu0_setup(n, b, rp1, col1, vt1, colour, status);
+  free(rp1); free(col1); free(vt1);
+  return h;
+}
+
+int64_t orc_bilu_nnz(const void *hv) {
+  const orc_ilu *h = hv;
+  return h->rp[h->n];
+}
+
+void orc_bilu_pattern(const void *hv, int64_t *rp, int32_t *col) {
+  const orc_ilu *h = hv;
+  memcpy(rp, h->rp, sizeof(int64_t) * (size_t)(h->n + 1));
+  memcpy(col, h->col, sizeof(int32_t) * (size_t)h->rp[h->n]);
+}
+
+int orc_bilu_colours_independent(const void *hv, const int32_t *colour) {
+  const orc_ilu *h = hv;
+  for (int64_t i = 0; i < h->n; i++)
+    for (int64_t p = h->rp[i]; p < h->rp[i + 1]; p++)
+      if (h->col[p] != i && colour[h->col[p]] == colour[i]) return 0;
+  return 1;
+}
+
+/* ======================================================================
  * CPR-FPF (Algorithm pc-fpf; its listing is garbled -- the third line
  * repeats the first and r is undefined -- so the five steps of the prose are
  * followed):  with f = D^-1 v (decoupling as a right-preconditioner factor,
@@ -1055,11 +1198,15 @@ void *orc_cpr_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, con
   free(ap);
   if (!h->amg) { *status = st; orc_cpr_free(h); return NULL; }
   h->colour = malloc(sizeof(int32_t) * nz1(n));
-  int nc = orc_colour_jp(n, rp, col, opts->seed ^ 0x85EBCA77u, h->colour);
+  if (opts->ilu_fill != 0 && opts->ilu_fill != 1) { *status = ORC_INVALID; orc_cpr_free(h); return NULL; }
+  int nc = opts->ilu_fill == 0
+               ? orc_colour_jp(n, rp, col, opts->seed ^ 0x85EBCA77u, h->colour)
+               : orc_colour_geo(opts->grid[0], opts->grid[1], opts->grid[2], n, rp, col, h->colour);
   if (nc < 0) { *status = nc; orc_cpr_free(h); return NULL; }
   h->n_colours = nc;
-  h->ilu = orc_bilu0_setup(n, b, h->rp, h->col, h->vt, h->colour, &st);
+  h->ilu = orc_biluk_setup(n, b, h->rp, h->col, h->vt, h->colour, opts->ilu_fill, &st);
   if (!h->ilu) { *status = st; orc_cpr_free(h); return NULL; }
+  if (!orc_bilu_colours_independent(h->ilu, h->colour)) { *status = ORC_INVALID; orc_cpr_free(h); return NULL; }
   return h;
 }
 
@@ -1127,6 +1274,8 @@ void orc_cpr_decoupled(const void *hv, double *vt, double *dinv) {
   memcpy(dinv, h->dinv, sizeof(double) * (size_t)(h->n * bb));
 }
 void orc_cpr_ilu_factors(const void *hv, double *F) { orc_bilu0_factors(((const orc_cpr *)hv)->ilu, F); }
+
+const void *orc_cpr_ilu(const void *hv) { return ((const orc_cpr *)hv)->ilu; }
 
 /* ======================================================================
  * Restarted flexible GMRES (Saad 1993) with right preconditioning and

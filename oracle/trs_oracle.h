@@ -93,6 +93,18 @@ void *orc_bilu0_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, c
 void orc_bilu0_solve(const void *h, const double *r, double *y);
 void orc_bilu0_factors(const void *h, double *F);
 void orc_bilu0_free(void *h);
+/* Block ILU(1) (Sec. "Preconditioners": block ILU(k), k = 1 recommended):
+ * the distance-2 order of a grid (cells (x + 2y + 3z) mod 7, other rows
+ * first-fit from colour 7) and the factorisation on the level-1 pattern.
+ * level 0 is orc_bilu0_setup.  The handle is freed by orc_bilu0_free; its
+ * factors (orc_bilu0_factors) follow orc_bilu_pattern. */
+int orc_colour_geo(int nx, int ny, int nz, int64_t n, const int64_t *rp, const int32_t *col,
+                   int32_t *colour);
+void *orc_biluk_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *vt,
+                      const int32_t *colour, int level, int *status);
+int64_t orc_bilu_nnz(const void *h);
+void orc_bilu_pattern(const void *h, int64_t *rp, int32_t *col);
+int orc_bilu_colours_independent(const void *h, const int32_t *colour);
 
 /* ---- CPR-FPF preconditioner and FGMRES ---- */
 #define ORC_CPR_FPF 0   /* F, P, F (Algorithm pc-fpf) */
@@ -106,6 +118,8 @@ typedef struct {
   uint32_t seed;
   int stages;        /* ORC_CPR_FPF / FP / PF */
   int decoupling;    /* ORC_DEC_* */
+  int ilu_fill;      /* 0: block ILU(0), Jones-Plassmann colours; 1: block ILU(1), distance-2 order */
+  int grid[3];       /* nx, ny, nz of the cells (rows 0 .. nx ny nz - 1), needed when ilu_fill = 1 */
 } orc_cpr_opts;
 
 void *orc_cpr_setup(int64_t n, int b, const int64_t *rp, const int32_t *col, const double *val,
@@ -116,6 +130,7 @@ const void *orc_cpr_amg(const void *h);
 void orc_cpr_colours(const void *h, int32_t *colour);
 void orc_cpr_decoupled(const void *h, double *vt, double *dinv);
 void orc_cpr_ilu_factors(const void *h, double *F);
+const void *orc_cpr_ilu(const void *h);
 void orc_cpr_free(void *h);
 
 typedef struct {

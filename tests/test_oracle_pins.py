@@ -465,6 +465,165 @@ def test_bilu0_block_diagonal_is_exact(oracle, synth):
     np.testing.assert_allclose(oracle.BILU0(A, vt, colour).solve(r), r, rtol=1e-15)
 
 
+# ------------------------------------------------------------ block ILU(1)
+def _graph(A):
+    G = np.zeros((A.n, A.n), bool)
+    G[A.row_of_block(), A.col] = True
+    np.fill_diagonal(G, False)
+    return G
+
+
+def test_colour_geo_is_distance2(oracle, synth):
+    """The order of block ILU(1): cells two or fewer cell-to-cell steps
+    apart never share a colour (7 colours), the other rows (wells) take
+    colours from 7 on and no two of them within two steps share one."""
+    s = tiny(synth, 9, 8, 5, 4, seed=16, n_pairs=2)
+    A = oracle.assemble(s)
+    colour, ncol = oracle.colour_geo(A, (s.nx, s.ny, s.nz))
+    nc = s.nx * s.ny * s.nz
+    G = _graph(A)
+    Gi = G.astype(int)
+    Gc = Gi[:nc, :nc]
+    d2 = (Gc + Gc @ Gc) > 0
+    np.fill_diagonal(d2, False)
+    a, c = np.nonzero(d2)
+    assert np.all(colour[a] != colour[c])
+    assert sorted(set(colour[:nc].tolist())) == list(range(7))
+    w = np.arange(nc, A.n)
+    assert len(w) == 4 and np.all(colour[w] >= 7)
+    dw = ((Gi + Gi @ Gi) > 0)[np.ix_(w, w)]
+    np.fill_diagonal(dw, False)
+    a, c = np.nonzero(dw)
+    assert np.all(colour[w][a] != colour[w][c])
+    assert ncol == colour.max() + 1
+
+
+def _level_of_fill(A, colour, p):
+    """The symbolic phase of ILU(p) by Gaussian elimination on a dense level
+    matrix in the colour-major order (Saad, Iterative Methods for Sparse
+    Linear Systems, Sec. 10.3.3): lev = 0 on the pattern, infinite
+    elsewhere; for every row i and earlier k with lev_ik <= p,
+    lev_ij = min(lev_ij, lev_ik + lev_kj + 1); entries above p dropped."""
+    n = A.n
+    order = np.lexsort((np.arange(n), colour))
+    P = np.zeros((n, n), bool)
+    P[A.row_of_block(), A.col] = True
+    lev = np.where(P[np.ix_(order, order)], 0.0, np.inf)
+    for i in range(n):
+        for k in range(i):
+            if lev[i, k] <= p:
+                lev[i, k + 1:] = np.minimum(lev[i, k + 1:], lev[i, k] + lev[k, k + 1:] + 1)
+        lev[i, lev[i] > p] = np.inf
+    out = np.zeros((n, n), bool)
+    out[np.ix_(order, order)] = np.isfinite(lev)
+    return out
+
+
+def _pattern_dense(n, rp, col):
+    P = np.zeros((n, n), bool)
+    P[np.repeat(np.arange(n), np.diff(rp)), col] = True
+    return P
+
+
+def test_bilu1_pattern_is_level_of_fill_one(oracle, synth):
+    s = tiny(synth, 7, 6, 4, 3, seed=19, n_pairs=2)
+    A = oracle.assemble(s)
+    vt, _ = oracle.decouple(A)
+    colour, _ = oracle.colour_geo(A, (s.nx, s.ny, s.nz))
+    ilu = oracle.BILU0(A, vt, colour, level=1)
+    rp, col = ilu.pattern()
+    P1 = _pattern_dense(A.n, rp, col)
+    np.testing.assert_array_equal(P1, _level_of_fill(A, colour, 1))
+    assert P1.sum() > 1.5 * A.nnzb                      # level-1 fill is present
+    np.testing.assert_array_equal(_pattern_dense(A.n, A.rp, A.col), _level_of_fill(A, colour, 0))
+    assert all(np.all(np.diff(col[rp[i]:rp[i + 1]]) > 0) for i in range(A.n))
+    # rows of one colour stay uncoupled in the factor pattern
+    a, c = np.nonzero(P1 & ~np.eye(A.n, dtype=bool))
+    assert np.all(colour[a] != colour[c])
+
+
+def _ilu_dense_from_pattern(n, b, rp, col, F, colour):
+    order = np.lexsort((np.arange(n), colour))
+    pos = np.empty(n, int)
+    pos[order] = np.arange(n)
+    L, U = np.eye(n * b), np.zeros((n * b, n * b))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    for p in range(len(col)):
+        i, j = rows[p], col[p]
+        blk = (slice(i * b, i * b + b), slice(j * b, j * b + b))
+        if i == j:
+            U[blk] = np.linalg.inv(F[p])
+        elif pos[j] < pos[i]:
+            L[blk] = F[p]
+        else:
+            U[blk] = F[p]
+    return L, U
+
+
+def test_bilu1_defining_identity(oracle, synth):
+    """(L U)_ij = Ã_ij on every block of the level-1 pattern, Ã_ij = 0 on the
+    fill blocks, which ILU(0) leaves wrong; the sweeps invert L U."""
+    s = tiny(synth, 7, 5, 4, 3, seed=20, n_pairs=2)
+    A = oracle.assemble(s)
+    vt, _ = oracle.decouple(A)
+    colour, _ = oracle.colour_geo(A, (s.nx, s.ny, s.nz))
+    ilu = oracle.BILU0(A, vt, colour, level=1)
+    rp, col = ilu.pattern()
+    L, U = _ilu_dense_from_pattern(A.n, A.b, rp, col, ilu.factors(), colour)
+    LU = L @ U
+    At = oracle.BSR(A.n, A.b, A.rp, A.col, vt).to_dense()
+    blk = np.ones((A.b, A.b), bool)
+    P1 = np.kron(_pattern_dense(A.n, rp, col), blk)
+    fill = P1 & ~np.kron(_pattern_dense(A.n, A.rp, A.col), blk)
+    assert np.abs((LU - At)[P1]).max() < 1e-11
+    ilu0 = oracle.BILU0(A, vt, colour, level=0)
+    L0, U0 = _ilu_dense_from_pattern(A.n, A.b, A.rp, A.col, ilu0.factors(), colour)
+    assert np.abs((L0 @ U0 - At)[fill]).max() > 1e-3
+    r = np.random.default_rng(5).standard_normal(A.n * A.b)
+    np.testing.assert_allclose(LU @ ilu.solve(r), r, rtol=1e-9, atol=1e-9)
+
+
+def test_cpr_ilu1_options_and_convergence(oracle, synth):
+    s = tiny(synth, 10, 9, 5, 4, seed=21, n_pairs=2)
+    A = oracle.assemble(s)
+    grid = (s.nx, s.ny, s.nz)
+    c1 = oracle.CPR(A, ilu_fill=1, grid=grid)
+    assert c1.info()[1] == 8                             # 7 cell colours + the wells
+    np.testing.assert_array_equal(c1.colours(), oracle.colour_geo(A, grid)[0])
+    r1 = oracle.fgmres(A, c1, s.rhs, rtol=1e-10)
+    r0 = oracle.fgmres(A, oracle.CPR(A), s.rhs, rtol=1e-10)
+    assert r1.converged and r1.true_relres <= 1e-10 and r1.iters < r0.iters
+    x = np.linalg.solve(A.to_dense(), s.rhs)
+    assert np.linalg.norm(r1.x - x) / np.linalg.norm(x) < 1e-8
+    for bad in (dict(ilu_fill=2, grid=grid), dict(ilu_fill=1),
+                dict(ilu_fill=1, grid=(s.nx * s.ny * s.nz, 1, 1))):
+        with pytest.raises(oracle.OracleError):
+            oracle.CPR(A, **bad)
+
+
+def test_cpr_ilu1_error_propagation(oracle, synth):
+    """CPR-FPF with F = ILU(1)(Ã)^-1: I - B Ã = (I - FÃ)(I - PÃ)(I - FÃ)."""
+    s = tiny(synth, 7, 3, 3, 3, seed=22, n_pairs=1)
+    A = oracle.assemble(s)
+    cpr = oracle.CPR(A, coarse_max=8, ilu_fill=1, grid=(s.nx, s.ny, s.nz))
+    vt, dinv = cpr.decoupled()
+    n, b = A.n, A.b
+    N = n * b
+    At = oracle.BSR(n, b, A.rp, A.col, vt).to_dense()
+    ilu = oracle.BILU0(A, vt, cpr.colours(), level=1)
+    I = np.eye(N)
+    Fm = np.column_stack([ilu.solve(I[:, k]) for k in range(N)])
+    Pp = np.column_stack([cpr.amg.vcycle(np.eye(n)[:, k]) for k in range(n)])
+    Pm = np.zeros((N, N))
+    Pm[np.ix_(np.arange(n) * b, np.arange(n) * b)] = Pp
+    EF, EP = I - Fm @ At, I - Pm @ At
+    B = (I - EF @ EP @ EF) @ np.linalg.inv(At)
+    v = np.random.default_rng(25).standard_normal(N)
+    f = np.einsum("irs,is->ir", dinv, v.reshape(n, b)).reshape(-1)
+    want = B @ f
+    np.testing.assert_allclose(cpr.apply(v), want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+
 # ------------------------------------------------------------------ CPR
 def test_cpr_identity_when_no_flux(oracle, synth):
     """With k = 0 and no wells, Ã = I and CPR(Ã)^-1 = I, so M^-1 v = D^-1 v."""
