@@ -66,6 +66,10 @@ def parse():
                    help="decoupling of the forward CPR")
     p.add_argument("--adjoint-decoupling", default="none", choices=["abf", "none", "frs", "frs+abf"],
                    help="decoupling of the CPR built on A^T for the adjoint solves")
+    p.add_argument("--ilu-fill", type=int, default=0, choices=[0, 1],
+                   help="level of fill of the block ILU stage (0: ILU(0), 1: ILU(1))")
+    p.add_argument("--no-ilu-compare", action="store_true",
+                   help="skip timing the other ILU level on the same system")
     p.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoother degree")
     p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"],
@@ -242,9 +246,11 @@ def run_sequence(args):
     g = torch.zeros(sysm.n_unknowns, dtype=torch.float64, device=dev)
     g[torch.from_numpy(np.unique(sysm.perf_cell).astype(np.int64) * sysm.b).to(dev)] = 1.0
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling)
+    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling,
+                ilu_fill=args.ilu_fill)
     AT = A.transpose()
-    MT = trs.CPR(AT, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.adjoint_decoupling)
+    MT = trs.CPR(AT, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.adjoint_decoupling,
+                 ilu_fill=args.ilu_fill)
     x = torch.zeros_like(ds.rhs)
     records = []
 
@@ -290,7 +296,7 @@ def run_sequence(args):
                            "unknowns": sysm.n_unknowns, "systems": args.sequence, "amg_rebuild_every": args.reuse,
                            "rtol": args.rtol, "precision": args.precision,
                            "decoupling": args.decoupling, "adjoint_decoupling": args.adjoint_decoupling,
-                           "restart": args.restart,
+                           "restart": args.restart, "ilu_fill": args.ilu_fill,
                            "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
                 "per_system": records, "clocks": clk.summary(), "gpu_launches": trs.kernel_launches() - l0}
         print(json.dumps(line), flush=True)
@@ -317,7 +323,8 @@ def main():
     sysm = make_workload(args.workload)
     ds = trs.DeviceSystem(sysm, dev)
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling)
+    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling,
+                ilu_fill=args.ilu_fill)
     x = torch.zeros_like(ds.rhs)
     info = M.info()
 
@@ -398,10 +405,35 @@ def main():
             ta.append(e0.elapsed_time(e1))
         other = {"method": alt, "ms_per_step": statistics.median(ta), "solve_ms": ra.stats["ms_solve"],
                  "iters": ra.stats["iters"], "true_relres": ra.stats["true_relres"]}
+    # the other ILU level of the F stage on the same system
+    other_ilu = None
+    if not args.no_ilu_compare:
+        fill = 1 - args.ilu_fill
+        Mi = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling,
+                     ilu_fill=fill)
+        for _ in range(2):
+            ds.assemble()
+            Mi.update(A, reuse_amg=False)
+            trs.krylov_solve(args.krylov, A, Mi, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+        torch.cuda.synchronize()
+        ti = []
+        for _ in range(max(1, min(args.steps, 5))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ds.assemble()
+            Mi.update(A, reuse_amg=False)
+            _, ri = trs.krylov_solve(args.krylov, A, Mi, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ti.append(e0.elapsed_time(e1))
+        other_ilu = {"ilu_fill": fill, "ms_per_step": statistics.median(ti), "setup_ms": ri.stats["ms_setup"],
+                     "solve_ms": ri.stats["ms_solve"], "iters": ri.stats["iters"],
+                     "true_relres": ri.stats["true_relres"], "n_colours": Mi.info()["n_colours"]}
+        del Mi
     # FP64-preconditioner path on the same system, for the mixed/FP64 comparison
     fp64 = None
     if not args.no_fp64_compare and args.precision == "fp32":
-        M64 = trs.CPR(A, precision="fp64")
+        M64 = trs.CPR(A, precision="fp64", decoupling=args.decoupling, ilu_fill=args.ilu_fill)
         for _ in range(2):
             ds.assemble()
             M64.update(A, reuse_amg=False)
@@ -475,13 +507,13 @@ def main():
                        "krylov": args.krylov,
                        "precision": "FP32 CPR inside FP64 Krylov" if args.precision == "fp32" else "FP64",
                        "rtol": args.rtol, "restart": args.restart, "cheb_degree": args.cheb_degree,
-                       "decoupling": args.decoupling,
+                       "decoupling": args.decoupling, "ilu_fill": args.ilu_fill,
                        "l2": "inputs larger than L2 (Jacobian inputs 0.9 GB, matrix 0.9 GB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iters": last["iters"], "true_relres": last["true_relres"], "host_true_relres": host_relres,
             "breakdown_ms": {"setup": last["ms_setup"], "solve": last["ms_solve"]},
             "amg_levels": info["n_levels"], "amg_rows": info["level_rows"], "n_colours": info["n_colours"],
-            "fp64_path": fp64, "other_krylov": other,
+            "fp64_path": fp64, "other_krylov": other, "other_ilu": other_ilu,
             "roofline": {"kernel": kname, "bound": "alu",
                          "achieved": spmv_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                          "frac": spmv_tflops / fp64_peak_tflops, "traffic": spmv_traffic,

@@ -84,6 +84,25 @@ typedef struct trs_cpr trs_cpr;
 #define TRS_DEC_FRS 2
 #define TRS_DEC_FRS_ABF 3
 
+/* Level of fill of the block ILU stage F (trs_cpr_opts.ilu_fill).  The
+ * paper's subdomain solves may be block ILU(k), and its recommended level is
+ * k = 1 (Sec. "Preconditioners", the RAS paragraph).
+ *   TRS_ILU0: block ILU(0) on the pattern of Ã, rows in the colour-major
+ *     order of a Jones-Plassmann colouring (about 6 colours on a 7-point
+ *     grid);
+ *   TRS_ILU1: block ILU(1): the pattern of Ã plus every (i, j) with a
+ *     neighbour k ordered before both (level of fill 1), rows in the
+ *     colour-major order of a distance-2 colouring: grid cell (x, y, z)
+ *     takes colour (x + 2y + 3z) mod 7, the other rows (wells), in index
+ *     order, the first colour from 7 on not taken by an earlier such row
+ *     that is adjacent to them or shares a neighbour with them.  Needs a
+ *     matrix created with grid_dims; TRS_ERR_UNSUPPORTED when two rows of
+ *     one colour are coupled in the factor pattern (a cell coupled to
+ *     another cell outside its 7-point star).  The fill pattern is built on
+ *     the host once, at trs_cpr_setup. */
+#define TRS_ILU0 0
+#define TRS_ILU1 1
+
 typedef struct {
   int32_t precision;     /* TRS_FP64 or TRS_FP32_PREC */
   double theta;          /* AMG strength threshold (default 0.08) */
@@ -93,6 +112,7 @@ typedef struct {
   uint32_t seed;         /* seed of the MIS-2 and colouring priorities */
   int32_t stages;        /* TRS_CPR_FPF (default), TRS_CPR_FP or TRS_CPR_PF */
   int32_t decoupling;    /* TRS_DEC_ABF (default), TRS_DEC_NONE, TRS_DEC_FRS, TRS_DEC_FRS_ABF */
+  int32_t ilu_fill;      /* level of fill of the block ILU stage: TRS_ILU0 (default) or TRS_ILU1 */
 } trs_cpr_opts;
 
 /* Krylov method (trs_solve_opts.method). */
@@ -227,10 +247,11 @@ void trs_cpr_default_opts(trs_cpr_opts *opts);
  * with row pivoting (GJE), Ã = D^-1 A; pressure matrix A_p = (Ã_ij)_00;
  * aggregation AMG of A_p (strength, MIS-2, unsmoothed aggregates, Galerkin
  * P^T A P, Chebyshev smoothing, dense LU at the coarsest level);
- * Jones-Plassmann multicolouring and block ILU(0) of Ã.  The handle keeps a
- * reference to nothing of A; A may change afterwards (see trs_cpr_update).
+ * multicolouring and block ILU(0) of Ã (block ILU(1) with opts->ilu_fill =
+ * TRS_ILU1).  The handle keeps a reference to nothing of A; A may change
+ * afterwards (see trs_cpr_update).
  * Errors: TRS_ERR_SINGULAR_BLOCK, TRS_ERR_COARSENING, TRS_ERR_INVALID,
- * TRS_ERR_OOM, TRS_ERR_CUDA. */
+ * TRS_ERR_UNSUPPORTED, TRS_ERR_OOM, TRS_ERR_CUDA. */
 trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *stream,
                          trs_cpr **out);
 

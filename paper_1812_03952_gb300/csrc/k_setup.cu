@@ -1327,9 +1327,10 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
       bstore<B, T>(BRef<T>{fell + ((int64_t)s * np + q) * BB, 1}, v);
     }
   }
-  if (idx < nft) {
+  if (idx < nft) {   // fill blocks of ILU(1) (no source block) start from zero
+    const int64_t src = ftsrc[idx];
 #pragma unroll
-    for (int e = 0; e < BB; e++) ftval[idx * BB + e] = at_tval[ftsrc[idx] * BB + e];
+    for (int e = 0; e < BB; e++) ftval[idx * BB + e] = src >= 0 ? at_tval[src * BB + e] : T(0);
   }
 }
 

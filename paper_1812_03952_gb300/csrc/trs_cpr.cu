@@ -158,6 +158,117 @@ void alloc_level_vectors(trs_cpr *M) {
   }
 }
 
+// ------------------------------------------------------ block ILU(1)
+// Distance-2 colours of a grid matrix: cell (x, y, z) takes (x + 2y + 3z)
+// mod 7, which differs between any two cells one or two 7-point steps apart
+// (the offsets are +-1, +-2, +-3 mod 7 and their pairwise sums, never 0 mod
+// 7 for |sum| <= 6); the other rows, in index order, take the first colour
+// from 7 on not taken by an earlier such row that is adjacent to them or
+// shares a neighbour with them.
+std::vector<int32_t> distance2_colours(const trs_bsr *A) {
+  const int64_t n = A->n, nc = A->g.nc;
+  const int64_t nx = A->g.nx, nxy = (int64_t)A->g.nx * A->g.ny;
+  const auto &rp = A->h_rp;
+  const auto &col = A->h_col;
+  std::vector<int32_t> c(n);
+  for (int64_t i = 0; i < nc; i++) c[i] = (int32_t)((i % nx + 2 * ((i / nx) % A->g.ny) + 3 * (i / nxy)) % 7);
+  for (int64_t w = nc; w < n; w++) {
+    uint64_t used = 0;
+    for (int64_t p = rp[w]; p < rp[w + 1]; p++) {
+      const int64_t k = col[p];
+      if (k == w) continue;
+      if (k >= nc && k < w) used |= 1ull << (c[k] - 7);
+      for (int64_t q = rp[k]; q < rp[k + 1]; q++) {
+        const int64_t j = col[q];
+        if (j >= nc && j < w) used |= 1ull << (c[j] - 7);
+      }
+    }
+    int f = 0;
+    while (f < kMaxColours - 7 && ((used >> f) & 1ull)) f++;
+    TRS_REQUIRE(f < kMaxColours - 7, TRS_ERR_UNSUPPORTED, "more than 64 colours needed");
+    c[w] = 7 + f;
+  }
+  return c;
+}
+
+// The factor structure of block ILU(1), once per pattern, on the host: the
+// level-1 fill of row i is every j, not already in row i, with a neighbour
+// k of i ordered before both i and j ((i, k), (k, j) stored).  Fill blocks
+// join the tail of their row (sorted by column, no source block: they start
+// from zero); the parallel sweeps need the rows of one colour uncoupled in
+// the resulting pattern, which is checked here.
+void build_ilu1_structure(trs_cpr *M, const trs_bsr *A, const std::vector<int32_t> &colour, cudaStream_t s) {
+  const int64_t n = M->n, nc = M->g.nc;
+  const auto &rp = A->h_rp;
+  const auto &col = A->h_col;
+  const auto hpos = download(M->pos.p, n, s);
+  const auto hcrow = download(M->crow.p, n, s);
+  const auto htptr = download(M->tptr.p, n + 1, s);
+  const auto htcol = download(M->tcol.p, M->ntail, s);
+  const auto hem = download(M->emask.p, nc, s);
+  std::vector<int64_t> fptr(n + 1, 0), stamp(n, -1);
+  std::vector<int32_t> fcol;
+  fcol.reserve((size_t)rp[n]);
+  for (int64_t i = 0; i < n; i++) {
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+      stamp[col[p]] = i;
+      TRS_REQUIRE(col[p] == i || colour[col[p]] != colour[i], TRS_ERR_UNSUPPORTED,
+                  "block ILU(1): two coupled rows share a colour (the order needs a 7-point grid)");
+    }
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+      const int64_t k = col[p];
+      if (hpos[k] >= hpos[i]) continue;
+      for (int64_t q = rp[k]; q < rp[k + 1]; q++) {
+        const int64_t j = col[q];
+        if (hpos[j] <= hpos[k] || stamp[j] == i) continue;
+        stamp[j] = i;
+        TRS_REQUIRE(colour[j] != colour[i], TRS_ERR_UNSUPPORTED,
+                    "block ILU(1): level-1 fill couples two rows of one colour (the order needs a 7-point grid)");
+        fcol.push_back((int32_t)j);
+      }
+    }
+    fptr[i + 1] = (int64_t)fcol.size();
+  }
+  std::vector<int64_t> ftptr(n + 1, 0), ftsrc;
+  std::vector<int32_t> ftcol;
+  std::vector<uint8_t> ftlow, lmask(n);
+  const size_t total = (size_t)(M->ntail + fptr[n]);
+  ftsrc.reserve(total);
+  ftcol.reserve(total);
+  ftlow.reserve(total);
+  std::vector<std::pair<int32_t, int64_t>> row;
+  for (int64_t q = 0; q < n; q++) {
+    const int64_t i = hcrow[q];
+    row.clear();
+    for (int64_t t = htptr[i]; t < htptr[i + 1]; t++) row.push_back({htcol[t], t});
+    for (int64_t u = fptr[i]; u < fptr[i + 1]; u++) row.push_back({fcol[u], -1});
+    std::sort(row.begin(), row.end());
+    for (const auto &e : row) {
+      ftcol.push_back(e.first);
+      ftsrc.push_back(e.second);
+      ftlow.push_back(hpos[e.first] < q ? 1 : 0);
+    }
+    ftptr[q + 1] = (int64_t)ftcol.size();
+    unsigned lm = 0;
+    if (i < nc)
+      for (int sl = 0; sl < kSlots; sl++)
+        if (sl != kSelf && ((hem[i] >> sl) & 1u) && hpos[i + M->g.off[sl]] < q) lm |= 1u << sl;
+    if (!row.empty()) lm |= kTailBit;
+    lmask[q] = (uint8_t)lm;
+  }
+  M->nft = (int64_t)ftcol.size();
+  M->ftptr.alloc(n + 1);
+  M->ftptr.upload(ftptr.data(), n + 1, s);
+  M->ftcol.alloc(std::max<size_t>(ftcol.size(), 1));
+  M->ftcol.upload(ftcol.data(), ftcol.size(), s);
+  M->ftlow.alloc(std::max<size_t>(ftlow.size(), 1));
+  M->ftlow.upload(ftlow.data(), ftlow.size(), s);
+  M->ftsrc.alloc(std::max<size_t>(ftsrc.size(), 1));
+  M->ftsrc.upload(ftsrc.data(), ftsrc.size(), s);
+  M->lmask.upload(lmask.data(), n, s);
+  TRS_CUDA(cudaStreamSynchronize(s));
+}
+
 // ------------------------------------------------- long-row ILU plan
 // Built once per pattern on the host from the colour-major structure: for
 // every long row, its earlier-ordered entries in ascending position and the
@@ -367,22 +478,32 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   M->ap_tval64.alloc(std::max<int64_t>(A->ntail, 1));
   // colouring of the block pattern and the colour-major order
   M->colour.alloc(n);
-  const int rounds = launch_colour(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->opts.seed ^ kColourSeedXor,
-                                   M->colour.p, s);
-  TRS_REQUIRE(rounds >= 0, TRS_ERR_UNSUPPORTED, "more than 64 colours needed");
+  std::vector<int32_t> hcolour;
+  if (M->opts.ilu_fill == TRS_ILU1) {
+    hcolour = distance2_colours(A);
+    M->colour.upload(hcolour.data(), n, s);
+  } else {
+    const int rounds = launch_colour(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->opts.seed ^ kColourSeedXor,
+                                     M->colour.p, s);
+    TRS_REQUIRE(rounds >= 0, TRS_ERR_UNSUPPORTED, "more than 64 colours needed");
+    hcolour = download(M->colour.p, n, s);
+  }
   {
-    auto hc = download(M->colour.p, n, s);
     int mx = 0;
-    for (auto c : hc) mx = std::max(mx, c + 1);
+    for (auto c : hcolour) mx = std::max(mx, c + 1);
     M->ncol = mx;
   }
   M->crow.alloc(n);
   M->pos.alloc(n);
   launch_colour_order(M->g, M->colour.p, M->ncol, M->cptr, M->cmid, M->crow.p, M->pos.p, s);
   M->lmask.alloc(n);
-  launch_ilu_structure(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->crow.p, M->pos.p, M->lmask.p, M->ftptr, M->ftcol,
-                       M->ftlow, M->ftsrc, s);
-  M->nft = M->ntail;
+  if (M->opts.ilu_fill == TRS_ILU1) {
+    build_ilu1_structure(M, A, hcolour, s);
+  } else {
+    launch_ilu_structure(M->g, M->emask.p, M->tptr.p, M->tcol.p, M->crow.p, M->pos.p, M->lmask.p, M->ftptr,
+                         M->ftcol, M->ftlow, M->ftsrc, s);
+    M->nft = M->ntail;
+  }
   build_long_row_plan(M, s);
   if (M->prec == TRS_FP32_PREC) {
     M->fell32.alloc((size_t)kSlots * bb * n);
@@ -943,6 +1064,7 @@ void trs_cpr_default_opts(trs_cpr_opts *o) {
   o->seed = 0x5EED1812u;
   o->stages = TRS_CPR_FPF;
   o->decoupling = TRS_DEC_ABF;
+  o->ilu_fill = TRS_ILU0;
 }
 
 void trs_solve_default_opts(trs_solve_opts *o) {
@@ -969,6 +1091,10 @@ trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *strea
                 "stages must be TRS_CPR_FPF, TRS_CPR_FP or TRS_CPR_PF");
     TRS_REQUIRE(o.decoupling >= TRS_DEC_ABF && o.decoupling <= TRS_DEC_FRS_ABF, TRS_ERR_INVALID,
                 "decoupling must be TRS_DEC_ABF, TRS_DEC_NONE, TRS_DEC_FRS or TRS_DEC_FRS_ABF");
+    TRS_REQUIRE(o.ilu_fill == TRS_ILU0 || o.ilu_fill == TRS_ILU1, TRS_ERR_INVALID,
+                "ilu_fill must be TRS_ILU0 or TRS_ILU1");
+    TRS_REQUIRE(o.ilu_fill == TRS_ILU0 || A->structured, TRS_ERR_UNSUPPORTED,
+                "block ILU(1) needs a matrix created with grid dimensions");
     cudaStream_t s = (cudaStream_t)stream;
     auto M = std::make_unique<trs_cpr>();
     M->opts = o;

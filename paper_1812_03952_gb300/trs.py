@@ -58,7 +58,7 @@ class TrsError(RuntimeError):
 class CprOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("theta", C.c_double), ("coarse_max", C.c_int32),
                 ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("seed", C.c_uint32),
-                ("stages", C.c_int32), ("decoupling", C.c_int32)]
+                ("stages", C.c_int32), ("decoupling", C.c_int32), ("ilu_fill", C.c_int32)]
 
 
 class SolveOpts(C.Structure):

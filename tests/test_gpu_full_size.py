@@ -80,3 +80,22 @@ def test_full_size_solve_meets_tolerance(trs, oracle, full, method):
     tr = _relres(oracle, Ao, sysm.rhs, x.cpu().numpy())
     assert tr <= 1.01e-6
     assert abs(tr - res.stats["true_relres"]) <= 1e-12
+
+
+def test_full_size_ilu1(trs, oracle, full):
+    """Block ILU(1) at the full size: the distance-2 colours bit for bit, one
+    FP64 application against the oracle's, and the benchmark's FP32 solve to
+    the true residual."""
+    sysm, ds, A, Ao = full
+    grid = (sysm.nx, sysm.ny, sysm.nz)
+    Mo = oracle.CPR(Ao, ilu_fill=1, grid=grid)
+    M = trs.CPR(A, precision="fp64", ilu_fill=1)
+    np.testing.assert_array_equal(M.colours(), Mo.colours())
+    v = np.random.default_rng(8).standard_normal(Ao.n * Ao.b)
+    z = M.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    zo = Mo.apply(v)
+    assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-11
+    M32 = trs.CPR(A, precision="fp32", ilu_fill=1)
+    x, res = trs.krylov_solve("fgmres", A, M32, ds.rhs, torch.empty_like(ds.rhs), rtol=1e-6)
+    assert res.status == trs.TRS_OK
+    assert _relres(oracle, Ao, sysm.rhs, x.cpu().numpy()) <= 1.01e-6
