@@ -1308,7 +1308,7 @@ __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol
 
 template <int B, class T>
 __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
-                           const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell,
+                           const T *at_tval, const int64_t *ftsrc, int64_t nft, int nslots, T *fell,
                            T *ftval) {
   constexpr int BB = B * B;
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -1316,9 +1316,9 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
   if (idx < np) {
     const int64_t q = idx, i = crow[q];
     const unsigned m = i < g.nc ? emask[i] : 0u;
-    for (int s = 0; s < kSlots; s++) {
+    for (int s = 0; s < nslots; s++) {   // stencil slots from Ã; ILU(1) fill slots from zero
       T v[BB];
-      if ((m >> s) & 1u) {
+      if (s < kSlots && ((m >> s) & 1u)) {
         bload<B, T>(BRef<T>{const_cast<T *>(at_ell) + ((int64_t)s * g.nc + i) * BB, 1}, v);
       } else {
 #pragma unroll
@@ -1334,29 +1334,6 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
   }
 }
 
-// entry k of row i (k != i) in factor storage, or p = nullptr
-template <int B, class T>
-__device__ BRef<T> ilu_find(const Geom &g, const uint8_t *emask, const int64_t *pos, const int64_t *ftptr,
-                         const int32_t *ftcol, T *fell, T *ftval, int64_t i, int64_t k) {
-  constexpr int BB = B * B;
-  const int64_t qi = pos[i], np = g.n_rows;
-  if (i < g.nc && k < g.nc) {
-    const int64_t d = k - i;
-    const unsigned m = emask[i];
-    for (int s = 0; s < kSlots; s++)
-      if (s != kSelf && ((m >> s) & 1u) && g.off[s] == d)
-        return BRef<T>{fell + ((int64_t)s * np + qi) * BB, 1};
-  }
-  int64_t lo = ftptr[qi], hi = ftptr[qi + 1] - 1;
-  while (lo <= hi) {
-    const int64_t mid = lo + (hi - lo) / 2;
-    const int64_t c = ftcol[mid];
-    if (c == k) return BRef<T>{ftval + mid * BB, 1};
-    if (c < k) lo = mid + 1; else hi = mid - 1;
-  }
-  return BRef<T>{nullptr, 0};
-}
-
 // IKJ ILU(0) of the rows at positions [q0, q1) (one colour): for every
 // earlier-ordered k of row i in ascending order, L_ik = W_ik U_kk^-1 and
 // W_ij -= L_ik U_kj for later-ordered j of row i with (k, j) stored; then
@@ -1364,21 +1341,25 @@ __device__ BRef<T> ilu_find(const Geom &g, const uint8_t *emask, const int64_t *
 // row k (its slots, then its tail) and locating each j in row i: by offset
 // for a slot neighbour, directly for j = i, by a search of row i's (short)
 // tail otherwise; the positions of row i's slot neighbours stay in
-// registers.
+// registers.  With ILU(1) (fmask given) the fill slots (fell slots 7 + f,
+// neighbour at off2[f]) are one more set of slots of every cell row: the
+// same IKJ steps on the level-1 pattern.
 template <int B, class T>
 __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
-                             const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, T *fell,
-                             T *ftval, int64_t q0, int64_t q1, int *err) {
+                             const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow,
+                             const uint32_t *fmask, T *fell, T *ftval, int64_t q0, int64_t q1, int *err) {
   constexpr int BB = B * B;
   const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (q >= q1) return;
   const int64_t np = g.n_rows, i = crow[q];
   const bool cell = i < g.nc;
   const unsigned m = cell ? emask[i] : 0u;
+  const unsigned fm = (cell && fmask) ? fmask[q] : 0u;
   const int64_t u0 = ftptr[q], u1 = ftptr[q + 1];
   int64_t spos[kSlots];
 #pragma unroll
   for (int s = 0; s < kSlots; s++) spos[s] = (s != kSelf && ((m >> s) & 1u)) ? pos[i + g.off[s]] : -1;
+  auto fslot = [&](int f) -> T * { return fell + ((int64_t)(kSlots + f) * np + q) * BB; };
   // reference to the entry of row i in column j with its position, or p = nullptr
   auto target = [&](int64_t j, int64_t &pj) -> BRef<T> {
     if (j == i) {
@@ -1392,6 +1373,12 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
           pj = spos[s];
           return BRef<T>{fell + ((int64_t)s * np + q) * BB, 1};
         }
+      if (fm)
+        for (int f = 0; f < kFill; f++)
+          if (((fm >> f) & 1u) && g.off2[f] == d) {
+            pj = pos[j];
+            return BRef<T>{fslot(f), 1};
+          }
     }
     for (int64_t u = u0; u < u1; u++)
       if (ftcol[u] == j) {
@@ -1414,6 +1401,16 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
         wref = BRef<T>{fell + ((int64_t)s * np + q) * BB, 1};
       }
     }
+    if (fm)
+      for (int f = 0; f < kFill; f++) {
+        if (!((fm >> f) & 1u)) continue;
+        const int64_t pc = pos[i + g.off2[f]];
+        if (pc > cur && pc < pbest) {
+          pbest = pc;
+          kr = i + g.off2[f];
+          wref = BRef<T>{fslot(f), 1};
+        }
+      }
     for (int64_t u = u0; u < u1; u++) {
       const int64_t c = ftcol[u];
       if (c == i) continue;
@@ -1431,35 +1428,37 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
     bload<B, T>(BRef<T>{fell + ((int64_t)kSelf * np + pbest) * BB, 1}, Uinv);
     bmul<B, T>(W, Uinv, L);
     bstore<B, T>(wref, L);
-    // row k: its slots, then its tail
-    const unsigned mk = kr < g.nc ? emask[kr] : 0u;
-    for (int s2 = 0; s2 < kSlots; s2++) {
-      if (s2 == kSelf || !((mk >> s2) & 1u)) continue;
+    // W_ij -= L_ik U_kj for the entry (k, j) of row k kept in `ub`
+    auto update = [&](int64_t j, const T *ub) {
       int64_t pj = -1;
-      const BRef<T> wr = target(kr + g.off[s2], pj);
-      if (!wr.p || pj <= pbest) continue;
+      const BRef<T> wr = target(j, pj);
+      if (!wr.p || pj <= pbest) return;
       T U[BB], P[BB], Wij[BB];
-      bload<B, T>(BRef<T>{fell + ((int64_t)s2 * np + pbest) * BB, 1}, U);
+      bload<B, T>(BRef<T>{const_cast<T *>(ub), 1}, U);
       bmul<B, T>(L, U, P);
       bload<B, T>(wr, Wij);
 #pragma unroll
       for (int e = 0; e < BB; e++) Wij[e] = Wij[e] - P[e];
       bstore<B, T>(wr, Wij);
+    };
+    // row k: its slots, its fill slots, then its tail
+    const bool kcell = kr < g.nc;
+    const unsigned mk = kcell ? emask[kr] : 0u;
+    for (int s2 = 0; s2 < kSlots; s2++) {
+      if (s2 == kSelf || !((mk >> s2) & 1u)) continue;
+      update(kr + g.off[s2], fell + ((int64_t)s2 * np + pbest) * BB);
     }
+    const unsigned fk = (kcell && fmask) ? fmask[pbest] : 0u;
+    if (fk)
+      for (int f = 0; f < kFill; f++) {
+        if (!((fk >> f) & 1u)) continue;
+        update(kr + g.off2[f], fell + ((int64_t)(kSlots + f) * np + pbest) * BB);
+      }
     const int64_t k0 = ftptr[pbest], k1 = ftptr[pbest + 1];
     for (int64_t uk = k0; uk < k1; uk++) {
       const int64_t j = ftcol[uk];
       if (j == kr) continue;
-      int64_t pj = -1;
-      const BRef<T> wr = target(j, pj);
-      if (!wr.p || pj <= pbest) continue;
-      T U[BB], P[BB], Wij[BB];
-      bload<B, T>(BRef<T>{ftval + uk * BB, 1}, U);
-      bmul<B, T>(L, U, P);
-      bload<B, T>(wr, Wij);
-#pragma unroll
-      for (int e = 0; e < BB; e++) Wij[e] = Wij[e] - P[e];
-      bstore<B, T>(wr, Wij);
+      update(j, ftval + uk * BB);
     }
   }
   // diagonal: slot 3 for cells, the tail entry for other rows
@@ -1486,8 +1485,8 @@ __global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, 
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint8_t *emask, const int32_t *crow,
                                                               const int64_t *pos, const int64_t *ftptr,
-                                                              const int32_t *ftcol, T *fell, T *ftval,
-                                                              int64_t q1, int64_t q2, int *err) {
+                                                              const int32_t *ftcol, const uint32_t *fmask,
+                                                              T *fell, T *ftval, int64_t q1, int64_t q2, int *err) {
   constexpr int BB = B * B;
   const int lane = threadIdx.x & 31;
   const int64_t q = q1 + blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
@@ -1544,9 +1543,12 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
     __syncwarp();
     if (lane < BB) ftval[ub * BB + lane] = s_L[wid][lane];
     // entries (k, j) of row k later than k with j stored in row i: lane e
-    // resolves entry e of row k (slots first, then the tail)
-    const int nk = kSlots + (int)(ku1 - ku0);
+    // resolves entry e of row k (slots first, then the ILU(1) fill slots,
+    // then the tail)
+    const int nks = fmask ? kSlots + kFill : kSlots;
+    const int nk = nks + (int)(ku1 - ku0);
     const unsigned mk = kr < g.nc ? emask[kr] : 0u;
+    const unsigned fk = (kr < g.nc && fmask) ? fmask[pb] : 0u;
     for (int e0 = 0; e0 < nk; e0 += 32) {
       const int e = e0 + lane;
       int64_t dst = -1, src = 0, srcs = 1;
@@ -1558,8 +1560,14 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
             src = ((int64_t)e * np + pb) * BB;  // into fell
             srcs = -1;                          // negative marks fell
           }
+        } else if (e < nks) {
+          if ((fk >> (e - kSlots)) & 1u) {
+            j = kr + g.off2[e - kSlots];
+            src = ((int64_t)e * np + pb) * BB;
+            srcs = -1;
+          }
         } else {
-          const int64_t uk = ku0 + (e - kSlots);
+          const int64_t uk = ku0 + (e - nks);
           j = ftcol[uk];
           if (j == kr) j = -1;
           src = uk * BB;
@@ -2011,25 +2019,28 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
 
 template <class T>
 void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
-                     const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell, T *ftval, cudaStream_t s) {
+                     const T *at_tval, const int64_t *ftsrc, int64_t nft, int nslots, T *fell, T *ftval,
+                     cudaStream_t s) {
   const int64_t n = std::max<int64_t>(g.n_rows, nft);
   TRS_DISPATCH_B(b, k_ilu_init<B, T><<<grid_of(n), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc, nft,
-                                                                     fell, ftval));
+                                                                     nslots, fell, ftval));
   TRS_LAUNCHED();
 }
 template void launch_ilu_init<double>(int, const Geom &, const uint8_t *, const int32_t *, const double *,
-                                      const double *, const int64_t *, int64_t, double *, double *, cudaStream_t);
+                                      const double *, const int64_t *, int64_t, int, double *, double *,
+                                      cudaStream_t);
 template void launch_ilu_init<float>(int, const Geom &, const uint8_t *, const int32_t *, const float *,
-                                     const float *, const int64_t *, int64_t, float *, float *, cudaStream_t);
+                                     const float *, const int64_t *, int64_t, int, float *, float *, cudaStream_t);
 
 template <class T>
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
-                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow, T *fell, T *ftval,
-                              int64_t q0, int64_t q1, int64_t q2, const LongRowPlan *plan, const LongRowColour *pc,
-                              int *err, cudaStream_t s) {
+                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow,
+                              const uint32_t *fmask, T *fell, T *ftval, int64_t q0, int64_t q1, int64_t q2,
+                              const LongRowPlan *plan, const LongRowColour *pc, int *err, cudaStream_t s) {
   if (q1 > q0) {
     TRS_DISPATCH_B(b, k_ilu_factor<B, T><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
-                                                                               ftlow, fell, ftval, q0, q1, err));
+                                                                               ftlow, fmask, fell, ftval, q0, q1,
+                                                                               err));
     TRS_LAUNCHED();
   }
   if (q2 > q1 && plan && pc) {
@@ -2052,19 +2063,19 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
   }
   if (q2 > q1) {
     const unsigned grid = (unsigned)((q2 - q1 + kWarps - 1) / kWarps);
-    TRS_DISPATCH_B(b, k_ilu_factor_long<B, T><<<grid, kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol, fell,
-                                                                        ftval, q1, q2, err));
+    TRS_DISPATCH_B(b, k_ilu_factor_long<B, T><<<grid, kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol, fmask,
+                                                                        fell, ftval, q1, q2, err));
     TRS_LAUNCHED();
   }
 }
 template void launch_ilu_factor_colour<double>(int, const Geom &, const uint8_t *, const int32_t *, const int64_t *,
-                                               const int64_t *, const int32_t *, const uint8_t *, double *,
-                                               double *, int64_t, int64_t, int64_t, const LongRowPlan *,
+                                               const int64_t *, const int32_t *, const uint8_t *, const uint32_t *,
+                                               double *, double *, int64_t, int64_t, int64_t, const LongRowPlan *,
                                                const LongRowColour *, int *, cudaStream_t);
 template void launch_ilu_factor_colour<float>(int, const Geom &, const uint8_t *, const int32_t *, const int64_t *,
-                                              const int64_t *, const int32_t *, const uint8_t *, float *, float *,
-                                              int64_t, int64_t, int64_t, const LongRowPlan *, const LongRowColour *,
-                                              int *, cudaStream_t);
+                                              const int64_t *, const int32_t *, const uint8_t *, const uint32_t *,
+                                              float *, float *, int64_t, int64_t, int64_t, const LongRowPlan *,
+                                              const LongRowColour *, int *, cudaStream_t);
 
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s) {
   if (!A->n) return;

@@ -314,6 +314,28 @@ __global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__
 }
 
 // ------------------------------------------------------------ ILU sweeps
+// t -= sum over the ILU(1) fill slots f in fm of F_f y_(i + off2[f])
+template <int B, class T>
+__device__ __forceinline__ void fill_slots_apply(const IluView<T> &F, unsigned fm, int64_t i, int64_t q,
+                                                 const T *y, T (&t)[B]) {
+  constexpr int BB = B * B;
+  if (!fm) return;
+  const int64_t np = F.g.n_rows;
+#pragma unroll
+  for (int f = 0; f < kFill; f++) {
+    if (!((fm >> f) & 1u)) continue;
+    const int64_t j = i + F.g.off2[f];
+    T yj[B];
+    load_blk<B>(y + j * B, yj);
+    T bv[BB];
+    load_block<B>(F.fell + ((int64_t)(kSlots + f) * np + q) * BB, bv);
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
+  }
+}
+
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__restrict__ rhs, T *y, int64_t q0,
                                                       int64_t q1, int64_t q2, int64_t cell_blocks) {
@@ -339,6 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__r
 #pragma unroll
         for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
     }
+    if (F.flmask) fill_slots_apply<B>(F, F.flmask[q], i, q, y, t);
     if (lm & kTailBit)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       if (!F.ftlow[u]) continue;
@@ -409,6 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
 #pragma unroll
         for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
     }
+    if (F.fmask) fill_slots_apply<B>(F, rhs ? F.flmask[q] : F.fmask[q] & ~F.flmask[q], i, q, y, t);
     if (lmq & kTailBit)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       const int64_t j = F.ftcol[u];

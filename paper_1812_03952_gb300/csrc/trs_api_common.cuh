@@ -86,6 +86,8 @@ struct trs_cpr {
   trs::DBuf<int64_t> pos, ftptr, ftsrc;
   trs::DBuf<int32_t> ftcol;
   trs::DBuf<uint8_t> lmask, ftlow;
+  trs::DBuf<uint32_t> fmask, flmask;   // ILU(1) fill slots by position
+  int nfslots = trs::kSlots;           // factor slots per position: 7, or 7 + 18 with ILU(1)
   int64_t nft = 0;
   trs::DBuf<double> fell64, ftval64;
   trs::DBuf<float> fell32, ftval32;

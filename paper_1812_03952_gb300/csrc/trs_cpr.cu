@@ -194,9 +194,10 @@ std::vector<int32_t> distance2_colours(const trs_bsr *A) {
 // The factor structure of block ILU(1), once per pattern, on the host: the
 // level-1 fill of row i is every j, not already in row i, with a neighbour
 // k of i ordered before both i and j ((i, k), (k, j) stored).  Fill blocks
-// join the tail of their row (sorted by column, no source block: they start
-// from zero); the parallel sweeps need the rows of one colour uncoupled in
-// the resulting pattern, which is checked here.
+// go to the fill slots of their row when they join two cells two 7-point
+// steps apart, and otherwise to the tail of their row (sorted by column, no
+// source block); all start from zero.  The parallel sweeps need the rows of
+// one colour uncoupled in the resulting pattern, which is checked here.
 void build_ilu1_structure(trs_cpr *M, const trs_bsr *A, const std::vector<int32_t> &colour, cudaStream_t s) {
   const int64_t n = M->n, nc = M->g.nc;
   const auto &rp = A->h_rp;
@@ -229,9 +230,19 @@ void build_ilu1_structure(trs_cpr *M, const trs_bsr *A, const std::vector<int32_
     }
     fptr[i + 1] = (int64_t)fcol.size();
   }
+  // fill slot of a cell-to-cell fill block (i, j), or -1: by the cells' grid displacement
+  const int64_t nx = M->g.nx, ny = M->g.ny, nxy = nx * ny;
+  auto fill_slot = [&](int64_t i, int64_t j) -> int {
+    if (i >= nc || j >= nc) return -1;
+    const int64_t dx = j % nx - i % nx, dy = (j / nx) % ny - (i / nx) % ny, dz = j / nxy - i / nxy;
+    for (int f = 0; f < kFill; f++)
+      if (kFillD[f][0] == dx && kFillD[f][1] == dy && kFillD[f][2] == dz) return f;
+    return -1;
+  };
   std::vector<int64_t> ftptr(n + 1, 0), ftsrc;
   std::vector<int32_t> ftcol;
   std::vector<uint8_t> ftlow, lmask(n);
+  std::vector<uint32_t> fmask(n, 0u), flmask(n, 0u);
   const size_t total = (size_t)(M->ntail + fptr[n]);
   ftsrc.reserve(total);
   ftcol.reserve(total);
@@ -241,7 +252,15 @@ void build_ilu1_structure(trs_cpr *M, const trs_bsr *A, const std::vector<int32_
     const int64_t i = hcrow[q];
     row.clear();
     for (int64_t t = htptr[i]; t < htptr[i + 1]; t++) row.push_back({htcol[t], t});
-    for (int64_t u = fptr[i]; u < fptr[i + 1]; u++) row.push_back({fcol[u], -1});
+    for (int64_t u = fptr[i]; u < fptr[i + 1]; u++) {
+      const int f = fill_slot(i, fcol[u]);
+      if (f >= 0) {
+        fmask[q] |= 1u << f;
+        if (hpos[fcol[u]] < q) flmask[q] |= 1u << f;
+      } else {
+        row.push_back({fcol[u], -1});
+      }
+    }
     std::sort(row.begin(), row.end());
     for (const auto &e : row) {
       ftcol.push_back(e.first);
@@ -266,6 +285,11 @@ void build_ilu1_structure(trs_cpr *M, const trs_bsr *A, const std::vector<int32_
   M->ftsrc.alloc(std::max<size_t>(ftsrc.size(), 1));
   M->ftsrc.upload(ftsrc.data(), ftsrc.size(), s);
   M->lmask.upload(lmask.data(), n, s);
+  M->fmask.alloc(n);
+  M->fmask.upload(fmask.data(), n, s);
+  M->flmask.alloc(n);
+  M->flmask.upload(flmask.data(), n, s);
+  M->nfslots = kSlots + kFill;
   TRS_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -285,6 +309,8 @@ void build_long_row_plan(trs_cpr *M, cudaStream_t s) {
   const auto hcol = download(M->ftcol.p, M->nft, s);
   const auto hem = download(M->emask.p, nc, s);
   const auto hcrow = download(M->crow.p, n, s);
+  const bool fill = M->nfslots > kSlots;
+  const auto hfm = fill ? download(M->fmask.p, n, s) : std::vector<uint32_t>();
   std::vector<int64_t> Lptr{0}, Lpk, Pptr{0}, Psrc;
   std::vector<int32_t> diag, Lu, Pdst;
   std::vector<std::pair<int64_t, int32_t>> Ls;
@@ -320,6 +346,15 @@ void build_long_row_plan(trs_cpr *M, cudaStream_t s) {
             if (d < 0) continue;
             Pdst.push_back(d);
             Psrc.push_back(~(((int64_t)s2 * n + pk) * bb));
+          }
+          for (int f = 0; fill && f < kFill; f++) {
+            if (!((hfm[pk] >> f) & 1u)) continue;
+            const int64_t j = kr + M->g.off2[f];
+            if (hpos[j] <= pk) continue;
+            const int32_t d = local(j);
+            if (d < 0) continue;
+            Pdst.push_back(d);
+            Psrc.push_back(~(((int64_t)(kSlots + f) * n + pk) * bb));
           }
         }
         for (int64_t uk = hft[pk]; uk < hft[pk + 1]; uk++) {
@@ -403,19 +438,20 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   }
   // block ILU(0) on Ã, in the preconditioner's precision
   const LongRowPlan plan = long_row_plan(M);
+  const uint32_t *fm = M->nfslots > kSlots ? M->fmask.p : nullptr;
   if (mixed) {
     launch_ilu_init<float>(b, M->g, M->emask.p, M->crow.p, M->at_ell32.p, M->at_tval32.p, M->ftsrc.p, M->nft,
-                           M->fell32.p, M->ftval32.p, s);
+                           M->nfslots, M->fell32.p, M->ftval32.p, s);
     for (int c = 0; c < M->ncol; c++)
       launch_ilu_factor_colour<float>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
-                                      M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], &plan,
+                                      fm, M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], &plan,
                                       M->lr_col.empty() ? nullptr : &M->lr_col[c], err.p, s);
   } else {
     launch_ilu_init<double>(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft,
-                            M->fell64.p, M->ftval64.p, s);
+                            M->nfslots, M->fell64.p, M->ftval64.p, s);
     for (int c = 0; c < M->ncol; c++)
       launch_ilu_factor_colour<double>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p,
-                                       M->ftlow.p, M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c],
+                                       M->ftlow.p, fm, M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c],
                                        M->cptr[c + 1], &plan, M->lr_col.empty() ? nullptr : &M->lr_col[c],
                                        err.p, s);
   }
@@ -506,10 +542,10 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   }
   build_long_row_plan(M, s);
   if (M->prec == TRS_FP32_PREC) {
-    M->fell32.alloc((size_t)kSlots * bb * n);
+    M->fell32.alloc((size_t)M->nfslots * bb * n);
     M->ftval32.alloc(std::max<int64_t>(M->nft * bb, 1));
   } else {
-    M->fell64.alloc((size_t)kSlots * bb * n);
+    M->fell64.alloc((size_t)M->nfslots * bb * n);
     M->ftval64.alloc(std::max<int64_t>(M->nft * bb, 1));
   }
   build_values(M, A, true, s);
@@ -544,7 +580,8 @@ MatView<T> at_view(const trs_cpr *M) {
 
 template <class T>
 IluView<T> ilu_view(const trs_cpr *M) {
-  IluView<T> v{M->g, M->crow.p, M->emask.p, M->lmask.p, M->ftptr.p, M->ftcol.p, M->ftlow.p, nullptr, nullptr};
+  IluView<T> v{M->g,    M->crow.p, M->emask.p, M->lmask.p, M->ftptr.p, M->ftcol.p, M->ftlow.p, nullptr, nullptr,
+               M->nfslots > kSlots ? M->fmask.p : nullptr, M->nfslots > kSlots ? M->flmask.p : nullptr};
   if constexpr (std::is_same<T, float>::value) { v.fell = M->fell32.p; v.ftval = M->ftval32.p; }
   else { v.fell = M->fell64.p; v.ftval = M->ftval64.p; }
   return v;

@@ -32,6 +32,13 @@ constexpr int kSelf = 3;
 // (lmask): the row also has entries in the tail, so that rows without any
 // (almost all cells) never read their tail pointers.
 constexpr unsigned kTailBit = 0x80u;
+// Block ILU(1) keeps the level-1 fill of a cell row that falls on one of the
+// 18 cells two 7-point steps away in fill slots next to the 7 stencil slots:
+// (dx, dy, dz) of fill slot s, ordered by (dz, dy, dx).
+constexpr int kFill = 18;
+constexpr int kFillD[kFill][3] = {{0, 0, -2}, {0, -1, -1}, {-1, 0, -1}, {1, 0, -1}, {0, 1, -1}, {0, -2, 0},
+                                  {-1, -1, 0}, {1, -1, 0}, {-2, 0, 0}, {2, 0, 0}, {-1, 1, 0}, {1, 1, 0},
+                                  {0, 2, 0}, {0, -1, 1}, {-1, 0, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 2}};
 constexpr int kMaxLevels = 16;
 constexpr int kDenseMax = 4096;
 constexpr int kMaxColours = 64;
@@ -134,6 +141,7 @@ struct Geom {
   int64_t nc;       // cells
   int64_t n_rows;   // cells + other rows
   int64_t off[kSlots];
+  int64_t off2[kFill];   // index offsets of the fill slots
   int nx, ny, nz;
 };
 
@@ -145,6 +153,7 @@ inline Geom make_geom(int nx, int ny, int nz, int64_t n_rows) {
   const int64_t sxy = (int64_t)nx * ny;
   int64_t o[kSlots] = {-sxy, -(int64_t)nx, -1, 0, 1, nx, sxy};
   for (int s = 0; s < kSlots; s++) g.off[s] = o[s];
+  for (int s = 0; s < kFill; s++) g.off2[s] = kFillD[s][0] + kFillD[s][1] * (int64_t)nx + kFillD[s][2] * sxy;
   return g;
 }
 

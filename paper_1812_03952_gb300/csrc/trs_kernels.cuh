@@ -25,8 +25,10 @@ struct IluView {
   const int64_t *ftptr;   // [n_rows+1] tail by position
   const int32_t *ftcol;   // natural column
   const uint8_t *ftlow;   // 1: L block, 0: U block
-  const T *fell;          // [7][n_rows][bb] by position (blocks contiguous); slot 3 = U_ii^-1
+  const T *fell;          // [7 (+18)][n_rows][bb] by position (blocks contiguous); slot 3 = U_ii^-1
   const T *ftval;         // [nft][bb]
+  const uint32_t *fmask;  // [n_rows] ILU(1): bit s, fill slot s (fell slot 7 + s) present; NULL for ILU(0)
+  const uint32_t *flmask; // [n_rows] ILU(1): bit s, fill slot s holds an L block
 };
 
 // Scalar operator of one AMG level: ELL-7 + tail (level 0) or CSR.
@@ -249,7 +251,8 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
                           cudaStream_t s);
 template <class T>
 void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
-                     const T *at_tval, const int64_t *ftsrc, int64_t nft, T *fell, T *ftval, cudaStream_t s);
+                     const T *at_tval, const int64_t *ftsrc, int64_t nft, int nslots, T *fell, T *ftval,
+                     cudaStream_t s);
 // Symbolic IKJ plan of the long rows (rows held in the tail: wells, general
 // rows), built once per pattern: for long row r, its earlier-ordered
 // entries k in ascending position (L_u: index in the row, L_pk: position of
@@ -274,7 +277,8 @@ struct LongRowColour {
 template <class T>
 void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const int32_t *crow,
                               const int64_t *pos, const int64_t *ftptr, const int32_t *ftcol,
-                              const uint8_t *ftlow, T *fell, T *ftval, int64_t q0, int64_t q1,
+                              const uint8_t *ftlow, const uint32_t *fmask, T *fell, T *ftval, int64_t q0,
+                              int64_t q1,
                               int64_t q2, const LongRowPlan *plan, const LongRowColour *pc, int *err,
                               cudaStream_t s);
 void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag, int mode,
