@@ -1306,32 +1306,58 @@ __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol
   }
 }
 
+// Factor storage from Ã: the 7 stencil slots of every position, gathered
+// from natural to colour-major order, then the tail entries (a thread per
+// entry; fill entries of ILU(1) have no source block and start from zero).
+// Blocks of a multiple of 16 bytes are copied a thread per position with
+// 128-bit accesses; other sizes (b = 3, 5) a warp per 32 consecutive blocks
+// of one slot, lane by lane over their elements, so that the stores stay
+// contiguous.
 template <int B, class T>
 __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
-                           const T *at_tval, const int64_t *ftsrc, int64_t nft, int nslots, T *fell,
+                           const T *at_tval, const int64_t *ftsrc, int64_t nft, int64_t slot_warps, T *fell,
                            T *ftval) {
   constexpr int BB = B * B;
-  const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t np = g.n_rows;
-  if (idx < np) {
-    const int64_t q = idx, i = crow[q];
-    const unsigned m = i < g.nc ? emask[i] : 0u;
-    for (int s = 0; s < nslots; s++) {   // stencil slots from Ã; ILU(1) fill slots from zero
-      T v[BB];
-      if (s < kSlots && ((m >> s) & 1u)) {
-        bload<B, T>(BRef<T>{const_cast<T *>(at_ell) + ((int64_t)s * g.nc + i) * BB, 1}, v);
-      } else {
+  const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w < slot_warps) {
+    if constexpr (BB * sizeof(T) % 16 == 0) {
+      const int64_t q = w * 32 + lane;   // slot_warps covers the positions once
+      if (q >= np) return;
+      const int64_t i = crow[q];
+      const unsigned m = i < g.nc ? emask[i] : 0u;
 #pragma unroll
-        for (int e = 0; e < BB; e++) v[e] = T(0);
+      for (int s = 0; s < kSlots; s++) {
+        T v[BB];
+        if ((m >> s) & 1u) {
+          bload<B, T>(BRef<T>{const_cast<T *>(at_ell) + ((int64_t)s * g.nc + i) * BB, 1}, v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < BB; e++) v[e] = T(0);
+        }
+        bstore<B, T>(BRef<T>{fell + ((int64_t)s * np + q) * BB, 1}, v);
       }
-      bstore<B, T>(BRef<T>{fell + ((int64_t)s * np + q) * BB, 1}, v);
+    } else {
+      const int64_t chunks = (np + 31) / 32;
+      const int s = (int)(w / chunks);
+      const int64_t q0 = (w % chunks) * 32;
+      const int64_t nq = np - q0 < 32 ? np - q0 : 32;
+      T *dst = fell + ((int64_t)s * np + q0) * BB;
+      for (int64_t e = lane; e < nq * BB; e += 32) {
+        const int64_t i = crow[q0 + e / BB];
+        T v = T(0);
+        if (i < g.nc && ((emask[i] >> s) & 1u)) v = at_ell[((int64_t)s * g.nc + i) * BB + e % BB];
+        dst[e] = v;
+      }
     }
+    return;
   }
-  if (idx < nft) {   // fill blocks of ILU(1) (no source block) start from zero
-    const int64_t src = ftsrc[idx];
+  const int64_t idx = (w - slot_warps) * 32 + lane;
+  if (idx >= nft) return;
+  const int64_t src = ftsrc[idx];
 #pragma unroll
-    for (int e = 0; e < BB; e++) ftval[idx * BB + e] = src >= 0 ? at_tval[src * BB + e] : T(0);
-  }
+  for (int e = 0; e < BB; e++) ftval[idx * BB + e] = src >= 0 ? at_tval[src * BB + e] : T(0);
 }
 
 // IKJ ILU(0) of the rows at positions [q0, q1) (one colour): for every
@@ -1343,9 +1369,10 @@ __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, co
 // tail otherwise; the positions of row i's slot neighbours stay in
 // registers.  With ILU(1) (fmask given) the fill slots (fell slots 7 + f,
 // neighbour at off2[f]) are one more set of slots of every cell row: the
-// same IKJ steps on the level-1 pattern.
+// same IKJ steps on the level-1 pattern.  The FP32 form is held to two
+// resident blocks per SM (b = 5 otherwise takes 207 registers and one).
 template <int B, class T>
-__global__ void k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow,
                              const uint32_t *fmask, T *fell, T *ftval, int64_t q0, int64_t q1, int *err) {
   constexpr int BB = B * B;
@@ -2021,9 +2048,16 @@ template <class T>
 void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
                      const T *at_tval, const int64_t *ftsrc, int64_t nft, int nslots, T *fell, T *ftval,
                      cudaStream_t s) {
-  const int64_t n = std::max<int64_t>(g.n_rows, nft);
-  TRS_DISPATCH_B(b, k_ilu_init<B, T><<<grid_of(n), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc, nft,
-                                                                     nslots, fell, ftval));
+  const int64_t np = g.n_rows, bb = (int64_t)b * b;
+  // ILU(1) fill slots (7 .. nslots - 1) start from zero
+  if (nslots > kSlots)
+    TRS_CUDA(cudaMemsetAsync(fell + (int64_t)kSlots * np * bb, 0, (size_t)(nslots - kSlots) * np * bb * sizeof(T), s));
+  const bool aligned = (bb * (int64_t)sizeof(T)) % 16 == 0;
+  const int64_t slot_warps = (aligned ? 1 : kSlots) * ((np + 31) / 32);
+  const int64_t threads = slot_warps * 32 + nft;
+  if (!threads) return;
+  TRS_DISPATCH_B(b, k_ilu_init<B, T><<<grid_of(threads), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc,
+                                                                           nft, slot_warps, fell, ftval));
   TRS_LAUNCHED();
 }
 template void launch_ilu_init<double>(int, const Geom &, const uint8_t *, const int32_t *, const double *,

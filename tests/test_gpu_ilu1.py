@@ -18,7 +18,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from test_gpu_parity import CASES, _case_id, _gpu_system, _rel, _sys  # noqa: E402
 
-ICASES = [CASES[0], CASES[3], CASES[4], CASES[5], CASES[6]]
+ICASES = CASES   # b = 1 ... 5, wells, shale, ragged tails
 
 
 @pytest.fixture(scope="module")
@@ -110,3 +110,34 @@ def test_ilu1_rejections(trs, oracle, synth):
     with pytest.raises(trs.TrsError) as ei:
         trs.CPR(ds.A, ilu_fill=2)
     assert ei.value.code == trs.TRS_ERR_INVALID
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 1, 1), (1, 1, 7), (3, 1, 2), (2, 2, 2), (4, 3, 2)])
+def test_ilu1_degenerate_grids(trs, oracle, synth, dims):
+    """Grids with fewer than 7 colours present, with and without wells, against a dense solve."""
+    s = synth.small_system(*dims, b=3, seed=42, n_pairs=1 if dims == (4, 3, 2) else 0)
+    ds = _gpu_system(trs, s)
+    Ao = oracle.assemble(s)
+    M = trs.CPR(ds.A, ilu_fill=1, precision="fp64")
+    np.testing.assert_array_equal(M.colours(), oracle.colour_geo(Ao, _grid(s))[0])
+    x, res = trs.fgmres_solve(ds.A, M, ds.rhs, rtol=1e-12)
+    assert res.status == trs.TRS_OK
+    assert _rel(x.cpu().numpy(), np.linalg.solve(Ao.to_dense(), s.rhs)) <= 1e-10
+
+
+def test_ilu1_adjoint(trs, oracle, synth):
+    """The adjoint solve with block ILU(1) in the CPR built on A^T."""
+    s = _sys(synth, 10, 8, 6, 4, seed=31, n_pairs=2)
+    ds = _gpu_system(trs, s)
+    Ao = oracle.assemble(s)
+    M = trs.CPR(ds.A, ilu_fill=1)
+    x, _ = trs.fgmres_solve(ds.A, M, ds.rhs, rtol=1e-11)
+    g = oracle.well_cell_indicator(s)
+    AT = ds.A.transpose()
+    MT = trs.CPR(AT, ilu_fill=1, decoupling="none")
+    lam, dA, res = trs.solve_adjoint(ds.A, AT, MT, torch.from_numpy(g).cuda(), x, want_dA=True, rtol=1e-11)
+    assert res.status == trs.TRS_OK
+    xo = oracle.fgmres(Ao, oracle.CPR(Ao), s.rhs, rtol=1e-11).x
+    lamo, dAo, _ = oracle.adjoint(Ao, g, xo, rtol=1e-11)
+    assert _rel(lam.cpu().numpy(), lamo) <= 1e-8
+    assert _rel(dA.cpu().numpy().reshape(dAo.shape), dAo) <= 1e-8
