@@ -173,6 +173,26 @@ __global__ void __launch_bounds__(kThreads) k_spmv(MatView<TA> A, const TX *__re
 inline int64_t cell_blocks_of(int64_t nc) { return (nc + kThreads - 1) / kThreads; }
 inline int64_t long_blocks_of(int64_t nl) { return (nl + kWarps - 1) / kWarps; }
 
+// Sum of B values over a block (warp butterflies, then the warps in index
+// order: a fixed order); the result is valid in thread 0.
+template <int B>
+__device__ __forceinline__ void block_sum(double (&acc)[B]) {
+  __shared__ double part[kWarps][B];
+#pragma unroll
+  for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int r = 0; r < B; r++) part[threadIdx.x >> 5][r] = acc[r];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      double t = part[0][r];
+      for (int w = 1; w < kWarps; w++) t = t + part[w][r];
+      acc[r] = t;
+    }
+}
+
 // ----------------------------------------------------- reduction helpers
 template <int KC>
 __device__ void block_partial(double (&acc)[KC], double *__restrict__ dst) {
@@ -314,7 +334,41 @@ __global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__
 }
 
 // ------------------------------------------------------------ ILU sweeps
-// t -= sum over the ILU(1) fill slots f in fm of F_f y_(i + off2[f])
+// The cell rows of a colour are swept by B lanes per block row: lane r of a
+// group computes row r of every block-vector product (t_r -= sum_c F_rc
+// y_j,c), so that a group reads each b x b block as one contiguous span and a
+// warp keeps 32 / B rows in flight.  The sums run in the same order as a
+// whole-row product would (slots, fill slots, tail; c ascending).
+template <int B>
+struct RowLanes {
+  static constexpr int kRowsPerWarp = 32 / B;
+  int r;            // block row of this lane
+  int base;         // first lane of the group
+  unsigned mask;    // the group's lanes
+  int64_t q;        // position of the row, or -1 for an idle lane
+  __device__ __forceinline__ RowLanes(int64_t q0, int64_t q1) {
+    const int lane = threadIdx.x & 31, g = lane / B;
+    r = lane - g * B;
+    base = g * B;
+    mask = ((1u << B) - 1u) << base;
+    const int64_t w = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
+    q = q0 + w * kRowsPerWarp + g;
+    if (g >= kRowsPerWarp || q >= q1) q = -1;
+  }
+};
+
+inline int64_t row_lane_blocks_of(int64_t rows, int b) {
+  const int64_t per_block = (int64_t)kWarps * (32 / b);
+  return (rows + per_block - 1) / per_block;
+}
+
+// Blocks of a multiple of 16 bytes (b = 1, 2, 4) are swept a thread per row
+// with 128-bit loads, which measured faster at b = 4; the others (b = 3, 5),
+// whose blocks take no vector loads, by B lanes per row.
+template <int B, class T>
+constexpr bool kRowLanes = B > 1 && (B * B * sizeof(T)) % 16 != 0;
+
+// t -= sum over the ILU(1) fill slots f in fm of F_f y_(i + off2[f]) (whole rows)
 template <int B, class T>
 __device__ __forceinline__ void fill_slots_apply(const IluView<T> &F, unsigned fm, int64_t i, int64_t q,
                                                  const T *y, T (&t)[B]) {
@@ -336,138 +390,79 @@ __device__ __forceinline__ void fill_slots_apply(const IluView<T> &F, unsigned f
   }
 }
 
+// t -= the slots in sm, the fill slots in fm and the lower (lower == true) or
+// upper tail entries of row i, a thread per whole row
 template <int B, class T>
-__global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__restrict__ rhs, T *y, int64_t q0,
-                                                      int64_t q1, int64_t q2, int64_t cell_blocks) {
+__device__ __forceinline__ void whole_row_sweep(const IluView<T> &F, int64_t i, int64_t q, unsigned sm, unsigned fm,
+                                                bool tail, bool lower, const T *y, T (&t)[B]) {
   constexpr int BB = B * B;
   const int64_t np = F.g.n_rows;
-  if (blockIdx.x < cell_blocks) {
-    const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
-    if (q >= q1) return;
-    const int64_t i = F.crow[q];
-    T t[B];
-    load_blk<B>(rhs + i * B, t);
-    const unsigned lm = F.lmask[q];
 #pragma unroll
-    for (int s = 0; s < kSlots; s++) {
-      if (!((lm >> s) & 1u)) continue;
-      const int64_t j = i + F.g.off[s];
-      T yj[B];
-      load_blk<B>(y + j * B, yj);
-      T bv[BB];
-      load_block<B>(F.fell + ((int64_t)s * np + q) * BB, bv);
+  for (int s = 0; s < kSlots; s++) {
+    if (!((sm >> s) & 1u)) continue;
+    const int64_t j = i + F.g.off[s];
+    T yj[B];
+    load_blk<B>(y + j * B, yj);
+    T bv[BB];
+    load_block<B>(F.fell + ((int64_t)s * np + q) * BB, bv);
 #pragma unroll
-      for (int r = 0; r < B; r++)
+    for (int r = 0; r < B; r++)
 #pragma unroll
-        for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
-    }
-    if (F.flmask) fill_slots_apply<B>(F, F.flmask[q], i, q, y, t);
-    if (lm & kTailBit)
+      for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
+  }
+  fill_slots_apply<B>(F, fm, i, q, y, t);
+  if (tail)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
-      if (!F.ftlow[u]) continue;
       const int64_t j = F.ftcol[u];
+      if (lower ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
       const T *blk = F.ftval + u * BB;
 #pragma unroll
       for (int r = 0; r < B; r++)
 #pragma unroll
         for (int c = 0; c < B; c++) t[r] = fma(-blk[r * B + c], y[j * B + c], t[r]);
     }
-    store_blk<B>(y + i * B, t);
-  } else {
-    const int lane = threadIdx.x & 31;
-    const int64_t q = q1 + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
-    if (q >= q2) return;
-    const int64_t i = F.crow[q];
-    double acc[B] = {};
-    for (int64_t u = F.ftptr[q] + lane; u < F.ftptr[q + 1]; u += 32) {
-      if (!F.ftlow[u]) continue;
-      const int64_t j = F.ftcol[u];
-      const T *blk = F.ftval + u * BB;
-#pragma unroll
-      for (int r = 0; r < B; r++)
-#pragma unroll
-        for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(y[j * B + c]), acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
-    if (lane == 0)
-#pragma unroll
-      for (int r = 0; r < B; r++) y[i * B + r] = static_cast<T>(to_d(rhs[i * B + r]) - acc[r]);
-  }
 }
 
-// Backward sweep of one colour: x_i = U_ii^-1 (y_i - sum over upper j of
-// U_ij x_j), written over y (and z = y1 + Pi e0 + x to zout when given).
-// With rhs given (the last colour, whose rows have no upper neighbour), the
-// forward sweep of the colour is done in the same pass: t = rhs_i - sum over
-// lower j of L_ij y_j, the same operations as k_ilu_fwd, then x_i = U_ii^-1 t.
-template <int B, class T, class TZ>
-__global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_t q0, int64_t q1, int64_t q2,
-                                                      int64_t cell_blocks, const T *__restrict__ y1,
-                                                      const T *__restrict__ e0, TZ *__restrict__ zout,
-                                                      const T *__restrict__ rhs) {
+// t_r -= sum over c of F_rc y_j,c for one b x b block F (row r at p)
+template <int B, class T>
+__device__ __forceinline__ void row_update(const T *__restrict__ p, const T *y, int64_t j, T &t) {
+  T row[B], yj[B];
+  load_blk<B>(p, row);
+  load_blk<B>(y + j * B, yj);
+#pragma unroll
+  for (int c = 0; c < B; c++) t = fma(-row[c], yj[c], t);
+}
+
+// lane r of row i's group: t_r -= the slots in sm, the fill slots in fm, and
+// the tail entries that are lower (lower == true) or upper (j != i)
+template <int B, class T>
+__device__ __forceinline__ void row_sweep(const IluView<T> &F, int64_t i, int64_t q, int r, unsigned sm, unsigned fm,
+                                          bool tail, bool lower, const T *y, T &t) {
   constexpr int BB = B * B;
   const int64_t np = F.g.n_rows;
-  T t[B];
-  int64_t i, q;
-  bool active;
-  if (blockIdx.x < cell_blocks) {
-    q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
-    active = q < q1;
-    if (!active) return;
-    i = F.crow[q];
-    load_blk<B>((rhs ? rhs : y) + i * B, t);
-    const unsigned lmq = F.lmask[q];
-    const unsigned um = rhs ? lmq : F.emask[i] & ~lmq & ~(1u << kSelf);
 #pragma unroll
-    for (int s = 0; s < kSlots; s++) {
-      if (!((um >> s) & 1u)) continue;
-      const int64_t j = i + F.g.off[s];
-      T yj[B];
-      load_blk<B>(y + j * B, yj);
-      T bv[BB];
-      load_block<B>(F.fell + ((int64_t)s * np + q) * BB, bv);
+  for (int s = 0; s < kSlots; s++)
+    if ((sm >> s) & 1u) row_update<B>(F.fell + ((int64_t)s * np + q) * BB + r * B, y, i + F.g.off[s], t);
+  if (fm)
 #pragma unroll
-      for (int r = 0; r < B; r++)
-#pragma unroll
-        for (int c = 0; c < B; c++) t[r] = fma(-bv[r * B + c], yj[c], t[r]);
-    }
-    if (F.fmask) fill_slots_apply<B>(F, rhs ? F.flmask[q] : F.fmask[q] & ~F.flmask[q], i, q, y, t);
-    if (lmq & kTailBit)
+    for (int f = 0; f < kFill; f++)
+      if ((fm >> f) & 1u) row_update<B>(F.fell + ((int64_t)(kSlots + f) * np + q) * BB + r * B, y, i + F.g.off2[f], t);
+  if (tail)
     for (int64_t u = F.ftptr[q]; u < F.ftptr[q + 1]; u++) {
       const int64_t j = F.ftcol[u];
-      if (rhs ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
-      const T *blk = F.ftval + u * BB;
-#pragma unroll
-      for (int r = 0; r < B; r++)
-#pragma unroll
-        for (int c = 0; c < B; c++) t[r] = fma(-blk[r * B + c], y[j * B + c], t[r]);
+      if (lower ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
+      row_update<B>(F.ftval + u * BB + r * B, y, j, t);
     }
-  } else {
-    const int lane = threadIdx.x & 31;
-    q = q1 + (blockIdx.x - cell_blocks) * (int64_t)kWarps + (threadIdx.x >> 5);
-    if (q >= q2) return;
-    i = F.crow[q];
-    double acc[B] = {};
-    for (int64_t u = F.ftptr[q] + lane; u < F.ftptr[q + 1]; u += 32) {
-      const int64_t j = F.ftcol[u];
-      if (rhs ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
-      const T *blk = F.ftval + u * BB;
-#pragma unroll
-      for (int r = 0; r < B; r++)
-#pragma unroll
-        for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(y[j * B + c]), acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < B; r++) acc[r] = warp_sum(acc[r]);
-    if (lane != 0) return;
-    const T *src = rhs ? rhs : y;
-#pragma unroll
-    for (int r = 0; r < B; r++) t[r] = static_cast<T>(to_d(src[i * B + r]) - acc[r]);
-  }
-  // x_i = U_ii^-1 t
+}
+
+// x_i = U_ii^-1 t written over y_i, and z_i = y1_i + Pi e0_i + x_i to zout
+template <int B, class T, class TZ>
+__device__ __forceinline__ void ilu_bwd_finish(const IluView<T> &F, int64_t q, int64_t i, const T (&t)[B], T *y,
+                                               const T *__restrict__ y1, const T *__restrict__ e0,
+                                               TZ *__restrict__ zout) {
+  constexpr int BB = B * B;
   T dg[BB];
-  load_block<B>(F.fell + ((int64_t)kSelf * np + q) * BB, dg);
+  load_block<B>(F.fell + ((int64_t)kSelf * F.g.n_rows + q) * BB, dg);
   T xv[B];
 #pragma unroll
   for (int r = 0; r < B; r++) {
@@ -485,6 +480,123 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
     for (int r = 0; r < B; r++) zo[r] = static_cast<TZ>(zb[r] + xv[r]);
     store_blk<B>(zout + i * B, zo);
   }
+}
+
+template <int B, class T>
+__global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__restrict__ rhs, T *y, int64_t q0,
+                                                      int64_t q1, int64_t q2, int64_t cell_blocks) {
+  constexpr int BB = B * B;
+  if (blockIdx.x < cell_blocks) {
+    if constexpr (kRowLanes<B, T>) {
+      const RowLanes<B> L(q0, q1);
+      if (L.q < 0) return;
+      const int64_t q = L.q, i = F.crow[q];
+      T t = rhs[i * B + L.r];
+      const unsigned lm = F.lmask[q];
+      row_sweep<B>(F, i, q, L.r, lm, F.flmask ? F.flmask[q] : 0u, lm & kTailBit, true, y, t);
+      y[i * B + L.r] = t;
+    } else {
+      const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
+      if (q >= q1) return;
+      const int64_t i = F.crow[q];
+      T t[B];
+      load_blk<B>(rhs + i * B, t);
+      const unsigned lm = F.lmask[q];
+      whole_row_sweep<B>(F, i, q, lm, F.flmask ? F.flmask[q] : 0u, lm & kTailBit, true, y, t);
+      store_blk<B>(y + i * B, t);
+    }
+  } else {
+    // a long row (a well), one block per row
+    const int64_t q = q1 + (blockIdx.x - cell_blocks);
+    if (q >= q2) return;
+    const int64_t i = F.crow[q];
+    double acc[B] = {};
+    for (int64_t u = F.ftptr[q] + threadIdx.x; u < F.ftptr[q + 1]; u += kThreads) {
+      if (!F.ftlow[u]) continue;
+      const int64_t j = F.ftcol[u];
+      const T *blk = F.ftval + u * BB;
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(y[j * B + c]), acc[r]);
+    }
+    block_sum<B>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int r = 0; r < B; r++) y[i * B + r] = static_cast<T>(to_d(rhs[i * B + r]) - acc[r]);
+  }
+}
+
+// Backward sweep of one colour: x_i = U_ii^-1 (y_i - sum over upper j of
+// U_ij x_j), written over y (and z = y1 + Pi e0 + x to zout when given).
+// With rhs given (the last colour, whose rows have no upper neighbour), the
+// forward sweep of the colour is done in the same pass: t = rhs_i - sum over
+// lower j of L_ij y_j, the same operations as k_ilu_fwd, then x_i = U_ii^-1 t.
+template <int B, class T, class TZ>
+__global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_t q0, int64_t q1, int64_t q2,
+                                                      int64_t cell_blocks, const T *__restrict__ y1,
+                                                      const T *__restrict__ e0, TZ *__restrict__ zout,
+                                                      const T *__restrict__ rhs) {
+  constexpr int BB = B * B;
+  const int64_t np = F.g.n_rows;
+  if (blockIdx.x < cell_blocks && !kRowLanes<B, T>) {
+    const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (q >= q1) return;
+    const int64_t i = F.crow[q];
+    T t[B];
+    load_blk<B>((rhs ? rhs : y) + i * B, t);
+    const unsigned lmq = F.lmask[q];
+    const unsigned um = rhs ? lmq : F.emask[i] & ~lmq & ~(1u << kSelf);
+    const unsigned fm = F.fmask ? (rhs ? F.flmask[q] : F.fmask[q] & ~F.flmask[q]) : 0u;
+    whole_row_sweep<B>(F, i, q, um, fm, lmq & kTailBit, rhs != nullptr, y, t);
+    ilu_bwd_finish<B, T, TZ>(F, q, i, t, y, y1, e0, zout);
+    return;
+  }
+  if (blockIdx.x < cell_blocks) {
+    const RowLanes<B> L(q0, q1);
+    if (L.q < 0) return;   // whole groups leave together
+    const int64_t q = L.q, i = F.crow[q];
+    const int r = L.r;
+    T t = (rhs ? rhs : y)[i * B + r];
+    const unsigned lmq = F.lmask[q];
+    const unsigned um = rhs ? lmq : F.emask[i] & ~lmq & ~(1u << kSelf);
+    const unsigned fm = F.fmask ? (rhs ? F.flmask[q] : F.fmask[q] & ~F.flmask[q]) : 0u;
+    row_sweep<B>(F, i, q, r, um, fm, lmq & kTailBit, rhs != nullptr, y, t);
+    // x_r = sum_c (U_ii^-1)_rc t_c, t_c from lane c of the group
+    T dg[B];
+    load_blk<B>(F.fell + ((int64_t)kSelf * np + q) * BB + r * B, dg);
+    T x = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) x = fma(dg[c], __shfl_sync(L.mask, t, L.base + c), x);
+    y[i * B + r] = x;
+    if (zout) {
+      T zb = y1 ? y1[i * B + r] : T(0);
+      if (r == 0) zb = zb + e0[i];
+      zout[i * B + r] = static_cast<TZ>(zb + x);
+    }
+    return;
+  }
+  // a long row (a well), one block per row
+  const int64_t q = q1 + (blockIdx.x - cell_blocks);
+  if (q >= q2) return;
+  const int64_t i = F.crow[q];
+  double acc[B] = {};
+  for (int64_t u = F.ftptr[q] + threadIdx.x; u < F.ftptr[q + 1]; u += kThreads) {
+    const int64_t j = F.ftcol[u];
+    if (rhs ? !F.ftlow[u] : (F.ftlow[u] || j == i)) continue;
+    const T *blk = F.ftval + u * BB;
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) acc[r] = fma(to_d(blk[r * B + c]), to_d(y[j * B + c]), acc[r]);
+  }
+  block_sum<B>(acc);
+  if (threadIdx.x != 0) return;
+  const T *src = rhs ? rhs : y;
+  T t[B];
+#pragma unroll
+  for (int r = 0; r < B; r++) t[r] = static_cast<T>(to_d(src[i * B + r]) - acc[r]);
+  ilu_bwd_finish<B, T, TZ>(F, q, i, t, y, y1, e0, zout);
 }
 
 // --------------------------------------------------- CPR residuals on Ã
@@ -1301,19 +1413,23 @@ void launch_dscale(int b, int64_t n_rows, const double *w, const double *div, do
 template <class T>
 void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, int64_t q1, int64_t q2,
                     cudaStream_t s) {
-  const int64_t cb = cell_blocks_of(q1 - q0), lb = long_blocks_of(q2 - q1);
-  if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_ilu_fwd<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, rhs, y, q0, q1, q2, cb));
+  TRS_DISPATCH_B(b, {
+    // cell rows: a thread or B lanes per row; long rows: one block per row
+    const int64_t cb = kRowLanes<B, T> ? row_lane_blocks_of(q1 - q0, B) : cell_blocks_of(q1 - q0), lb = q2 - q1;
+    if (cb + lb == 0) return;
+    k_ilu_fwd<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, rhs, y, q0, q1, q2, cb);
+  });
   TRS_LAUNCHED();
 }
 
 template <class T, class TZ>
 void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, int64_t q2, const T *y1,
                     const T *e0, TZ *zout, const T *rhs, cudaStream_t s) {
-  const int64_t cb = cell_blocks_of(q1 - q0), lb = long_blocks_of(q2 - q1);
-  if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_ilu_bwd<B, T, TZ><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0,
-                                                                                 zout, rhs));
+  TRS_DISPATCH_B(b, {
+    const int64_t cb = kRowLanes<B, T> ? row_lane_blocks_of(q1 - q0, B) : cell_blocks_of(q1 - q0), lb = q2 - q1;
+    if (cb + lb == 0) return;
+    k_ilu_bwd<B, T, TZ><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0, zout, rhs);
+  });
   TRS_LAUNCHED();
 }
 
