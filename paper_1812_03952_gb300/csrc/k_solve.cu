@@ -25,6 +25,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <class T>
 __device__ __forceinline__ double to_d(T v) { return static_cast<double>(v); }
 
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 // b consecutive entries of a block vector (16-byte aligned for b = 2, 4:
 // the base pointers come from cudaMalloc-class allocations and block starts
 // are multiples of b entries), with 128-bit accesses where they fit.
@@ -149,6 +154,7 @@ template <int B, class TA, class TX>
 __global__ void __launch_bounds__(kThreads) k_spmv(MatView<TA> A, const TX *__restrict__ x,
                                                    double *__restrict__ y, double alpha, double beta,
                                                    int64_t cell_blocks) {
+  pdl_enter();
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
     if (i >= A.g.nc) return;
@@ -249,6 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(MatView<double> A, c
                                                             double *__restrict__ r, int64_t cell_blocks,
                                                             int64_t rows_per_block_long, double *partial,
                                                             unsigned int *counter, double *out) {
+  pdl_enter();
   // grid-stride over cell rows and long rows so that the grid stays fixed
   double acc2[1] = {0.0};
   const int64_t nc = A.g.nc, nl = A.g.n_rows - nc;
@@ -282,6 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(MatView<double> A, c
 
 __global__ void __launch_bounds__(kThreads) k_norm2(const double *__restrict__ x, int64_t n, double *partial,
                                                     unsigned int *counter, double *out) {
+  pdl_enter();
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
     acc[0] = fma(x[i], x[i], acc[0]);
@@ -311,6 +319,7 @@ template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_dscale(int64_t n, const double *__restrict__ w,
                                                      const double *__restrict__ div, double *__restrict__ vout,
                                                      const T *__restrict__ dinv, T *__restrict__ f, Seed<T> sd) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   double v[B];
@@ -485,6 +494,7 @@ __device__ __forceinline__ void ilu_bwd_finish(const IluView<T> &F, int64_t q, i
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_ilu_fwd(IluView<T> F, const T *__restrict__ rhs, T *y, int64_t q0,
                                                       int64_t q1, int64_t q2, int64_t cell_blocks) {
+  pdl_enter();
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     if constexpr (kRowLanes<B, T>) {
@@ -537,6 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_bwd(IluView<T> F, T *y, int64_
                                                       int64_t cell_blocks, const T *__restrict__ y1,
                                                       const T *__restrict__ e0, TZ *__restrict__ zout,
                                                       const T *__restrict__ rhs) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t np = F.g.n_rows;
   if (blockIdx.x < cell_blocks && !kRowLanes<B, T>) {
@@ -605,6 +616,7 @@ template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__restrict__ atp,
                                                       const T *__restrict__ f, const T *__restrict__ y,
                                                       T *__restrict__ rp, int64_t cell_blocks, int unit) {
+  pdl_enter();
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -651,6 +663,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_full(MatView<T> At, const T 
                                                          const T *__restrict__ y1, const T *__restrict__ e0,
                                                          T *__restrict__ r, int64_t cell_blocks, int unit,
                                                          Seed<T> sd) {
+  pdl_enter();
   constexpr int BB = B * B;
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -761,6 +774,7 @@ template <class T>
 __global__ void k_cheb_resid_init(ScalarOp<T> op, const T *__restrict__ r, const T *__restrict__ e,
                                   const T *__restrict__ dinv, T inv_theta, T *__restrict__ res,
                                   T *__restrict__ d) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= op.n) return;
   const T v = r[i] - scalar_rowdot(op, i, e);
@@ -772,6 +786,7 @@ __global__ void k_cheb_resid_init(ScalarOp<T> op, const T *__restrict__ r, const
 template <class T>
 __global__ void k_cheb_step(ScalarOp<T> op, const T *res_in, T *res_out, const T *__restrict__ d,
                             const T *__restrict__ dinv, T c1, T c2, T *__restrict__ dn, T *e, int last) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= op.n) return;
   const T rv = res_in[i] - scalar_rowdot(op, i, d);
@@ -795,6 +810,7 @@ template <class T>
 __global__ void k_cheb_first(ScalarOp<T> op, const T *__restrict__ r, const T *__restrict__ dinv, T inv_theta,
                              T c1, T c2, T *__restrict__ res_out, T *__restrict__ d_out, T *__restrict__ dn,
                              T *__restrict__ e, int last) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= op.n) return;
   auto dval = [&](int64_t j) { return (dinv[j] * r[j]) * inv_theta; };
@@ -822,6 +838,7 @@ template <class T>
 __global__ void k_restrict_resid(ScalarOp<T> op, int64_t nc, const int64_t *__restrict__ mptr,
                                  const int32_t *__restrict__ midx, const T *__restrict__ r,
                                  const T *__restrict__ e, T *__restrict__ rc) {
+  pdl_enter();
   const int64_t I = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / kGroup;
   if (I >= nc) return;  // the whole group leaves together
   const int k = threadIdx.x & (kGroup - 1);
@@ -846,6 +863,7 @@ __global__ void k_restrict_resid(ScalarOp<T> op, int64_t nc, const int64_t *__re
 template <class T>
 __global__ void k_prolong(int64_t n, const int32_t *__restrict__ agg, const T *__restrict__ ec,
                           T *__restrict__ e) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   const int32_t a = agg[i];
@@ -855,6 +873,7 @@ __global__ void k_prolong(int64_t n, const int32_t *__restrict__ agg, const T *_
 template <class T>
 __global__ void k_dense_gemv(int64_t n, const double *__restrict__ Minv, const T *__restrict__ r,
                              T *__restrict__ e) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int64_t i = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -913,6 +932,7 @@ __device__ void coarse_cheb(const CoarseLevel<T> &L, int deg, bool zero_init) {
 
 template <class T>
 __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseHierarchy<T> h) {
+  pdl_enter();
   const int tid = threadIdx.x, nt = blockDim.x;
   const int last = h.nlev - 1;
   for (int l = h.l0; l < last; l++) {
@@ -954,6 +974,7 @@ template <int KC>
 __global__ void __launch_bounds__(kThreads) k_multidot(const double *__restrict__ V, int64_t N, int K,
                                                        const double *__restrict__ w, double *partial,
                                                        unsigned int *counter, double *out) {
+  pdl_enter();
   // out[k] = <V_k, w> for k < K, out[K] = <w, w>
   const int KT = K + 1;
   for (int k0 = 0; k0 < KT; k0 += KC) {
@@ -977,6 +998,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update(const double *__restric
                                                          const double *__restrict__ h, double *__restrict__ w,
                                                          int want_norm, double *partial, unsigned int *counter,
                                                          double *out) {
+  pdl_enter();
   __shared__ double sh[kMaxRestart + 1];
   for (int k = threadIdx.x; k < K; k += kThreads) sh[k] = h[k];
   __syncthreads();
@@ -1039,6 +1061,7 @@ template <int KM>
 __global__ void __launch_bounds__(kThreads) k_cgs_dots(const double *__restrict__ V, int64_t N, int K,
                                                        const double *__restrict__ w, double *partial,
                                                        unsigned int *counter, double *out) {
+  pdl_enter();
   double acc[KM] = {};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
     const double wi = w[i];
@@ -1057,6 +1080,7 @@ template <int KM>
 __global__ void __launch_bounds__(kThreads) k_cgs_update_dots(const double *__restrict__ V, int64_t N, int K,
                                                               const double *__restrict__ h, double *__restrict__ w,
                                                               double *partial, unsigned int *counter, double *out) {
+  pdl_enter();
   __shared__ double sh[KM];
   for (int k = threadIdx.x; k < K; k += kThreads) sh[k] = h[k];
   __syncthreads();
@@ -1080,6 +1104,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_dots(const double *__re
 __global__ void k_givens(int j, int m, double *H, const double *h1, const double *h2, const double *hn2,
                          const double *wn2, double *cs, double *sn, double *g, double *hnorm,
                          double *status, double inv_bnorm) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int k = 0; k <= j; k++) H[k * m + j] = h1[k] + h2[k];
   const double hn = sqrt(hn2[0]);
@@ -1103,6 +1128,7 @@ __global__ void k_givens(int j, int m, double *H, const double *h1, const double
 }
 
 __global__ void k_lsq(int jdone, int m, const double *H, const double *g, double *y) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = jdone - 1; i >= 0; i--) {
     double s = g[i];
@@ -1114,6 +1140,7 @@ __global__ void k_lsq(int jdone, int m, const double *H, const double *g, double
 template <class TZ>
 __global__ void __launch_bounds__(kThreads) k_xupdate(const TZ *__restrict__ Z, int64_t N, int K,
                                                       const double *__restrict__ y, double *__restrict__ x) {
+  pdl_enter();
   __shared__ double sy[kMaxRestart];
   for (int k = threadIdx.x; k < K; k += kThreads) sy[k] = y[k];
   __syncthreads();
@@ -1126,6 +1153,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(const TZ *__restrict__ Z, 
 
 template <class TS, class TD>
 __global__ void k_cast(const TS *__restrict__ a, TD *__restrict__ b, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
     b[i] = static_cast<TD>(a[i]);
 }
@@ -1135,6 +1163,7 @@ __global__ void k_cast(const TS *__restrict__ a, TD *__restrict__ b, int64_t n) 
 template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_cpr_combine(int64_t n, const T *__restrict__ y1,
                                                           const T *__restrict__ e0, double *__restrict__ z) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   T v[B];
@@ -1148,6 +1177,7 @@ __global__ void __launch_bounds__(kThreads) k_cpr_combine(int64_t n, const T *__
 // rp = Pi_r f, the pressure entries (the first step of CPR-PF)
 template <class T>
 __global__ void k_pressure_of(int64_t n, int b, const T *__restrict__ f, T *__restrict__ rp) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i < n) rp[i] = f[i * b];
 }
@@ -1187,6 +1217,7 @@ __device__ __forceinline__ bool last_block_sums(const double *partial, unsigned 
 
 // (Re)start from the true residual r (r^ = r): rho = <r^, r> = ||r||^2.
 __global__ void k_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double rtol) {
+  pdl_enter();
   sc->rho = rr[0];
   sc->rho_old = 1.0;
   sc->alpha = 1.0;
@@ -1205,6 +1236,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_dir(int64_t n, const double *
                                                        const BicgScalars *__restrict__ sc, int first,
                                                        const T *__restrict__ dinv, T *__restrict__ f,
                                                        Seed<T> sd) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   double rv[B], pv[B];
@@ -1244,6 +1276,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_spmv(MatView<double> A, const
                                                         double *__restrict__ y, const double *__restrict__ w,
                                                         int64_t cell_blocks, double *part, unsigned int *counter,
                                                         BicgScalars *sc) {
+  pdl_enter();
   double acc2[ND] = {};
   if (blockIdx.x < cell_blocks) {
     const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -1329,6 +1362,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_spmv(MatView<double> A, const
 __global__ void __launch_bounds__(kThreads) k_bicg_s(int64_t N, const double *__restrict__ r,
                                                      const double *__restrict__ v, double *__restrict__ s,
                                                      double *partial, unsigned int *counter, BicgScalars *sc) {
+  pdl_enter();
   const double alpha = sc->alpha;
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
@@ -1352,6 +1386,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(int64_t N, const double *_
                                                       const double *__restrict__ t, const double *__restrict__ rh,
                                                       double *__restrict__ x, double *__restrict__ r,
                                                       double *partial, unsigned int *counter, BicgScalars *sc) {
+  pdl_enter();
   const double alpha = sc->alpha, omega = sc->half != 0.0 ? 0.0 : sc->omega;
   double acc[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
@@ -1373,6 +1408,28 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(int64_t N, const double *_
 
 inline unsigned grid_of(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// Programmatic dependent launch (sm_90 and later): every kernel of this unit
+// is launched with programmatic stream serialisation, so that the next kernel
+// in the stream is scheduled while this one drains instead of after it; each
+// kernel waits (griddepcontrol.wait: the previous grid complete and its
+// memory visible) before it touches memory, and lets its successor launch
+// once all of its own blocks run.  Stream order is kept: nothing is read
+// before the producer has finished.
+template <class... KArgs, class... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TRS_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(std::forward<Args>(args))...));
+}
+
 }  // namespace
 
 // ================================================================ launchers
@@ -1381,7 +1438,7 @@ void launch_spmv(int b, const MatView<TA> &A, const TX *x, double *y, double alp
                  cudaStream_t s) {
   const int64_t cb = cell_blocks_of(A.g.nc), lb = long_blocks_of(A.g.n_rows - A.g.nc);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_spmv<B, TA, TX><<<(unsigned)(cb + lb), kThreads, 0, s>>>(A, x, y, alpha, beta, cb));
+  TRS_DISPATCH_B(b, launch_pdl(k_spmv<B, TA, TX>, (unsigned)(cb + lb), kThreads, 0, s, A, x, y, alpha, beta, cb));
   TRS_LAUNCHED();
 }
 template void launch_spmv<double, double>(int, const MatView<double> &, const double *, double *, double,
@@ -1391,13 +1448,13 @@ template void launch_spmv<double, float>(int, const MatView<double> &, const flo
 
 void launch_true_residual(int b, const MatView<double> &A, const double *x, const double *rhs, double *r,
                           const RedScratch &red, double *out_norm2, cudaStream_t s) {
-  TRS_DISPATCH_B(b, k_true_residual<B><<<red.grid, kThreads, 0, s>>>(A, x, rhs, r, 0, 0, red.partial,
+  TRS_DISPATCH_B(b, launch_pdl(k_true_residual<B>, red.grid, kThreads, 0, s, A, x, rhs, r, 0, 0, red.partial,
                                                                       red.counter, out_norm2));
   TRS_LAUNCHED();
 }
 
 void launch_norm2(const double *x, int64_t n, const RedScratch &red, double *out, cudaStream_t s) {
-  k_norm2<<<red.grid, kThreads, 0, s>>>(x, n, red.partial, red.counter, out);
+  launch_pdl(k_norm2, red.grid, kThreads, 0, s, x, n, red.partial, red.counter, out);
   TRS_LAUNCHED();
 }
 
@@ -1406,7 +1463,7 @@ void launch_dscale(int b, int64_t n_rows, const double *w, const double *div, do
                    const int32_t *colour, T *y0, cudaStream_t s) {
   if (!n_rows) return;
   const Seed<T> sd{colour, y0};
-  TRS_DISPATCH_B(b, k_dscale<B, T><<<grid_of(n_rows), kThreads, 0, s>>>(n_rows, w, div, vout, dinv, f, sd));
+  TRS_DISPATCH_B(b, launch_pdl(k_dscale<B, T>, grid_of(n_rows), kThreads, 0, s, n_rows, w, div, vout, dinv, f, sd));
   TRS_LAUNCHED();
 }
 
@@ -1417,7 +1474,7 @@ void launch_ilu_fwd(int b, const IluView<T> &F, const T *rhs, T *y, int64_t q0, 
     // cell rows: a thread or B lanes per row; long rows: one block per row
     const int64_t cb = kRowLanes<B, T> ? row_lane_blocks_of(q1 - q0, B) : cell_blocks_of(q1 - q0), lb = q2 - q1;
     if (cb + lb == 0) return;
-    k_ilu_fwd<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, rhs, y, q0, q1, q2, cb);
+    launch_pdl(k_ilu_fwd<B, T>, (unsigned)(cb + lb), kThreads, 0, s, F, rhs, y, q0, q1, q2, cb);
   });
   TRS_LAUNCHED();
 }
@@ -1428,7 +1485,7 @@ void launch_ilu_bwd(int b, const IluView<T> &F, T *y, int64_t q0, int64_t q1, in
   TRS_DISPATCH_B(b, {
     const int64_t cb = kRowLanes<B, T> ? row_lane_blocks_of(q1 - q0, B) : cell_blocks_of(q1 - q0), lb = q2 - q1;
     if (cb + lb == 0) return;
-    k_ilu_bwd<B, T, TZ><<<(unsigned)(cb + lb), kThreads, 0, s>>>(F, y, q0, q1, q2, cb, y1, e0, zout, rhs);
+    launch_pdl(k_ilu_bwd<B, T, TZ>, (unsigned)(cb + lb), kThreads, 0, s, F, y, q0, q1, q2, cb, y1, e0, zout, rhs);
   });
   TRS_LAUNCHED();
 }
@@ -1438,7 +1495,7 @@ void launch_resid_p(int b, const MatView<T> &At, const T *atp, const T *f, const
                     cudaStream_t s) {
   const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_resid_p<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, atp, f, y, rp, cb, unit));
+  TRS_DISPATCH_B(b, launch_pdl(k_resid_p<B, T>, (unsigned)(cb + lb), kThreads, 0, s, At, atp, f, y, rp, cb, unit));
   TRS_LAUNCHED();
 }
 
@@ -1448,21 +1505,21 @@ void launch_resid_full(int b, const MatView<T> &At, const T *f, const T *y1, con
   const int64_t cb = cell_blocks_of(At.g.nc), lb = long_blocks_of(At.g.n_rows - At.g.nc);
   if (cb + lb == 0) return;
   const Seed<T> sd{colour, x0};
-  TRS_DISPATCH_B(b, k_resid_full<B, T><<<(unsigned)(cb + lb), kThreads, 0, s>>>(At, f, y1, e0, r, cb, unit, sd));
+  TRS_DISPATCH_B(b, launch_pdl(k_resid_full<B, T>, (unsigned)(cb + lb), kThreads, 0, s, At, f, y1, e0, r, cb, unit, sd));
   TRS_LAUNCHED();
 }
 
 template <class T>
 void launch_cpr_combine(int b, int64_t n, const T *y1, const T *e0, double *z, cudaStream_t s) {
   if (!n) return;
-  TRS_DISPATCH_B(b, k_cpr_combine<B, T><<<grid_of(n), kThreads, 0, s>>>(n, y1, e0, z));
+  TRS_DISPATCH_B(b, launch_pdl(k_cpr_combine<B, T>, grid_of(n), kThreads, 0, s, n, y1, e0, z));
   TRS_LAUNCHED();
 }
 
 template <class T>
 void launch_pressure_of(int b, int64_t n, const T *f, T *rp, cudaStream_t s) {
   if (!n) return;
-  k_pressure_of<T><<<grid_of(n), kThreads, 0, s>>>(n, b, f, rp);
+  launch_pdl(k_pressure_of<T>, grid_of(n), kThreads, 0, s, n, b, f, rp);
   TRS_LAUNCHED();
 }
 
@@ -1470,14 +1527,14 @@ template <class T>
 void launch_cheb_resid_init(const ScalarOp<T> &op, const T *r, const T *e, const T *dinv, double inv_theta,
                             T *res, T *d, cudaStream_t s) {
   if (!op.n) return;
-  k_cheb_resid_init<T><<<grid_of(op.n), kThreads, 0, s>>>(op, r, e, dinv, static_cast<T>(inv_theta), res, d);
+  launch_pdl(k_cheb_resid_init<T>, grid_of(op.n), kThreads, 0, s, op, r, e, dinv, static_cast<T>(inv_theta), res, d);
   TRS_LAUNCHED();
 }
 template <class T>
 void launch_cheb_step(const ScalarOp<T> &op, const T *res_in, T *res_out, const T *d, const T *dinv, double c1,
                       double c2, T *dn, T *e, int last, cudaStream_t s) {
   if (!op.n) return;
-  k_cheb_step<T><<<grid_of(op.n), kThreads, 0, s>>>(op, res_in, res_out, d, dinv, static_cast<T>(c1),
+  launch_pdl(k_cheb_step<T>, grid_of(op.n), kThreads, 0, s, op, res_in, res_out, d, dinv, static_cast<T>(c1),
                                                     static_cast<T>(c2), dn, e, last);
   TRS_LAUNCHED();
 }
@@ -1485,7 +1542,7 @@ template <class T>
 void launch_cheb_first(const ScalarOp<T> &op, const T *r, const T *dinv, double inv_theta, double c1, double c2,
                        T *res_out, T *d_out, T *dn, T *e, int last, cudaStream_t s) {
   if (!op.n) return;
-  k_cheb_first<T><<<grid_of(op.n), kThreads, 0, s>>>(op, r, dinv, static_cast<T>(inv_theta), static_cast<T>(c1),
+  launch_pdl(k_cheb_first<T>, grid_of(op.n), kThreads, 0, s, op, r, dinv, static_cast<T>(inv_theta), static_cast<T>(c1),
                                                      static_cast<T>(c2), res_out, d_out, dn, e, last);
   TRS_LAUNCHED();
 }
@@ -1493,59 +1550,59 @@ template <class T>
 void launch_restrict_resid(const ScalarOp<T> &op, int64_t nc, const int64_t *mptr, const int32_t *midx, const T *r,
                            const T *e, T *rc, cudaStream_t s) {
   if (!nc) return;
-  k_restrict_resid<T><<<grid_of(nc * kGroup), kThreads, 0, s>>>(op, nc, mptr, midx, r, e, rc);
+  launch_pdl(k_restrict_resid<T>, grid_of(nc * kGroup), kThreads, 0, s, op, nc, mptr, midx, r, e, rc);
   TRS_LAUNCHED();
 }
 template <class T>
 void launch_prolong(int64_t n, const int32_t *agg, const T *ec, T *e, cudaStream_t s) {
   if (!n) return;
-  k_prolong<T><<<grid_of(n), kThreads, 0, s>>>(n, agg, ec, e);
+  launch_pdl(k_prolong<T>, grid_of(n), kThreads, 0, s, n, agg, ec, e);
   TRS_LAUNCHED();
 }
 template <class T>
 void launch_dense_gemv(int64_t n, const double *Minv, const T *r, T *e, cudaStream_t s) {
   if (!n) return;
-  k_dense_gemv<T><<<(unsigned)((n + kWarps - 1) / kWarps), kThreads, 0, s>>>(n, Minv, r, e);
+  launch_pdl(k_dense_gemv<T>, (unsigned)((n + kWarps - 1) / kWarps), kThreads, 0, s, n, Minv, r, e);
   TRS_LAUNCHED();
 }
 
 void launch_multidot(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
-  k_multidot<16><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
+  launch_pdl(k_multidot<16>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
   TRS_LAUNCHED();
 }
 void launch_cgs_update(const double *V, int64_t N, int K, const double *h, double *w, int want_norm,
                        const RedScratch &red, double *out, cudaStream_t s) {
-  k_cgs_update<<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, want_norm, red.partial, red.counter, out);
+  launch_pdl(k_cgs_update, red.grid, kThreads, 0, s, V, N, K, h, w, want_norm, red.partial, red.counter, out);
   TRS_LAUNCHED();
 }
 void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
-  if (K + 1 <= 8) k_cgs_dots<8><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
-  else if (K + 1 <= 16) k_cgs_dots<16><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
-  else if (K + 1 <= 32) k_cgs_dots<32><<<red.grid, kThreads, 0, s>>>(V, N, K, w, red.partial, red.counter, out);
+  if (K + 1 <= 8) launch_pdl(k_cgs_dots<8>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
+  else if (K + 1 <= 16) launch_pdl(k_cgs_dots<16>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
+  else if (K + 1 <= 32) launch_pdl(k_cgs_dots<32>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
   else throw Error(TRS_ERR_UNSUPPORTED, "fused CGS2 supports at most 31 basis vectors");
   TRS_LAUNCHED();
 }
 void launch_cgs_update_dots(const double *V, int64_t N, int K, const double *h, double *w, const RedScratch &red,
                             double *out, cudaStream_t s) {
   if (K <= 8)
-    k_cgs_update_dots<8><<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, red.partial, red.counter, out);
+    launch_pdl(k_cgs_update_dots<8>, red.grid, kThreads, 0, s, V, N, K, h, w, red.partial, red.counter, out);
   else if (K <= 16)
-    k_cgs_update_dots<16><<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, red.partial, red.counter, out);
+    launch_pdl(k_cgs_update_dots<16>, red.grid, kThreads, 0, s, V, N, K, h, w, red.partial, red.counter, out);
   else if (K <= 32)
-    k_cgs_update_dots<32><<<red.grid, kThreads, 0, s>>>(V, N, K, h, w, red.partial, red.counter, out);
+    launch_pdl(k_cgs_update_dots<32>, red.grid, kThreads, 0, s, V, N, K, h, w, red.partial, red.counter, out);
   else throw Error(TRS_ERR_UNSUPPORTED, "fused CGS2 supports at most 31 basis vectors");
   TRS_LAUNCHED();
 }
 void launch_givens(int j, int m, double *H, const double *h1, const double *h2, const double *hn2,
                    const double *wn2, double *cs, double *sn, double *g, double *hnorm_out, double *status,
                    double inv_bnorm, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(j, m, H, h1, h2, hn2, wn2, cs, sn, g, hnorm_out, status, inv_bnorm);
+  launch_pdl(k_givens, 1, 32, 0, s, j, m, H, h1, h2, hn2, wn2, cs, sn, g, hnorm_out, status, inv_bnorm);
   TRS_LAUNCHED();
 }
 void launch_lsq(int jdone, int m, const double *H, const double *g, double *y, cudaStream_t s) {
-  k_lsq<<<1, 32, 0, s>>>(jdone, m, H, g, y);
+  launch_pdl(k_lsq, 1, 32, 0, s, jdone, m, H, g, y);
   TRS_LAUNCHED();
 }
 template <class TZ>
@@ -1553,12 +1610,12 @@ void launch_xupdate(const TZ *Z, int64_t N, int K, const double *y, double *x, c
   if (!N || !K) return;
   unsigned grid = grid_of(N);
   if (grid > 152u * 16u) grid = 152u * 16u;
-  k_xupdate<TZ><<<grid, kThreads, 0, s>>>(Z, N, K, y, x);
+  launch_pdl(k_xupdate<TZ>, grid, kThreads, 0, s, Z, N, K, y, x);
   TRS_LAUNCHED();
 }
 template <class T>
 void launch_vcycle_coarse(const CoarseHierarchy<T> &h, cudaStream_t s) {
-  k_vcycle_coarse<T><<<1, 1024, 0, s>>>(h);
+  launch_pdl(k_vcycle_coarse<T>, 1, 1024, 0, s, h);
   TRS_LAUNCHED();
 }
 template void launch_vcycle_coarse<float>(const CoarseHierarchy<float> &, cudaStream_t);
@@ -1569,12 +1626,12 @@ void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {
   if (!n) return;
   unsigned grid = grid_of(n);
   if (grid > 152u * 16u) grid = 152u * 16u;
-  k_cast<TS, TD><<<grid, kThreads, 0, s>>>(src, dst, n);
+  launch_pdl(k_cast<TS, TD>, grid, kThreads, 0, s, src, dst, n);
   TRS_LAUNCHED();
 }
 
 void launch_bicg_start(BicgScalars *sc, const double *rr, double bnorm, double rtol, cudaStream_t s) {
-  k_bicg_start<<<1, 1, 0, s>>>(sc, rr, bnorm, rtol);
+  launch_pdl(k_bicg_start, 1, 1, 0, s, sc, rr, bnorm, rtol);
   TRS_LAUNCHED();
 }
 
@@ -1583,7 +1640,7 @@ void launch_bicg_dir(int b, int64_t n, const double *r, const double *v, double 
                      int first, const T *dinv, T *f, const int32_t *colour, T *y0, cudaStream_t s) {
   if (!n) return;
   const Seed<T> sd{colour, y0};
-  TRS_DISPATCH_B(b, k_bicg_dir<B, T><<<grid_of(n), kThreads, 0, s>>>(n, r, v, p, sc, first, dinv, f, sd));
+  TRS_DISPATCH_B(b, launch_pdl(k_bicg_dir<B, T>, grid_of(n), kThreads, 0, s, n, r, v, p, sc, first, dinv, f, sd));
   TRS_LAUNCHED();
 }
 template void launch_bicg_dir<double>(int, int64_t, const double *, const double *, double *, const BicgScalars *,
@@ -1597,23 +1654,23 @@ void launch_bicg_spmv(int b, const MatView<double> &A, const double *x, double *
                       double *part, unsigned int *counter, BicgScalars *sc, cudaStream_t s) {
   const int64_t cb = cell_blocks_of(A.g.nc), nb = bicg_spmv_blocks(A.g);
   if (nd == 1) {
-    TRS_DISPATCH_B(b, k_bicg_spmv<B, 1><<<(unsigned)nb, kThreads, 0, s>>>(A, x, y, w, cb, part, counter, sc));
+    TRS_DISPATCH_B(b, launch_pdl(k_bicg_spmv<B, 1>, (unsigned)nb, kThreads, 0, s, A, x, y, w, cb, part, counter, sc));
   } else {
-    TRS_DISPATCH_B(b, k_bicg_spmv<B, 2><<<(unsigned)nb, kThreads, 0, s>>>(A, x, y, w, cb, part, counter, sc));
+    TRS_DISPATCH_B(b, launch_pdl(k_bicg_spmv<B, 2>, (unsigned)nb, kThreads, 0, s, A, x, y, w, cb, part, counter, sc));
   }
   TRS_LAUNCHED();
 }
 
 void launch_bicg_s(int64_t N, const double *r, const double *v, double *sv, const RedScratch &red,
                    BicgScalars *sc, cudaStream_t s) {
-  k_bicg_s<<<red.grid, kThreads, 0, s>>>(N, r, v, sv, red.partial, red.counter, sc);
+  launch_pdl(k_bicg_s, red.grid, kThreads, 0, s, N, r, v, sv, red.partial, red.counter, sc);
   TRS_LAUNCHED();
 }
 
 void launch_bicg_xr(int64_t N, const double *ph, const double *sh, const double *sv, const double *t,
                     const double *rh, double *x, double *r, const RedScratch &red, BicgScalars *sc,
                     cudaStream_t s) {
-  k_bicg_xr<<<red.grid, kThreads, 0, s>>>(N, ph, sh, sv, t, rh, x, r, red.partial, red.counter, sc);
+  launch_pdl(k_bicg_xr, red.grid, kThreads, 0, s, N, ph, sh, sv, t, rh, x, r, red.partial, red.counter, sc);
   TRS_LAUNCHED();
 }
 
