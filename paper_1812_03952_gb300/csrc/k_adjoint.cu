@@ -26,6 +26,7 @@ template <int B>
 __global__ void __launch_bounds__(kThreads) k_spmv_t(MatView<double> A, const int64_t *tc_ptr, const int64_t *tc_src,
                                                      const int32_t *tc_row, const double *x, double *y, double alpha,
                                                      double beta, int64_t cell_blocks) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t nc = A.g.nc;
   if (blockIdx.x < cell_blocks) {
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_t(MatView<double> A, const in
 __global__ void k_transpose_values(int b, int64_t nnzb, const int64_t *src_canon, const int64_t *map_src,
                                    const double *ell_src, const double *tval_src, int64_t nc,
                                    const int64_t *map_dst, double *ell_dst, double *tval_dst) {
+  pdl_enter();
   const int bb = b * b;
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (idx >= nnzb * bb) return;
@@ -99,6 +101,7 @@ __global__ void k_transpose_values(int b, int64_t nnzb, const int64_t *src_canon
 template <int B>
 __global__ void k_outer_product(int64_t nnzb, const int32_t *urow, const int32_t *ucol, const double *lambda,
                                 const double *x, double *dA) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (idx >= nnzb * BB) return;
@@ -122,6 +125,7 @@ template <int B>
 __global__ void k_chain_theta(Geom g, const uint8_t *emask, const double *perm, int is_log, double kvkh,
                               double c_t, const double *M, const double *lambda, const double *x,
                               double *dtheta) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.nc) return;
@@ -163,7 +167,7 @@ void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double a
   const int64_t cb = (A.g.nc + kThreads - 1) / kThreads;
   const int64_t lb = (A.g.n_rows - A.g.nc + kWarps - 1) / kWarps;
   if (cb + lb == 0) return;
-  TRS_DISPATCH_B(b, k_spmv_t<B><<<(unsigned)(cb + lb), kThreads, 0, s>>>(A.view(), A.tc_ptr.p, A.tc_src.p,
+  TRS_DISPATCH_B(b, launch_pdl(k_spmv_t<B>, (unsigned)(cb + lb), kThreads, 0, s, A.view(), A.tc_ptr.p, A.tc_src.p,
                                                                          A.tc_row.p, x, y, alpha, beta, cb));
   TRS_LAUNCHED();
 }
@@ -172,7 +176,7 @@ void launch_transpose_values(int bb, int64_t nnzb, const int64_t *src_canon, con
                              const double *ell_src, const double *tval_src, int64_t nc, const int64_t *map_dst,
                              double *ell_dst, double *tval_dst, int b, cudaStream_t s) {
   if (!nnzb) return;
-  k_transpose_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(b, nnzb, src_canon, map_src, ell_src, tval_src, nc,
+  launch_pdl(k_transpose_values, grid_of(nnzb * bb), kThreads, 0, s, b, nnzb, src_canon, map_src, ell_src, tval_src, nc,
                                                              map_dst, ell_dst, tval_dst);
   TRS_LAUNCHED();
 }
@@ -180,7 +184,7 @@ void launch_transpose_values(int bb, int64_t nnzb, const int64_t *src_canon, con
 void launch_outer_product(int b, const trs_bsr &A, const double *lambda, const double *x, double *dA,
                           cudaStream_t s) {
   if (!A.nnzb) return;
-  TRS_DISPATCH_B(b, k_outer_product<B><<<grid_of(A.nnzb * B * B), kThreads, 0, s>>>(A.nnzb, A.urow.p, A.ucol.p,
+  TRS_DISPATCH_B(b, launch_pdl(k_outer_product<B>, grid_of(A.nnzb * B * B), kThreads, 0, s, A.nnzb, A.urow.p, A.ucol.p,
                                                                                     lambda, x, dA));
   TRS_LAUNCHED();
 }
@@ -188,7 +192,7 @@ void launch_outer_product(int b, const trs_bsr &A, const double *lambda, const d
 void launch_chain_theta(int b, const trs_bsr &A, const double *perm, int perm_is_log, double kvkh, double c_t,
                         const double *M, const double *lambda, const double *x, double *dtheta, cudaStream_t s) {
   if (!A.g.nc) return;
-  TRS_DISPATCH_B(b, k_chain_theta<B><<<grid_of(A.g.nc), kThreads, 0, s>>>(A.g, A.emask.p, perm, perm_is_log,
+  TRS_DISPATCH_B(b, launch_pdl(k_chain_theta<B>, grid_of(A.g.nc), kThreads, 0, s, A.g, A.emask.p, perm, perm_is_log,
                                                                           kvkh, c_t, M, lambda, x, dtheta));
   TRS_LAUNCHED();
 }

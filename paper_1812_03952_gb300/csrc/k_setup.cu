@@ -40,6 +40,7 @@ constexpr int kScanItems = 16;
 constexpr int kScanChunk = kThreads * kScanItems;
 
 __global__ void k_scan_reduce(const int64_t *in, int64_t n, int64_t *bsum) {
+  pdl_enter();
   __shared__ int64_t sm[kWarps];
   int64_t base = (int64_t)blockIdx.x * kScanChunk, s = 0;
   for (int k = threadIdx.x; k < kScanChunk; k += kThreads) {
@@ -57,6 +58,7 @@ __global__ void k_scan_reduce(const int64_t *in, int64_t n, int64_t *bsum) {
 }
 
 __global__ void k_scan_bsums(int64_t *bsum, int64_t nb, int64_t *total) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   int64_t run = 0;
   for (int64_t b = 0; b < nb; b++) {
@@ -68,6 +70,7 @@ __global__ void k_scan_bsums(int64_t *bsum, int64_t nb, int64_t *total) {
 }
 
 __global__ void k_scan_apply(const int64_t *in, int64_t *out, int64_t n, const int64_t *bsum) {
+  pdl_enter();
   __shared__ int64_t wsum[kWarps];
   const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
   int64_t v[kScanItems];
@@ -101,6 +104,7 @@ __global__ void k_scan_apply(const int64_t *in, int64_t *out, int64_t n, const i
 // ------------------------------------------------------- value layout
 __global__ void k_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval, int64_t nc,
                                  double *ell, double *tval) {
+  pdl_enter();
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (idx >= nnzb * bb) return;
   const int64_t p = idx / bb, e = idx % bb, loc = map[p];
@@ -114,6 +118,7 @@ __global__ void k_scatter_values(int64_t nnzb, int bb, const int64_t *map, const
 
 __global__ void k_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell,
                                 const double *tval, int64_t nc, int aos, double *uval) {
+  pdl_enter();
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (idx >= nnzb * bb) return;
   const int64_t p = idx / bb, e = idx % bb, loc = map[p];
@@ -200,6 +205,7 @@ __global__ void k_assemble_cells(Geom g, const uint8_t *emask, double *ell, doub
                                  int is_log, double kvkh, double c_t, const double *M, const double *acc,
                                  const int64_t *cperf_ptr, const int64_t *cperf_idx, const int64_t *perf_cw,
                                  const double *wi, const double *lam) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (c >= g.nc) return;
@@ -240,6 +246,7 @@ template <int B>
 __global__ void k_assemble_wells(int nw, double *tval, const int64_t *wperf_ptr, const int64_t *wperf_idx,
                                  const int64_t *perf_wc, const int64_t *wdiag, const double *wi,
                                  const double *lam) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int w = blockIdx.x * kThreads + threadIdx.x;
   if (w >= nw) return;
@@ -261,6 +268,7 @@ __global__ void k_assemble_wells(int nw, double *tval, const int64_t *wperf_ptr,
 
 template <int B>
 __global__ void k_scale_diag(Geom g, double *ell, double *tval, const int64_t *tdiag, const double *sc) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.n_rows) return;
@@ -413,6 +421,7 @@ __device__ __forceinline__ bool unit_diagonal(int mode) { return mode == TRS_DEC
 template <int B>
 __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, double *at_ell, double *at_p,
                            double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t nc = A.g.nc, n = A.g.n_rows;
@@ -478,6 +487,7 @@ __global__ void k_decouple(MatView<double> A, const int64_t *tdiag, int mode, do
 template <int B>
 __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mode, float *at_ell, float *at_p,
                                  float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t nc = A.g.nc, n = A.g.n_rows;
@@ -560,6 +570,7 @@ __global__ void k_decouple_mixed(MatView<double> A, const int64_t *tdiag, int mo
 
 // ------------------------------------------------------- pressure CSR
 __global__ void k_ap_rowlen(Geom g, const uint8_t *emask, const int64_t *tptr, int64_t *len) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.n_rows) return;
   int64_t l = tptr[i + 1] - tptr[i];
@@ -571,6 +582,7 @@ __global__ void k_ap_rowlen(Geom g, const uint8_t *emask, const int64_t *tptr, i
 __global__ void k_ap_fill(Geom g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
                           const double *ap_ell, const double *ap_tval, const int64_t *rp, int32_t *col,
                           double *val) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.n_rows) return;
   int64_t q = rp[i], t = tptr[i];
@@ -602,6 +614,7 @@ __device__ __forceinline__ int64_t bsearch_col(const int64_t *rp, const int32_t 
 
 __global__ void k_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int64_t *dpos,
                            double *dval) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   const int64_t d = bsearch_col(rp, col, i, i);
@@ -617,6 +630,7 @@ constexpr int kStrengthLanes = 8;
 
 __global__ void k_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                            const double *dval, double theta, uint8_t *sflag, int32_t *sdeg) {
+  pdl_enter();
   const int64_t gid = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   const int64_t i = gid / kStrengthLanes;
   const int sub = (int)(gid % kStrengthLanes);
@@ -648,6 +662,7 @@ __global__ void k_strength(int64_t n, const int64_t *rp, const int32_t *col, con
 enum : int8_t { kOut = 0, kUndecided = 1, kIn = 2 };
 
 __global__ void k_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   state[i] = sdeg[i] > 0 ? kUndecided : kOut;
@@ -666,6 +681,7 @@ __device__ __forceinline__ uint64_t mis2_word(int8_t state, int64_t i, uint32_t 
 // gathers are in flight together (the maximum does not depend on order).
 __global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
                              const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   uint64_t best = in_w ? in_w[i] : mis2_word(state[i], i, seed);
@@ -689,6 +705,7 @@ __global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, c
 
 __global__ void k_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state,
                               unsigned long long *undecided) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   const int8_t s = state[i];
@@ -704,6 +721,7 @@ __global__ void k_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int
 }
 
 __global__ void k_in_flag(int64_t n, const int8_t *state, int64_t *flag) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   flag[i] = state[i] == kIn ? 1 : 0;
@@ -713,6 +731,7 @@ __global__ void k_in_flag(int64_t n, const int8_t *state, int64_t *flag) {
 // in column order
 __global__ void k_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
                             const int32_t *sdeg, const int8_t *state, const int64_t *rootid, int32_t *first) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   int32_t a = -1;
@@ -728,6 +747,7 @@ __global__ void k_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, co
 // the rest join the first-pass neighbour of largest |a_ij|, smaller id on ties
 __global__ void k_agg_pass2(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                             const uint8_t *sflag, const int32_t *sdeg, const int32_t *first, int32_t *agg) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   int32_t a = first[i];
@@ -747,6 +767,7 @@ __global__ void k_agg_pass2(int64_t n, const int64_t *rp, const int32_t *col, co
 }
 
 __global__ void k_member_count(int64_t n, const int32_t *agg, int64_t *cnt) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   if (agg[i] >= 0) atomicAdd((unsigned long long *)&cnt[agg[i]], 1ull);
@@ -754,6 +775,7 @@ __global__ void k_member_count(int64_t n, const int32_t *agg, int64_t *cnt) {
 
 __global__ void k_member_fill(int64_t n, const int32_t *agg, const int64_t *mptr, int64_t *cursor,
                               int32_t *midx) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   const int32_t a = agg[i];
@@ -763,6 +785,7 @@ __global__ void k_member_fill(int64_t n, const int32_t *agg, const int64_t *mptr
 }
 
 __global__ void k_member_sort(int64_t na, const int64_t *mptr, int32_t *midx) {
+  pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (a >= na) return;
   for (int64_t t = mptr[a] + 1; t < mptr[a + 1]; t++) {
@@ -788,6 +811,7 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
                                                        const int32_t *midx, int fill, int64_t *ccount,
                                                        const int64_t *crp, int32_t *ccol, double *cval,
                                                        int32_t *long_rows, int *n_long) {
+  pdl_enter();
   __shared__ uint64_t sK[kWarps][kGalCap];
   __shared__ double sV[kWarps][kGalCap];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -917,6 +941,7 @@ __global__ void __launch_bounds__(kThreads) k_galerkin_long(const int64_t *rp, c
                                                             const int *n_long, int fill, int64_t *ccount,
                                                             const int64_t *crp, int32_t *ccol, double *cval,
                                                             int *err) {
+  pdl_enter();
   extern __shared__ unsigned long long gsm[];
   unsigned long long *key = gsm;                                     // [kGalLongMax]
   double *sv = reinterpret_cast<double *>(gsm + kGalLongMax);        // [kGalLongMax]
@@ -994,6 +1019,7 @@ __global__ void __launch_bounds__(kThreads) k_galerkin_long(const int64_t *rp, c
 // atomic per block.
 __global__ void k_gershgorin(int64_t n, const int64_t *rp, const double *val, const int64_t *dpos,
                              double *dinv, unsigned long long *lam_bits) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   unsigned long long qb = 0ull;
   if (i < n) {
@@ -1027,6 +1053,7 @@ __global__ void k_gershgorin(int64_t n, const int64_t *rp, const double *val, co
 // pivot of column k+1 among them; the last block to finish swaps and scales
 // the next pivot row.  The right half ends as A^-1.
 __global__ void k_csr_to_aug(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double *aug) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   for (int64_t p = rp[i]; p < rp[i + 1]; p++) aug[i * 2 * n + col[p]] = val[p];
@@ -1079,6 +1106,7 @@ __device__ void gj_pivot_row(int n, int k, int p, double *aug, int *err) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_gj_first(int n, double *aug, int *err) {
+  pdl_enter();
   const int64_t w = 2 * (int64_t)n;
   double v = -1.0;
   int r = n;
@@ -1092,6 +1120,7 @@ __global__ void __launch_bounds__(kThreads) k_gj_first(int n, double *aug, int *
 
 __global__ void __launch_bounds__(kThreads) k_gj_step(int n, int k, double *aug, double *pv, int *pr,
                                                      unsigned int *counter, int *err) {
+  pdl_enter();
   const int64_t w = 2 * (int64_t)n;
   if (*err) return;
   double v = -1.0;
@@ -1139,6 +1168,7 @@ constexpr int kDenseSmall = 64;
 
 __global__ void __launch_bounds__(1024) k_gj_small(int n, const int64_t *rp, const int32_t *col,
                                                    const double *val, double *inv, int *err) {
+  pdl_enter();
   __shared__ double a[kDenseSmall][2 * kDenseSmall];
   __shared__ double fk[kDenseSmall];
   __shared__ double bv[32];
@@ -1200,6 +1230,7 @@ __global__ void __launch_bounds__(1024) k_gj_small(int n, const int64_t *rp, con
 }
 
 __global__ void k_aug_to_inv(int64_t n, const double *aug, double *inv) {
+  pdl_enter();
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (idx >= n * n) return;
   const int64_t i = idx / n, j = idx % n;
@@ -1213,6 +1244,7 @@ __global__ void k_aug_to_inv(int64_t n, const double *aug, double *inv) {
 __global__ void k_colour_round(Geom g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
                                uint32_t seed, const int32_t *cin, int32_t *cout, unsigned long long *coloured,
                                int *overflow) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.n_rows) return;
   const int32_t ci = cin[i];
@@ -1254,6 +1286,7 @@ __global__ void k_colour_round(Geom g, const uint8_t *emask, const int64_t *tptr
 }
 
 __global__ void k_colour_count(Geom g, const int32_t *colour, unsigned long long *cnt, unsigned long long *cnt_cells) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= g.n_rows) return;
   atomicAdd(&cnt[colour[i]], 1ull);
@@ -1261,6 +1294,7 @@ __global__ void k_colour_count(Geom g, const int32_t *colour, unsigned long long
 }
 
 __global__ void k_colour_flag(int64_t n, const int32_t *colour, int c, int64_t *flag) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
   flag[i] = colour[i] == c ? 1 : 0;
@@ -1268,6 +1302,7 @@ __global__ void k_colour_flag(int64_t n, const int32_t *colour, int c, int64_t *
 
 __global__ void k_colour_place(int64_t n, const int32_t *colour, int c, const int64_t *rank, int64_t base,
                                int32_t *crow, int64_t *pos) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n || colour[i] != c) return;
   const int64_t q = base + rank[i];
@@ -1278,6 +1313,7 @@ __global__ void k_colour_place(int64_t n, const int32_t *colour, int c, const in
 // ------------------------------------------------------------------ ILU(0)
 __global__ void k_ilu_lmask_len(Geom g, const uint8_t *emask, const int64_t *tptr, const int32_t *crow,
                                 const int64_t *pos, uint8_t *lmask, int64_t *len) {
+  pdl_enter();
   const int64_t q = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (q >= g.n_rows) return;
   const int64_t i = crow[q];
@@ -1295,6 +1331,7 @@ __global__ void k_ilu_lmask_len(Geom g, const uint8_t *emask, const int64_t *tpt
 __global__ void k_ilu_tail_fill(Geom g, const int64_t *tptr, const int32_t *tcol, const int32_t *crow,
                                 const int64_t *pos, const int64_t *ftptr, int32_t *ftcol, uint8_t *ftlow,
                                 int64_t *ftsrc) {
+  pdl_enter();
   const int64_t q = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (q >= g.n_rows) return;
   const int64_t i = crow[q];
@@ -1317,6 +1354,7 @@ template <int B, class T>
 __global__ void k_ilu_init(Geom g, const uint8_t *emask, const int32_t *crow, const T *at_ell,
                            const T *at_tval, const int64_t *ftsrc, int64_t nft, int64_t slot_warps, T *fell,
                            T *ftval) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t np = g.n_rows;
   const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
@@ -1375,6 +1413,7 @@ template <int B, class T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k_ilu_factor(Geom g, const uint8_t *emask, const int32_t *crow, const int64_t *pos,
                              const int64_t *ftptr, const int32_t *ftcol, const uint8_t *ftlow,
                              const uint32_t *fmask, T *fell, T *ftval, int64_t q0, int64_t q1, int *err) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (q >= q1) return;
@@ -1514,6 +1553,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_factor_long(Geom g, const uint
                                                               const int64_t *pos, const int64_t *ftptr,
                                                               const int32_t *ftcol, const uint32_t *fmask,
                                                               T *fell, T *ftval, int64_t q1, int64_t q2, int *err) {
+  pdl_enter();
   constexpr int BB = B * B;
   const int lane = threadIdx.x & 31;
   const int64_t q = q1 + blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
@@ -1660,6 +1700,7 @@ template <int B, class T>
 __global__ void __launch_bounds__(kThreads) k_ilu_factor_planned(
     int64_t np, const int64_t *ftptr, LongRowPlan plan, int64_t first, int64_t q1, int ub_in_smem, T *fell,
     T *ftval, int *err) {
+  pdl_enter();
   constexpr int BB = B * B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t r = first + blockIdx.x, q = q1 + blockIdx.x;
@@ -1747,25 +1788,25 @@ void exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *total, 
   }
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
   TBuf<int64_t> bsum(nb, s);
-  k_scan_reduce<<<(unsigned)nb, kThreads, 0, s>>>(in, n, bsum.p);
+  launch_pdl(k_scan_reduce, (unsigned)nb, kThreads, 0, s, in, n, bsum.p);
   TRS_LAUNCHED();
-  k_scan_bsums<<<1, 32, 0, s>>>(bsum.p, nb, total);
+  launch_pdl(k_scan_bsums, 1, 32, 0, s, bsum.p, nb, total);
   TRS_LAUNCHED();
-  k_scan_apply<<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, bsum.p);
+  launch_pdl(k_scan_apply, (unsigned)nb, kThreads, 0, s, in, out, n, bsum.p);
   TRS_LAUNCHED();
 }
 
 void launch_scatter_values(int64_t nnzb, int bb, const int64_t *map, const double *uval, int64_t nc, double *ell,
                            double *tval, cudaStream_t s) {
   if (!nnzb) return;
-  k_scatter_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(nnzb, bb, map, uval, nc, ell, tval);
+  launch_pdl(k_scatter_values, grid_of(nnzb * bb), kThreads, 0, s, nnzb, bb, map, uval, nc, ell, tval);
   TRS_LAUNCHED();
 }
 
 void launch_gather_values(int64_t nnzb, int bb, const int64_t *map, const double *ell, const double *tval,
                           int64_t nc, double *uval, cudaStream_t s, int aos) {
   if (!nnzb) return;
-  k_gather_values<<<grid_of(nnzb * bb), kThreads, 0, s>>>(nnzb, bb, map, ell, tval, nc, aos, uval);
+  launch_pdl(k_gather_values, grid_of(nnzb * bb), kThreads, 0, s, nnzb, bb, map, ell, tval, nc, aos, uval);
   TRS_LAUNCHED();
 }
 
@@ -1774,13 +1815,13 @@ void launch_assemble(int b, trs_bsr *A, const double *perm, int perm_is_log, dou
   A->tval.zero(s);
   TRS_DISPATCH_B(b, {
     if (A->g.nc) {
-      k_assemble_cells<B><<<grid_of(A->g.nc), kThreads, 0, s>>>(
+      launch_pdl(k_assemble_cells<B>, grid_of(A->g.nc), kThreads, 0, s, 
           A->g, A->emask.p, A->ell.p, A->tval.p, perm, perm_is_log, kvkh, c_t, M, acc, A->cperf_ptr.p,
           A->cperf_idx.p, A->perf_cw.p, wi, lam);
       TRS_LAUNCHED();
     }
     if (A->n_wells)
-      k_assemble_wells<B><<<grid_of(A->n_wells), kThreads, 0, s>>>(A->n_wells, A->tval.p, A->wperf_ptr.p,
+      launch_pdl(k_assemble_wells<B>, grid_of(A->n_wells), kThreads, 0, s, A->n_wells, A->tval.p, A->wperf_ptr.p,
                                                                    A->wperf_idx.p, A->perf_wc.p, A->wdiag.p,
                                                                    wi, lam);
   });
@@ -1791,7 +1832,7 @@ void launch_decouple(int b, const MatView<double> &A, const int64_t *tdiag, int 
                      double *at_p, double *at_tval, double *dinv, double *ap_ell, double *ap_tval, int *err,
                      cudaStream_t s) {
   if (!A.g.n_rows) return;
-  TRS_DISPATCH_B(b, k_decouple<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_p, at_tval,
+  TRS_DISPATCH_B(b, launch_pdl(k_decouple<B>, grid_of(A.g.n_rows), kThreads, 0, s, A, tdiag, mode, at_ell, at_p, at_tval,
                                                                            dinv, ap_ell, ap_tval, err));
   TRS_LAUNCHED();
 }
@@ -1800,70 +1841,70 @@ void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag
                            float *at_p, float *at_tval, float *dinv, double *ap_ell, double *ap_tval, int *err,
                            cudaStream_t s) {
   if (!A.g.n_rows) return;
-  TRS_DISPATCH_B(b, k_decouple_mixed<B><<<grid_of(A.g.n_rows), kThreads, 0, s>>>(A, tdiag, mode, at_ell, at_p,
+  TRS_DISPATCH_B(b, launch_pdl(k_decouple_mixed<B>, grid_of(A.g.n_rows), kThreads, 0, s, A, tdiag, mode, at_ell, at_p,
                                                                                  at_tval, dinv, ap_ell, ap_tval,
                                                                                  err));
   TRS_LAUNCHED();
 }
 
 void launch_ap_csr_rowlen(const Geom &g, const uint8_t *emask, const int64_t *tptr, int64_t *len, cudaStream_t s) {
-  k_ap_rowlen<<<grid_of(g.n_rows), kThreads, 0, s>>>(g, emask, tptr, len);
+  launch_pdl(k_ap_rowlen, grid_of(g.n_rows), kThreads, 0, s, g, emask, tptr, len);
   TRS_LAUNCHED();
 }
 
 void launch_ap_csr_fill(const Geom &g, const uint8_t *emask, const int64_t *tptr, const int32_t *tcol,
                         const double *ap_ell, const double *ap_tval, const int64_t *rp, int32_t *col, double *val,
                         cudaStream_t s) {
-  k_ap_fill<<<grid_of(g.n_rows), kThreads, 0, s>>>(g, emask, tptr, tcol, ap_ell, ap_tval, rp, col, val);
+  launch_pdl(k_ap_fill, grid_of(g.n_rows), kThreads, 0, s, g, emask, tptr, tcol, ap_ell, ap_tval, rp, col, val);
   TRS_LAUNCHED();
 }
 
 void launch_diag_pos(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int64_t *dpos,
                      double *dval, cudaStream_t s) {
   if (!n) return;
-  k_diag_pos<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, val, dpos, dval);
+  launch_pdl(k_diag_pos, grid_of(n), kThreads, 0, s, n, rp, col, val, dpos, dval);
   TRS_LAUNCHED();
 }
 
 void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *dval,
                      double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s) {
   if (!n) return;
-  k_strength<<<grid_of(n * kStrengthLanes), kThreads, 0, s>>>(n, rp, col, val, dval, theta, sflag, sdeg);
+  launch_pdl(k_strength, grid_of(n * kStrengthLanes), kThreads, 0, s, n, rp, col, val, dval, theta, sflag, sdeg);
   TRS_LAUNCHED();
 }
 
 void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_t s) {
-  k_mis2_init<<<grid_of(n), kThreads, 0, s>>>(n, sdeg, state);
+  launch_pdl(k_mis2_init, grid_of(n), kThreads, 0, s, n, sdeg, state);
   TRS_LAUNCHED();
 }
 
 void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int8_t *state,
                        const uint64_t *in_w, uint32_t seed, uint64_t *out_w, cudaStream_t s) {
   if (n >= (int64_t(1) << 30)) throw Error(TRS_ERR_UNSUPPORTED, "AMG levels are limited to 2^30 rows");
-  k_mis2_sweep<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, sflag, state, in_w, seed, out_w);
+  launch_pdl(k_mis2_sweep, grid_of(n), kThreads, 0, s, n, rp, col, sflag, state, in_w, seed, out_w);
   TRS_LAUNCHED();
 }
 
 void launch_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state, unsigned long long *undecided,
                         cudaStream_t s) {
-  k_mis2_decide<<<grid_of(n), kThreads, 0, s>>>(n, seed, t2w, state, undecided);
+  launch_pdl(k_mis2_decide, grid_of(n), kThreads, 0, s, n, seed, t2w, state, undecided);
   TRS_LAUNCHED();
 }
 
 void launch_in_flag(int64_t n, const int8_t *state, int64_t *flag, cudaStream_t s) {
-  k_in_flag<<<grid_of(n), kThreads, 0, s>>>(n, state, flag);
+  launch_pdl(k_in_flag, grid_of(n), kThreads, 0, s, n, state, flag);
   TRS_LAUNCHED();
 }
 
 void launch_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int32_t *sdeg,
                       const int8_t *state, const int64_t *rootid, int32_t *first, cudaStream_t s) {
-  k_agg_pass1<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, sflag, sdeg, state, rootid, first);
+  launch_pdl(k_agg_pass1, grid_of(n), kThreads, 0, s, n, rp, col, sflag, sdeg, state, rootid, first);
   TRS_LAUNCHED();
 }
 
 void launch_agg_pass2(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const uint8_t *sflag,
                       const int32_t *sdeg, const int32_t *first, int32_t *agg, cudaStream_t s) {
-  k_agg_pass2<<<grid_of(n), kThreads, 0, s>>>(n, rp, col, val, sflag, sdeg, first, agg);
+  launch_pdl(k_agg_pass2, grid_of(n), kThreads, 0, s, n, rp, col, val, sflag, sdeg, first, agg);
   TRS_LAUNCHED();
 }
 
@@ -1873,13 +1914,13 @@ void launch_members(int64_t n, const int32_t *agg, int64_t n_agg, DBuf<int64_t> 
   cnt.zero();
   cursor.zero();
   if (mptr.n < (size_t)(n_agg + 1)) mptr.alloc(n_agg + 1);
-  k_member_count<<<grid_of(n), kThreads, 0, s>>>(n, agg, cnt.p);
+  launch_pdl(k_member_count, grid_of(n), kThreads, 0, s, n, agg, cnt.p);
   TRS_LAUNCHED();
   exclusive_scan(cnt.p, mptr.p, n_agg + 1, nullptr, s);
   if (midx.n < (size_t)std::max<int64_t>(n, 1)) midx.alloc(std::max<int64_t>(n, 1));  // members <= n
-  k_member_fill<<<grid_of(n), kThreads, 0, s>>>(n, agg, mptr.p, cursor.p, midx.p);
+  launch_pdl(k_member_fill, grid_of(n), kThreads, 0, s, n, agg, mptr.p, cursor.p, midx.p);
   TRS_LAUNCHED();
-  k_member_sort<<<grid_of(n_agg), kThreads, 0, s>>>(n_agg, mptr.p, midx.p);
+  launch_pdl(k_member_sort, grid_of(n_agg), kThreads, 0, s, n_agg, mptr.p, midx.p);
   TRS_LAUNCHED();
 }
 
@@ -1899,10 +1940,10 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
   err.zero();
   const unsigned grid = (unsigned)((n_agg + kWarps - 1) / kWarps);
   const unsigned long_grid = 152;
-  k_galerkin<<<grid, kThreads, 0, s>>>(n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 0, cnt.p, nullptr,
+  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 0, cnt.p, nullptr,
                                        nullptr, nullptr, long_rows.p, n_long.p);
   TRS_LAUNCHED();
-  k_galerkin_long<<<long_grid, kThreads, long_smem, s>>>(F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
+  launch_pdl(k_galerkin_long, long_grid, kThreads, long_smem, s, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
                                                          n_long.p, 0, cnt.p, nullptr, nullptr, nullptr, err.p);
   TRS_LAUNCHED();
   C.n = n_agg;
@@ -1915,10 +1956,10 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
   TRS_REQUIRE(!herr, TRS_ERR_UNSUPPORTED, "a coarse AMG row has more than 8192 Galerkin contributions");
   if (C.col.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.col.alloc(std::max<int64_t>(C.nnz, 1));
   if (C.val.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.val.alloc(std::max<int64_t>(C.nnz, 1));
-  k_galerkin<<<grid, kThreads, 0, s>>>(n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 1, nullptr, C.rp.p,
+  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 1, nullptr, C.rp.p,
                                        C.col.p, C.val.p, long_rows.p, n_long.p);
   TRS_LAUNCHED();
-  k_galerkin_long<<<long_grid, kThreads, long_smem, s>>>(F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
+  launch_pdl(k_galerkin_long, long_grid, kThreads, long_smem, s, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
                                                          n_long.p, 1, nullptr, C.rp.p, C.col.p, C.val.p, err.p);
   TRS_LAUNCHED();
 }
@@ -1926,7 +1967,7 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
 void launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, unsigned long long *lam_bits,
                             cudaStream_t s) {
   TRS_CUDA(cudaMemsetAsync(lam_bits, 0, sizeof(unsigned long long), s));
-  k_gershgorin<<<grid_of(A.n), kThreads, 0, s>>>(A.n, A.rp.p, A.val.p, dpos, dinv, lam_bits);
+  launch_pdl(k_gershgorin, grid_of(A.n), kThreads, 0, s, A.n, A.rp.p, A.val.p, dpos, dinv, lam_bits);
   TRS_LAUNCHED();
 }
 
@@ -1936,7 +1977,7 @@ int launch_dense_inverse(const Csr &A, DBuf<double> &inv, cudaStream_t s) {
     TBuf<int> err(1, s);
     err.zero();
     if (inv.n < (size_t)std::max(n * n, 1)) inv.alloc((size_t)std::max(n * n, 1));
-    k_gj_small<<<1, 1024, 0, s>>>(n, A.rp.p, A.col.p, A.val.p, inv.p, err.p);
+    launch_pdl(k_gj_small, 1, 1024, 0, s, n, A.rp.p, A.col.p, A.val.p, inv.p, err.p);
     TRS_LAUNCHED();
     int herr = 0;
     TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1951,12 +1992,12 @@ int launch_dense_inverse(const Csr &A, DBuf<double> &inv, cudaStream_t s) {
   aug.zero();
   err.zero();
   counter.zero();
-  k_csr_to_aug<<<grid_of(n), kThreads, 0, s>>>(n, A.rp.p, A.col.p, A.val.p, aug.p);
+  launch_pdl(k_csr_to_aug, grid_of(n), kThreads, 0, s, n, A.rp.p, A.col.p, A.val.p, aug.p);
   TRS_LAUNCHED();
-  k_gj_first<<<1, kThreads, 0, s>>>(n, aug.p, err.p);
+  launch_pdl(k_gj_first, 1, kThreads, 0, s, n, aug.p, err.p);
   TRS_LAUNCHED();
   for (int k = 0; k < n; k++) {
-    k_gj_step<<<grid, kThreads, 0, s>>>(n, k, aug.p, pv.p, pr.p, counter.p, err.p);
+    launch_pdl(k_gj_step, grid, kThreads, 0, s, n, k, aug.p, pv.p, pr.p, counter.p, err.p);
     TRS_LAUNCHED();
   }
   int herr = 0;
@@ -1964,7 +2005,7 @@ int launch_dense_inverse(const Csr &A, DBuf<double> &inv, cudaStream_t s) {
   TRS_CUDA(cudaStreamSynchronize(s));
   if (herr) return 1;
   if (inv.n < (size_t)n * n) inv.alloc((size_t)n * n);
-  k_aug_to_inv<<<grid_of((int64_t)n * n), kThreads, 0, s>>>(n, aug.p, inv.p);
+  launch_pdl(k_aug_to_inv, grid_of((int64_t)n * n), kThreads, 0, s, n, aug.p, inv.p);
   TRS_LAUNCHED();
   return 0;
 }
@@ -1982,7 +2023,7 @@ int launch_colour(const Geom &g, const uint8_t *emask, const int64_t *tptr, cons
   unsigned long long done = 0;
   int rounds = 0;
   while (done < (unsigned long long)n) {
-    k_colour_round<<<grid_of(n), kThreads, 0, s>>>(g, emask, tptr, tcol, seed, a, bbuf, cnt.p, overflow.p);
+    launch_pdl(k_colour_round, grid_of(n), kThreads, 0, s, g, emask, tptr, tcol, seed, a, bbuf, cnt.p, overflow.p);
     TRS_LAUNCHED();
     std::swap(a, bbuf);
     int ov = 0;
@@ -2003,7 +2044,7 @@ void launch_colour_order(const Geom &g, const int32_t *colour, int ncol, std::ve
   TBuf<unsigned long long> cnt(kMaxColours, s), cntc(kMaxColours, s);
   cnt.zero();
   cntc.zero();
-  k_colour_count<<<grid_of(n), kThreads, 0, s>>>(g, colour, cnt.p, cntc.p);
+  launch_pdl(k_colour_count, grid_of(n), kThreads, 0, s, g, colour, cnt.p, cntc.p);
   TRS_LAUNCHED();
   auto hc = download(cnt.p, kMaxColours, s);
   auto hcc = download(cntc.p, kMaxColours, s);
@@ -2015,10 +2056,10 @@ void launch_colour_order(const Geom &g, const int32_t *colour, int ncol, std::ve
   }
   TBuf<int64_t> flag(n, s), rank(n, s);
   for (int c = 0; c < ncol; c++) {
-    k_colour_flag<<<grid_of(n), kThreads, 0, s>>>(n, colour, c, flag.p);
+    launch_pdl(k_colour_flag, grid_of(n), kThreads, 0, s, n, colour, c, flag.p);
     TRS_LAUNCHED();
     exclusive_scan(flag.p, rank.p, n, nullptr, s);
-    k_colour_place<<<grid_of(n), kThreads, 0, s>>>(n, colour, c, rank.p, cptr[c], crow, pos);
+    launch_pdl(k_colour_place, grid_of(n), kThreads, 0, s, n, colour, c, rank.p, cptr[c], crow, pos);
     TRS_LAUNCHED();
   }
   TRS_CUDA(cudaStreamSynchronize(s));
@@ -2030,7 +2071,7 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
   const int64_t n = g.n_rows;
   TBuf<int64_t> len(n + 1, s);
   len.zero();
-  k_ilu_lmask_len<<<grid_of(n), kThreads, 0, s>>>(g, emask, tptr, crow, pos, lmask, len.p);
+  launch_pdl(k_ilu_lmask_len, grid_of(n), kThreads, 0, s, g, emask, tptr, crow, pos, lmask, len.p);
   TRS_LAUNCHED();
   ftptr.alloc(n + 1);
   exclusive_scan(len.p, ftptr.p, n + 1, nullptr, s);
@@ -2040,7 +2081,7 @@ void launch_ilu_structure(const Geom &g, const uint8_t *emask, const int64_t *tp
   ftcol.alloc(std::max<int64_t>(nft, 1));
   ftlow.alloc(std::max<int64_t>(nft, 1));
   ftsrc.alloc(std::max<int64_t>(nft, 1));
-  k_ilu_tail_fill<<<grid_of(n), kThreads, 0, s>>>(g, tptr, tcol, crow, pos, ftptr.p, ftcol.p, ftlow.p, ftsrc.p);
+  launch_pdl(k_ilu_tail_fill, grid_of(n), kThreads, 0, s, g, tptr, tcol, crow, pos, ftptr.p, ftcol.p, ftlow.p, ftsrc.p);
   TRS_LAUNCHED();
 }
 
@@ -2056,7 +2097,7 @@ void launch_ilu_init(int b, const Geom &g, const uint8_t *emask, const int32_t *
   const int64_t slot_warps = (aligned ? 1 : kSlots) * ((np + 31) / 32);
   const int64_t threads = slot_warps * 32 + nft;
   if (!threads) return;
-  TRS_DISPATCH_B(b, k_ilu_init<B, T><<<grid_of(threads), kThreads, 0, s>>>(g, emask, crow, at_ell, at_tval, ftsrc,
+  TRS_DISPATCH_B(b, launch_pdl(k_ilu_init<B, T>, grid_of(threads), kThreads, 0, s, g, emask, crow, at_ell, at_tval, ftsrc,
                                                                            nft, slot_warps, fell, ftval));
   TRS_LAUNCHED();
 }
@@ -2072,7 +2113,7 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
                               const uint32_t *fmask, T *fell, T *ftval, int64_t q0, int64_t q1, int64_t q2,
                               const LongRowPlan *plan, const LongRowColour *pc, int *err, cudaStream_t s) {
   if (q1 > q0) {
-    TRS_DISPATCH_B(b, k_ilu_factor<B, T><<<grid_of(q1 - q0), kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol,
+    TRS_DISPATCH_B(b, launch_pdl(k_ilu_factor<B, T>, grid_of(q1 - q0), kThreads, 0, s, g, emask, crow, pos, ftptr, ftcol,
                                                                                ftlow, fmask, fell, ftval, q0, q1,
                                                                                err));
     TRS_LAUNCHED();
@@ -2088,7 +2129,7 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
       TRS_DISPATCH_B(b, {
         auto kfn = k_ilu_factor_planned<B, T>;
         TRS_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        kfn<<<(unsigned)(q2 - q1), kThreads, bytes, s>>>(g.n_rows, ftptr, *plan, pc->first, q1, ub, fell, ftval,
+        launch_pdl(kfn, (unsigned)(q2 - q1), kThreads, bytes, s, g.n_rows, ftptr, *plan, pc->first, q1, ub, fell, ftval,
                                                          err);
       });
       TRS_LAUNCHED();
@@ -2097,7 +2138,7 @@ void launch_ilu_factor_colour(int b, const Geom &g, const uint8_t *emask, const 
   }
   if (q2 > q1) {
     const unsigned grid = (unsigned)((q2 - q1 + kWarps - 1) / kWarps);
-    TRS_DISPATCH_B(b, k_ilu_factor_long<B, T><<<grid, kThreads, 0, s>>>(g, emask, crow, pos, ftptr, ftcol, fmask,
+    TRS_DISPATCH_B(b, launch_pdl(k_ilu_factor_long<B, T>, grid, kThreads, 0, s, g, emask, crow, pos, ftptr, ftcol, fmask,
                                                                         fell, ftval, q1, q2, err));
     TRS_LAUNCHED();
   }
@@ -2113,7 +2154,7 @@ template void launch_ilu_factor_colour<float>(int, const Geom &, const uint8_t *
 
 void launch_scale_diagonal(int b, trs_bsr *A, const double *sc, cudaStream_t s) {
   if (!A->n) return;
-  TRS_DISPATCH_B(b, k_scale_diag<B><<<grid_of(A->n), kThreads, 0, s>>>(A->g, A->ell.p, A->tval.p, A->tdiag.p, sc));
+  TRS_DISPATCH_B(b, launch_pdl(k_scale_diag<B>, grid_of(A->n), kThreads, 0, s, A->g, A->ell.p, A->tval.p, A->tdiag.p, sc));
   TRS_LAUNCHED();
 }
 

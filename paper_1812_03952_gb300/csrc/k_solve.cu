@@ -25,10 +25,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <class T>
 __device__ __forceinline__ double to_d(T v) { return static_cast<double>(v); }
 
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" :::);
-}
+
 
 // b consecutive entries of a block vector (16-byte aligned for b = 2, 4:
 // the base pointers come from cudaMalloc-class allocations and block starts
@@ -1408,27 +1405,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(int64_t N, const double *_
 
 inline unsigned grid_of(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-// Programmatic dependent launch (sm_90 and later): every kernel of this unit
-// is launched with programmatic stream serialisation, so that the next kernel
-// in the stream is scheduled while this one drains instead of after it; each
-// kernel waits (griddepcontrol.wait: the previous grid complete and its
-// memory visible) before it touches memory, and lets its successor launch
-// once all of its own blocks run.  Stream order is kept: nothing is read
-// before the producer has finished.
-template <class... KArgs, class... Args>
-void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  TRS_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(std::forward<Args>(args))...));
-}
+
 
 }  // namespace
 

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/trs.h"
@@ -137,6 +138,33 @@ std::vector<T> download(const T *d, size_t count, cudaStream_t s) {
 }
 
 // Geometry of the structured part.
+// Programmatic dependent launch (sm_90 and later): every kernel of the library
+// is launched with programmatic stream serialisation, so that the next kernel
+// in the stream is scheduled while this one drains instead of after it; each
+// kernel waits (griddepcontrol.wait: the previous grid complete and its
+// memory visible) before it touches memory, and lets its successor launch
+// once all of its own blocks run.  Stream order is kept: nothing is read
+// before the producer has finished.
+template <class... KArgs, class... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TRS_CUDA(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(std::forward<Args>(args))...));
+}
+
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 struct Geom {
   int64_t nc;       // cells
   int64_t n_rows;   // cells + other rows
