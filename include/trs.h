@@ -14,12 +14,16 @@
  * (Sec. "Preconditioners", Algorithm pc-fpf) applied to the ABF-decoupled
  * matrix D^-1 A (Sec. "Decoupling Methods", Eqs. decoupled-eq and
  * decoupled-abf), with a pressure-AMG stage and a multicolour block ILU(0)
- * "F" stage.  All arithmetic runs in CUDA kernels on the current device.
+ * (or ILU(1)) "F" stage; BiCGSTAB is offered beside FGMRES.  All arithmetic
+ * runs in CUDA kernels on the current device.
  *
  * Conventions for every entry point:
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream); device work is ordered on it.  Calls that return results to
- *     the host synchronise that stream.
+ *     the host synchronise that stream.  The library's kernels use
+ *     programmatic dependent launch: each waits for the work before it in
+ *     the stream to complete before touching memory, so ordering with the
+ *     caller's own work on the stream is ordinary stream order.
  *   - "device pointer" arguments must point to memory of the current device,
  *     "host pointer" arguments to host memory.  Vectors are FP64 arrays of
  *     n_block_rows * b entries, block by block, owned by the caller; device

@@ -850,8 +850,15 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
   }
   int iters = 0, cycles = 0;
   double relres = 0.0;
+  bool x_zero = !o.use_x0;
   while (result != TRS_OK) {
-    launch_true_residual(M->b, Av, x, b, M->r.p, red, M->norms.p, s);
+    if (x_zero) {   // from x = 0 the residual is b itself: no SpMV
+      TRS_CUDA(cudaMemcpyAsync(M->r.p, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      TRS_CUDA(cudaMemcpyAsync(M->norms.p, M->norms.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      x_zero = false;
+    } else {
+      launch_true_residual(M->b, Av, x, b, M->r.p, red, M->norms.p, s);
+    }
     double hn[2];
     TRS_CUDA(cudaMemcpyAsync(hn, M->norms.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TRS_CUDA(cudaStreamSynchronize(s));
@@ -964,8 +971,15 @@ trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, co
     local.converged = 1;
     result = TRS_OK;
   }
+  bool x_zero = !o.use_x0;
   while (result != TRS_OK) {
-    launch_true_residual(M->b, Av, x, b, r, red, M->norms.p, s);
+    if (x_zero) {   // from x = 0 the residual is b itself: no SpMV
+      TRS_CUDA(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      TRS_CUDA(cudaMemcpyAsync(M->norms.p, M->norms.p + 2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      x_zero = false;
+    } else {
+      launch_true_residual(M->b, Av, x, b, r, red, M->norms.p, s);
+    }
     double hn[2];
     TRS_CUDA(cudaMemcpyAsync(hn, M->norms.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TRS_CUDA(cudaStreamSynchronize(s));
