@@ -328,3 +328,24 @@ def test_update_reuse_amg(trs, oracle, synth):
             np.testing.assert_array_equal(rp1, crp)
             np.testing.assert_array_equal(col1, ccol)
             np.testing.assert_array_equal(val1, cval)
+
+
+def test_stream_order_with_caller_kernels(trs, synth):
+    """The library's kernels start with a programmatic-dependent-launch wait:
+    a caller's kernel queued just before a call on the same stream (here a
+    torch scaling of b and of x0) must be complete before the library reads
+    its output, and a caller's kernel queued just after must see the result."""
+    s = _sys(synth, 12, 10, 6, 4, seed=51, n_pairs=2)
+    ds = _gpu_system(trs, s)
+    M = trs.CPR(ds.A, precision="fp64")
+    x_ref, _ = trs.fgmres_solve(ds.A, M, ds.rhs * 3.0, x=torch.zeros_like(ds.rhs), rtol=1e-10, use_x0=True)
+    for _ in range(3):
+        b = ds.rhs.clone()
+        b.mul_(3.0)                                   # queued right before the solve
+        x = torch.full_like(b, 7.0)
+        x.mul_(0.0)                                   # x0 = 0, written by a caller kernel
+        x, res = trs.fgmres_solve(ds.A, M, b, x=x, rtol=1e-10, use_x0=True)
+        y = x * 2.0                                   # queued right after
+        assert res.status == trs.TRS_OK
+        assert torch.equal(x, x_ref)
+        assert torch.equal(y, x_ref * 2.0)
