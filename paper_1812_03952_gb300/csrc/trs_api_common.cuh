@@ -106,4 +106,16 @@ struct trs_cpr {
   trs::DBuf<unsigned int> counter;
   int red_grid = 0;
   double ms_setup = 0.0;
+  // side stream of the setup: the block ILU factorisation runs on it while
+  // the AMG hierarchy is built on the caller's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  trs_cpr() = default;
+  trs_cpr(const trs_cpr &) = delete;
+  trs_cpr &operator=(const trs_cpr &) = delete;
+  ~trs_cpr() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+  }
 };

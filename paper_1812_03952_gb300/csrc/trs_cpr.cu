@@ -413,6 +413,42 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   else
     launch_decouple(b, A->view(), A->tdiag.p, mode, M->at_ell64.p, M->at_p64.p, M->at_tval64.p, M->dinv64.p,
                     M->ap_ell64.p, M->ap_tval64.p, err.p, s);
+  // The block ILU factorisation (of Ã) and the AMG hierarchy (of A_p) are
+  // independent once the decoupling is done: the factorisation runs on the
+  // side stream while the hierarchy, latency-bound and synchronised with the
+  // host level by level, is built on s; s waits for both at the end.
+  if (!M->side) {
+    TRS_CUDA(cudaStreamCreateWithFlags(&M->side, cudaStreamNonBlocking));
+    TRS_CUDA(cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming));
+    TRS_CUDA(cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming));
+  }
+  cudaStream_t s2 = M->side;
+  TRS_CUDA(cudaEventRecord(M->ev_fork, s));
+  TRS_CUDA(cudaStreamWaitEvent(s2, M->ev_fork, 0));
+  TBuf<int> err2(1, s2);
+  err2.zero();
+  {
+    const LongRowPlan plan = long_row_plan(M);
+    const uint32_t *fm = M->nfslots > kSlots ? M->fmask.p : nullptr;
+    if (mixed) {
+      launch_ilu_init<float>(b, M->g, M->emask.p, M->crow.p, M->at_ell32.p, M->at_tval32.p, M->ftsrc.p, M->nft,
+                             M->nfslots, M->fell32.p, M->ftval32.p, s2);
+      for (int c = 0; c < M->ncol; c++)
+        launch_ilu_factor_colour<float>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p,
+                                        M->ftlow.p, fm, M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c],
+                                        M->cptr[c + 1], &plan, M->lr_col.empty() ? nullptr : &M->lr_col[c],
+                                        err2.p, s2);
+    } else {
+      launch_ilu_init<double>(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft,
+                              M->nfslots, M->fell64.p, M->ftval64.p, s2);
+      for (int c = 0; c < M->ncol; c++)
+        launch_ilu_factor_colour<double>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p,
+                                         M->ftlow.p, fm, M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c],
+                                         M->cptr[c + 1], &plan, M->lr_col.empty() ? nullptr : &M->lr_col[c],
+                                         err2.p, s2);
+    }
+  }
+  TRS_CUDA(cudaEventRecord(M->ev_join, s2));
   if (rebuild_amg) {
     if (M->lev.empty()) M->lev.emplace_back();
     Csr &C0 = M->lev[0].A;
@@ -436,25 +472,6 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   } else {
     refresh_hierarchy(M, s);
   }
-  // block ILU(0) on Ã, in the preconditioner's precision
-  const LongRowPlan plan = long_row_plan(M);
-  const uint32_t *fm = M->nfslots > kSlots ? M->fmask.p : nullptr;
-  if (mixed) {
-    launch_ilu_init<float>(b, M->g, M->emask.p, M->crow.p, M->at_ell32.p, M->at_tval32.p, M->ftsrc.p, M->nft,
-                           M->nfslots, M->fell32.p, M->ftval32.p, s);
-    for (int c = 0; c < M->ncol; c++)
-      launch_ilu_factor_colour<float>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p, M->ftlow.p,
-                                      fm, M->fell32.p, M->ftval32.p, M->cptr[c], M->cmid[c], M->cptr[c + 1], &plan,
-                                      M->lr_col.empty() ? nullptr : &M->lr_col[c], err.p, s);
-  } else {
-    launch_ilu_init<double>(b, M->g, M->emask.p, M->crow.p, M->at_ell64.p, M->at_tval64.p, M->ftsrc.p, M->nft,
-                            M->nfslots, M->fell64.p, M->ftval64.p, s);
-    for (int c = 0; c < M->ncol; c++)
-      launch_ilu_factor_colour<double>(b, M->g, M->emask.p, M->crow.p, M->pos.p, M->ftptr.p, M->ftcol.p,
-                                       M->ftlow.p, fm, M->fell64.p, M->ftval64.p, M->cptr[c], M->cmid[c],
-                                       M->cptr[c + 1], &plan, M->lr_col.empty() ? nullptr : &M->lr_col[c],
-                                       err.p, s);
-  }
   if (mixed) {
     auto cast = [&](DBuf<double> &src, DBuf<float> &dst, int64_t cnt) {
       reserve(dst, cnt);
@@ -468,10 +485,12 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
       if (l > 0) cast(L.A.val, L.val32, L.A.nnz);
     }
   }
-  int herr = 0;
-  TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaStreamWaitEvent(s, M->ev_join, 0));
+  int herr[2] = {0, 0};
+  TRS_CUDA(cudaMemcpyAsync(&herr[0], err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaMemcpyAsync(&herr[1], err2.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaStreamSynchronize(s));
-  TRS_REQUIRE(!herr, TRS_ERR_SINGULAR_BLOCK, "a singular diagonal or block ILU(0) pivot block");
+  TRS_REQUIRE(!herr[0] && !herr[1], TRS_ERR_SINGULAR_BLOCK, "a singular diagonal or block ILU pivot block");
 }
 
 void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
