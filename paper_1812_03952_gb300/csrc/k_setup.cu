@@ -803,7 +803,10 @@ __global__ void k_member_sort(int64_t na, const int64_t *mptr, int32_t *midx) {
 // puts equal J together in staging order, and the first lane of each run
 // sums its run's values from 0.0 in that order (the definition's order).
 // Rows with more pairs than the staging area go to k_galerkin_long.
-// fill == 0 counts the distinct J, fill == 1 writes them.
+// fill == 0 counts the distinct J, fill == 1 writes them at crp[I];
+// fill == 2 counts them and writes them at I * kGalCap of ccol/cval (a
+// padded area that k_gal_compact packs once the counts are scanned), so that
+// the staging and the sort run once.
 constexpr int kGalCap = 256;
 
 __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t *rp, const int32_t *col,
@@ -860,8 +863,12 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
     }
     total += ctot;
   }
+  const bool padded = fill == 2;
   if (!staged) {
-    if (!fill && lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)I;
+    if ((!fill || padded) && lane == 0) {
+      long_rows[atomicAdd(n_long, 1)] = (int32_t)I;
+      if (padded) ccount[I] = -1;   // counted and written by k_galerkin_long
+    }
     return;
   }
   // bitonic sort of the keys, padded with the largest key to a power of two
@@ -898,13 +905,42 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
       double sum = 0.0;
       for (int u = t; u < total && (uint32_t)(sK[wid][u] >> 32) == J; u++)
         sum = sum + sV[wid][(int)(sK[wid][u] & 0xffffffffu)];
-      const int64_t at = crp[I] + count + __popc(hm & ((1u << lane) - 1u));
+      const int64_t at = (padded ? I * kGalCap : crp[I]) + count + __popc(hm & ((1u << lane) - 1u));
       ccol[at] = (int32_t)J;
       cval[at] = sum;
     }
     count += __popc(hm);
   }
-  if (!fill && lane == 0) ccount[I] = count;
+  if ((!fill || padded) && lane == 0) ccount[I] = count;
+}
+
+// Counts of the warp rows for the scan; long rows (-1) are counted by
+// k_galerkin_long into the zeroed entries.
+__global__ void k_gal_count_merge(int64_t na, const int64_t *pcount, int64_t *count) {
+  pdl_enter();
+  const int64_t I = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (I >= na) return;
+  const int64_t c = pcount[I];
+  count[I] = c < 0 ? 0 : c;
+}
+
+// Packs the rows written by k_galerkin (fill == 2) from their padded area
+// into the scanned CSR: a warp per coarse row (rows marked -1 are long rows,
+// written by k_galerkin_long).
+__global__ void __launch_bounds__(kThreads) k_gal_compact(int64_t na, const int64_t *pcount, const int32_t *pcol,
+                                                          const double *pval, const int64_t *crp, int32_t *ccol,
+                                                          double *cval) {
+  pdl_enter();
+  const int lane = threadIdx.x & 31;
+  const int64_t I = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5);
+  if (I >= na) return;
+  const int64_t c = pcount[I];
+  if (c < 0) return;
+  const int64_t src = I * kGalCap, dst = crp[I];
+  for (int64_t t = lane; t < c; t += 32) {
+    ccol[dst + t] = pcol[src + t];
+    cval[dst + t] = pval[src + t];
+  }
 }
 
 // Long coarse rows: one block per row.  The (J, a) pairs are staged in
@@ -1932,16 +1968,20 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
     TRS_CUDA(cudaFuncSetAttribute(k_galerkin_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)long_smem));
     attr_set = true;
   }
-  TBuf<int64_t> cnt(n_agg + 1, s);
-  TBuf<int32_t> long_rows(std::max<int64_t>(n_agg, 1), s);
+  TBuf<int64_t> cnt(n_agg + 1, s), pcnt(std::max<int64_t>(n_agg, 1), s);
+  TBuf<int32_t> long_rows(std::max<int64_t>(n_agg, 1), s), pcol(std::max<int64_t>(n_agg, 1) * kGalCap, s);
+  TBuf<double> pval(std::max<int64_t>(n_agg, 1) * kGalCap, s);
   TBuf<int> n_long(1, s), err(1, s);
   cnt.zero();
   n_long.zero();
   err.zero();
   const unsigned grid = (unsigned)((n_agg + kWarps - 1) / kWarps);
   const unsigned long_grid = 152;
-  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 0, cnt.p, nullptr,
-                                       nullptr, nullptr, long_rows.p, n_long.p);
+  // warp rows: counted and written to their padded area in one pass
+  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 2, pcnt.p, nullptr,
+             pcol.p, pval.p, long_rows.p, n_long.p);
+  TRS_LAUNCHED();
+  launch_pdl(k_gal_count_merge, grid_of(n_agg), kThreads, 0, s, n_agg, (const int64_t *)pcnt.p, cnt.p);
   TRS_LAUNCHED();
   launch_pdl(k_galerkin_long, long_grid, kThreads, long_smem, s, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
                                                          n_long.p, 0, cnt.p, nullptr, nullptr, nullptr, err.p);
@@ -1956,8 +1996,8 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
   TRS_REQUIRE(!herr, TRS_ERR_UNSUPPORTED, "a coarse AMG row has more than 8192 Galerkin contributions");
   if (C.col.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.col.alloc(std::max<int64_t>(C.nnz, 1));
   if (C.val.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.val.alloc(std::max<int64_t>(C.nnz, 1));
-  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 1, nullptr, C.rp.p,
-                                       C.col.p, C.val.p, long_rows.p, n_long.p);
+  launch_pdl(k_gal_compact, grid, kThreads, 0, s, n_agg, (const int64_t *)pcnt.p, (const int32_t *)pcol.p,
+             (const double *)pval.p, (const int64_t *)C.rp.p, C.col.p, C.val.p);
   TRS_LAUNCHED();
   launch_pdl(k_galerkin_long, long_grid, kThreads, long_smem, s, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
                                                          n_long.p, 1, nullptr, C.rp.p, C.col.p, C.val.p, err.p);
