@@ -679,6 +679,28 @@ __device__ __forceinline__ uint64_t mis2_word(int8_t state, int64_t i, uint32_t 
 // forms the words from the states (in_w == nullptr), the second reads the
 // first sweep's words.  Entries are read eight at a time so that their
 // gathers are in flight together (the maximum does not depend on order).
+// max over {i} U strong(i) of the first sweep's words w1
+__device__ __forceinline__ uint64_t mis2_sweep_row_w(int64_t i, const int64_t *rp, const int32_t *col,
+                                                     const uint8_t *sflag, const uint64_t *w1) {
+  uint64_t best = w1[i];
+  const int64_t e = rp[i + 1];
+  for (int64_t p0 = rp[i]; p0 < e; p0 += 8) {
+    int32_t jj[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int64_t p = p0 + u;
+      jj[u] = (p < e && sflag[p]) ? col[p] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      if (jj[u] < 0) continue;
+      const uint64_t w = w1[jj[u]];
+      best = w > best ? w : best;
+    }
+  }
+  return best;
+}
+
 __global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
                              const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w) {
   pdl_enter();
@@ -703,14 +725,17 @@ __global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, c
   out_w[i] = best;
 }
 
-__global__ void k_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state,
-                              unsigned long long *undecided) {
+// The second sweep fused with the decision: row i's distance-2 maximum is
+// formed from the first sweep's words (which no state write of this kernel
+// touches) and decides row i at once; the undecided rows are counted.
+__global__ void k_mis2_sweep_decide(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
+                                    int8_t *state, const uint64_t *w1, uint32_t seed,
+                                    unsigned long long *undecided) {
   pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
-  const int8_t s = state[i];
-  if (s != kUndecided) return;
-  const uint64_t w = t2w[i];
+  if (state[i] != kUndecided) return;
+  const uint64_t w = mis2_sweep_row_w(i, rp, col, sflag, w1);
   if (w == mis2_word(kUndecided, i, seed)) {
     state[i] = kIn;
   } else if ((int8_t)(w >> 62) == kIn) {
@@ -1921,9 +1946,9 @@ void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const u
   TRS_LAUNCHED();
 }
 
-void launch_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state, unsigned long long *undecided,
-                        cudaStream_t s) {
-  launch_pdl(k_mis2_decide, grid_of(n), kThreads, 0, s, n, seed, t2w, state, undecided);
+void launch_mis2_sweep_decide(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, int8_t *state,
+                              const uint64_t *w1, uint32_t seed, unsigned long long *undecided, cudaStream_t s) {
+  launch_pdl(k_mis2_sweep_decide, grid_of(n), kThreads, 0, s, n, rp, col, sflag, state, w1, seed, undecided);
   TRS_LAUNCHED();
 }
 

@@ -73,22 +73,23 @@ void build_hierarchy(trs_cpr *M, cudaStream_t s) {
     TBuf<uint8_t> sflag(std::max<int64_t>(nnz, 1), s);
     TBuf<int32_t> sdeg(n, s);
     launch_strength(n, F.A.rp.p, F.A.col.p, F.A.val.p, F.dval.p, o.theta, sflag.p, sdeg.p, s);
-    // MIS-2 rounds; the undecided count is read every second round (an extra
-    // round after completion changes nothing)
+    // MIS-2 rounds (first sweep; second sweep with the decision), each
+    // counting its undecided rows in its own counter; the count is read
+    // every second round (an extra round after completion changes nothing)
     const uint32_t seed = o.seed ^ (kLevelSeedMul * (uint32_t)(l + 1));
+    constexpr int kMaxRounds = 10000;
     TBuf<int8_t> state(n, s);
-    TBuf<uint64_t> w1(n, s), w2(n, s);
-    TBuf<unsigned long long> und(1, s);
+    TBuf<uint64_t> w1(n, s);
+    TBuf<unsigned long long> und(kMaxRounds, s);
+    und.zero();
     launch_mis2_init(n, sdeg.p, state.p, s);
     for (int round = 0;; round++) {
-      TRS_REQUIRE(round < 10000, TRS_ERR_COARSENING, "MIS-2 did not terminate");
-      und.zero();
+      TRS_REQUIRE(round < kMaxRounds, TRS_ERR_COARSENING, "MIS-2 did not terminate");
       launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, nullptr, seed, w1.p, s);
-      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, w1.p, seed, w2.p, s);
-      launch_mis2_decide(n, seed, w2.p, state.p, und.p, s);
+      launch_mis2_sweep_decide(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, w1.p, seed, und.p + round, s);
       if (round % 2 == 0) continue;
       unsigned long long left = 0;
-      TRS_CUDA(cudaMemcpyAsync(&left, und.p, sizeof(left), cudaMemcpyDeviceToHost, s));
+      TRS_CUDA(cudaMemcpyAsync(&left, und.p + round, sizeof(left), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
       if (!left) break;
     }

@@ -225,8 +225,10 @@ void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_
 void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
                        const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w,
                        cudaStream_t s);
-void launch_mis2_decide(int64_t n, uint32_t seed, const uint64_t *t2w, int8_t *state,
-                        unsigned long long *undecided, cudaStream_t s);
+// the second sweep and the decision in one launch (the undecided rows are
+// added to *undecided)
+void launch_mis2_sweep_decide(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, int8_t *state,
+                              const uint64_t *w1, uint32_t seed, unsigned long long *undecided, cudaStream_t s);
 void launch_in_flag(int64_t n, const int8_t *state, int64_t *flag, cudaStream_t s);
 void launch_agg_pass1(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
                       const int32_t *sdeg, const int8_t *state, const int64_t *rootid, int32_t *first,
