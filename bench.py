@@ -2,7 +2,7 @@
 """Benchmark of one Newton-step linear solve on a GB300.
 
 A step is one pass of the whole hot path over the 128x128x64, b = 4 synthetic
-thermal Jacobian (1,048,576 cells, 8 SAGD wells, 4,194,312 unknowns):
+thermal Jacobian (1,048,576 cells, 8 SAGD wells, 4,194,336 unknowns with the wells padded to b x b blocks):
 transmissibility/Jacobian assembly on the GPU, full CPR-FPF setup (ABF
 decoupling, pressure AMG, colouring, block ILU(0)), and FGMRES(30) to a true
 FP64 relative residual of 1e-6 -- with the CPR stored and applied in FP32
