@@ -675,11 +675,11 @@ __device__ __forceinline__ uint64_t mis2_word(int8_t state, int64_t i, uint32_t 
   return ((uint64_t)(uint8_t)state << 62) | ((uint64_t)fmix32((uint32_t)i ^ seed) << 30) | (uint64_t)i;
 }
 
-// out_i = max over {i} U strong(i) of the packed tuple; the first sweep
-// forms the words from the states (in_w == nullptr), the second reads the
-// first sweep's words.  Entries are read eight at a time so that their
-// gathers are in flight together (the maximum does not depend on order).
-// max over {i} U strong(i) of the first sweep's words w1
+// The two max-propagation sweeps of a round: the first forms
+// out_i = max over {i} U strong(i) of the packed tuples of the states, the
+// second (mis2_sweep_row_w) the same maximum over the first sweep's words.
+// Entries are read eight at a time so that their gathers are in flight
+// together (the maximum does not depend on order).
 __device__ __forceinline__ uint64_t mis2_sweep_row_w(int64_t i, const int64_t *rp, const int32_t *col,
                                                      const uint8_t *sflag, const uint64_t *w1) {
   uint64_t best = w1[i];
@@ -702,11 +702,11 @@ __device__ __forceinline__ uint64_t mis2_sweep_row_w(int64_t i, const int64_t *r
 }
 
 __global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
-                             const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w) {
+                             const int8_t *state, uint32_t seed, uint64_t *out_w) {
   pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
   if (i >= n) return;
-  uint64_t best = in_w ? in_w[i] : mis2_word(state[i], i, seed);
+  uint64_t best = mis2_word(state[i], i, seed);
   const int64_t e = rp[i + 1];
   for (int64_t p0 = rp[i]; p0 < e; p0 += 8) {
     int32_t jj[8];
@@ -718,7 +718,7 @@ __global__ void k_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, c
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       if (jj[u] < 0) continue;
-      const uint64_t w = in_w ? in_w[jj[u]] : mis2_word(state[jj[u]], jj[u], seed);
+      const uint64_t w = mis2_word(state[jj[u]], jj[u], seed);
       best = w > best ? w : best;
     }
   }
@@ -827,18 +827,17 @@ __global__ void k_member_sort(int64_t na, const int64_t *mptr, int32_t *midx) {
 // order, with keys J << 32 | staging index; a warp bitonic sort of the keys
 // puts equal J together in staging order, and the first lane of each run
 // sums its run's values from 0.0 in that order (the definition's order).
-// Rows with more pairs than the staging area go to k_galerkin_long.
-// fill == 0 counts the distinct J, fill == 1 writes them at crp[I];
-// fill == 2 counts them and writes them at I * kGalCap of ccol/cval (a
-// padded area that k_gal_compact packs once the counts are scanned), so that
-// the staging and the sort run once.
+// Rows with more pairs than the staging area go to k_galerkin_long (their
+// count is marked -1).  The distinct J of a row are counted and written, with
+// their sums, at I * kGalCap of pcol/pval: a padded area that k_gal_compact
+// packs once the counts are scanned, so that the staging and the sort run
+// once.
 constexpr int kGalCap = 256;
 
 __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t *rp, const int32_t *col,
                                                        const double *val, const int32_t *agg, const int64_t *mptr,
-                                                       const int32_t *midx, int fill, int64_t *ccount,
-                                                       const int64_t *crp, int32_t *ccol, double *cval,
-                                                       int32_t *long_rows, int *n_long) {
+                                                       const int32_t *midx, int64_t *pcount, int32_t *pcol,
+                                                       double *pval, int32_t *long_rows, int *n_long) {
   pdl_enter();
   __shared__ uint64_t sK[kWarps][kGalCap];
   __shared__ double sV[kWarps][kGalCap];
@@ -888,11 +887,10 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
     }
     total += ctot;
   }
-  const bool padded = fill == 2;
   if (!staged) {
-    if ((!fill || padded) && lane == 0) {
+    if (lane == 0) {
       long_rows[atomicAdd(n_long, 1)] = (int32_t)I;
-      if (padded) ccount[I] = -1;   // counted and written by k_galerkin_long
+      pcount[I] = -1;   // counted and written by k_galerkin_long
     }
     return;
   }
@@ -926,17 +924,17 @@ __global__ void __launch_bounds__(kThreads) k_galerkin(int64_t na, const int64_t
       head = J != 0xffffffffu && (t == 0 || (uint32_t)(sK[wid][t - 1] >> 32) != J);
     }
     const unsigned hm = __ballot_sync(0xffffffffu, head);
-    if (fill && head) {
+    if (head) {
       double sum = 0.0;
       for (int u = t; u < total && (uint32_t)(sK[wid][u] >> 32) == J; u++)
         sum = sum + sV[wid][(int)(sK[wid][u] & 0xffffffffu)];
-      const int64_t at = (padded ? I * kGalCap : crp[I]) + count + __popc(hm & ((1u << lane) - 1u));
-      ccol[at] = (int32_t)J;
-      cval[at] = sum;
+      const int64_t at = I * kGalCap + count + __popc(hm & ((1u << lane) - 1u));
+      pcol[at] = (int32_t)J;
+      pval[at] = sum;
     }
     count += __popc(hm);
   }
-  if ((!fill || padded) && lane == 0) ccount[I] = count;
+  if (lane == 0) pcount[I] = count;
 }
 
 // Counts of the warp rows for the scan; long rows (-1) are counted by
@@ -949,7 +947,7 @@ __global__ void k_gal_count_merge(int64_t na, const int64_t *pcount, int64_t *co
   count[I] = c < 0 ? 0 : c;
 }
 
-// Packs the rows written by k_galerkin (fill == 2) from their padded area
+// Packs the rows written by k_galerkin from their padded area
 // into the scanned CSR: a warp per coarse row (rows marked -1 are long rows,
 // written by k_galerkin_long).
 __global__ void __launch_bounds__(kThreads) k_gal_compact(int64_t na, const int64_t *pcount, const int32_t *pcol,
@@ -1940,9 +1938,9 @@ void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_
 }
 
 void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, const int8_t *state,
-                       const uint64_t *in_w, uint32_t seed, uint64_t *out_w, cudaStream_t s) {
+                       uint32_t seed, uint64_t *out_w, cudaStream_t s) {
   if (n >= (int64_t(1) << 30)) throw Error(TRS_ERR_UNSUPPORTED, "AMG levels are limited to 2^30 rows");
-  launch_pdl(k_mis2_sweep, grid_of(n), kThreads, 0, s, n, rp, col, sflag, state, in_w, seed, out_w);
+  launch_pdl(k_mis2_sweep, grid_of(n), kThreads, 0, s, n, rp, col, sflag, state, seed, out_w);
   TRS_LAUNCHED();
 }
 
@@ -2003,8 +2001,8 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
   const unsigned grid = (unsigned)((n_agg + kWarps - 1) / kWarps);
   const unsigned long_grid = 152;
   // warp rows: counted and written to their padded area in one pass
-  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, 2, pcnt.p, nullptr,
-             pcol.p, pval.p, long_rows.p, n_long.p);
+  launch_pdl(k_galerkin, grid, kThreads, 0, s, n_agg, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, pcnt.p, pcol.p,
+             pval.p, long_rows.p, n_long.p);
   TRS_LAUNCHED();
   launch_pdl(k_gal_count_merge, grid_of(n_agg), kThreads, 0, s, n_agg, (const int64_t *)pcnt.p, cnt.p);
   TRS_LAUNCHED();
@@ -2014,9 +2012,10 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
   C.n = n_agg;
   if (C.rp.n < (size_t)(n_agg + 1)) C.rp.alloc(n_agg + 1);
   exclusive_scan(cnt.p, C.rp.p, n_agg + 1, nullptr, s);
-  int herr = 0;
+  int herr = 0, hlong = 0;
   TRS_CUDA(cudaMemcpyAsync(&C.nnz, C.rp.p + n_agg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRS_CUDA(cudaMemcpyAsync(&hlong, n_long.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaStreamSynchronize(s));
   TRS_REQUIRE(!herr, TRS_ERR_UNSUPPORTED, "a coarse AMG row has more than 8192 Galerkin contributions");
   if (C.col.n < (size_t)std::max<int64_t>(C.nnz, 1)) C.col.alloc(std::max<int64_t>(C.nnz, 1));
@@ -2024,9 +2023,11 @@ void launch_galerkin(const Csr &F, const int32_t *agg, int64_t n_agg, const int6
   launch_pdl(k_gal_compact, grid, kThreads, 0, s, n_agg, (const int64_t *)pcnt.p, (const int32_t *)pcol.p,
              (const double *)pval.p, (const int64_t *)C.rp.p, C.col.p, C.val.p);
   TRS_LAUNCHED();
-  launch_pdl(k_galerkin_long, long_grid, kThreads, long_smem, s, F.rp.p, F.col.p, F.val.p, agg, mptr, midx, long_rows.p,
-                                                         n_long.p, 1, nullptr, C.rp.p, C.col.p, C.val.p, err.p);
-  TRS_LAUNCHED();
+  if (hlong) {
+    launch_pdl(k_galerkin_long, long_grid, kThreads, long_smem, s, F.rp.p, F.col.p, F.val.p, agg, mptr, midx,
+               long_rows.p, n_long.p, 1, nullptr, C.rp.p, C.col.p, C.val.p, err.p);
+    TRS_LAUNCHED();
+  }
 }
 
 void launch_gershgorin_dinv(const Csr &A, const int64_t *dpos, double *dinv, unsigned long long *lam_bits,

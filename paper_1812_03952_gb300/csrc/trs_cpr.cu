@@ -85,7 +85,7 @@ void build_hierarchy(trs_cpr *M, cudaStream_t s) {
     launch_mis2_init(n, sdeg.p, state.p, s);
     for (int round = 0;; round++) {
       TRS_REQUIRE(round < kMaxRounds, TRS_ERR_COARSENING, "MIS-2 did not terminate");
-      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, nullptr, seed, w1.p, s);
+      launch_mis2_sweep(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, seed, w1.p, s);
       launch_mis2_sweep_decide(n, F.A.rp.p, F.A.col.p, sflag.p, state.p, w1.p, seed, und.p + round, s);
       if (round % 2 == 0) continue;
       unsigned long long left = 0;

@@ -223,8 +223,7 @@ void launch_strength(int64_t n, const int64_t *rp, const int32_t *col, const dou
                      const double *dval, double theta, uint8_t *sflag, int32_t *sdeg, cudaStream_t s);
 void launch_mis2_init(int64_t n, const int32_t *sdeg, int8_t *state, cudaStream_t s);
 void launch_mis2_sweep(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag,
-                       const int8_t *state, const uint64_t *in_w, uint32_t seed, uint64_t *out_w,
-                       cudaStream_t s);
+                       const int8_t *state, uint32_t seed, uint64_t *out_w, cudaStream_t s);
 // the second sweep and the decision in one launch (the undecided rows are
 // added to *undecided)
 void launch_mis2_sweep_decide(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *sflag, int8_t *state,
