@@ -157,6 +157,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv(MatView<TA> A, const TX *__re
     if (i >= A.g.nc) return;
     double acc[B] = {};
     cell_row_apply<B>(A, i, x, acc);
+    if (alpha == 1.0 && beta == 0.0) {   // y = A x: no scaling on the FP64 unit (1.0 * v is v exactly)
+      store_blk<B>(y + i * B, acc);
+      return;
+    }
 #pragma unroll
     for (int r = 0; r < B; r++)
       y[i * B + r] = (beta == 0.0) ? alpha * acc[r] : fma(alpha, acc[r], beta * y[i * B + r]);
