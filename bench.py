@@ -381,8 +381,8 @@ def main():
     spmv_tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
     spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     # DRAM traffic per launch from the ncu capture of the 96x96x48 case
-    # (417.0 + 11.9 MB for 3,061,224 blocks), scaled by the blocks of this matrix
-    spmv_traffic = (428.922368e6 * nnzb / 3061224.0
+    # (418.9 + 10.9 MB for 3,061,224 blocks), scaled by the blocks of this matrix
+    spmv_traffic = (429.822464e6 * nnzb / 3061224.0
                     if args.workload == "128x128x64_b4" and args.krylov == "fgmres" else None)
     # the other Krylov method on the same system and preconditioner
     other = None
