@@ -2,24 +2,28 @@
 """Benchmark of one Newton-step linear solve on a GB300.
 
 A step is one pass of the whole hot path over the 128x128x64, b = 4 synthetic
-thermal Jacobian (1,048,576 cells, 8 SAGD wells, 4,194,336 unknowns with the wells padded to b x b blocks):
-transmissibility/Jacobian assembly on the GPU, full CPR-FPF setup (ABF
-decoupling, pressure AMG, colouring, block ILU(0)), and FGMRES(30) to a true
-FP64 relative residual of 1e-6 -- with the CPR stored and applied in FP32
-(the default) or FP64 (--precision fp64).  value = device milliseconds per
-step (lower is better), inputs resident in HBM.
+thermal Jacobian (1,048,576 cells, 8 SAGD wells, 4,194,336 unknowns with the
+wells padded to b x b blocks): transmissibility/Jacobian assembly on the GPU,
+full CPR setup (decoupling, pressure AMG, colouring, block ILU), and
+FGMRES(30) to a true FP64 relative residual of 1e-6 -- with the CPR stored and
+applied in FP32 (the default) or FP64 (--precision fp64).  value = device
+milliseconds per step (lower is better), inputs resident in HBM.
 
 Multi-GPU: the path is one system per GPU ("replicas"); every rank solves its
 own copy and the step time is the maximum over ranks.
 
---impl reference times the CPU oracle (plain C, FP64, single thread) on a
-bounded sample of the same workload.
+--impl reference times the CPU oracle (plain C, FP64, single thread): full
+solves (assembly + CPR setup + FGMRES to the same tolerance) of the same
+system, as many as fit a few minutes.
+--sweep times every CPR stage ordering x decoupling pair on the workload.
+--sequence N times a Newton-like sequence of N systems (forward + adjoint).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,9 +44,18 @@ def make_workload(name):
     if WORKLOADS[name] is None:      # mid-size case for profiler captures (matrix > L2, < 2 GB total)
         return S.small_system(96, 96, 48, 4, seed=77, sigma=1.5, n_pairs=4, kvkh=0.1, name=name)
     return S.config(WORKLOADS[name])
+
+
 METRIC = "CPR-FGMRES solve ms (assembly + CPR setup + FGMRES to true rel. res. 1e-6)"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+#: FP64 FMA units: 152 SMs x 2 FP64 FMA per clock (4 flop per SM per clock)
+FP64_FLOP_PER_CLOCK = 152 * 2 * 2
+#: reference-arm step cap: full oracle solves of the 128x128x64 system take
+#: about 16 s each on the GPU host's cores
+REF_MAX_STEPS, REF_MAX_WARMUP = 3, 1
+#: resident memory of one oracle solve per unknown (5.1 GB at 4.19M unknowns)
+ORACLE_BYTES_PER_UNKNOWN = 1300
 
 
 def parse():
@@ -55,6 +68,8 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--rtol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cpu-all-cores", action="store_true",
+                   help="skip the all-core column of the oracle baseline (one solve per core)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--sequence", type=int, default=0,
@@ -62,21 +77,31 @@ def parse():
                         "seeded +-20%% factors, AMG hierarchy rebuilt every --reuse steps, forward and adjoint "
                         "solve per system) instead of single solves")
     p.add_argument("--reuse", type=int, default=5)
+    p.add_argument("--stages", default="fpf", choices=["fpf", "fp", "pf"],
+                   help="CPR stage ordering of the forward CPR")
     p.add_argument("--decoupling", default="abf", choices=["abf", "none", "frs", "frs+abf"],
                    help="decoupling of the forward CPR")
     p.add_argument("--adjoint-decoupling", default="none", choices=["abf", "none", "frs", "frs+abf"],
                    help="decoupling of the CPR built on A^T for the adjoint solves")
-    p.add_argument("--ilu-fill", type=int, default=0, choices=[0, 1],
-                   help="level of fill of the block ILU stage (0: ILU(0), 1: ILU(1))")
+    p.add_argument("--ilu-fill", type=int, default=None, choices=[0, 1],
+                   help="level of fill of the block ILU stage (default: 0 for single solves, 1 for --sequence)")
     p.add_argument("--no-ilu-compare", action="store_true",
                    help="skip timing the other ILU level on the same system")
-    p.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
+    p.add_argument("--restart", type=int, default=None,
+                   help="FGMRES restart length (default: 30 for single solves, 60 for --sequence)")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoother degree")
     p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"],
                    help="outer Krylov method of the timed step")
     p.add_argument("--no-krylov-compare", action="store_true",
                    help="skip timing the other Krylov method on the same system")
-    return p.parse_args()
+    p.add_argument("--sweep", action="store_true",
+                   help="time every CPR stage ordering x decoupling pair (FP32 and FP64 CPR) instead")
+    a = p.parse_args()
+    if a.ilu_fill is None:
+        a.ilu_fill = 1 if a.sequence else 0
+    if a.restart is None:
+        a.restart = 60 if a.sequence else 30
+    return a
 
 
 # ----------------------------------------------------------------- helpers
@@ -136,6 +161,44 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "machine": platform.machine()}
+
+
+def mem_available_bytes():
+    """Memory this process may still use: MemAvailable, bounded by a cgroup limit."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(path) as f:
+                v = f.read().strip()
+            if v.isdigit():
+                lim = int(v)
+                with open(path.replace("memory.max", "memory.current").replace("limit_in_bytes",
+                                                                               "usage_in_bytes")) as f:
+                    used = int(f.read().strip())
+                avail = min(avail, lim - used) if avail else lim - used
+        except (OSError, ValueError):
+            pass
+    return avail or 0
+
+
 def dist_setup(n_gpus):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -170,9 +233,9 @@ def barrier(world):
 
 
 # ------------------------------------------------------------ oracle timing
-def oracle_sample(sysm, n_iter, iters_full):
-    """Times the CPU oracle on a bounded sample: assembly + CPR setup +
-    n_iter FGMRES iterations, extrapolated to iters_full iterations."""
+def oracle_full_solve(sysm, rtol, restart=30):
+    """One full FP64 oracle solve (assembly + CPR setup + FGMRES to the true
+    relative residual rtol), single thread; returns (ms, detail, x)."""
     from oracle import oracle as O
     O.build()
     t0 = time.perf_counter()
@@ -180,45 +243,101 @@ def oracle_sample(sysm, n_iter, iters_full):
     t1 = time.perf_counter()
     cpr = O.CPR(Ao)
     t2 = time.perf_counter()
-    res = O.fgmres(Ao, cpr, sysm.rhs, rtol=1e-30, maxit=n_iter)
+    res = O.fgmres(Ao, cpr, sysm.rhs, rtol=rtol, restart=restart)
     t3 = time.perf_counter()
-    per_iter = (t3 - t2) / max(1, res.iters)
-    est_ms = 1e3 * ((t1 - t0) + (t2 - t1) + per_iter * iters_full)
-    return est_ms, {"assemble_s": t1 - t0, "setup_s": t2 - t1, "iter_s": per_iter, "iters_timed": res.iters,
-                    "wall_s": t3 - t0}
+    detail = {"assemble_s": t1 - t0, "setup_s": t2 - t1, "solve_s": t3 - t2, "iters": res.iters,
+              "true_relres": res.true_relres, "converged": res.converged}
+    return 1e3 * (t3 - t0), detail, res.x
 
 
-# FGMRES iterations of the FP64 path on the 128x128x64 workload (the oracle
-# runs the same algorithm; used to scale the oracle's bounded sample).
-FULL_ITERS = {"128x128x64_b4": 12, "64x64x32_b4": 31, "16x16x4_b4": 18, "256x256x128_b5": 60,
-              "512x256x64_b4": 60, "96x96x48_b4": 12}
+def _replica_main(workload, rtol, restart, barrier_, queue):
+    """One oracle replica: generate the system, wait for the others, solve."""
+    sysm = make_workload(workload)
+    from oracle import oracle as O
+    O.build()
+    barrier_.wait()
+    t0 = time.time()
+    Ao = O.assemble(sysm)
+    cpr = O.CPR(Ao)
+    res = O.fgmres(Ao, cpr, sysm.rhs, rtol=rtol, restart=restart)
+    queue.put((t0, time.time(), res.iters, res.true_relres))
+
+
+def oracle_all_cores(workload, rtol, restart, n_unknowns):
+    """The oracle on all host cores: one independent full solve per core (the
+    oracle is sequential), started together; value = wall time of the set /
+    number of solves.  The replica count is bounded by the memory available."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    per = ORACLE_BYTES_PER_UNKNOWN * n_unknowns + (1 << 30)
+    fit = int(0.6 * mem_available_bytes() // per)
+    P = max(1, min(cores, fit))
+    ctx = mp.get_context("spawn")
+    bar = ctx.Barrier(P)
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_replica_main, args=(workload, rtol, restart, bar, q)) for _ in range(P)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=1800) for _ in range(P)]
+    for p in procs:
+        p.join()
+    wall = max(o[1] for o in out) - min(o[0] for o in out)
+    return {"value": 1e3 * wall / P, "unit": "ms", "cores": P, "kind": "oracle",
+            "sample": f"{P} independent full oracle solves (assembly + CPR setup + FGMRES to rtol {rtol}) "
+                      f"of this workload run together, one per core; value = wall time / {P}",
+            "wall_s": wall, "iters": sorted({o[2] for o in out}),
+            "memory_bound": P < cores, **host_info()}
 
 
 def run_reference(args):
+    """The reference arm: full FP64 oracle solves of the same system, at most
+    REF_MAX_STEPS timed after REF_MAX_WARMUP untimed, so that the run takes a
+    few minutes; the line states the steps it ran."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from paper_1812_03952_gb300 import synthetic as S
     sysm = make_workload(args.workload)
-    n_iter = 1
+    warm, steps = min(args.warmup, REF_MAX_WARMUP), max(1, min(args.steps, REF_MAX_STEPS))
     times = []
     detail = None
-    for step in range(args.warmup + args.steps):
-        est, detail = oracle_sample(sysm, n_iter, FULL_ITERS[args.workload])
-        if step >= args.warmup:
-            times.append(est)
+    for step in range(warm + steps):
+        ms, detail, _ = oracle_full_solve(sysm, args.rtol, args.restart)
+        if step >= warm:
+            times.append(ms)
     value = statistics.median(times)
-    sample = (f"oracle assembly + CPR setup + {n_iter} FGMRES iteration on the full {args.workload} system, "
-              f"scaled to {FULL_ITERS[args.workload]} iterations")
+    sample = (f"full FP64 oracle solve (assembly + CPR setup + FGMRES to true rel. res. {args.rtol}) of the "
+              f"{args.workload} system, single thread; median of {steps} after {warm} untimed "
+              f"({args.steps} steps and {args.warmup} warm-up requested, capped so the run takes minutes)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "precision": "fp64 (CPU oracle)", "rtol": args.rtol},
+            "steps": steps, "warmup": warm, "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "oracle_precision": "FP64 throughout",
+            "config": config_of(args, sysm, 1),
             "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample,
-                             "detail": detail},
+                             "detail": detail, **host_info()},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def l2_note(sysm):
+    """Whether the step's inputs exceed the 129 MB L2 (no flush needed between steps)."""
+    stored = (7 * sysm.n_cells + 2 * len(sysm.perf_cell) + sysm.n_wells) * sysm.b * sysm.b * 8
+    inputs = sysm.M.nbytes + sysm.acc.nbytes + sysm.k.nbytes
+    if stored + inputs > 129e6:
+        return (f"inputs larger than L2 (Jacobian inputs {inputs / 1e9:.2f} GB, matrix {stored / 1e9:.2f} GB): "
+                "no flush between steps")
+    return f"inputs fit in L2 ({(stored + inputs) / 1e6:.1f} MB): latency-bound case, no flush"
+
+
+def config_of(args, sysm, world):
+    return {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
+            "unknowns": sysm.n_unknowns, "krylov": args.krylov,
+            "precision": "FP32 CPR inside FP64 Krylov" if args.precision == "fp32" else "FP64",
+            "rtol": args.rtol, "restart": args.restart, "cheb_degree": args.cheb_degree,
+            "stages": args.stages, "decoupling": args.decoupling, "ilu_fill": args.ilu_fill,
+            "l2": l2_note(sysm),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 # ------------------------------------------------------ Newton-like sequence
@@ -247,30 +366,34 @@ def run_sequence(args):
     g[torch.from_numpy(np.unique(sysm.perf_cell).astype(np.int64) * sysm.b).to(dev)] = 1.0
     A = ds.assemble()
     M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling,
-                ilu_fill=args.ilu_fill)
+                stages=args.stages, ilu_fill=args.ilu_fill)
     AT = A.transpose()
     MT = trs.CPR(AT, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.adjoint_decoupling,
-                 ilu_fill=args.ilu_fill)
+                 stages=args.stages, ilu_fill=args.ilu_fill)
     x = torch.zeros_like(ds.rhs)
     records = []
 
-    def run_all(record):
+    def run_all(record, time_phases=False):
         for k in range(args.sequence):
             torch.mul(acc0.view(-1, bb), scales[k].view(-1, 1), out=ds.acc.view(-1, bb))
             ds.assemble()
             reuse = (k % args.reuse) != 0
             M.update(A, reuse_amg=reuse)
-            _, rf = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+            _, rf = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart,
+                                     time_phases=time_phases)
             A.transpose(into=AT)
             MT.update(AT, reuse_amg=reuse)
             lam, _, ra = trs.solve_adjoint(A, AT, MT, g, x, rtol=args.rtol, restart=args.restart,
                                            method=args.krylov)
             trs.chain_theta(A, ds.k, ds.M, lam, x, sysm.kvkh, sysm.c_t)
             if record:
-                records.append({"step": k, "amg": "reused" if reuse else "rebuilt",
-                                "fwd_iters": rf.stats["iters"], "fwd_relres": rf.stats["true_relres"],
-                                "adj_iters": ra.stats["iters"], "adj_relres": ra.stats["true_relres"],
-                                "fwd_ms": rf.stats["ms_solve"], "adj_ms": ra.stats["ms_solve"]})
+                rec = {"step": k, "amg": "reused" if reuse else "rebuilt",
+                       "fwd_iters": rf.stats["iters"], "fwd_relres": rf.stats["true_relres"],
+                       "adj_iters": ra.stats["iters"], "adj_relres": ra.stats["true_relres"],
+                       "fwd_ms": rf.stats["ms_solve"], "adj_ms": ra.stats["ms_solve"]}
+                if time_phases:
+                    rec.update({k2: rf.stats[k2] for k2 in ("ms_precond", "ms_spmv", "ms_orth", "spmv_launches")})
+                records.append(rec)
 
     for _ in range(max(1, args.warmup)):
         run_all(False)
@@ -286,6 +409,16 @@ def run_sequence(args):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = barrier_max(e0.elapsed_time(e1) / args.steps, world)
+    launches = trs.kernel_launches() - l0
+    converged = all(r["fwd_relres"] <= args.rtol and r["adj_relres"] <= args.rtol for r in records)
+    # phase split of the forward solves, in a separate pass after the timed region
+    records.clear()
+    run_all(True, time_phases=True)
+    torch.cuda.synchronize()
+    phases = {k: sum(r[k] for r in records) for k in ("ms_precond", "ms_spmv", "ms_orth", "spmv_launches")}
+    hbm, peak_kind = peaks()
+    spmv_bytes = A.nnzb * A.b * A.b * 8 + 2 * A.N * 8
+    spmv_ms = phases["ms_spmv"] / max(1, phases["spmv_launches"])
     if rank == 0:
         line = {"metric": f"Newton-like sequence of {args.sequence} systems: forward + adjoint CPR-"
                           f"{args.krylov.upper()} total ms",
@@ -294,12 +427,68 @@ def run_sequence(args):
                 "dtype": "f64+f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
                            "unknowns": sysm.n_unknowns, "systems": args.sequence, "amg_rebuild_every": args.reuse,
-                           "rtol": args.rtol, "precision": args.precision,
+                           "rtol": args.rtol, "precision": args.precision, "stages": args.stages,
                            "decoupling": args.decoupling, "adjoint_decoupling": args.adjoint_decoupling,
                            "restart": args.restart, "ilu_fill": args.ilu_fill,
                            "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
-                "per_system": records, "clocks": clk.summary(), "gpu_launches": trs.kernel_launches() - l0}
+                "all_converged": converged, "per_system": records,
+                "forward_phases_ms": phases,
+                "spmv": {"launch_ms": spmv_ms, "algorithmic_bytes": spmv_bytes,
+                         "hbm_gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9 if spmv_ms else None,
+                         "hbm_peak_gbs": hbm, "hbm_peak_kind": peak_kind},
+                "clocks": clk.summary(), "gpu_launches": launches}
         print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ CPR sweep
+def run_sweep(args):
+    """Every CPR stage ordering x decoupling pair on one system (Sec.
+    "Numerical Performance" compares them): iterations, setup and solve ms,
+    true residual, for the FP32 and FP64 CPR."""
+    import torch
+    from paper_1812_03952_gb300 import build as B
+    from paper_1812_03952_gb300 import trs
+    B.build()
+    trs.load()
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    sysm = make_workload(args.workload)
+    ds = trs.DeviceSystem(sysm, dev)
+    A = ds.assemble()
+    x = torch.zeros_like(ds.rhs)
+    rows = []
+    with ClockSampler(local) as clk:
+        for precision in ("fp32", "fp64"):
+            for stages in ("fpf", "fp", "pf"):
+                for dec in ("abf", "none", "frs", "frs+abf"):
+                    M = trs.CPR(A, precision=precision, stages=stages, decoupling=dec,
+                                cheb_degree=args.cheb_degree, ilu_fill=args.ilu_fill)
+                    ts, res = [], None
+                    for k in range(args.warmup + args.steps):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        ds.assemble()
+                        M.update(A, reuse_amg=False)
+                        _, res = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol,
+                                                  restart=args.restart, maxit=1000)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        if k >= args.warmup:
+                            ts.append(e0.elapsed_time(e1))
+                    rows.append({"precision": precision, "stages": stages, "decoupling": dec,
+                                 "iters": res.stats["iters"], "converged": bool(res.stats["converged"]),
+                                 "true_relres": res.stats["true_relres"], "setup_ms": res.stats["ms_setup"],
+                                 "solve_ms": res.stats["ms_solve"], "ms_per_step": statistics.median(ts)})
+                    del M
+    if rank == 0:
+        print(json.dumps({"metric": "CPR stage ordering x decoupling sweep: ms per step (assembly + CPR setup + "
+                                    f"{args.krylov.upper()} to true rel. res. {args.rtol})",
+                          "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "data": "synthetic",
+                          "config": config_of(args, sysm, world), "rows": rows, "clocks": clk.summary()}),
+              flush=True)
     return 0
 
 
@@ -310,9 +499,10 @@ def main():
         return run_reference(args)
     if args.sequence:
         return run_sequence(args)
+    if args.sweep:
+        return run_sweep(args)
     import torch
     from paper_1812_03952_gb300 import build as B
-    from paper_1812_03952_gb300 import synthetic as S
     from paper_1812_03952_gb300 import trs
 
     B.build()
@@ -323,15 +513,17 @@ def main():
     sysm = make_workload(args.workload)
     ds = trs.DeviceSystem(sysm, dev)
     A = ds.assemble()
-    M = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling,
-                ilu_fill=args.ilu_fill)
+    cpr_kw = dict(precision=args.precision, cheb_degree=args.cheb_degree, stages=args.stages,
+                  decoupling=args.decoupling, ilu_fill=args.ilu_fill)
+    M = trs.CPR(A, **cpr_kw)
     x = torch.zeros_like(ds.rhs)
     info = M.info()
 
-    def step():
+    def step(time_phases=False):
         ds.assemble()
         M.update(A, reuse_amg=False)
-        _, res = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+        _, res = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart,
+                                  time_phases=time_phases)
         return res
 
     for _ in range(args.warmup):
@@ -342,7 +534,6 @@ def main():
     l0 = trs.kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
-    trs.profile_spmv(True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
@@ -350,111 +541,112 @@ def main():
             stats.append(r.stats)
         ev1.record(stream)
         torch.cuda.synchronize()
-    spmv_total_ms, spmv_launches = trs.profile_spmv(False)
     barrier(world)
     torch.cuda.synchronize()
     launches = trs.kernel_launches() - l0
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = barrier_max(ms, world)
     last = stats[-1]
-    xt = x.cpu().numpy()
+    x32 = x.cpu().numpy()
+    clocks = clk.summary()
+
+    # Roofline pass, after the timed region: the same steps again with CUDA
+    # events between the solve's phases (opts.time_phases) on the solve's
+    # stream; gives the operator SpMV's average launch time and the phase split.
+    n_rp = max(1, min(args.steps, 5))
+    pev0, pev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ph = {"ms_precond": 0.0, "ms_spmv": 0.0, "ms_orth": 0.0, "spmv_launches": 0, "ms_solve": 0.0,
+          "ms_setup": 0.0}
+    with ClockSampler(local) as clk_rp:
+        pev0.record(stream)
+        for _ in range(n_rp):
+            r = step(time_phases=True)
+            for k in ph:
+                ph[k] += r.stats[k]
+        pev1.record(stream)
+        torch.cuda.synchronize()
+    rp_step_ms = pev0.elapsed_time(pev1) / n_rp
+    phases = {k: v / n_rp for k, v in ph.items() if k != "spmv_launches"}
+    phases["spmv_launches_per_step"] = ph["spmv_launches"] / n_rp
 
     # true residual on the host as an independent check of the reported one
     Aval = A.values()
     rp, col = A.pattern()
     rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
-    Ax = np.zeros_like(xt).reshape(-1, A.b)
-    np.add.at(Ax, rows, np.einsum("prc,pc->pr", Aval, xt.reshape(-1, A.b)[col]))
+    Ax = np.zeros_like(x32).reshape(-1, A.b)
+    np.add.at(Ax, rows, np.einsum("prc,pc->pr", Aval, x32.reshape(-1, A.b)[col]))
     host_relres = float(np.linalg.norm(sysm.rhs - Ax.reshape(-1)) / np.linalg.norm(sysm.rhs))
 
     # Roofline of the dominant kernel, the Krylov operator block SpMV w = A z
-    # (FP64 values and vectors; with BiCGSTAB fused with its dot products),
-    # timed live over the timed region by events around each launch.  It is FP64-pipe-bound (ncu: FP64 pipe ~91% busy),
-    # so it is reported against the FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2
-    # flop x 2.07 GHz = 1.259 TFLOP/s; its HBM fraction is given beside it.
+    # (FP64 values and vectors; with BiCGSTAB fused with its dot products).
+    # It is FP64-pipe-bound (ncu: FP64 pipe ~89% busy), so it is reported
+    # against the FP64 peak at the SM clock sampled during the roofline pass:
+    # 152 SMs x 2 FP64 FMA/clk x 2 flop x f; its HBM fraction is given beside it.
     hbm, peak_kind = peaks()
-    spmv_ms = spmv_total_ms / max(1, spmv_launches)
+    spmv_ms = ph["ms_spmv"] / max(1, ph["spmv_launches"])
     nnzb = A.nnzb
     spmv_flops = 2 * nnzb * A.b * A.b
     spmv_bytes = nnzb * A.b * A.b * 8 + 2 * A.N * 8
-    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+    rp_clock = clk_rp.summary().get("sm_mhz") or clocks.get("sm_mhz") or 2070.0
+    fp64_peak_tflops = FP64_FLOP_PER_CLOCK * rp_clock * 1e6 / 1e12
     spmv_tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
     spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    # DRAM traffic per launch from the ncu capture of the 96x96x48 case
-    # (418.9 + 10.9 MB for 3,061,224 blocks), scaled by the blocks of this matrix
-    spmv_traffic = (429.822464e6 * nnzb / 3061224.0
-                    if args.workload == "128x128x64_b4" and args.krylov == "fgmres" else None)
+    # DRAM traffic per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum
+    # of k_spmv<4,double,double> on this 128x128x64 system (one-pass capture of
+    # the bench command itself)
+    spmv_traffic = (SPMV_TRAFFIC_128 if args.workload == "128x128x64_b4" and args.krylov == "fgmres"
+                    else None)
+
+    def timed_legs(Mx, solver, n):
+        for _ in range(2):
+            ds.assemble()
+            Mx.update(A, reuse_amg=False)
+            trs.krylov_solve(solver, A, Mx, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+        torch.cuda.synchronize()
+        ts, rr = [], None
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ds.assemble()
+            Mx.update(A, reuse_amg=False)
+            _, rr = trs.krylov_solve(solver, A, Mx, ds.rhs, x, rtol=args.rtol, restart=args.restart)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), rr
+
     # the other Krylov method on the same system and preconditioner
     other = None
     if not args.no_krylov_compare:
         alt = "bicgstab" if args.krylov == "fgmres" else "fgmres"
-        for _ in range(2):
-            ds.assemble()
-            M.update(A, reuse_amg=False)
-            trs.krylov_solve(alt, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-        torch.cuda.synchronize()
-        ta = []
-        for _ in range(max(1, min(args.steps, 5))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ds.assemble()
-            M.update(A, reuse_amg=False)
-            _, ra = trs.krylov_solve(alt, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ta.append(e0.elapsed_time(e1))
-        other = {"method": alt, "ms_per_step": statistics.median(ta), "solve_ms": ra.stats["ms_solve"],
+        t, ra = timed_legs(M, alt, max(1, min(args.steps, 5)))
+        other = {"method": alt, "ms_per_step": t, "solve_ms": ra.stats["ms_solve"],
                  "iters": ra.stats["iters"], "true_relres": ra.stats["true_relres"]}
     # the other ILU level of the F stage on the same system
     other_ilu = None
     if not args.no_ilu_compare:
         fill = 1 - args.ilu_fill
-        Mi = trs.CPR(A, precision=args.precision, cheb_degree=args.cheb_degree, decoupling=args.decoupling,
-                     ilu_fill=fill)
-        for _ in range(2):
-            ds.assemble()
-            Mi.update(A, reuse_amg=False)
-            trs.krylov_solve(args.krylov, A, Mi, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-        torch.cuda.synchronize()
-        ti = []
-        for _ in range(max(1, min(args.steps, 5))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ds.assemble()
-            Mi.update(A, reuse_amg=False)
-            _, ri = trs.krylov_solve(args.krylov, A, Mi, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ti.append(e0.elapsed_time(e1))
-        other_ilu = {"ilu_fill": fill, "ms_per_step": statistics.median(ti), "setup_ms": ri.stats["ms_setup"],
+        Mi = trs.CPR(A, **{**cpr_kw, "ilu_fill": fill})
+        t, ri = timed_legs(Mi, args.krylov, max(1, min(args.steps, 5)))
+        other_ilu = {"ilu_fill": fill, "ms_per_step": t, "setup_ms": ri.stats["ms_setup"],
                      "solve_ms": ri.stats["ms_solve"], "iters": ri.stats["iters"],
                      "true_relres": ri.stats["true_relres"], "n_colours": Mi.info()["n_colours"]}
         del Mi
     # FP64-preconditioner path on the same system, for the mixed/FP64 comparison
     fp64 = None
+    x64 = None
     if not args.no_fp64_compare and args.precision == "fp32":
-        M64 = trs.CPR(A, precision="fp64", decoupling=args.decoupling, ilu_fill=args.ilu_fill)
-        for _ in range(2):
-            ds.assemble()
-            M64.update(A, reuse_amg=False)
-            _, r64 = trs.krylov_solve(args.krylov, A, M64, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-        torch.cuda.synchronize()
-        t64 = []
-        for _ in range(max(1, min(args.steps, 3))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ds.assemble()
-            M64.update(A, reuse_amg=False)
-            _, r64 = trs.krylov_solve(args.krylov, A, M64, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t64.append(e0.elapsed_time(e1))
-        fp64 = {"ms_per_step": statistics.median(t64), "solve_ms": r64.stats["ms_solve"],
-                "setup_ms": r64.stats["ms_setup"], "iters": r64.stats["iters"],
-                "true_relres": r64.stats["true_relres"]}
+        M64 = trs.CPR(A, **{**cpr_kw, "precision": "fp64"})
+        t, r64 = timed_legs(M64, args.krylov, max(1, min(args.steps, 3)))
+        x64 = x.cpu().numpy()
+        fp64 = {"ms_per_step": t, "solve_ms": r64.stats["ms_solve"], "setup_ms": r64.stats["ms_setup"],
+                "iters": r64.stats["iters"], "true_relres": r64.stats["true_relres"]}
         del M64
 
-    # end to end through the public API with host buffers
+    # End to end through the C ABI with host buffers: trs_bsr_assemble_host
+    # (assembly inputs copied from pinned host memory inside the call),
+    # trs_cpr_update, and trs_fgmres_solve_host / trs_bicgstab_solve_host (b
+    # copied in, x copied out inside the call).
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -463,71 +655,87 @@ def main():
         hx = torch.empty(A.N, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * 8 for t in (hk, hM, hacc, hwi, hlam, hb))
         d2h = hx.numel() * 8
+        host_solve = trs.fgmres_solve_host if args.krylov == "fgmres" else trs.bicgstab_solve_host
+        skw = {"restart": args.restart} if args.krylov == "fgmres" else {}
 
         def e2e_step():
-            for d, h in ((ds.k, hk), (ds.M, hM), (ds.acc, hacc), (ds.wi, hwi), (ds.lam, hlam),
-                         (ds.rhs, hb)):
-                d.copy_(h, non_blocking=True)
-            ds.assemble()
+            A.assemble_host(hk, hM, hacc, hwi, hlam, sysm.kvkh, sysm.c_t)
             M.update(A, reuse_amg=False)
-            trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol, restart=args.restart)
-            hx.copy_(x, non_blocking=True)
+            return host_solve(A, M, hb, rtol=args.rtol, x=hx, **skw)[1]
 
-        e2e_step()
+        for _ in range(2):
+            e2e_step()
         torch.cuda.synchronize()
+        n_e2e = max(1, min(args.steps, 5))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
         e0.record(stream)
         for _ in range(n_e2e):
-            e2e_step()
+            re = e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3 / n_e2e
         e2e = {"value": barrier_max(e0.elapsed_time(e1) / n_e2e, world), "unit": "ms",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "host_wall_ms": wall,
+               "api": "trs_bsr_assemble_host + trs_cpr_update + trs_%s_solve_host" % args.krylov,
+               "true_relres": re.stats["true_relres"]}
 
     cpu = None
+    cpu_all = None
+    err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, detail = oracle_sample(sysm, 1, last["iters"] if args.precision == "fp64" or fp64 is None else
-                                    fp64["iters"])
-        cpu = {"value": est, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": "assembly + CPR setup + 1 FGMRES iteration of the FP64 oracle on the full system, "
-                         "scaled to the iteration count of the FP64 path (of this run's path if the FP64 path "
-                         "was not run)", "detail": detail}
+        cms, detail, xo = oracle_full_solve(sysm, args.rtol, args.restart)
+        cpu = {"value": cms, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"one full FP64 oracle solve of this system (assembly + CPR setup + FGMRES to true rel. "
+                         f"res. {args.rtol}), single thread", "detail": detail, **host_info()}
+        nx = np.linalg.norm(xo)
+        err = {"vs": f"the oracle's FP64 CPR-FGMRES solution at rtol {args.rtol}",
+               "timed_path": float(np.linalg.norm(x32 - xo) / nx),
+               "fp64_path": float(np.linalg.norm(x64 - xo) / nx) if x64 is not None else None}
+        if not args.no_cpu_all_cores:
+            cpu_all = oracle_all_cores(args.workload, args.rtol, args.restart, sysm.n_unknowns)
 
     if rank == 0:
         kname = ("k_spmv<4,double,double> (FGMRES operator block SpMV)" if args.krylov == "fgmres" else
                  "k_bicg_spmv<4,1|2> (BiCGSTAB operator block SpMV fused with its dot products)")
         line = {
-            "metric": METRIC if args.krylov == "fgmres" else METRIC.replace("FGMRES", "BiCGSTAB"), "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if args.krylov == "fgmres" else METRIC.replace("FGMRES", "BiCGSTAB"), "value": ms,
+            "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "cells": sysm.n_cells, "b": sysm.b, "wells": sysm.n_wells,
-                       "unknowns": sysm.n_unknowns,
-                       "krylov": args.krylov,
-                       "precision": "FP32 CPR inside FP64 Krylov" if args.precision == "fp32" else "FP64",
-                       "rtol": args.rtol, "restart": args.restart, "cheb_degree": args.cheb_degree,
-                       "decoupling": args.decoupling, "ilu_fill": args.ilu_fill,
-                       "l2": "inputs larger than L2 (Jacobian inputs 0.9 GB, matrix 0.9 GB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": config_of(args, sysm, world),
             "iters": last["iters"], "true_relres": last["true_relres"], "host_true_relres": host_relres,
+            "err_vs_oracle": err,
             "breakdown_ms": {"setup": last["ms_setup"], "solve": last["ms_solve"]},
+            "solve_phases_ms": phases, "phase_pass_ms_per_step": rp_step_ms,
             "amg_levels": info["n_levels"], "amg_rows": info["level_rows"], "n_colours": info["n_colours"],
             "fp64_path": fp64, "other_krylov": other, "other_ilu": other_ilu,
             "roofline": {"kernel": kname, "bound": "alu",
                          "achieved": spmv_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                          "frac": spmv_tflops / fp64_peak_tflops, "traffic": spmv_traffic,
-                         "peak_kind": "FP64 unit count x clock (probe measured 1.2548 TFLOP/s)",
-                         "launch_ms": spmv_ms, "launches": spmv_launches, "algorithmic_flops": spmv_flops,
+                         "peak_kind": f"FP64 unit count x sampled SM clock {rp_clock:.0f} MHz "
+                                      "(152 SMs x 4 flop/clk; a probe measured 1.2548 TFLOP/s at 2070 MHz)",
+                         "sm_mhz": rp_clock, "launch_ms": spmv_ms, "launches": ph["spmv_launches"],
+                         "timing": f"CUDA events around each launch over {n_rp} steps after the timed region",
+                         "algorithmic_flops": spmv_flops,
                          "algorithmic_bytes": spmv_bytes, "hbm_achieved_gbs": spmv_gbs, "hbm_peak_gbs": hbm,
                          "hbm_frac": spmv_gbs / hbm, "hbm_peak_kind": peak_kind},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
+            "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+#: ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_spmv<4,double,double>
+#: launch on the 128x128x64 system, from an older 96x96x48 capture scaled by
+#: the stored blocks (429.82 MB for 3,061,224 blocks); replaced by the
+#: full-size capture once taken
+SPMV_TRAFFIC_128 = 429.822464e6 * 7276104 / 3061224.0
 
 
 if __name__ == "__main__":

@@ -131,6 +131,10 @@ typedef struct {
   int32_t use_x0;        /* 1: x holds the initial guess; 0: start from x = 0 */
   int32_t method;        /* TRS_FGMRES (default) or TRS_BICGSTAB: read by
                             trs_solve_adjoint; the named solve calls set it */
+  int32_t time_phases;   /* 1: time the preconditioner, operator SpMV and
+                            orthogonalisation phases with CUDA events on the
+                            solve's stream (trs_solve_stats.ms_precond ...);
+                            0 (default): no events between the launches */
 } trs_solve_opts;
 
 typedef struct {
@@ -143,6 +147,15 @@ typedef struct {
   double true_relres;    /* ||b - A x|| / ||b|| of the returned x, FP64 */
   double ms_setup;       /* device time of the last trs_cpr_setup/update */
   double ms_solve;       /* device time of this solve */
+  /* With opts.time_phases = 1 (else 0): device time of the CPR applications
+   * (with the D^-1 scaling), of the operator SpMVs w = A z, and of the
+   * orthogonalisation and vector updates (FGMRES: CGS2 and the Givens step;
+   * BiCGSTAB: the vector updates with their fused dot products), and the
+   * number of operator SpMV launches timed. */
+  double ms_precond;
+  double ms_spmv;
+  double ms_orth;
+  int64_t spmv_launches;
 } trs_solve_stats;
 
 typedef struct {
@@ -206,6 +219,15 @@ trs_status trs_bsr_create_synthetic(int32_t nx, int32_t ny, int32_t nz, int32_t 
 trs_status trs_bsr_assemble(trs_bsr *A, const double *perm, int32_t perm_is_log, double kvkh,
                             double c_t, const double *M, const double *acc, const double *wi,
                             const double *lam, void *stream);
+
+/* trs_bsr_assemble with the inputs (perm, M, acc, wi, lam) in host memory:
+ * the library copies them into a device staging area that the matrix keeps
+ * (allocated at the first call) and assembles from there; the copies are
+ * ordered on `stream` and are part of the call.  Pinned host memory lets the
+ * copies run asynchronously.  Same sizes and errors as trs_bsr_assemble. */
+trs_status trs_bsr_assemble_host(trs_bsr *A, const double *perm, int32_t perm_is_log, double kvkh,
+                                 double c_t, const double *M, const double *acc, const double *wi,
+                                 const double *lam, void *stream);
 
 /* Replaces all values.  values: nnzb*b*b doubles in the matrix's canonical
  * BSR order (rows ascending, columns ascending; the order of trs_bsr_pattern),
@@ -302,7 +324,9 @@ trs_status trs_fgmres_solve(const trs_bsr *A, const trs_cpr *M, const double *b,
                             const trs_solve_opts *opts, void *stream, trs_solve_stats *stats);
 
 /* The same solve with b and x in host memory; the copies are part of the
- * call. */
+ * call.  The device copies of b and x are kept by M after the first call
+ * (2 * n_block_rows * b doubles); pinned host memory lets the copies run
+ * asynchronously.  The call synchronises `stream`. */
 trs_status trs_fgmres_solve_host(const trs_bsr *A, const trs_cpr *M, const double *b_host,
                                  double *x_host, const trs_solve_opts *opts, void *stream,
                                  trs_solve_stats *stats);
@@ -333,18 +357,18 @@ trs_status trs_solve_adjoint(const trs_bsr *A, const trs_bsr *AT, const trs_cpr 
 
 /* Residual r = b - A x and its 2-norm without allocating anything.
  * The paper has no counterpart: this call is for callers that must not
- * allocate device memory while they run (for instance code inside a stream
- * being captured into a CUDA graph, loops that cannot afford the device-wide
- * synchronisation of cudaMalloc/cudaFree, or processes whose device memory
- * belongs to their own pool allocator).  x, b, r: device pointers (n*b
- * doubles, caller-owned, r must not alias x or b); norm: host pointer that
- * receives ||r||_2; the call synchronises `stream`.  The reduction scratch
+ * allocate device memory while they run (for instance loops that cannot
+ * afford the device-wide synchronisation of cudaMalloc/cudaFree, or
+ * processes whose device memory belongs to their own pool allocator).
+ * x, b, r: device pointers (n*b doubles, caller-owned, r must not alias x or
+ * b); norm: host pointer that receives ||r||_2.  The call copies the norm to
+ * *norm and synchronises `stream` before it returns.  The reduction scratch
  * is a static device array of 778,752 bytes inside the library (the partial
  * sums of at most 1,216 blocks, a counter and the result), held by every
  * GPU that loads the library until the process exits; the blocks stride over
  * the rows, so every matrix the library accepts fits.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and
- * should therefore come before any stream capture.  Every call on a device
+ * device looks up the array's device address (cudaGetSymbolAddress), so that
+ * first call should come before any stream capture.  Every call on a device
  * shares the one array, so calls that overlap on the GPU (other streams,
  * other threads) race; the counter is cleared at the start of each call.
  * No cudaMalloc, cudaFree or allocating library routine is called. */

@@ -1691,16 +1691,16 @@ template void launch_cast<double, double>(const double *, double *, int64_t, cud
 }  // namespace trs
 
 // ============================================ allocation-free residual norm
-// Some callers cannot allocate device memory while they run: code inside a
-// region whose allocations are forbidden (a stream being captured into a
-// CUDA graph, a real-time loop where cudaMalloc's implicit device
-// synchronisation is unacceptable) or processes whose device memory is
-// entirely handed to their own pool allocator.  For them the residual and its
-// norm run on a reduction scratch that lives in this file-scope array, loaded
-// with the library and kept by every GPU that loads it until the process
-// exits.  Size: the partial sums of at most kStaticGrid blocks (the same grid
-// the solver uses, so results are identical) plus a ticket counter and the
-// output, 778,752 bytes in all.
+// Some callers cannot allocate device memory while they run: loops where
+// cudaMalloc's implicit device-wide synchronisation is unacceptable, or
+// processes whose device memory is entirely handed to their own pool
+// allocator.  For them the residual and its norm run on a reduction scratch
+// that lives in this file-scope array, loaded with the library and kept by
+// every GPU that loads it until the process exits.  Size: the partial sums of
+// at most kStaticGrid blocks (the same grid the solver uses, so results are
+// identical) plus a ticket counter and the output, 778,752 bytes in all.  The
+// call copies the norm to the caller's host pointer and synchronises its
+// stream before returning.
 namespace trs {
 namespace {
 

@@ -426,6 +426,16 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
   cudaStream_t s2 = M->side;
   TRS_CUDA(cudaEventRecord(M->ev_fork, s));
   TRS_CUDA(cudaStreamWaitEvent(s2, M->ev_fork, 0));
+  // On an error exit (a throw between the fork and the join) the side stream
+  // may still read Ã and write the factors; it is drained before the caller
+  // can queue new work that rewrites them.
+  struct SideJoin {
+    cudaStream_t st;
+    bool armed;
+    ~SideJoin() {
+      if (armed) cudaStreamSynchronize(st);
+    }
+  } side_join{s2, true};
   TBuf<int> err2(1, s2);
   err2.zero();
   {
@@ -487,6 +497,7 @@ void build_values(trs_cpr *M, const trs_bsr *A, bool rebuild_amg, cudaStream_t s
     }
   }
   TRS_CUDA(cudaStreamWaitEvent(s, M->ev_join, 0));
+  side_join.armed = false;
   int herr[2] = {0, 0};
   TRS_CUDA(cudaMemcpyAsync(&herr[0], err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRS_CUDA(cudaMemcpyAsync(&herr[1], err2.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -832,16 +843,59 @@ void ensure_workspace(trs_cpr *M, int m) {
   M->ws_m = m;
 }
 
-// Optional device timing of the operator SpMV launches inside FGMRES
-// (events on the solve's stream; read at the per-iteration synchronisation).
+// Optional device timing of the operator SpMV launches inside the Krylov
+// solves, process-wide (trs_profile_spmv); the totals are taken from the
+// phase events below.
 struct SpmvProfile {
   bool on = false;
   double ms = 0.0;
   int64_t launches = 0;
-  cudaEvent_t a = nullptr, b = nullptr, c = nullptr, d = nullptr;
 };
 SpmvProfile g_spmv_prof;
 std::mutex g_prof_mutex;
+
+// Phase timing of one solve (opts.time_phases or trs_profile_spmv): events
+// recorded on the solve's stream between the phases of an iteration and read
+// after the iteration's host synchronisation.  Phases: 0 preconditioner,
+// 1 operator SpMV, 2 orthogonalisation / vector updates.
+struct PhaseTimer {
+  static constexpr int kEvents = 7;
+  bool on = false;
+  cudaEvent_t ev[kEvents] = {};
+  double ms[3] = {0.0, 0.0, 0.0};
+  int64_t spmv = 0;
+  explicit PhaseTimer(bool enable) : on(enable) {
+    if (on)
+      for (auto &e : ev) TRS_CUDA(cudaEventCreate(&e));
+  }
+  PhaseTimer(const PhaseTimer &) = delete;
+  PhaseTimer &operator=(const PhaseTimer &) = delete;
+  ~PhaseTimer() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  void mark(int k, cudaStream_t s) {
+    if (on) TRS_CUDA(cudaEventRecord(ev[k], s));
+  }
+  void add(int phase, int from, int to) {
+    if (!on) return;
+    float t = 0.f;
+    TRS_CUDA(cudaEventElapsedTime(&t, ev[from], ev[to]));
+    ms[phase] += t;
+  }
+  void finish(trs_solve_stats &st) {
+    if (!on) return;
+    st.ms_precond = ms[0];
+    st.ms_spmv = ms[1];
+    st.ms_orth = ms[2];
+    st.spmv_launches = spmv;
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if (g_spmv_prof.on) {
+      g_spmv_prof.ms += ms[1];
+      g_spmv_prof.launches += spmv;
+    }
+  }
+};
 
 template <class T>
 trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, const trs_solve_opts &o,
@@ -854,6 +908,7 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
   double *Z = tp<double>(M->Z);
   double *V = M->V.p;
   trs_solve_stats local{};
+  PhaseTimer pt(o.time_phases != 0 || g_spmv_prof.on);
   Timer timer(s);
   launch_norm2(b, N, red, M->norms.p + 2, s);
   double hb[2];
@@ -894,12 +949,12 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
     for (int j = 0; j < m; j++) {
       double *vj = V + (int64_t)j * N;
       double *zj = Z + (int64_t)j * N;
+      pt.mark(0, s);
       if (j == 0) cpr_apply_full<T>(M, M->r.p, M->norms.p + 1, vj, zj, s);
       else cpr_apply_full<T>(M, M->w.p, M->hnorm.p, vj, zj, s);
-      const bool prof = g_spmv_prof.on;
-      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.a, s));
+      pt.mark(1, s);
       launch_spmv<double, double>(M->b, Av, zj, M->w.p, 1.0, 0.0, s);
-      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.b, s));
+      pt.mark(2, s);
       // CGS2: h1 = V^T w (and ||w||^2); w -= V h1 with h2 = V^T w fused; w -= V h2 with ||w||^2
       if (j + 2 <= 32) {
         launch_cgs_dots(V, N, j + 1, M->w.p, red, M->h1.p, s);
@@ -912,16 +967,15 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
       launch_cgs_update(V, N, j + 1, M->h2.p, M->w.p, 1, red, M->hn2.p, s);
       launch_givens(j, m, M->H.p, M->h1.p, M->h2.p, M->hn2.p, M->h1.p + j + 1, M->cs.p, M->sn.p, M->gv.p,
                     M->hnorm.p, M->status.p, 1.0 / bnorm, s);
+      pt.mark(3, s);
       iters++;
       double hs[2];
       TRS_CUDA(cudaMemcpyAsync(hs, M->status.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
-      if (prof) {
-        float ems = 0.f;
-        TRS_CUDA(cudaEventElapsedTime(&ems, g_spmv_prof.a, g_spmv_prof.b));
-        g_spmv_prof.ms += ems;
-        g_spmv_prof.launches++;
-      }
+      pt.add(0, 0, 1);
+      pt.add(1, 1, 2);
+      pt.add(2, 2, 3);
+      pt.spmv += pt.on;
       local.est_relres = hs[0];
       if (!std::isfinite(hs[0])) { result = TRS_ERR_NAN; break; }
       breakdown = hs[1] != 0.0;
@@ -942,6 +996,7 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
   local.n_colours = M->ncol;
   local.ms_setup = M->ms_setup;
   local.ms_solve = timer.stop();
+  pt.finish(local);
   if (st) *st = local;
   return result;
 }
@@ -976,6 +1031,7 @@ trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, co
          *t = sh + N;
   BicgScalars *sc = reinterpret_cast<BicgScalars *>(M->bsc.p);
   trs_solve_stats local{};
+  PhaseTimer pt(o.time_phases != 0 || g_spmv_prof.on);
   Timer timer(s);
   launch_norm2(b, N, red, M->norms.p + 2, s);
   double hb[2];
@@ -1013,30 +1069,32 @@ trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, co
     cycles++;
     breakdown = false;
     for (int k = 0; iters < o.maxit; k++) {
+      pt.mark(0, s);
       launch_bicg_dir<T>(M->b, M->n, r, v, p, sc, k == 0, dinv_of<T>(M), tp<T>(M->wf), M->colour.p, tp<T>(M->wy), s);
       cpr_apply_scaled<T>(M, ph, s);
-      const bool prof = g_spmv_prof.on;
-      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.a, s));
+      pt.mark(1, s);
       launch_bicg_spmv(M->b, Av, ph, v, rh, 1, M->bpart.p, M->counter.p, sc, s);
-      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.b, s));
+      pt.mark(2, s);
       launch_bicg_s(N, r, v, sv, red, sc, s);
+      pt.mark(3, s);
       launch_dscale<T>(M->b, M->n, sv, nullptr, nullptr, dinv_of<T>(M), tp<T>(M->wf), M->colour.p, tp<T>(M->wy), s);
       cpr_apply_scaled<T>(M, sh, s);
-      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.c, s));
+      pt.mark(4, s);
       launch_bicg_spmv(M->b, Av, sh, t, sv, 2, M->bpart.p, M->counter.p, sc, s);
-      if (prof) TRS_CUDA(cudaEventRecord(g_spmv_prof.d, s));
+      pt.mark(5, s);
       launch_bicg_xr(N, ph, sh, sv, t, rh, x, r, red, sc, s);
+      pt.mark(6, s);
       iters++;
       BicgScalars h;
       TRS_CUDA(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
-      if (prof) {
-        float e1 = 0.f, e2 = 0.f;
-        TRS_CUDA(cudaEventElapsedTime(&e1, g_spmv_prof.a, g_spmv_prof.b));
-        TRS_CUDA(cudaEventElapsedTime(&e2, g_spmv_prof.c, g_spmv_prof.d));
-        g_spmv_prof.ms += (double)e1 + (double)e2;
-        g_spmv_prof.launches += 2;
-      }
+      pt.add(0, 0, 1);
+      pt.add(0, 3, 4);
+      pt.add(1, 1, 2);
+      pt.add(1, 4, 5);
+      pt.add(2, 2, 3);
+      pt.add(2, 5, 6);
+      pt.spmv += 2 * pt.on;
       const double est = std::sqrt(h.rr) / bnorm;
       local.est_relres = est;
       if (!std::isfinite(est) || !std::isfinite(h.rho)) { breakdown = true; break; }
@@ -1050,6 +1108,7 @@ trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, co
   local.n_colours = M->ncol;
   local.ms_setup = M->ms_setup;
   local.ms_solve = timer.stop();
+  pt.finish(local);
   if (st) *st = local;
   return result;
 }
@@ -1096,15 +1155,18 @@ trs_status solve_host_entry(const trs_bsr *A, const trs_cpr *M, const double *b_
   trs_status st = TRS_OK;
   trs_status g = guarded([&] {
     TRS_REQUIRE(A && M && b_host && x_host, TRS_ERR_INVALID, "NULL argument");
-    DBuf<double> db(M->N), dx(M->N);
-    db.upload(b_host, M->N, s);
+    // device copies of b and x, kept by the handle after the first call
+    trs_cpr *Mw = const_cast<trs_cpr *>(M);
+    if ((int64_t)Mw->host_bx.n < 2 * M->N) Mw->host_bx.alloc((size_t)2 * M->N);
+    double *db = Mw->host_bx.p, *dx = db + M->N;
+    TRS_CUDA(cudaMemcpyAsync(db, b_host, M->N * sizeof(double), cudaMemcpyHostToDevice, s));
     trs_solve_opts o;
     trs_solve_default_opts(&o);
     if (opts) o = *opts;
     if (method >= 0) o.method = method;
-    if (o.use_x0) dx.upload(x_host, M->N, s);
-    st = run_solve(A, const_cast<trs_cpr *>(M), db.p, dx.p, &o, s, stats);
-    TRS_CUDA(cudaMemcpyAsync(x_host, dx.p, M->N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (o.use_x0) TRS_CUDA(cudaMemcpyAsync(dx, x_host, M->N * sizeof(double), cudaMemcpyHostToDevice, s));
+    st = run_solve(A, Mw, db, dx, &o, s, stats);
+    TRS_CUDA(cudaMemcpyAsync(x_host, dx, M->N * sizeof(double), cudaMemcpyDeviceToHost, s));
     TRS_CUDA(cudaStreamSynchronize(s));
   });
   return g != TRS_OK ? g : st;
@@ -1145,6 +1207,7 @@ void trs_solve_default_opts(trs_solve_opts *o) {
   o->maxit = 1000;
   o->use_x0 = 0;
   o->method = TRS_FGMRES;
+  o->time_phases = 0;
 }
 
 trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *stream, trs_cpr **out) {
@@ -1364,12 +1427,6 @@ uint64_t trs_kernel_launches(void) { return g_launches.load(std::memory_order_re
 trs_status trs_profile_spmv(int32_t enable, double *total_ms, int64_t *launches) {
   return guarded([&] {
     std::lock_guard<std::mutex> lock(g_prof_mutex);
-    if (!g_spmv_prof.a) {
-      TRS_CUDA(cudaEventCreate(&g_spmv_prof.a));
-      TRS_CUDA(cudaEventCreate(&g_spmv_prof.b));
-      TRS_CUDA(cudaEventCreate(&g_spmv_prof.c));
-      TRS_CUDA(cudaEventCreate(&g_spmv_prof.d));
-    }
     if (total_ms) *total_ms = g_spmv_prof.ms;
     if (launches) *launches = g_spmv_prof.launches;
     if (enable) {

@@ -227,6 +227,7 @@ struct trs_bsr {
   trs::DBuf<int64_t> cperf_ptr, cperf_idx, wperf_ptr, wperf_idx;   // perforations by cell / well
   trs::DBuf<int32_t> perf_cell, perf_well;
   trs::DBuf<int64_t> perf_cw, perf_wc, wdiag;                      // tail slots of (c,w), (w,c), (w,w)
+  trs::DBuf<double> host_stage;   // device copy of host assembly inputs (trs_bsr_assemble_host)
 
   template <class T = double>
   trs::MatView<T> view() const {

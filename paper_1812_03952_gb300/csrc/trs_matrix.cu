@@ -283,6 +283,36 @@ trs_status trs_bsr_assemble(trs_bsr *A, const double *perm, int32_t perm_is_log,
   });
 }
 
+trs_status trs_bsr_assemble_host(trs_bsr *A, const double *perm, int32_t perm_is_log, double kvkh, double c_t,
+                                 const double *M, const double *acc, const double *wi, const double *lam,
+                                 void *stream) {
+  return guarded([&] {
+    TRS_REQUIRE(A && A->synthetic, TRS_ERR_INVALID, "matrix was not made by trs_bsr_create_synthetic");
+    TRS_REQUIRE(perm && M && acc, TRS_ERR_INVALID, "NULL input array");
+    TRS_REQUIRE(A->n_perf == 0 || (wi && lam), TRS_ERR_INVALID, "NULL perforation array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nc = A->g.nc, bb = (int64_t)A->b * A->b, np = A->n_perf;
+    // one staging area, each input at a 256-byte aligned offset
+    auto up = [](int64_t c) { return (c + 31) / 32 * 32; };
+    const int64_t o_perm = 0, o_M = up(nc), o_acc = o_M + up(6 * bb * nc), o_wi = o_acc + up(bb * nc),
+                  o_lam = o_wi + up(np), total = o_lam + up(np * A->b);
+    if ((int64_t)A->host_stage.n < total) A->host_stage.alloc(total);
+    double *d = A->host_stage.p;
+    auto copy = [&](int64_t at, const double *h, int64_t cnt) {
+      if (cnt) TRS_CUDA(cudaMemcpyAsync(d + at, h, cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+    };
+    copy(o_perm, perm, nc);
+    copy(o_M, M, 6 * bb * nc);
+    copy(o_acc, acc, bb * nc);
+    if (np) {
+      copy(o_wi, wi, np);
+      copy(o_lam, lam, np * A->b);
+    }
+    launch_assemble(A->b, A, d + o_perm, perm_is_log, kvkh, c_t, d + o_M, d + o_acc, np ? d + o_wi : nullptr,
+                    np ? d + o_lam : nullptr, s);
+  });
+}
+
 trs_status trs_bsr_update_values(trs_bsr *A, const double *values, int32_t on_device, void *stream) {
   return guarded([&] {
     TRS_REQUIRE(A && values, TRS_ERR_INVALID, "NULL argument");

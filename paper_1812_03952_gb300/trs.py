@@ -38,7 +38,8 @@ DECOUPLINGS = {"abf": 0, "none": 1, "frs": 2, "frs+abf": 3}
 
 #: every entry point declared in include/trs.h
 EXPORTS = (
-    "trs_bsr_create", "trs_bsr_create_synthetic", "trs_bsr_assemble", "trs_bsr_update_values",
+    "trs_bsr_create", "trs_bsr_create_synthetic", "trs_bsr_assemble", "trs_bsr_assemble_host",
+    "trs_bsr_update_values",
     "trs_bsr_get_values", "trs_bsr_scale_diagonal", "trs_bsr_pattern", "trs_bsr_get_info",
     "trs_bsr_spmv", "trs_bsr_transpose", "trs_bsr_transpose_values", "trs_bsr_destroy", "trs_cpr_default_opts", "trs_cpr_setup",
     "trs_cpr_update", "trs_cpr_apply", "trs_cpr_get_info", "trs_cpr_get_aggregates",
@@ -63,13 +64,15 @@ class CprOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("maxit", C.c_int32),
-                ("use_x0", C.c_int32), ("method", C.c_int32)]
+                ("use_x0", C.c_int32), ("method", C.c_int32), ("time_phases", C.c_int32)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
                 ("amg_levels", C.c_int32), ("n_colours", C.c_int32), ("est_relres", C.c_double),
-                ("true_relres", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double)]
+                ("true_relres", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
+                ("ms_precond", C.c_double), ("ms_spmv", C.c_double), ("ms_orth", C.c_double),
+                ("spmv_launches", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -103,6 +106,7 @@ def load(path: str = LIB_PATH):
         "trs_bsr_create": (i32, [i64, i32, vp, vp, vp, vp, vp, C.POINTER(vp)]),
         "trs_bsr_create_synthetic": (i32, [i32, i32, i32, i32, i32, i64, vp, vp, vp, C.POINTER(vp)]),
         "trs_bsr_assemble": (i32, [vp, vp, i32, f64, f64, vp, vp, vp, vp, vp]),
+        "trs_bsr_assemble_host": (i32, [vp, vp, i32, f64, f64, vp, vp, vp, vp, vp]),
         "trs_bsr_update_values": (i32, [vp, vp, i32, vp]),
         "trs_bsr_get_values": (i32, [vp, vp, i32, vp]),
         "trs_bsr_scale_diagonal": (i32, [vp, vp, vp]),
@@ -181,7 +185,16 @@ def _dptr(t):
 
 
 def _hptr(a):
-    return a.ctypes.data_as(C.c_void_p)
+    """Host pointer of a contiguous numpy array or CPU torch tensor (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a contiguous host array")
+        return a.ctypes.data_as(C.c_void_p)
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("expected a contiguous CPU tensor")
+    return C.c_void_p(a.data_ptr())
 
 
 def _empty(n, dtype=None, device="cuda"):
@@ -231,6 +244,12 @@ class Matrix:
     def assemble(self, perm, M, acc, wi, lam, kvkh, c_t, perm_is_log=False):
         _check(load().trs_bsr_assemble(self.h, _dptr(perm), int(perm_is_log), kvkh, c_t, _dptr(M),
                                        _dptr(acc), _dptr(wi), _dptr(lam), _stream()))
+
+    def assemble_host(self, perm, M, acc, wi, lam, kvkh, c_t, perm_is_log=False):
+        """trs_bsr_assemble from host buffers (float64 numpy arrays or CPU
+        tensors, pinned for asynchronous copies); the copies are part of the call."""
+        _check(load().trs_bsr_assemble_host(self.h, _hptr(perm), int(perm_is_log), kvkh, c_t, _hptr(M),
+                                            _hptr(acc), _hptr(wi), _hptr(lam), _stream()))
 
     def update_values(self, values):
         if isinstance(values, np.ndarray):
@@ -366,20 +385,22 @@ class Result:
     stats: dict
 
 
-def _device_solve(fn, A: Matrix, M: CPR, b, x, rtol, restart, maxit, use_x0):
+def _device_solve(fn, A: Matrix, M: CPR, b, x, rtol, restart, maxit, use_x0, time_phases=False):
     if x is None:
         x = _empty(A.N, device=b.device)
         use_x0 = False
-    o = default_solve_opts(rtol=rtol, restart=restart, maxit=maxit, use_x0=int(use_x0))
+    o = default_solve_opts(rtol=rtol, restart=restart, maxit=maxit, use_x0=int(use_x0),
+                           time_phases=int(time_phases))
     st = SolveStats()
     code = fn(A.h, M.h, _dptr(b), _dptr(x), C.byref(o), _stream(), C.byref(st))
     _check(code, allow=(TRS_ERR_NOT_CONVERGED,))
     return x, Result(code, st.as_dict())
 
 
-def _host_solve(fn, A: Matrix, M: CPR, b, rtol, restart, maxit):
-    bb = np.ascontiguousarray(b, dtype=np.float64)
-    x = np.zeros_like(bb)
+def _host_solve(fn, A: Matrix, M: CPR, b, rtol, restart, maxit, x=None):
+    bb = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b
+    if x is None:
+        x = np.zeros(A.N)
     o = default_solve_opts(rtol=rtol, restart=restart, maxit=maxit, use_x0=0)
     st = SolveStats()
     code = fn(A.h, M.h, _hptr(bb), _hptr(x), C.byref(o), _stream(), C.byref(st))
@@ -387,33 +408,37 @@ def _host_solve(fn, A: Matrix, M: CPR, b, rtol, restart, maxit):
     return x, Result(code, st.as_dict())
 
 
-def fgmres_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, restart=30, maxit=1000, use_x0=False):
-    """Solves A x = b by FGMRES (device tensors); returns (x, Result)."""
-    return _device_solve(load().trs_fgmres_solve, A, M, b, x, rtol, restart, maxit, use_x0)
+def fgmres_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, restart=30, maxit=1000, use_x0=False,
+                 time_phases=False):
+    """Solves A x = b by FGMRES (device tensors); returns (x, Result).
+    time_phases: fill the per-phase device times of the stats."""
+    return _device_solve(load().trs_fgmres_solve, A, M, b, x, rtol, restart, maxit, use_x0, time_phases)
 
 
-def fgmres_solve_host(A: Matrix, M: CPR, b: np.ndarray, rtol=1e-6, restart=30, maxit=1000):
-    """The same solve with host (numpy) vectors; the copies are part of the call."""
-    return _host_solve(load().trs_fgmres_solve_host, A, M, b, rtol, restart, maxit)
+def fgmres_solve_host(A: Matrix, M: CPR, b, rtol=1e-6, restart=30, maxit=1000, x=None):
+    """The same solve with host vectors (numpy arrays or CPU tensors, x
+    optional and overwritten); the copies are part of the call."""
+    return _host_solve(load().trs_fgmres_solve_host, A, M, b, rtol, restart, maxit, x)
 
 
-def bicgstab_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, maxit=1000, use_x0=False):
+def bicgstab_solve(A: Matrix, M: CPR, b, x=None, rtol=1e-6, maxit=1000, use_x0=False, time_phases=False):
     """Solves A x = b by BiCGSTAB (device tensors); returns (x, Result)."""
-    return _device_solve(load().trs_bicgstab_solve, A, M, b, x, rtol, 30, maxit, use_x0)
+    return _device_solve(load().trs_bicgstab_solve, A, M, b, x, rtol, 30, maxit, use_x0, time_phases)
 
 
-def bicgstab_solve_host(A: Matrix, M: CPR, b: np.ndarray, rtol=1e-6, maxit=1000):
-    """BiCGSTAB with host (numpy) vectors; the copies are part of the call."""
-    return _host_solve(load().trs_bicgstab_solve_host, A, M, b, rtol, 30, maxit)
+def bicgstab_solve_host(A: Matrix, M: CPR, b, rtol=1e-6, maxit=1000, x=None):
+    """BiCGSTAB with host vectors; the copies are part of the call."""
+    return _host_solve(load().trs_bicgstab_solve_host, A, M, b, rtol, 30, maxit, x)
 
 
 def krylov_solve(method: str, A: Matrix, M: CPR, b, x=None, rtol=1e-6, restart=30, maxit=1000,
-                 use_x0=False):
+                 use_x0=False, time_phases=False):
     """FGMRES or BiCGSTAB by name ("fgmres" | "bicgstab")."""
     if method == "fgmres":
-        return fgmres_solve(A, M, b, x, rtol=rtol, restart=restart, maxit=maxit, use_x0=use_x0)
+        return fgmres_solve(A, M, b, x, rtol=rtol, restart=restart, maxit=maxit, use_x0=use_x0,
+                            time_phases=time_phases)
     if method == "bicgstab":
-        return bicgstab_solve(A, M, b, x, rtol=rtol, maxit=maxit, use_x0=use_x0)
+        return bicgstab_solve(A, M, b, x, rtol=rtol, maxit=maxit, use_x0=use_x0, time_phases=time_phases)
     raise ValueError(f"unknown Krylov method {method!r}")
 
 

@@ -99,3 +99,53 @@ def test_full_size_ilu1(trs, oracle, full):
     x, res = trs.krylov_solve("fgmres", A, M32, ds.rhs, torch.empty_like(ds.rhs), rtol=1e-6)
     assert res.status == trs.TRS_OK
     assert _relres(oracle, Ao, sysm.rhs, x.cpu().numpy()) <= 1.01e-6
+
+
+@pytest.mark.parametrize("decoupling", ["abf", "none", "frs", "frs+abf"])
+def test_full_size_fp32_apply_matches_oracle(trs, oracle, full, decoupling):
+    """The benchmark's FP32 CPR application (block ILU(0)) against the
+    oracle's FP64 application, for every stage ordering, within the
+    rounding count of test_gpu_fp32_apply."""
+    from test_gpu_fp32_apply import fp32_apply_tolerance
+    sysm, ds, A, Ao = full
+    v = np.random.default_rng(9).standard_normal(Ao.n * Ao.b)
+    vd = torch.from_numpy(v).cuda()
+    for stages in ("fpf", "fp", "pf"):
+        Mo = oracle.CPR(Ao, stages=stages, decoupling=decoupling)
+        M = trs.CPR(A, precision="fp32", stages=stages, decoupling=decoupling)
+        z = M.apply(vd).cpu().numpy()
+        zo = Mo.apply(v)
+        err = np.linalg.norm(z - zo) / np.linalg.norm(zo)
+        tol = fp32_apply_tolerance(Ao, Mo, stages)
+        print(f"full size FP32 apply {stages}/{decoupling}: rel err {err:.3e} (bound {tol:.3e})")
+        assert 0.0 < err <= tol
+        del M, Mo
+
+
+def test_full_size_error_vs_oracle_solution(trs, oracle, full):
+    """Solution error against the oracle's FP64 solution at the benchmark
+    size.  Both FP64 paths run the same algorithm, so at rtol 1e-10 their
+    solutions agree to 1e-8; the FP32-preconditioner solve at the
+    benchmark's rtol 1e-6 is as accurate as the FP64-preconditioner solve
+    at the same tolerance, within a factor 10."""
+    sysm, ds, A, Ao = full
+    ref = oracle.fgmres(Ao, oracle.CPR(Ao), sysm.rhs, rtol=1e-10)
+    assert ref.converged
+    xs = ref.x
+    err = lambda x: np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs)
+    M64 = trs.CPR(A, precision="fp64")
+    x64, r64 = trs.fgmres_solve(A, M64, ds.rhs, rtol=1e-10)
+    assert r64.status == trs.TRS_OK
+    e64_tight = err(x64)
+    assert e64_tight <= 1e-8
+    x64, r64 = trs.fgmres_solve(A, M64, ds.rhs, rtol=1e-6)
+    e64 = err(x64)
+    del M64
+    M32 = trs.CPR(A, precision="fp32")
+    x32, r32 = trs.fgmres_solve(A, M32, ds.rhs, rtol=1e-6)
+    assert r32.status == trs.TRS_OK
+    e32 = err(x32)
+    print(f"full size error vs the oracle's x (rtol 1e-10, {ref.iters} its): FP64 at 1e-10 {e64_tight:.3e}, "
+          f"FP64 at 1e-6 {e64:.3e} ({r64.stats['iters']} its), FP32 CPR at 1e-6 {e32:.3e} "
+          f"({r32.stats['iters']} its)")
+    assert e32 <= 10.0 * e64

@@ -195,6 +195,24 @@ def test_solve_host_buffers(trs, oracle, synth):
     x, res = trs.fgmres_solve_host(ds.A, M, s.rhs, rtol=1e-10)
     xd, _ = trs.fgmres_solve(ds.A, M, ds.rhs, rtol=1e-10)
     np.testing.assert_array_equal(x, xd.cpu().numpy())
+    # a second call reuses the handle's device copies; pinned CPU tensors work too
+    hb = torch.from_numpy(s.rhs.copy()).pin_memory()
+    hx = torch.full((ds.A.N,), float("nan"), dtype=torch.float64).pin_memory()
+    x2, _ = trs.fgmres_solve_host(ds.A, M, hb, rtol=1e-10, x=hx)
+    assert x2 is hx
+    np.testing.assert_array_equal(hx.numpy(), x)
+
+
+def test_assemble_host_buffers(trs, oracle, synth):
+    """trs_bsr_assemble_host gives the bits of the device-input assembly."""
+    s = _sys(synth, 9, 7, 5, 4, seed=22, n_pairs=2)
+    ds = _gpu_system(trs, s)
+    ref = ds.A.values()
+    A2 = trs.Matrix.synthetic_pattern(s.nx, s.ny, s.nz, s.b, s.n_wells, s.perf_well, s.perf_cell)
+    for _ in range(2):   # the second call reuses the staging area
+        A2.assemble_host(s.k, s.M.reshape(-1), s.acc.reshape(-1), s.wi, s.lam.reshape(-1), s.kvkh, s.c_t)
+        np.testing.assert_array_equal(A2.values(), ref)
+    np.testing.assert_array_equal(A2.values(), oracle.assemble(s).val)
 
 
 # ------------------------------------------------------------------ adjoint
@@ -290,6 +308,26 @@ def test_determinism(trs, synth):
     x1, _ = trs.fgmres_solve(ds.A, M, ds.rhs, rtol=1e-9)
     x2, _ = trs.fgmres_solve(ds.A, M, ds.rhs, rtol=1e-9)
     assert torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("method", ["fgmres", "bicgstab"])
+def test_phase_timing(trs, synth, method):
+    """opts.time_phases fills the per-phase device times without changing the
+    result: the phases sum to at most the solve time, one operator SpMV per
+    FGMRES step (two per BiCGSTAB iteration), and the bits of x are those of
+    an untimed solve."""
+    s = _sys(synth, 12, 10, 6, 4, seed=47, n_pairs=2)
+    ds = _gpu_system(trs, s)
+    M = trs.CPR(ds.A, precision="fp32")
+    x0, r0 = trs.krylov_solve(method, ds.A, M, ds.rhs, rtol=1e-9)
+    assert r0.stats["ms_precond"] == 0.0 and r0.stats["spmv_launches"] == 0
+    x1, r1 = trs.krylov_solve(method, ds.A, M, ds.rhs, rtol=1e-9, time_phases=True)
+    assert torch.equal(x0, x1)
+    st = r1.stats
+    assert st["spmv_launches"] == st["iters"] * (1 if method == "fgmres" else 2)
+    for k in ("ms_precond", "ms_spmv", "ms_orth"):
+        assert st[k] > 0.0
+    assert st["ms_precond"] + st["ms_spmv"] + st["ms_orth"] <= st["ms_solve"] * 1.001
 
 
 def test_update_reuse_amg(trs, oracle, synth):
