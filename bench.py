@@ -96,6 +96,9 @@ def parse():
                    help="skip timing the other Krylov method on the same system")
     p.add_argument("--sweep", action="store_true",
                    help="time every CPR stage ordering x decoupling pair (FP32 and FP64 CPR) instead")
+    p.add_argument("--jacobian", default="synthetic", choices=["synthetic", "physics"],
+                   help="physics: the step assembles the thermal model's Jacobian and residual "
+                        "(water + heavy oil + energy) on the workload's grid and wells and solves J d = R")
     a = p.parse_args()
     if a.ilu_fill is None:
         a.ilu_fill = 1 if a.sequence else 0
@@ -455,9 +458,18 @@ def run_sweep(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     sysm = make_workload(args.workload)
-    ds = trs.DeviceSystem(sysm, dev)
-    A = ds.assemble()
-    x = torch.zeros_like(ds.rhs)
+    if args.jacobian == "physics":
+        from paper_1812_03952_gb300 import synthetic as S
+        phys = trs.ThermalSystem(sysm, S.thermal_state(sysm, S.SEED_BASE + 77), S.SWT, S.SLT)
+        rhs = phys.assemble()
+        A = phys.A
+        assemble = phys.assemble
+    else:
+        ds = trs.DeviceSystem(sysm, dev)
+        A = ds.assemble()
+        rhs = ds.rhs
+        assemble = ds.assemble
+    x = torch.zeros_like(rhs)
     rows = []
     with ClockSampler(local) as clk:
         for precision in ("fp32", "fp64"):
@@ -469,9 +481,9 @@ def run_sweep(args):
                     for k in range(args.warmup + args.steps):
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
-                        ds.assemble()
+                        assemble()
                         M.update(A, reuse_amg=False)
-                        _, res = trs.krylov_solve(args.krylov, A, M, ds.rhs, x, rtol=args.rtol,
+                        _, res = trs.krylov_solve(args.krylov, A, M, rhs, x, rtol=args.rtol,
                                                   restart=args.restart, maxit=1000)
                         e1.record(stream)
                         torch.cuda.synchronize()
@@ -484,11 +496,82 @@ def run_sweep(args):
                     del M
     if rank == 0:
         print(json.dumps({"metric": "CPR stage ordering x decoupling sweep: ms per step (assembly + CPR setup + "
-                                    f"{args.krylov.upper()} to true rel. res. {args.rtol})",
+                                    f"{args.krylov.upper()} to true rel. res. {args.rtol})"
+                                    + (", physics Jacobian" if args.jacobian == "physics" else ""),
                           "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
                           "warmup": args.warmup, "data": "synthetic",
                           "config": config_of(args, sysm, world), "rows": rows, "clocks": clk.summary()}),
               flush=True)
+    return 0
+
+
+# ------------------------------------------------- physics Jacobian step
+def run_physics(args):
+    """One Newton step of the thermal model: the Jacobian dR/du and residual
+    R(u) assembled on the GPU (water + heavy oil + energy, Sec. "Mathematical
+    Model"), CPR setup on it, and the CPR-Krylov solve of J d = R."""
+    import torch
+    from paper_1812_03952_gb300 import build as B
+    from paper_1812_03952_gb300 import synthetic as S
+    from paper_1812_03952_gb300 import trs
+    B.build()
+    trs.load()
+    rank, world, local = dist_setup(args.gpus)
+    stream = torch.cuda.current_stream()
+    sysm = make_workload(args.workload)
+    if sysm.b != 4:
+        raise SystemExit("the thermal model has b = 4")
+    state = S.thermal_state(sysm, S.SEED_BASE + 77)
+    ts = trs.ThermalSystem(sysm, state, S.SWT, S.SLT)
+    R = ts.assemble()
+    M = trs.CPR(ts.A, precision=args.precision, cheb_degree=args.cheb_degree, stages=args.stages,
+                decoupling=args.decoupling, ilu_fill=args.ilu_fill)
+    d = torch.zeros_like(R)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    asm = []
+
+    def step(record=False):
+        if record:
+            ea.record(stream)
+        ts.assemble()
+        if record:
+            eb.record(stream)
+        M.update(ts.A, reuse_amg=False)
+        _, res = trs.krylov_solve(args.krylov, ts.A, M, R, d, rtol=args.rtol, restart=args.restart)
+        if record:
+            asm.append(ea.elapsed_time(eb))
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    l0 = trs.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = barrier_max(e0.elapsed_time(e1) / args.steps, world)
+    launches = trs.kernel_launches() - l0
+    for _ in range(max(1, min(args.steps, 5))):
+        step(record=True)
+    asm_ms = statistics.median(asm)
+    if rank == 0:
+        line = {"metric": "Newton step with the physics Jacobian: thermal assembly + CPR setup + CPR-"
+                          f"{args.krylov.upper()} to true rel. res. {args.rtol} (ms)",
+                "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64+f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": {**config_of(args, sysm, world), "jacobian": "physics (water + heavy oil + energy)",
+                           "gas_cells": int(state.gas.sum()), "dt_day": state.params["dt"]},
+                "iters": res.stats["iters"], "converged": bool(res.stats["converged"]),
+                "true_relres": res.stats["true_relres"],
+                "breakdown_ms": {"assembly": asm_ms, "setup": res.stats["ms_setup"], "solve": res.stats["ms_solve"]},
+                "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -501,6 +584,8 @@ def main():
         return run_sequence(args)
     if args.sweep:
         return run_sweep(args)
+    if args.jacobian == "physics":
+        return run_physics(args)
     import torch
     from paper_1812_03952_gb300 import build as B
     from paper_1812_03952_gb300 import trs
@@ -591,9 +676,8 @@ def main():
     fp64_peak_tflops = FP64_FLOP_PER_CLOCK * rp_clock * 1e6 / 1e12
     spmv_tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
     spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    # DRAM traffic per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum
-    # of k_spmv<4,double,double> on this 128x128x64 system (one-pass capture of
-    # the bench command itself)
+    # DRAM traffic per launch of k_spmv<4,double,double> on this 128x128x64
+    # system, from ncu (see SPMV_TRAFFIC_128)
     spmv_traffic = (SPMV_TRAFFIC_128 if args.workload == "128x128x64_b4" and args.krylov == "fgmres"
                     else None)
 
@@ -732,10 +816,9 @@ def main():
 
 
 #: ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_spmv<4,double,double>
-#: launch on the 128x128x64 system, from an older 96x96x48 capture scaled by
-#: the stored blocks (429.82 MB for 3,061,224 blocks); replaced by the
-#: full-size capture once taken
-SPMV_TRAFFIC_128 = 429.822464e6 * 7276104 / 3061224.0
+#: launch on the 128x128x64 system (one-pass capture of this bench's own
+#: command: 994.32 MB read, 30.50 MB written)
+SPMV_TRAFFIC_128 = (994.32 + 30.50) * 1e6
 
 
 if __name__ == "__main__":

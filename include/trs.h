@@ -290,7 +290,9 @@ trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *strea
 trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void *stream);
 
 /* z = M^-1 v = CPR(Ã)^-1 (D^-1 v): one application of the preconditioner
- * (device pointers, FP64; computed in the handle's precision). */
+ * (device pointers, FP64; computed in the handle's precision).  Synchronises
+ * `stream` to check the grid barriers of the V-cycle kernel (TRS_ERR_CUDA if
+ * one timed out). */
 trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *stream);
 
 trs_status trs_cpr_get_info(const trs_cpr *M, trs_cpr_info *info);
@@ -307,7 +309,8 @@ trs_status trs_cpr_get_level(const trs_cpr *M, int32_t level, int64_t *row_ptr, 
                              double *val);
 
 /* Applies one AMG V-cycle of the pressure hierarchy to r (device pointers,
- * n_0 doubles): e = AMG(A_p)^-1 r. */
+ * n_0 doubles): e = AMG(A_p)^-1 r.  Synchronises `stream` like
+ * trs_cpr_apply. */
 trs_status trs_cpr_vcycle(const trs_cpr *M, const double *r, double *e, void *stream);
 
 void trs_cpr_destroy(trs_cpr *M);
@@ -388,6 +391,68 @@ trs_status trs_outer_product(const trs_bsr *A, const double *lambda, const doubl
 trs_status trs_chain_theta(const trs_bsr *A, const double *perm, int32_t perm_is_log,
                            double kvkh, double c_t, const double *M, const double *lambda,
                            const double *x, double *dtheta, void *stream);
+
+/* ------------------------------------------------ thermal model Jacobian */
+
+/* Parameters of the thermal model assembled by trs_thermal_assemble (Sec.
+ * "Mathematical Model").  Units: p kPa, T C, lengths m, time day, amounts
+ * gmol, energy kJ, permeability mD, viscosity cP. */
+typedef struct {
+  double dx, dy, dz;          /* cell sizes */
+  double depth_top;           /* depth of the top face of layer 0 (z grows downward) */
+  double dt;                  /* time step of the backward Euler discretisation */
+  double kvkh;                /* vertical / horizontal permeability ratio */
+  double gravity;             /* m/s^2 (0 switches gravity off) */
+  double phi_ref, cpor, ctpor, p_ref, T_ref;  /* phi = phi_ref (1 + cpor (p - p_ref) - ctpor (T - T_ref)) */
+  double cp1_r, cp2_r;        /* rock U_r = cp1_r (T - T_ref) + cp2_r / 2 (T^2 - T_ref^2), kJ/m^3 */
+  double kt_w, kt_o, kt_g, kt_r;  /* thermal conductivities, kJ/(m day C) */
+  double rho_w_ref, cp_w, ct1_w, ct2_w, cpt_w;  /* water molar density correlation (Sec. "Density") */
+  double mw_w;                /* molar mass of water, kg/gmol */
+  double avisc_w, bvisc_w;    /* mu_w = avisc_w exp(bvisc_w / T_K), cP */
+  double kv1, kv2, kv3, kv4, kv5;  /* K_W = (kv1/p + kv2 p + kv3) exp(kv4 / (T - kv5)) */
+  double per_eps;             /* PER: K*_W = S_w / (S_w + per_eps) K_W */
+  double tc_w, pc_w;          /* critical temperature (C) and pressure (kPa) of water (Redlich-Kwong) */
+  double cpg[5];              /* H_gW = integral from T_ref of sum_k cpg[k] t^k, kJ/gmol */
+  double hvr, ev;             /* heat of vaporisation hvr (tc_w - T)^ev */
+  double rho_o_ref, cp_o, ct1_o, ct2_o, cpt_o;  /* oil component density correlation */
+  double mw_o;                /* molar mass of the oil component */
+  double avisc_o, bvisc_o;    /* mu_o = avisc_o exp(bvisc_o / T_K) */
+  double cpl1_o;              /* H_o = cpl1_o (T - T_ref) (liquid-based enthalpy) */
+  double mug_a, mug_b;        /* mu_g = mug_a + mug_b T */
+  double h_inj;               /* enthalpy of the steam the injectors inject, kJ/gmol */
+  double R_gas;               /* gas constant, kJ/(gmol K) */
+} trs_thermal_params;
+
+/* Jacobian and residual of one Newton step of the thermal model for a
+ * matrix made by trs_bsr_create_synthetic with b = 4: one component set,
+ * water in the water and gas phases and one heavy-oil component in the oil
+ * phase (Sec. "Mathematical Model").  Unknowns per cell (p, S_w, S_g, T);
+ * equations: water and oil moles (Eq. eq4.2), energy (Eq. eq4.3) and the gas
+ * constraint K*_W(p, T, S_w) - 1 = 0 where gas exists, S_g = 0 where not
+ * (Sec. "Spatial Discretization").  Backward Euler in time; two-point fluxes
+ * with the harmonic mean of the permeabilities and upstream k_r rho / mu and
+ * enthalpy per phase; conduction with the harmonic mean of the bulk
+ * conductivities; densities, Redlich-Kwong gas, viscosities, porosity,
+ * tables with Stone's model II, enthalpies by the paper's correlations.
+ * Wells (Sec. "Well Modeling"): well_type[w] = 0, an injector at the fixed
+ * rate well_target[w] (gmol/day) with Q = wi (p_b - p) of steam
+ * (unweighted mobility); 1, a producer at the fixed BHP well_target[w] (kPa)
+ * with Q_a = wi c lambda_a (p_b - p) from the cell's mobilities.
+ * Host pointers: prm; swt (nswt x 3: S_w, k_rw, k_row) and slt (nslt x 3:
+ * S_l, k_rg, k_rog), 2..32 rows with increasing saturations.  Device
+ * pointers: perm (n_cells, mD), u and u_old ((n_cells + n_wells) * 4: cells
+ * (p, S_w, S_g, T), wells (p_b, 0, 0, 0)), gas (n_cells bytes), wi (n_perf),
+ * well_type (n_wells int32), well_target (n_wells), residual (out, n * 4:
+ * R(u), with R = u on the padding entries of well blocks).  The values of
+ * A become dR/du.  The matrix keeps a scratch of 50 doubles per cell for
+ * the cell properties (allocated at the first call).
+ * Errors: TRS_ERR_INVALID, TRS_ERR_UNSUPPORTED (b != 4), TRS_ERR_OOM,
+ * TRS_ERR_CUDA. */
+trs_status trs_thermal_assemble(trs_bsr *A, const trs_thermal_params *prm, const double *swt, int32_t nswt,
+                                const double *slt, int32_t nslt, const double *perm, const double *u,
+                                const double *u_old, const uint8_t *gas, const double *wi,
+                                const int32_t *well_type, const double *well_target, double *residual,
+                                void *stream);
 
 /* --------------------------------------------------------------- misc */
 const char *trs_last_error(void);

@@ -14,7 +14,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
-SOURCES = [os.path.join(HERE, "trs_oracle.c")]
+SOURCES = [os.path.join(HERE, "trs_oracle.c"), os.path.join(HERE, "trs_thermal.c")]
 
 i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
@@ -38,6 +38,29 @@ def build(force: bool = False) -> str:
 class _Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
                 ("est_relres", C.c_double), ("true_relres", C.c_double)]
+
+
+class _ThermalParams(C.Structure):
+    _fields_ = [(f, C.c_double) for f in (
+        "dx", "dy", "dz", "depth_top", "dt", "kvkh", "gravity",
+        "phi_ref", "cpor", "ctpor", "p_ref", "T_ref", "cp1_r", "cp2_r",
+        "kt_w", "kt_o", "kt_g", "kt_r",
+        "rho_w_ref", "cp_w", "ct1_w", "ct2_w", "cpt_w", "mw_w", "avisc_w", "bvisc_w",
+        "kv1", "kv2", "kv3", "kv4", "kv5", "per_eps", "tc_w", "pc_w")] + [
+        ("cpg", C.c_double * 5)] + [(f, C.c_double) for f in (
+            "hvr", "ev", "rho_o_ref", "cp_o", "ct1_o", "ct2_o", "cpt_o", "mw_o", "avisc_o", "bvisc_o",
+            "cpl1_o", "mug_a", "mug_b", "h_inj", "R_gas")]
+
+
+def thermal_params(d: dict) -> _ThermalParams:
+    """The parameter struct of trs_thermal.c from a dict of named values."""
+    P = _ThermalParams()
+    for name, _ in _ThermalParams._fields_:
+        if name == "cpg":
+            P.cpg = (C.c_double * 5)(*[d[f"cpg{k}"] for k in range(1, 6)])
+        else:
+            setattr(P, name, float(d[name]))
+    return P
 
 
 class _CprOpts(C.Structure):
@@ -170,6 +193,25 @@ def lib():
         L.orc_chain_theta.restype = C.c_int
         L.orc_chain_theta.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, f64p, C.c_double,
                                       C.c_double, f64p, i64p, i32p, f64p, f64p]
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        tp = C.POINTER(_ThermalParams)
+        common = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, tp, f64p, C.c_int, f64p, C.c_int, f64p,
+                  i32p, i32p, f64p, i32p, f64p, u8p, f64p, f64p]
+        rowsp = C.c_void_p
+        L.orc_thermal_residual.restype = C.c_int
+        L.orc_thermal_residual.argtypes = common + [C.c_int64, rowsp, f64p]
+        L.orc_thermal_jacobian.restype = C.c_int
+        L.orc_thermal_jacobian.argtypes = common + [C.c_int64, rowsp, i64p, i32p, f64p]
+        L.orc_thermal_props.restype = None
+        L.orc_thermal_props.argtypes = [tp, f64p, C.c_int, f64p, C.c_int, f64p, f64p]
+        L.orc_rk_z.restype = C.c_double
+        L.orc_rk_z.argtypes = [C.c_double, C.c_double]
+        L.orc_thermal_totals.restype = None
+        L.orc_thermal_totals.argtypes = [C.c_int, C.c_int, C.c_int, tp, f64p, C.c_int, f64p, C.c_int, f64p,
+                                         f64p]
+        L.orc_thermal_well_sources.restype = None
+        L.orc_thermal_well_sources.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, tp, f64p,
+                                               C.c_int, f64p, C.c_int, i32p, i32p, f64p, i32p, f64p, f64p]
         _lib = L
     return _lib
 
@@ -566,3 +608,76 @@ def well_cell_indicator(sysm):
     cells = np.unique(sysm.perf_cell)
     g[cells.astype(np.int64) * sysm.b] = 1.0
     return g
+
+
+# ------------------------------------------------------------- thermal model
+class Thermal:
+    """Residual and Jacobian of the water + heavy-oil thermal model on a
+    synthetic system's grid and wells (trs_thermal.c), for a ThermalState."""
+
+    def __init__(self, sysm, state, swt, slt):
+        self.s = sysm
+        self.t = state
+        self.P = thermal_params(state.params)
+        self.swt = np.ascontiguousarray(swt, dtype=np.float64)
+        self.slt = np.ascontiguousarray(slt, dtype=np.float64)
+
+    def _args(self, u):
+        s, t = self.s, self.t
+        return (s.nx, s.ny, s.nz, s.n_wells, len(s.perf_cell), C.byref(self.P), self.swt.reshape(-1),
+                len(self.swt), self.slt.reshape(-1), len(self.slt), s.k, s.perf_well, s.perf_cell, t.wi,
+                t.well_type, t.well_target, t.gas, np.ascontiguousarray(u, dtype=np.float64), t.u_old)
+
+    @staticmethod
+    def _rows(rows):
+        if rows is None:
+            return 0, None, None
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        return len(r), r.ctypes.data_as(C.c_void_p), r
+
+    def residual(self, u=None, rows=None):
+        """R(u); with rows, only those cell rows (and the well rows) are filled."""
+        R = np.zeros(self.s.n_unknowns)
+        nr, rp_, keep = self._rows(rows)
+        _check(lib().orc_thermal_residual(*self._args(self.t.u if u is None else u), nr, rp_, R),
+               "thermal residual")
+        return R
+
+    def jacobian(self, u=None, rows=None, pattern=None) -> BSR:
+        """dR/du in BSR on the pattern of the synthetic assembly (7-point +
+        wells); with rows, only those cell rows (and the well rows) are filled."""
+        A0 = pattern if pattern is not None else assemble(self.s)
+        val = np.zeros_like(A0.val)
+        nr, rp_, keep = self._rows(rows)
+        _check(lib().orc_thermal_jacobian(*self._args(self.t.u if u is None else u), nr, rp_, A0.rp, A0.col,
+                                          val.reshape(-1)), "thermal jacobian")
+        return BSR(A0.n, A0.b, A0.rp, A0.col, val)
+
+    def props(self, u_cell):
+        out = np.zeros(16)
+        lib().orc_thermal_props(C.byref(self.P), self.swt.reshape(-1), len(self.swt), self.slt.reshape(-1),
+                                len(self.slt), np.ascontiguousarray(u_cell, dtype=np.float64), out)
+        keys = ("phi", "rho_w", "rho_o", "rho_g", "lam_w", "lam_o", "lam_g", "H_w", "H_o", "H_g", "U_w", "U_o",
+                "U_g", "U_r", "K_T", "K_star")
+        return dict(zip(keys, out))
+
+    def totals(self, u):
+        out = np.zeros(3)
+        s = self.s
+        lib().orc_thermal_totals(s.nx, s.ny, s.nz, C.byref(self.P), self.swt.reshape(-1), len(self.swt),
+                                 self.slt.reshape(-1), len(self.slt), np.ascontiguousarray(u, dtype=np.float64),
+                                 out)
+        return out
+
+    def well_sources(self, u=None):
+        out = np.zeros(3)
+        s, t = self.s, self.t
+        lib().orc_thermal_well_sources(s.nx, s.ny, s.nz, s.n_wells, len(s.perf_cell), C.byref(self.P),
+                                       self.swt.reshape(-1), len(self.swt), self.slt.reshape(-1), len(self.slt),
+                                       s.perf_well, s.perf_cell, t.wi, t.well_type,
+                                       np.ascontiguousarray(t.u if u is None else u, dtype=np.float64), out)
+        return out
+
+
+def rk_z(A, B):
+    return lib().orc_rk_z(float(A), float(B))

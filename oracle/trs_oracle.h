@@ -157,6 +157,61 @@ int orc_chain_theta(int nx, int ny, int nz, int b, const double *k, double kvkh,
                     const double *M, const int64_t *rp, const int32_t *col, const double *dA,
                     double *dtheta);
 
+/* ---- thermal model: residual and Jacobian of one Newton step (trs_thermal.c) ----
+ * One component set: water (water and gas phases) and one heavy-oil component
+ * (oil phase).  Units: p kPa, T C, lengths m, time day, amounts gmol, energy kJ,
+ * permeability mD, viscosity cP. */
+typedef struct {
+  double dx, dy, dz;          /* cell sizes */
+  double depth_top;           /* depth of the top face of layer 0 (z grows downward) */
+  double dt;                  /* time step */
+  double kvkh;                /* vertical / horizontal permeability */
+  double gravity;             /* m/s^2 */
+  double phi_ref, cpor, ctpor, p_ref, T_ref;
+  double cp1_r, cp2_r;        /* rock heat capacity, kJ/(m^3 C) and kJ/(m^3 C^2) */
+  double kt_w, kt_o, kt_g, kt_r;  /* thermal conductivities, kJ/(m day C) */
+  double rho_w_ref, cp_w, ct1_w, ct2_w, cpt_w, mw_w;
+  double avisc_w, bvisc_w;    /* mu_w = avisc exp(bvisc / T_K) */
+  double kv1, kv2, kv3, kv4, kv5, per_eps;
+  double tc_w, pc_w;          /* critical temperature (C) and pressure (kPa) of water */
+  double cpg[5];              /* gas heat-capacity polynomial of water, kJ/(gmol C^(k+1)) */
+  double hvr, ev;             /* heat of vaporisation hvr (T_c - T)^ev */
+  double rho_o_ref, cp_o, ct1_o, ct2_o, cpt_o, mw_o;
+  double avisc_o, bvisc_o;
+  double cpl1_o;              /* liquid heat capacity of the oil component, kJ/(gmol C) */
+  double mug_a, mug_b;        /* mu_g = mug_a + mug_b T (T in C) */
+  double h_inj;               /* enthalpy of injected steam, kJ/gmol */
+  double R_gas;               /* gas constant, kJ/(gmol K) */
+} orc_thermal_params;
+
+/* Residual R(u) (n*4 doubles; cells then wells, wells' padding entries
+ * R = u) and Jacobian dR/du on the pattern rp/col (that of orc_assemble for
+ * the same grid and perforations), values in canonical BSR order.  rows:
+ * NULL for every row, else the n_rows cell rows to compute (the well rows are
+ * always computed; other entries are left as they are, zero them first).
+ * swt: nswt x 3 (S_w, k_rw, k_row); slt: nslt x 3 (S_l, k_rg, k_rog).
+ * well_type: 0 = injector at a fixed rate, 1 = producer at a fixed BHP. */
+int orc_thermal_residual(int nx, int ny, int nz, int nw, int64_t np, const orc_thermal_params *P,
+                         const double *swt, int nswt, const double *slt, int nslt, const double *k,
+                         const int32_t *perf_well, const int32_t *perf_cell, const double *wi,
+                         const int32_t *well_type, const double *well_target, const uint8_t *gas,
+                         const double *u, const double *u_old, int64_t n_rows, const int64_t *rows, double *R);
+int orc_thermal_jacobian(int nx, int ny, int nz, int nw, int64_t np, const orc_thermal_params *P,
+                         const double *swt, int nswt, const double *slt, int nslt, const double *k,
+                         const int32_t *perf_well, const int32_t *perf_cell, const double *wi,
+                         const int32_t *well_type, const double *well_target, const uint8_t *gas,
+                         const double *u, const double *u_old, int64_t n_rows, const int64_t *rows,
+                         const int64_t *rp, const int32_t *col, double *val);
+void orc_thermal_props(const orc_thermal_params *P, const double *swt, int nswt, const double *slt, int nslt,
+                       const double *u, double *out);
+double orc_rk_z(double A, double B);
+void orc_thermal_totals(int nx, int ny, int nz, const orc_thermal_params *P, const double *swt, int nswt,
+                        const double *slt, int nslt, const double *u, double *out);
+void orc_thermal_well_sources(int nx, int ny, int nz, int nw, int64_t np, const orc_thermal_params *P,
+                              const double *swt, int nswt, const double *slt, int nslt,
+                              const int32_t *perf_well, const int32_t *perf_cell, const double *wi,
+                              const int32_t *well_type, const double *u, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@ UNITS = {
     "k_adjoint.cu": [],
     "trs_matrix.cu": [],
     "trs_cpr.cu": [],
+    "k_thermal.cu": [],
 }
 HEADERS = ["trs_internal.cuh", "trs_kernels.cuh", "trs_api_common.cuh"]
 

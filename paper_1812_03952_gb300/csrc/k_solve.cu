@@ -22,6 +22,35 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp sums of KM per-lane values by reduce-scatter: at each of the first
+// log2(KM) levels a lane keeps one half of its values, adds the partner's
+// copy of that half and hands over the other half, then the last 5 -
+// log2(KM) levels add one value.  KM - 1 + 5 - log2(KM) FP64 additions per
+// lane instead of 5 KM (on GB300 the additions of a shuffle reduction share
+// the FP64 pipe with the dot products themselves).  Returns the warp total of
+// value v(lane) = (lane >> (5 - log2 KM)) & (KM - 1); the lanes with
+// lane % (32 / KM) == 0 hold the KM totals once each.
+template <int KM>
+__device__ __forceinline__ double warp_reduce_scatter(double (&a)[KM], int lane) {
+  static_assert(KM >= 1 && KM <= 32 && (KM & (KM - 1)) == 0, "KM must be a power of two up to 32");
+  int o = 16;
+#pragma unroll
+  for (int h = KM / 2; h >= 1; h /= 2) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; i++) {
+      const double keep = upper ? a[i + h] : a[i];
+      const double send = upper ? a[i] : a[i + h];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    o >>= 1;
+  }
+  double v = a[0];
+#pragma unroll
+  for (; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <class T>
 __device__ __forceinline__ double to_d(T v) { return static_cast<double>(v); }
 
@@ -205,11 +234,9 @@ template <int KC>
 __device__ void block_partial(double (&acc)[KC], double *__restrict__ dst) {
   __shared__ double sm[kWarps][KC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int u = 0; u < KC; u++) {
-    double v = warp_sum(acc[u]);
-    if (lane == 0) sm[warp][u] = v;
-  }
+  constexpr int kSpan = 32 / KC;
+  const double v = warp_reduce_scatter<KC>(acc, lane);
+  if ((lane & (kSpan - 1)) == 0) sm[warp][lane / kSpan] = v;
   __syncthreads();
   if (threadIdx.x < KC) {
     double s = 0.0;
@@ -887,113 +914,182 @@ __global__ void k_dense_gemv(int64_t n, const double *__restrict__ Minv, const T
 // The V-cycle from level h.l0 down, by one block of 1024 threads: the same
 // Chebyshev, residual, restriction, coarsest solve and prolongation steps as
 // the per-level kernels above (identical arithmetic), separated by block
-// barriers instead of launches.
-template <class T>
+// barriers instead of launches.  The same steps also run on the whole grid
+// (k_vcycle_mid), separated by grid barriers; there every vector written in
+// the kernel is read with ld.global.cg (L2), since an SM's L1 may hold a
+// line that another SM has rewritten since.
+template <class T, bool G>
+__device__ __forceinline__ T vld(const T *p) {
+  if constexpr (G) return __ldcg(p);
+  else return *p;
+}
+
+template <class T, bool G = false>
 __device__ __forceinline__ T csr_rowdot(const CoarseLevel<T> &L, int64_t i, const T *x) {
   T acc = T(0);
-  for (int64_t p = L.rp[i]; p < L.rp[i + 1]; p++) acc = fma(L.val[p], x[L.col[p]], acc);
+  for (int64_t p = L.rp[i]; p < L.rp[i + 1]; p++) acc = fma(L.val[p], vld<T, G>(x + L.col[p]), acc);
   return acc;
 }
 
-template <class T>
-__device__ void coarse_cheb(const CoarseLevel<T> &L, int deg, bool zero_init) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+// block barrier
+struct BlockSync {
+  __device__ __forceinline__ bool operator()() const {
+    __syncthreads();
+    return true;
+  }
+};
+
+// Grid barrier of a cooperative launch: the last block to arrive advances the
+// generation word; the others wait for it a bounded time (kGridSpinLimit
+// rounds of about 0.1 us, about 1 s), after which they set the error word,
+// and every block leaves the kernel at its next barrier.
+constexpr unsigned kGridSpinLimit = 10000000u;
+#ifndef TRS_GRID_SPIN_NS
+#define TRS_GRID_SPIN_NS 100
+#endif
+struct GridSync {
+  unsigned *count;
+  unsigned *gen;
+  int *err;
+  __device__ bool operator()() const {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!*reinterpret_cast<volatile int *>(err)) {
+        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+          *reinterpret_cast<volatile unsigned *>(count) = 0u;
+          __threadfence();
+          atomicAdd(gen, 1u);
+        } else {
+          unsigned it = 0;
+          while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
+            if (++it > kGridSpinLimit) {
+              atomicExch(err, 1);
+              break;
+            }
+            if (TRS_GRID_SPIN_NS) __nanosleep(TRS_GRID_SPIN_NS);
+          }
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    return !*reinterpret_cast<volatile int *>(err);
+  }
+};
+
+template <class T, bool G, class Sync>
+__device__ bool coarse_cheb(const CoarseLevel<T> &L, int deg, bool zero_init, int64_t tid, int64_t nt,
+                            const Sync &sync) {
   const T *r = L.r;
   T *e = L.e, *res = L.res, *d = L.d, *dn = L.dn;
   if (zero_init) {
     for (int64_t i = tid; i < L.n; i += nt) {
-      d[i] = (L.dinv[i] * r[i]) * L.inv_theta;
+      d[i] = (L.dinv[i] * vld<T, G>(r + i)) * L.inv_theta;
       e[i] = T(0);
     }
   } else {
     for (int64_t i = tid; i < L.n; i += nt) {
-      const T v = r[i] - csr_rowdot(L, i, e);
+      const T v = vld<T, G>(r + i) - csr_rowdot<T, G>(L, i, e);
       res[i] = v;
       d[i] = (L.dinv[i] * v) * L.inv_theta;
     }
   }
-  __syncthreads();
+  if (!sync()) return false;
   const T *res_in = zero_init ? r : res;
   for (int k = 1; k < deg; k++) {
     const int last = (k == deg - 1);
     for (int64_t i = tid; i < L.n; i += nt) {
-      const T rv = res_in[i] - csr_rowdot(L, i, d);
+      const T rv = vld<T, G>(res_in + i) - csr_rowdot<T, G>(L, i, d);
       res[i] = rv;
-      const T di = d[i];
+      const T di = vld<T, G>(d + i);
       const T nv = fma(L.c1[k], di, L.c2[k] * (L.dinv[i] * rv));
-      const T ev = e[i] + di;
+      const T ev = vld<T, G>(e + i) + di;
       if (last) e[i] = ev + nv;
       else { e[i] = ev; dn[i] = nv; }
     }
-    __syncthreads();
+    if (!sync()) return false;
     res_in = res;
     T *t = d; d = dn; dn = t;
   }
+  return true;
+}
+
+// pre-smoothing, residual and restriction of level l into level l + 1
+template <class T, bool G, class Sync>
+__device__ bool level_down(const CoarseHierarchy<T> &h, int l, int64_t tid, int64_t nt, const Sync &sync) {
+  const CoarseLevel<T> &L = h.lv[l];
+  if (!coarse_cheb<T, G>(L, h.deg, true, tid, nt, sync)) return false;
+  for (int64_t i = tid; i < L.n; i += nt) L.res[i] = vld<T, G>(L.r + i) - csr_rowdot<T, G>(L, i, L.e);
+  if (!sync()) return false;
+  const CoarseLevel<T> &C = h.lv[l + 1];
+  for (int64_t I = tid; I < C.n; I += nt) {
+    T acc = T(0);
+    for (int64_t t = L.mptr[I]; t < L.mptr[I + 1]; t++) acc = acc + vld<T, G>(L.res + L.midx[t]);
+    C.r[I] = acc;
+  }
+  return sync();
+}
+
+// prolongation from level l + 1 and post-smoothing of level l
+template <class T, bool G, class Sync>
+__device__ bool level_up(const CoarseHierarchy<T> &h, int l, int64_t tid, int64_t nt, const Sync &sync) {
+  const CoarseLevel<T> &L = h.lv[l];
+  const CoarseLevel<T> &C = h.lv[l + 1];
+  for (int64_t i = tid; i < L.n; i += nt) {
+    const int32_t a = L.agg[i];
+    if (a >= 0) L.e[i] = vld<T, G>(L.e + i) + vld<T, G>(C.e + a);
+  }
+  if (!sync()) return false;
+  return coarse_cheb<T, G>(L, h.deg, false, tid, nt, sync);
+}
+
+// levels h.l0 .. last by the calling block (block barriers), the coarsest by
+// the dense inverse
+// (G: vectors read through L2, for the block of a grid kernel whose other
+// blocks wrote them)
+template <class T, bool G>
+__device__ void coarse_block(const CoarseHierarchy<T> &h) {
+  const BlockSync bs;
+  const int64_t tid = threadIdx.x, nt = blockDim.x;
+  const int last = h.nlev - 1;
+  for (int l = h.l0; l < last; l++) level_down<T, G>(h, l, tid, nt, bs);
+  {
+    const CoarseLevel<T> &C = h.lv[last];
+    for (int64_t i = tid; i < C.n; i += nt) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < C.n; j++) acc = fma(h.cinv[i * C.n + j], to_d(vld<T, G>(C.r + j)), acc);
+      C.e[i] = static_cast<T>(acc);
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= h.l0; l--) level_up<T, G>(h, l, tid, nt, bs);
 }
 
 template <class T>
 __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseHierarchy<T> h) {
   pdl_enter();
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int last = h.nlev - 1;
-  for (int l = h.l0; l < last; l++) {
-    const CoarseLevel<T> &L = h.lv[l];
-    coarse_cheb(L, h.deg, true);
-    for (int64_t i = tid; i < L.n; i += nt) L.res[i] = L.r[i] - csr_rowdot(L, i, L.e);
-    __syncthreads();
-    const CoarseLevel<T> &C = h.lv[l + 1];
-    for (int64_t I = tid; I < C.n; I += nt) {
-      T acc = T(0);
-      for (int64_t t = L.mptr[I]; t < L.mptr[I + 1]; t++) acc = acc + L.res[L.midx[t]];
-      C.r[I] = acc;
-    }
-    __syncthreads();
-  }
-  {
-    const CoarseLevel<T> &C = h.lv[last];
-    for (int64_t i = tid; i < C.n; i += nt) {
-      double acc = 0.0;
-      for (int64_t j = 0; j < C.n; j++) acc = fma(h.cinv[i * C.n + j], to_d(C.r[j]), acc);
-      C.e[i] = static_cast<T>(acc);
-    }
-    __syncthreads();
-  }
-  for (int l = last - 1; l >= h.l0; l--) {
-    const CoarseLevel<T> &L = h.lv[l];
-    const CoarseLevel<T> &C = h.lv[l + 1];
-    for (int64_t i = tid; i < L.n; i += nt) {
-      const int32_t a = L.agg[i];
-      if (a >= 0) L.e[i] = L.e[i] + C.e[a];
-    }
-    __syncthreads();
-    coarse_cheb(L, h.deg, false);
-  }
+  coarse_block<T, false>(h);
+}
+
+// The V-cycle from level l1 down on the whole grid of a cooperative launch:
+// levels l1 .. h.l0 - 1 (above the single-block size) with grid barriers,
+// levels h.l0 .. last by block 0 alone while the others wait, then back up.
+// A barrier that times out sets *bar.err and ends the kernel; the host reads
+// the word after the V-cycle's solve iteration.
+template <class T>
+__global__ void __launch_bounds__(1024) k_vcycle_mid(CoarseHierarchy<T> h, int l1, GridSync bar) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  for (int l = l1; l < h.l0; l++)
+    if (!level_down<T, true>(h, l, tid, nt, bar)) return;
+  if (blockIdx.x == 0) coarse_block<T, true>(h);
+  if (!bar()) return;
+  for (int l = h.l0 - 1; l >= l1; l--)
+    if (!level_up<T, true>(h, l, tid, nt, bar)) return;
 }
 
 // ------------------------------------------------------- FGMRES / CGS2
-template <int KC>
-__global__ void __launch_bounds__(kThreads) k_multidot(const double *__restrict__ V, int64_t N, int K,
-                                                       const double *__restrict__ w, double *partial,
-                                                       unsigned int *counter, double *out) {
-  pdl_enter();
-  // out[k] = <V_k, w> for k < K, out[K] = <w, w>
-  const int KT = K + 1;
-  for (int k0 = 0; k0 < KT; k0 += KC) {
-    double acc[KC] = {};
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
-      const double wi = w[i];
-#pragma unroll
-      for (int u = 0; u < KC; u++) {
-        const int k = k0 + u;
-        if (k < K) acc[u] = fma(V[(int64_t)k * N + i], wi, acc[u]);
-        else if (k == K) acc[u] = fma(wi, wi, acc[u]);
-      }
-    }
-    block_partial<KC>(acc, partial + (int64_t)blockIdx.x * kRedStride + k0);
-  }
-  last_block_finish(partial, counter, KT, out, 0);
-}
-
 // w -= sum_k h_k V_k; if want_norm: out[0] = ||w||^2
 __global__ void __launch_bounds__(kThreads) k_cgs_update(const double *__restrict__ V, int64_t N, int K,
                                                          const double *__restrict__ h, double *__restrict__ w,
@@ -1038,23 +1134,57 @@ __device__ void last_block_finish_kb(const double *partial, unsigned int *counte
 }
 
 template <int KM>
-__device__ void block_partial_kb(double (&acc)[KM], int K, double *partial) {
-  __shared__ double sm[kWarps][KM];
+__device__ void block_partial_kb(double (&acc)[KM], int K, double *partial, const double *extra = nullptr) {
+  // partial[k][block] for k < K from acc, and for k = K from *extra if given
+  __shared__ double sm[kWarps][KM + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int u = 0; u < KM; u++) {
-    if (u < K) {
-      const double v = warp_sum(acc[u]);
-      if (lane == 0) sm[warp][u] = v;
-    }
+  constexpr int kSpan = 32 / KM;
+  const double v = warp_reduce_scatter<KM>(acc, lane);
+  if ((lane & (kSpan - 1)) == 0) sm[warp][lane / kSpan] = v;
+  if (extra) {
+    const double e = warp_sum(*extra);
+    if (lane == 0) sm[warp][KM] = e;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < K; k += kThreads) {
+  const int Kt = K + (extra ? 1 : 0);
+  for (int k = threadIdx.x; k < Kt; k += kThreads) {
+    const int src = k < K ? k : KM;
     double t = 0.0;
-    for (int w = 0; w < kWarps; w++) t += sm[w][k];
+    for (int w = 0; w < kWarps; w++) t += sm[w][src];
     partial[(int64_t)k * gridDim.x + blockIdx.x] = t;
   }
   __syncthreads();
+}
+
+// out[k] = <V_k, w> for k < K, out[K] = <w, w>, for any K up to the
+// largest restart: chunks of KC vectors, one pass over each chunk, partial
+// sums stored [k][block] and finished a warp per k.
+template <int KC>
+__global__ void __launch_bounds__(kThreads) k_multidot(const double *__restrict__ V, int64_t N, int K,
+                                                       const double *__restrict__ w, double *partial,
+                                                       unsigned int *counter, double *out) {
+  pdl_enter();
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int Kc = min(KC, K - k0);
+    const bool last = k0 + KC >= K;
+    const double *Vc = V + (int64_t)k0 * N;
+    double acc[KC] = {};
+    double ww = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
+      const double wi = w[i];
+      if (last) ww = fma(wi, wi, ww);
+#pragma unroll
+      for (int g = 0; g < KC; g += 4) {
+        if (g < Kc) {
+#pragma unroll
+          for (int u = g; u < g + 4; u++)
+            if (u < Kc) acc[u] = fma(Vc[(int64_t)u * N + i], wi, acc[u]);
+        }
+      }
+    }
+    block_partial_kb<KC>(acc, Kc, partial + (int64_t)k0 * gridDim.x, last ? &ww : nullptr);
+  }
+  last_block_finish_kb(partial, counter, K + 1, out);
 }
 
 // out[k] = <V_k, w> for k < K, out[K] = <w, w>
@@ -1064,15 +1194,22 @@ __global__ void __launch_bounds__(kThreads) k_cgs_dots(const double *__restrict_
                                                        unsigned int *counter, double *out) {
   pdl_enter();
   double acc[KM] = {};
+  double ww = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
     const double wi = w[i];
+    ww = fma(wi, wi, ww);
+    // groups of four: K is the same for every thread, so a group past K is
+    // branched over rather than issued with its lanes masked off
 #pragma unroll
-    for (int u = 0; u < KM; u++) {
-      if (u < K) acc[u] = fma(V[(int64_t)u * N + i], wi, acc[u]);
-      else if (u == K) acc[u] = fma(wi, wi, acc[u]);
+    for (int g = 0; g < KM; g += 4) {
+      if (g < K) {
+#pragma unroll
+        for (int u = g; u < g + 4; u++)
+          if (u < K) acc[u] = fma(V[(int64_t)u * N + i], wi, acc[u]);
+      }
     }
   }
-  block_partial_kb<KM>(acc, K + 1, partial);
+  block_partial_kb<KM>(acc, K, partial, &ww);
   last_block_finish_kb(partial, counter, K + 1, out);
 }
 
@@ -1088,13 +1225,27 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_dots(const double *__re
   double acc[KM] = {};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
     double t = w[i];
+    double vv[KM];
 #pragma unroll
-    for (int u = 0; u < KM; u++)
-      if (u < K) t = fma(-sh[u], V[(int64_t)u * N + i], t);
+    for (int g = 0; g < KM; g += 4) {
+      if (g < K) {
+#pragma unroll
+        for (int u = g; u < g + 4; u++)
+          if (u < K) {
+            vv[u] = V[(int64_t)u * N + i];
+            t = fma(-sh[u], vv[u], t);
+          }
+      }
+    }
     w[i] = t;
 #pragma unroll
-    for (int u = 0; u < KM; u++)
-      if (u < K) acc[u] = fma(V[(int64_t)u * N + i], t, acc[u]);
+    for (int g = 0; g < KM; g += 4) {
+      if (g < K) {
+#pragma unroll
+        for (int u = g; u < g + 4; u++)
+          if (u < K) acc[u] = fma(vv[u], t, acc[u]);
+      }
+    }
   }
   block_partial_kb<KM>(acc, K, partial);
   last_block_finish_kb(partial, counter, K, out);
@@ -1547,9 +1698,32 @@ void launch_dense_gemv(int64_t n, const double *Minv, const T *r, T *e, cudaStre
   TRS_LAUNCHED();
 }
 
+// Grid of one wave: the blocks of `kernel` that fit on the device at once
+// (at most cap).  The FP64-bound Gram-Schmidt kernels stride over the vector,
+// so one resident wave avoids a tail wave and keeps the number of partial
+// sums (and their reduction) small.  Looked up once per kernel and device.
+template <class... KArgs>
+unsigned resident_grid(void (*kernel)(KArgs...), unsigned cap) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void *, int>, unsigned>> cache;
+  int dev = 0;
+  TRS_CUDA(cudaGetDevice(&dev));
+  const void *key = reinterpret_cast<const void *>(kernel);
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto &e : cache)
+    if (e.first.first == key && e.first.second == dev) return std::min(cap, e.second);
+  int per_sm = 0, sms = 0;
+  TRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+  TRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned g = (unsigned)std::max(1, per_sm * sms);
+  cache.push_back({{key, dev}, g});
+  return std::min(cap, g);
+}
+
 void launch_multidot(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
-  launch_pdl(k_multidot<16>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
+  launch_pdl(k_multidot<32>, resident_grid(k_multidot<32>, (unsigned)red.grid), kThreads, 0, s, V, N, K, w,
+             red.partial, red.counter, out);
   TRS_LAUNCHED();
 }
 void launch_cgs_update(const double *V, int64_t N, int K, const double *h, double *w, int want_norm,
@@ -1559,20 +1733,31 @@ void launch_cgs_update(const double *V, int64_t N, int K, const double *h, doubl
 }
 void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
-  if (K + 1 <= 8) launch_pdl(k_cgs_dots<8>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
-  else if (K + 1 <= 16) launch_pdl(k_cgs_dots<16>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
-  else if (K + 1 <= 32) launch_pdl(k_cgs_dots<32>, red.grid, kThreads, 0, s, V, N, K, w, red.partial, red.counter, out);
+  const unsigned cap = (unsigned)red.grid;
+  if (K + 1 <= 8)
+    launch_pdl(k_cgs_dots<8>, resident_grid(k_cgs_dots<8>, cap), kThreads, 0, s, V, N, K, w, red.partial,
+               red.counter, out);
+  else if (K + 1 <= 16)
+    launch_pdl(k_cgs_dots<16>, resident_grid(k_cgs_dots<16>, cap), kThreads, 0, s, V, N, K, w, red.partial,
+               red.counter, out);
+  else if (K + 1 <= 32)
+    launch_pdl(k_cgs_dots<32>, resident_grid(k_cgs_dots<32>, cap), kThreads, 0, s, V, N, K, w, red.partial,
+               red.counter, out);
   else throw Error(TRS_ERR_UNSUPPORTED, "fused CGS2 supports at most 31 basis vectors");
   TRS_LAUNCHED();
 }
 void launch_cgs_update_dots(const double *V, int64_t N, int K, const double *h, double *w, const RedScratch &red,
                             double *out, cudaStream_t s) {
+  const unsigned cap = (unsigned)red.grid;
   if (K <= 8)
-    launch_pdl(k_cgs_update_dots<8>, red.grid, kThreads, 0, s, V, N, K, h, w, red.partial, red.counter, out);
+    launch_pdl(k_cgs_update_dots<8>, resident_grid(k_cgs_update_dots<8>, cap), kThreads, 0, s, V, N, K, h, w,
+               red.partial, red.counter, out);
   else if (K <= 16)
-    launch_pdl(k_cgs_update_dots<16>, red.grid, kThreads, 0, s, V, N, K, h, w, red.partial, red.counter, out);
+    launch_pdl(k_cgs_update_dots<16>, resident_grid(k_cgs_update_dots<16>, cap), kThreads, 0, s, V, N, K, h, w,
+               red.partial, red.counter, out);
   else if (K <= 32)
-    launch_pdl(k_cgs_update_dots<32>, red.grid, kThreads, 0, s, V, N, K, h, w, red.partial, red.counter, out);
+    launch_pdl(k_cgs_update_dots<32>, resident_grid(k_cgs_update_dots<32>, cap), kThreads, 0, s, V, N, K, h, w,
+               red.partial, red.counter, out);
   else throw Error(TRS_ERR_UNSUPPORTED, "fused CGS2 supports at most 31 basis vectors");
   TRS_LAUNCHED();
 }
@@ -1601,6 +1786,45 @@ void launch_vcycle_coarse(const CoarseHierarchy<T> &h, cudaStream_t s) {
 }
 template void launch_vcycle_coarse<float>(const CoarseHierarchy<float> &, cudaStream_t);
 template void launch_vcycle_coarse<double>(const CoarseHierarchy<double> &, cudaStream_t);
+
+// One block of 1024 threads per SM, launched cooperatively so that every
+// block is resident (the grid barriers need it).  Plain stream order before
+// and after it (no programmatic dependent launch).
+template <class T>
+void launch_vcycle_mid(const CoarseHierarchy<T> &h, int l1, unsigned *bar, cudaStream_t s) {
+  static std::mutex mu;
+  static int grid_of_dev[64] = {};
+  int dev = 0;
+  TRS_CUDA(cudaGetDevice(&dev));
+  TRS_REQUIRE(dev >= 0 && dev < 64, TRS_ERR_UNSUPPORTED, "device ordinal above 63");
+  int grid;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!grid_of_dev[dev]) {
+      int per_sm = 0, sms = 0;
+      TRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vcycle_mid<T>, 1024, 0));
+      TRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      TRS_REQUIRE(per_sm >= 1, TRS_ERR_UNSUPPORTED, "grid V-cycle kernel does not fit an SM");
+      grid_of_dev[dev] = sms;
+    }
+    grid = grid_of_dev[dev];
+  }
+  const GridSync gs{bar, bar + 1, reinterpret_cast<int *>(bar + 2)};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TRS_CUDA(cudaLaunchKernelEx(&cfg, k_vcycle_mid<T>, h, l1, gs));
+  TRS_LAUNCHED();
+}
+template void launch_vcycle_mid<float>(const CoarseHierarchy<float> &, int, unsigned *, cudaStream_t);
+template void launch_vcycle_mid<double>(const CoarseHierarchy<double> &, int, unsigned *, cudaStream_t);
 
 template <class TS, class TD>
 void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {

@@ -165,6 +165,14 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" :::);
 }
 
+// Relative-permeability tables of the thermal model, passed by value.
+constexpr int kThermalTableMax = 32;
+struct ThermalTables {
+  int nswt, nslt;
+  double swt[3 * kThermalTableMax];   // S_w, k_rw, k_row
+  double slt[3 * kThermalTableMax];   // S_l, k_rg, k_rog
+};
+
 struct Geom {
   int64_t nc;       // cells
   int64_t n_rows;   // cells + other rows
@@ -228,6 +236,7 @@ struct trs_bsr {
   trs::DBuf<int32_t> perf_cell, perf_well;
   trs::DBuf<int64_t> perf_cw, perf_wc, wdiag;                      // tail slots of (c,w), (w,c), (w,w)
   trs::DBuf<double> host_stage;   // device copy of host assembly inputs (trs_bsr_assemble_host)
+  trs::DBuf<double> thermal_props;  // per-cell thermal properties with derivatives (trs_thermal_assemble)
 
   template <class T = double>
   trs::MatView<T> view() const {

@@ -267,6 +267,12 @@ trs_status trs_bsr_create_synthetic(int32_t nx, int32_t ny, int32_t nz, int32_t 
     A->perf_wc.upload(pwc.data(), n_perf, s);
     A->wdiag.alloc(wdiag.size());
     A->wdiag.upload(wdiag.data(), n_wells, s);
+    A->perf_cell.alloc(std::max<int64_t>(n_perf, 1));
+    A->perf_well.alloc(std::max<int64_t>(n_perf, 1));
+    if (n_perf) {
+      A->perf_cell.upload(perf_cell, n_perf, s);
+      A->perf_well.upload(perf_well, n_perf, s);
+    }
     TRS_CUDA(cudaStreamSynchronize(s));
     *out = A.release();
   });

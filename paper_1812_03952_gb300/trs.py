@@ -46,7 +46,7 @@ EXPORTS = (
     "trs_cpr_get_colours", "trs_cpr_get_decoupled", "trs_cpr_get_level", "trs_cpr_vcycle",
     "trs_cpr_destroy", "trs_solve_default_opts", "trs_fgmres_solve", "trs_fgmres_solve_host",
     "trs_bicgstab_solve", "trs_bicgstab_solve_host", "trs_solve_adjoint", "trs_outer_product", "trs_chain_theta", "trs_last_error", "trs_version",
-    "trs_kernel_launches", "trs_residual_norm_noalloc", "trs_profile_spmv",
+    "trs_kernel_launches", "trs_residual_norm_noalloc", "trs_profile_spmv", "trs_thermal_assemble",
 )
 
 
@@ -76,6 +76,30 @@ class SolveStats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+#: field order of trs_thermal_params (include/trs.h)
+THERMAL_FIELDS = (
+    "dx", "dy", "dz", "depth_top", "dt", "kvkh", "gravity",
+    "phi_ref", "cpor", "ctpor", "p_ref", "T_ref", "cp1_r", "cp2_r",
+    "kt_w", "kt_o", "kt_g", "kt_r",
+    "rho_w_ref", "cp_w", "ct1_w", "ct2_w", "cpt_w", "mw_w", "avisc_w", "bvisc_w",
+    "kv1", "kv2", "kv3", "kv4", "kv5", "per_eps", "tc_w", "pc_w")
+THERMAL_FIELDS_2 = ("hvr", "ev", "rho_o_ref", "cp_o", "ct1_o", "ct2_o", "cpt_o", "mw_o", "avisc_o", "bvisc_o",
+                    "cpl1_o", "mug_a", "mug_b", "h_inj", "R_gas")
+
+
+class ThermalParams(C.Structure):
+    _fields_ = ([(f, C.c_double) for f in THERMAL_FIELDS] + [("cpg", C.c_double * 5)]
+                + [(f, C.c_double) for f in THERMAL_FIELDS_2])
+
+    @classmethod
+    def from_dict(cls, d):
+        P = cls()
+        for f in THERMAL_FIELDS + THERMAL_FIELDS_2:
+            setattr(P, f, float(d[f]))
+        P.cpg = (C.c_double * 5)(*[float(d[f"cpg{k}"]) for k in range(1, 6)])
+        return P
 
 
 class BsrInfo(C.Structure):
@@ -143,6 +167,8 @@ def load(path: str = LIB_PATH):
         "trs_kernel_launches": (C.c_uint64, []),
         "trs_residual_norm_noalloc": (i32, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "trs_profile_spmv": (i32, [i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "trs_thermal_assemble": (i32, [vp, C.POINTER(ThermalParams), vp, i32, vp, i32, vp, vp, vp, vp, vp, vp,
+                                       vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -474,6 +500,44 @@ def chain_theta(A: Matrix, perm, M, lam, x, kvkh, c_t, perm_is_log=False):
     _check(load().trs_chain_theta(A.h, _dptr(perm), int(perm_is_log), kvkh, c_t, _dptr(M), _dptr(lam),
                                   _dptr(x), _dptr(dth), _stream()))
     return dth
+
+
+class ThermalSystem:
+    """The thermal model on a synthetic system's grid and wells, resident on
+    the GPU: permeability, state, previous state, gas flags and well data;
+    assemble() fills A (made by trs_bsr_create_synthetic, b = 4) with the
+    Jacobian dR/du and returns the residual R(u) as a device tensor."""
+
+    def __init__(self, sysm, state, swt, slt, device="cuda"):
+        import torch
+        if sysm.b != 4:
+            raise ValueError("the thermal model has b = 4")
+        self.sysm = sysm
+        self.state = state
+        self.P = ThermalParams.from_dict(state.params)
+        self.swt = np.ascontiguousarray(swt, dtype=np.float64)
+        self.slt = np.ascontiguousarray(slt, dtype=np.float64)
+        t = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.A = Matrix.synthetic_pattern(sysm.nx, sysm.ny, sysm.nz, sysm.b, sysm.n_wells,
+                                          sysm.perf_well, sysm.perf_cell)
+        self.k = t(sysm.k)
+        self.u = t(state.u)
+        self.u_old = t(state.u_old)
+        self.gas = t(state.gas)
+        one = lambda a, dtype: t(a) if len(a) else torch.zeros(1, dtype=dtype, device=device)
+        self.wi = one(state.wi, torch.float64)
+        self.well_type = one(state.well_type, torch.int32)
+        self.well_target = one(state.well_target, torch.float64)
+        self.R = _empty(sysm.n_unknowns, device=device)
+
+    def assemble(self, u=None):
+        uu = self.u if u is None else u
+        _check(load().trs_thermal_assemble(self.A.h, C.byref(self.P), _hptr(self.swt), len(self.swt),
+                                           _hptr(self.slt), len(self.slt), _dptr(self.k), _dptr(uu),
+                                           _dptr(self.u_old), _dptr(self.gas), _dptr(self.wi),
+                                           _dptr(self.well_type), _dptr(self.well_target), _dptr(self.R),
+                                           _stream()))
+        return self.R
 
 
 class DeviceSystem:
