@@ -290,9 +290,7 @@ trs_status trs_cpr_setup(const trs_bsr *A, const trs_cpr_opts *opts, void *strea
 trs_status trs_cpr_update(trs_cpr *M, const trs_bsr *A, int32_t reuse_amg, void *stream);
 
 /* z = M^-1 v = CPR(Ã)^-1 (D^-1 v): one application of the preconditioner
- * (device pointers, FP64; computed in the handle's precision).  Synchronises
- * `stream` to check the grid barriers of the V-cycle kernel (TRS_ERR_CUDA if
- * one timed out). */
+ * (device pointers, FP64; computed in the handle's precision). */
 trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *stream);
 
 trs_status trs_cpr_get_info(const trs_cpr *M, trs_cpr_info *info);
@@ -309,8 +307,7 @@ trs_status trs_cpr_get_level(const trs_cpr *M, int32_t level, int64_t *row_ptr, 
                              double *val);
 
 /* Applies one AMG V-cycle of the pressure hierarchy to r (device pointers,
- * n_0 doubles): e = AMG(A_p)^-1 r.  Synchronises `stream` like
- * trs_cpr_apply. */
+ * n_0 doubles): e = AMG(A_p)^-1 r. */
 trs_status trs_cpr_vcycle(const trs_cpr *M, const double *r, double *e, void *stream);
 
 void trs_cpr_destroy(trs_cpr *M);

@@ -914,179 +914,87 @@ __global__ void k_dense_gemv(int64_t n, const double *__restrict__ Minv, const T
 // The V-cycle from level h.l0 down, by one block of 1024 threads: the same
 // Chebyshev, residual, restriction, coarsest solve and prolongation steps as
 // the per-level kernels above (identical arithmetic), separated by block
-// barriers instead of launches.  The same steps also run on the whole grid
-// (k_vcycle_mid), separated by grid barriers; there every vector written in
-// the kernel is read with ld.global.cg (L2), since an SM's L1 may hold a
-// line that another SM has rewritten since.
-template <class T, bool G>
-__device__ __forceinline__ T vld(const T *p) {
-  if constexpr (G) return __ldcg(p);
-  else return *p;
-}
-
-template <class T, bool G = false>
+// barriers instead of launches.
+template <class T>
 __device__ __forceinline__ T csr_rowdot(const CoarseLevel<T> &L, int64_t i, const T *x) {
   T acc = T(0);
-  for (int64_t p = L.rp[i]; p < L.rp[i + 1]; p++) acc = fma(L.val[p], vld<T, G>(x + L.col[p]), acc);
+  for (int64_t p = L.rp[i]; p < L.rp[i + 1]; p++) acc = fma(L.val[p], x[L.col[p]], acc);
   return acc;
 }
 
-// block barrier
-struct BlockSync {
-  __device__ __forceinline__ bool operator()() const {
-    __syncthreads();
-    return true;
-  }
-};
-
-// Grid barrier of a cooperative launch: the last block to arrive advances the
-// generation word; the others wait for it a bounded time (kGridSpinLimit
-// rounds of about 0.1 us, about 1 s), after which they set the error word,
-// and every block leaves the kernel at its next barrier.
-constexpr unsigned kGridSpinLimit = 10000000u;
-#ifndef TRS_GRID_SPIN_NS
-#define TRS_GRID_SPIN_NS 100
-#endif
-struct GridSync {
-  unsigned *count;
-  unsigned *gen;
-  int *err;
-  __device__ bool operator()() const {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (!*reinterpret_cast<volatile int *>(err)) {
-        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
-        __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-          *reinterpret_cast<volatile unsigned *>(count) = 0u;
-          __threadfence();
-          atomicAdd(gen, 1u);
-        } else {
-          unsigned it = 0;
-          while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
-            if (++it > kGridSpinLimit) {
-              atomicExch(err, 1);
-              break;
-            }
-            if (TRS_GRID_SPIN_NS) __nanosleep(TRS_GRID_SPIN_NS);
-          }
-        }
-        __threadfence();
-      }
-    }
-    __syncthreads();
-    return !*reinterpret_cast<volatile int *>(err);
-  }
-};
-
-template <class T, bool G, class Sync>
-__device__ bool coarse_cheb(const CoarseLevel<T> &L, int deg, bool zero_init, int64_t tid, int64_t nt,
-                            const Sync &sync) {
+template <class T>
+__device__ void coarse_cheb(const CoarseLevel<T> &L, int deg, bool zero_init) {
+  const int tid = threadIdx.x, nt = blockDim.x;
   const T *r = L.r;
   T *e = L.e, *res = L.res, *d = L.d, *dn = L.dn;
   if (zero_init) {
     for (int64_t i = tid; i < L.n; i += nt) {
-      d[i] = (L.dinv[i] * vld<T, G>(r + i)) * L.inv_theta;
+      d[i] = (L.dinv[i] * r[i]) * L.inv_theta;
       e[i] = T(0);
     }
   } else {
     for (int64_t i = tid; i < L.n; i += nt) {
-      const T v = vld<T, G>(r + i) - csr_rowdot<T, G>(L, i, e);
+      const T v = r[i] - csr_rowdot(L, i, e);
       res[i] = v;
       d[i] = (L.dinv[i] * v) * L.inv_theta;
     }
   }
-  if (!sync()) return false;
+  __syncthreads();
   const T *res_in = zero_init ? r : res;
   for (int k = 1; k < deg; k++) {
     const int last = (k == deg - 1);
     for (int64_t i = tid; i < L.n; i += nt) {
-      const T rv = vld<T, G>(res_in + i) - csr_rowdot<T, G>(L, i, d);
+      const T rv = res_in[i] - csr_rowdot(L, i, d);
       res[i] = rv;
-      const T di = vld<T, G>(d + i);
+      const T di = d[i];
       const T nv = fma(L.c1[k], di, L.c2[k] * (L.dinv[i] * rv));
-      const T ev = vld<T, G>(e + i) + di;
+      const T ev = e[i] + di;
       if (last) e[i] = ev + nv;
       else { e[i] = ev; dn[i] = nv; }
     }
-    if (!sync()) return false;
+    __syncthreads();
     res_in = res;
     T *t = d; d = dn; dn = t;
   }
-  return true;
-}
-
-// pre-smoothing, residual and restriction of level l into level l + 1
-template <class T, bool G, class Sync>
-__device__ bool level_down(const CoarseHierarchy<T> &h, int l, int64_t tid, int64_t nt, const Sync &sync) {
-  const CoarseLevel<T> &L = h.lv[l];
-  if (!coarse_cheb<T, G>(L, h.deg, true, tid, nt, sync)) return false;
-  for (int64_t i = tid; i < L.n; i += nt) L.res[i] = vld<T, G>(L.r + i) - csr_rowdot<T, G>(L, i, L.e);
-  if (!sync()) return false;
-  const CoarseLevel<T> &C = h.lv[l + 1];
-  for (int64_t I = tid; I < C.n; I += nt) {
-    T acc = T(0);
-    for (int64_t t = L.mptr[I]; t < L.mptr[I + 1]; t++) acc = acc + vld<T, G>(L.res + L.midx[t]);
-    C.r[I] = acc;
-  }
-  return sync();
-}
-
-// prolongation from level l + 1 and post-smoothing of level l
-template <class T, bool G, class Sync>
-__device__ bool level_up(const CoarseHierarchy<T> &h, int l, int64_t tid, int64_t nt, const Sync &sync) {
-  const CoarseLevel<T> &L = h.lv[l];
-  const CoarseLevel<T> &C = h.lv[l + 1];
-  for (int64_t i = tid; i < L.n; i += nt) {
-    const int32_t a = L.agg[i];
-    if (a >= 0) L.e[i] = vld<T, G>(L.e + i) + vld<T, G>(C.e + a);
-  }
-  if (!sync()) return false;
-  return coarse_cheb<T, G>(L, h.deg, false, tid, nt, sync);
-}
-
-// levels h.l0 .. last by the calling block (block barriers), the coarsest by
-// the dense inverse
-// (G: vectors read through L2, for the block of a grid kernel whose other
-// blocks wrote them)
-template <class T, bool G>
-__device__ void coarse_block(const CoarseHierarchy<T> &h) {
-  const BlockSync bs;
-  const int64_t tid = threadIdx.x, nt = blockDim.x;
-  const int last = h.nlev - 1;
-  for (int l = h.l0; l < last; l++) level_down<T, G>(h, l, tid, nt, bs);
-  {
-    const CoarseLevel<T> &C = h.lv[last];
-    for (int64_t i = tid; i < C.n; i += nt) {
-      double acc = 0.0;
-      for (int64_t j = 0; j < C.n; j++) acc = fma(h.cinv[i * C.n + j], to_d(vld<T, G>(C.r + j)), acc);
-      C.e[i] = static_cast<T>(acc);
-    }
-    __syncthreads();
-  }
-  for (int l = last - 1; l >= h.l0; l--) level_up<T, G>(h, l, tid, nt, bs);
 }
 
 template <class T>
 __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseHierarchy<T> h) {
   pdl_enter();
-  coarse_block<T, false>(h);
-}
-
-// The V-cycle from level l1 down on the whole grid of a cooperative launch:
-// levels l1 .. h.l0 - 1 (above the single-block size) with grid barriers,
-// levels h.l0 .. last by block 0 alone while the others wait, then back up.
-// A barrier that times out sets *bar.err and ends the kernel; the host reads
-// the word after the V-cycle's solve iteration.
-template <class T>
-__global__ void __launch_bounds__(1024) k_vcycle_mid(CoarseHierarchy<T> h, int l1, GridSync bar) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
-  for (int l = l1; l < h.l0; l++)
-    if (!level_down<T, true>(h, l, tid, nt, bar)) return;
-  if (blockIdx.x == 0) coarse_block<T, true>(h);
-  if (!bar()) return;
-  for (int l = h.l0 - 1; l >= l1; l--)
-    if (!level_up<T, true>(h, l, tid, nt, bar)) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int last = h.nlev - 1;
+  for (int l = h.l0; l < last; l++) {
+    const CoarseLevel<T> &L = h.lv[l];
+    coarse_cheb(L, h.deg, true);
+    for (int64_t i = tid; i < L.n; i += nt) L.res[i] = L.r[i] - csr_rowdot(L, i, L.e);
+    __syncthreads();
+    const CoarseLevel<T> &C = h.lv[l + 1];
+    for (int64_t I = tid; I < C.n; I += nt) {
+      T acc = T(0);
+      for (int64_t t = L.mptr[I]; t < L.mptr[I + 1]; t++) acc = acc + L.res[L.midx[t]];
+      C.r[I] = acc;
+    }
+    __syncthreads();
+  }
+  {
+    const CoarseLevel<T> &C = h.lv[last];
+    for (int64_t i = tid; i < C.n; i += nt) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < C.n; j++) acc = fma(h.cinv[i * C.n + j], to_d(C.r[j]), acc);
+      C.e[i] = static_cast<T>(acc);
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= h.l0; l--) {
+    const CoarseLevel<T> &L = h.lv[l];
+    const CoarseLevel<T> &C = h.lv[l + 1];
+    for (int64_t i = tid; i < L.n; i += nt) {
+      const int32_t a = L.agg[i];
+      if (a >= 0) L.e[i] = L.e[i] + C.e[a];
+    }
+    __syncthreads();
+    coarse_cheb(L, h.deg, false);
+  }
 }
 
 // ------------------------------------------------------- FGMRES / CGS2
@@ -1787,44 +1695,6 @@ void launch_vcycle_coarse(const CoarseHierarchy<T> &h, cudaStream_t s) {
 template void launch_vcycle_coarse<float>(const CoarseHierarchy<float> &, cudaStream_t);
 template void launch_vcycle_coarse<double>(const CoarseHierarchy<double> &, cudaStream_t);
 
-// One block of 1024 threads per SM, launched cooperatively so that every
-// block is resident (the grid barriers need it).  Plain stream order before
-// and after it (no programmatic dependent launch).
-template <class T>
-void launch_vcycle_mid(const CoarseHierarchy<T> &h, int l1, unsigned *bar, cudaStream_t s) {
-  static std::mutex mu;
-  static int grid_of_dev[64] = {};
-  int dev = 0;
-  TRS_CUDA(cudaGetDevice(&dev));
-  TRS_REQUIRE(dev >= 0 && dev < 64, TRS_ERR_UNSUPPORTED, "device ordinal above 63");
-  int grid;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!grid_of_dev[dev]) {
-      int per_sm = 0, sms = 0;
-      TRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vcycle_mid<T>, 1024, 0));
-      TRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      TRS_REQUIRE(per_sm >= 1, TRS_ERR_UNSUPPORTED, "grid V-cycle kernel does not fit an SM");
-      grid_of_dev[dev] = sms;
-    }
-    grid = grid_of_dev[dev];
-  }
-  const GridSync gs{bar, bar + 1, reinterpret_cast<int *>(bar + 2)};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(1024);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  TRS_CUDA(cudaLaunchKernelEx(&cfg, k_vcycle_mid<T>, h, l1, gs));
-  TRS_LAUNCHED();
-}
-template void launch_vcycle_mid<float>(const CoarseHierarchy<float> &, int, unsigned *, cudaStream_t);
-template void launch_vcycle_mid<double>(const CoarseHierarchy<double> &, int, unsigned *, cudaStream_t);
 
 template <class TS, class TD>
 void launch_cast(const TS *src, TD *dst, int64_t n, cudaStream_t s) {

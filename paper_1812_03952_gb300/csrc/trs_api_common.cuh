@@ -103,7 +103,6 @@ struct trs_cpr {
   trs::DBuf<char> Z;
   trs::DBuf<double> bw, bsc, bpart;   // BiCGSTAB vectors (r^, p, v, p^, s, s^, t), scalars, SpMV partials
   trs::DBuf<double> host_bx;          // device copies of b and x for the host-buffer solves (2 N)
-  trs::DBuf<unsigned> coop;           // grid barrier of the V-cycle kernel: count, generation, error
   trs::DBuf<double> partial;
   trs::DBuf<unsigned int> counter;
   int red_grid = 0;

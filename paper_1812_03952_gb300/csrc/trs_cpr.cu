@@ -542,10 +542,6 @@ void setup_all(trs_cpr *M, const trs_bsr *A, cudaStream_t s) {
   }
   M->ap_ell64.alloc(std::max<int64_t>((int64_t)kSlots * nc, 1));
   M->ap_ell64.zero(s);
-  if (!M->coop.p) {
-    M->coop.alloc(4);
-    M->coop.zero(s);
-  }
   M->ap_tval64.alloc(std::max<int64_t>(A->ntail, 1));
   // colouring of the block pattern and the colour-major order
   M->colour.alloc(n);
@@ -739,15 +735,6 @@ CoarseHierarchy<T> coarse_hierarchy(const trs_cpr *M, int l0) {
   return h;
 }
 
-// Synchronises s and fails if a grid barrier of the V-cycle kernel timed out.
-void check_grid_barrier(const trs_cpr *M, cudaStream_t s) {
-  if (!M->coop.p) return;
-  int err = 0;
-  TRS_CUDA(cudaMemcpyAsync(&err, M->coop.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TRS_CUDA(cudaStreamSynchronize(s));
-  TRS_REQUIRE(!err, TRS_ERR_CUDA, "a grid barrier of the V-cycle kernel timed out");
-}
-
 template <class T>
 void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
   const int L = M->nlev;
@@ -759,14 +746,6 @@ void vcycle(const trs_cpr *M, int l, const T *r, T *e, cudaStream_t s) {
   if (l > 0 && l == coarse_fuse_level(M)) {
     // r and e are this level's own buffers (written by the restriction above)
     launch_vcycle_coarse<T>(coarse_hierarchy<T>(M, l), s);
-    return;
-  }
-  if (l > 0 && l < coarse_fuse_level(M) && Lv.A.n <= kGridVcycleRows) {
-    // this level and those below it up to the single-block ones: one
-    // cooperative launch with grid barriers between the steps
-    CoarseHierarchy<T> h = coarse_hierarchy<T>(M, l);
-    h.l0 = coarse_fuse_level(M);
-    launch_vcycle_mid<T>(h, l, M->coop.p, s);
     return;
   }
   if (l == L - 1) {
@@ -991,11 +970,8 @@ trs_status fgmres(const trs_bsr *A, trs_cpr *M, const double *b, double *x, cons
       pt.mark(3, s);
       iters++;
       double hs[2];
-      int coop_err = 0;
       TRS_CUDA(cudaMemcpyAsync(hs, M->status.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      TRS_CUDA(cudaMemcpyAsync(&coop_err, M->coop.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
-      TRS_REQUIRE(!coop_err, TRS_ERR_CUDA, "a grid barrier of the V-cycle kernel timed out");
       pt.add(0, 0, 1);
       pt.add(1, 1, 2);
       pt.add(2, 2, 3);
@@ -1110,11 +1086,8 @@ trs_status bicgstab(const trs_bsr *A, trs_cpr *M, const double *b, double *x, co
       pt.mark(6, s);
       iters++;
       BicgScalars h;
-      int coop_err = 0;
       TRS_CUDA(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
-      TRS_CUDA(cudaMemcpyAsync(&coop_err, M->coop.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
       TRS_CUDA(cudaStreamSynchronize(s));
-      TRS_REQUIRE(!coop_err, TRS_ERR_CUDA, "a grid barrier of the V-cycle kernel timed out");
       pt.add(0, 0, 1);
       pt.add(0, 3, 4);
       pt.add(1, 1, 2);
@@ -1289,7 +1262,6 @@ trs_status trs_cpr_apply(const trs_cpr *M, const double *v, double *z, void *str
     } else {
       cpr_apply_full<double>(M, v, nullptr, nullptr, z, s);
     }
-    check_grid_barrier(M, s);
   });
 }
 
@@ -1305,7 +1277,6 @@ trs_status trs_cpr_vcycle(const trs_cpr *M, const double *r, double *e, void *st
     } else {
       vcycle<double>(M, 0, r, e, s);
     }
-    check_grid_barrier(M, s);
   });
 }
 

@@ -81,16 +81,7 @@ struct CoarseHierarchy {
 
 template <class T>
 void launch_vcycle_coarse(const CoarseHierarchy<T> &h, cudaStream_t s);
-// levels l1 .. h.l0 - 1 on the whole grid with grid barriers, then h.l0 ..
-// last on one block; bar: 3 words (count, generation, error), zero at first use
-template <class T>
-void launch_vcycle_mid(const CoarseHierarchy<T> &h, int l1, unsigned *bar, cudaStream_t s);
-// Levels of at most this many rows (and above the single-block size) run in
-// the grid-synchronised V-cycle kernel; 0 keeps one launch per step.
-#ifndef TRS_GRID_VCYCLE_ROWS
-#define TRS_GRID_VCYCLE_ROWS 0
-#endif
-constexpr int64_t kGridVcycleRows = TRS_GRID_VCYCLE_ROWS;
+
 
 // Reduction scratch: per-block partial sums and a ticket counter.
 struct RedScratch {
