@@ -18,6 +18,8 @@
 //     respect to the cell and to the neighbour, each from a dual-number pass)
 //     and the perforations, written into the row's ELL blocks and tail;
 //   k_thermal_wells: per well, the well equation.
+#include <type_traits>
+
 #include "trs_api_common.cuh"
 #include "trs_kernels.cuh"
 
@@ -137,9 +139,29 @@ __device__ __forceinline__ D4 dpow(const D4 &a, double e) {
   return r;
 }
 
+// the same operations on plain values (no derivative carried)
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ double val(const D4 &x) { return x.v; }
+__device__ __forceinline__ double dexp(double a) { return exp(a); }
+__device__ __forceinline__ double dlog(double a) { return log(a); }
+__device__ __forceinline__ double dpow(double a, double e) { return pow(a, e); }
+// the promotion of a value to a dual number with zero derivatives
+__device__ __forceinline__ D4 dual(double a) { return cst(a); }
+__device__ __forceinline__ D4 dual(const D4 &a) { return a; }
+
 // ------------------------------------------------------------- properties
 // piecewise-linear interpolation of column c of an n x 3 table on its closed
 // interval, constant beyond the ends (the end segments' slopes at the ends)
+__device__ double table(const double *tab, int n, int c, double s) {
+  if (s < tab[0]) return tab[c];
+  if (s > tab[(n - 1) * 3]) return tab[(n - 1) * 3 + c];
+  int i = 0;
+  while (i + 1 < n - 1 && s >= tab[(i + 1) * 3]) i++;
+  const double x0 = tab[i * 3], x1 = tab[(i + 1) * 3], y0 = tab[i * 3 + c], y1 = tab[(i + 1) * 3 + c];
+  const double slope = (y1 - y0) / (x1 - x0);
+  return y0 + slope * (s - x0);
+}
+
 __device__ D4 table(const double *tab, int n, int c, const D4 &s) {
   if (s.v < tab[0]) return cst(tab[c]);
   if (s.v > tab[(n - 1) * 3]) return cst(tab[(n - 1) * 3 + c]);
@@ -157,8 +179,7 @@ __device__ D4 table(const double *tab, int n, int c, const D4 &s) {
 // Largest real root of Z^3 - Z^2 + (A - B - B^2) Z - A B = 0 (Redlich-Kwong,
 // Sec. "Compressibility Factor of Real Gas"): Newton's method on the values
 // from above the largest root, then dZ = -(f_A dA + f_B dB) / f_Z.
-__device__ D4 rk_z(const D4 &A, const D4 &B) {
-  const double a = A.v, b = B.v;
+__device__ double rk_z(double a, double b) {
   const double c1 = a - b - b * b, c0 = -a * b;
   double z = 1.0 + fabs(c1) + fabs(c0);
   for (int it = 0; it < 200; it++) {
@@ -168,6 +189,13 @@ __device__ D4 rk_z(const D4 &A, const D4 &B) {
     z = z - dz;
     if (fabs(dz) <= 1e-16 * fabs(z)) break;
   }
+  return z;
+}
+
+__device__ D4 rk_z(const D4 &A, const D4 &B) {
+  const double a = A.v, b = B.v;
+  const double c1 = a - b - b * b;
+  const double z = rk_z(a, b);
   const double fz = (3.0 * z - 2.0) * z + c1;
   const double fa = z - b, fb = -z - 2.0 * b * z - a;
   D4 r;
@@ -177,39 +205,43 @@ __device__ D4 rk_z(const D4 &A, const D4 &B) {
   return r;
 }
 
+template <class N>
 struct CellProps {
-  D4 phi, rho[3], lam[3], H[3], gam[3], KT, Kstar;
+  N phi, rho[3], lam[3], H[3], gam[3], KT, Kstar;
 };
 
-__device__ void cell_props(const trs_thermal_params &P, const ThermalTables &tb, const D4 &p, const D4 &Sw,
-                           const D4 &Sg, const D4 &T, CellProps &o) {
-  const D4 So = 1.0 - Sw - Sg;
-  const D4 TK = T + 273.15, dp = p - P.p_ref, dT = T - P.T_ref;
+// N = D4: with the derivatives with respect to the cell's unknowns; N =
+// double: values only (the old time level)
+template <class N>
+__device__ void cell_props(const trs_thermal_params &P, const ThermalTables &tb, const N &p, const N &Sw,
+                           const N &Sg, const N &T, CellProps<N> &o) {
+  const N So = 1.0 - Sw - Sg;
+  const N TK = T + 273.15, dp = p - P.p_ref, dT = T - P.T_ref;
   o.phi = P.phi_ref * (1.0 + P.cpor * dp - P.ctpor * dT);
   o.rho[0] = P.rho_w_ref * dexp(P.cp_w * dp - P.ct1_w * dT - 0.5 * P.ct2_w * dT * dT + P.cpt_w * dp * dT);
   o.rho[1] = P.rho_o_ref * dexp(P.cp_o * dp - P.ct1_o * dT - 0.5 * P.ct2_o * dT * dT + P.cpt_o * dp * dT);
   {
     const double TcK = P.tc_w + 273.15;
-    const D4 A = 0.427480 * (p / P.pc_w) * dpow(TcK / TK, 2.5);
-    const D4 B = 0.086640 * (p / P.pc_w) * (TcK / TK);
-    const D4 Z = rk_z(A, B);
+    const N A = 0.427480 * (p / P.pc_w) * dpow(TcK / TK, 2.5);
+    const N B = 0.086640 * (p / P.pc_w) * (TcK / TK);
+    const N Z = rk_z(A, B);
     o.rho[2] = p / (Z * P.R_gas * TK);
   }
-  D4 mu[3];
+  N mu[3];
   mu[0] = P.avisc_w * dexp(P.bvisc_w / TK);
   mu[1] = P.avisc_o * dexp(P.bvisc_o / TK);
   mu[2] = P.mug_a + P.mug_b * T;
-  const D4 krw = table(tb.swt, tb.nswt, 1, Sw), krow = table(tb.swt, tb.nswt, 2, Sw);
-  const D4 Sl = 1.0 - Sg;
-  const D4 krg = table(tb.slt, tb.nslt, 1, Sl), krog = table(tb.slt, tb.nslt, 2, Sl);
+  const N krw = table(tb.swt, tb.nswt, 1, Sw), krow = table(tb.swt, tb.nswt, 2, Sw);
+  const N Sl = 1.0 - Sg;
+  const N krg = table(tb.slt, tb.nslt, 1, Sl), krog = table(tb.slt, tb.nslt, 2, Sl);
   const double krocw = tb.swt[2];
-  D4 kro = krocw * ((krow / cst(krocw) + krw) * (krog / cst(krocw) + krg) - krw - krg);
-  if (kro.v < 0.0) kro = cst(0.0);
+  N kro = krocw * ((krow / krocw + krw) * (krog / krocw + krg) - krw - krg);
+  if (val(kro) < 0.0) kro = kro * 0.0;
   o.lam[0] = krw * o.rho[0] / mu[0];
   o.lam[1] = kro * o.rho[1] / mu[1];
   o.lam[2] = krg * o.rho[2] / mu[2];
   // gas-based water enthalpy: integral of the heat-capacity polynomial from T_ref
-  D4 hg = cst(0.0), tp = T;
+  N hg = T * 0.0, tp = T;
   double rp = P.T_ref;
 #pragma unroll
   for (int k = 0; k < 5; k++) {
@@ -217,7 +249,8 @@ __device__ void cell_props(const trs_thermal_params &P, const ThermalTables &tb,
     tp = tp * T;
     rp = rp * P.T_ref;
   }
-  const D4 hv = T.v >= P.tc_w ? cst(0.0) : P.hvr * dexp(P.ev * dlog(P.tc_w - T));
+  N hv = T * 0.0;
+  if (val(T) < P.tc_w) hv = P.hvr * dexp(P.ev * dlog(P.tc_w - T));
   o.H[0] = hg - hv;
   o.H[1] = P.cpl1_o * dT;
   o.H[2] = hg;
@@ -229,23 +262,25 @@ __device__ void cell_props(const trs_thermal_params &P, const ThermalTables &tb,
 }
 
 // accumulated water and oil of a cell of volume V
-__device__ void amounts(const CellProps &o, const D4 &Sw, const D4 &Sg, double V, D4 (&N)[3]) {
-  const D4 So = 1.0 - Sw - Sg;
-  N[0] = V * o.phi * (o.rho[0] * Sw + o.rho[2] * Sg);
-  N[1] = V * o.phi * o.rho[1] * So;
+template <class N>
+__device__ void amounts(const CellProps<N> &o, const N &Sw, const N &Sg, double V, N (&Nm)[3]) {
+  const N So = 1.0 - Sw - Sg;
+  Nm[0] = V * o.phi * (o.rho[0] * Sw + o.rho[2] * Sg);
+  Nm[1] = V * o.phi * o.rho[1] * So;
 }
 
 // accumulated energy: fluids' internal energy U = H - p / rho and the rock's
 // (constant rock volume (1 - phi_ref) V, Sec. "Energy Conservation Equation")
-__device__ D4 energy_amount(const trs_thermal_params &P, const CellProps &o, const D4 &p, const D4 &Sw,
-                            const D4 &Sg, const D4 &T, double V) {
-  const D4 So = 1.0 - Sw - Sg;
-  const D4 S[3] = {Sw, So, Sg};
-  D4 e = cst(0.0);
+template <class N>
+__device__ N energy_amount(const trs_thermal_params &P, const CellProps<N> &o, const N &p, const N &Sw,
+                           const N &Sg, const N &T, double V) {
+  const N So = 1.0 - Sw - Sg;
+  const N S[3] = {Sw, So, Sg};
+  N e = T * 0.0;
 #pragma unroll
   for (int a = 0; a < 3; a++) e = e + o.rho[a] * S[a] * (o.H[a] - p / o.rho[a]);
-  const D4 dT = T - P.T_ref;
-  const D4 Ur = P.cp1_r * dT + 0.5 * P.cp2_r * (T * T - P.T_ref * P.T_ref);
+  const N dT = T - P.T_ref;
+  const N Ur = P.cp1_r * dT + 0.5 * P.cp2_r * (T * T - P.T_ref * P.T_ref);
   return V * (o.phi * e + (1.0 - P.phi_ref) * Ur);
 }
 
@@ -289,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_thermal_cells(Geom g, trs_thermal_
   const double V = P.dx * P.dy * P.dz;
   const D4 p = var(u[c * kNV + 0], 0), Sw = var(u[c * kNV + 1], 1), Sg = var(u[c * kNV + 2], 2),
            T = var(u[c * kNV + 3], 3);
-  CellProps o;
+  CellProps<D4> o;
   cell_props(P, tb, p, Sw, Sg, T, o);
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -304,15 +339,12 @@ __global__ void __launch_bounds__(kThreads) k_thermal_cells(Geom g, trs_thermal_
   // the old time level: values only
   double No[3];
   {
-    const D4 po = cst(u_old[c * kNV + 0]), Swo = cst(u_old[c * kNV + 1]), Sgo = cst(u_old[c * kNV + 2]),
-             To = cst(u_old[c * kNV + 3]);
-    CellProps oo;
+    const double po = u_old[c * kNV + 0], Swo = u_old[c * kNV + 1], Sgo = u_old[c * kNV + 2],
+                 To = u_old[c * kNV + 3];
+    CellProps<double> oo;
     cell_props(P, tb, po, Swo, Sgo, To, oo);
-    D4 Nd[3];
-    amounts(oo, Swo, Sgo, V, Nd);
-    No[0] = Nd[0].v;
-    No[1] = Nd[1].v;
-    No[2] = energy_amount(P, oo, po, Swo, Sgo, To, V).v;
+    amounts(oo, Swo, Sgo, V, No);
+    No[2] = energy_amount(P, oo, po, Swo, Sgo, To, V);
   }
   const double idt = 1.0 / P.dt;
   double blk[kNV * kNV];
@@ -330,38 +362,65 @@ __global__ void __launch_bounds__(kThreads) k_thermal_cells(Geom g, trs_thermal_
   for (int e = 0; e < kNV * kNV; e++) ell[((int64_t)kSelf * kNV * kNV + e) * nc + c] = blk[e];
 }
 
+// A cell's unknown k as a dual number (its derivative carried) or as a value.
+template <class N>
+__device__ __forceinline__ N unknown(double a, int k);
+template <>
+__device__ __forceinline__ D4 unknown<D4>(double a, int k) { return var(a, k); }
+template <>
+__device__ __forceinline__ double unknown<double>(double a, int) { return a; }
+// A stored property with its derivatives (D4) or its value only (double).
+template <class N>
+__device__ __forceinline__ N prop(const double *base, int64_t nc, int64_t c, int q);
+template <>
+__device__ __forceinline__ D4 prop<D4>(const double *base, int64_t nc, int64_t c, int q) {
+  return load_d4(base, nc, c, q, true);
+}
+template <>
+__device__ __forceinline__ double prop<double>(const double *base, int64_t nc, int64_t c, int q) {
+  return base[(int64_t)(q * (kNV + 1)) * nc + c];
+}
+
 // Water, oil and energy out of cell c through one face to cell j, with the
-// derivatives with respect to c's unknowns (wrt_c) or j's (!wrt_c).
-__device__ void face_flux(const trs_thermal_params &P, const double *props, int64_t nc, int64_t c, int64_t j,
-                          const double *u, double Tgeo, double al, double zc, double zj, bool wrt_c, D4 (&F)[3]) {
-  const D4 pc = wrt_c ? var(u[c * kNV], 0) : cst(u[c * kNV]);
-  const D4 pj = wrt_c ? cst(u[j * kNV]) : var(u[j * kNV], 0);
-  const D4 Swc = wrt_c ? var(u[c * kNV + 1], 1) : cst(u[c * kNV + 1]);
-  const D4 Sgc = wrt_c ? var(u[c * kNV + 2], 2) : cst(u[c * kNV + 2]);
-  const D4 Swj = wrt_c ? cst(u[j * kNV + 1]) : var(u[j * kNV + 1], 1);
-  const D4 Sgj = wrt_c ? cst(u[j * kNV + 2]) : var(u[j * kNV + 2], 2);
-  const D4 Tc = wrt_c ? var(u[c * kNV + 3], 3) : cst(u[c * kNV + 3]);
-  const D4 Tj = wrt_c ? cst(u[j * kNV + 3]) : var(u[j * kNV + 3], 3);
-  const D4 Sc[3] = {Swc, 1.0 - Swc - Sgc, Sgc};
-  const D4 Sj[3] = {Swj, 1.0 - Swj - Sgj, Sgj};
+// derivatives with respect to c's unknowns (WC) or j's (!WC); the other
+// cell's quantities enter as plain values.
+template <bool WC>
+__device__ void face_flux(const double *props, int64_t nc, int64_t c, int64_t j, const double *u, double Tgeo,
+                          double al, double zc, double zj, D4 (&F)[3]) {
+  using NC = typename std::conditional<WC, D4, double>::type;
+  using NJ = typename std::conditional<WC, double, D4>::type;
+  const NC pc = unknown<NC>(u[c * kNV], 0), Swc = unknown<NC>(u[c * kNV + 1], 1),
+           Sgc = unknown<NC>(u[c * kNV + 2], 2), Tc = unknown<NC>(u[c * kNV + 3], 3);
+  const NJ pj = unknown<NJ>(u[j * kNV], 0), Swj = unknown<NJ>(u[j * kNV + 1], 1),
+           Sgj = unknown<NJ>(u[j * kNV + 2], 2), Tj = unknown<NJ>(u[j * kNV + 3], 3);
+  const NC Sc[3] = {Swc, 1.0 - Swc - Sgc, Sgc};
+  const NJ Sj[3] = {Swj, 1.0 - Swj - Sgj, Sgj};
   F[0] = F[1] = F[2] = cst(0.0);
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const D4 gc = load_d4(props, nc, c, 6 + a, wrt_c), gj = load_d4(props, nc, j, 6 + a, !wrt_c);
-    const D4 ssum = Sc[a] + Sj[a];
+    const NC gc = prop<NC>(props, nc, c, 6 + a);
+    const NJ gj = prop<NJ>(props, nc, j, 6 + a);
+    const D4 ssum = dual(Sc[a] + Sj[a]);
     const D4 gbar = ssum.v > 0.0 ? (Sc[a] * gc + Sj[a] * gj) / ssum : 0.5 * (gc + gj);
     const D4 dphi = (pc - pj) - gbar * (zc - zj);
-    const bool up_c = dphi.v >= 0.0;
-    const D4 lam = up_c ? load_d4(props, nc, c, a, wrt_c) : load_d4(props, nc, j, a, !wrt_c);
-    const D4 H = up_c ? load_d4(props, nc, c, 3 + a, wrt_c) : load_d4(props, nc, j, 3 + a, !wrt_c);
-    const D4 f = Tgeo * lam * dphi;
+    D4 f, fH;
+    if (dphi.v >= 0.0) {   // c upstream
+      const NC lam = prop<NC>(props, nc, c, a), H = prop<NC>(props, nc, c, 3 + a);
+      f = (Tgeo * lam) * dphi;
+      fH = H * f;
+    } else {
+      const NJ lam = prop<NJ>(props, nc, j, a), H = prop<NJ>(props, nc, j, 3 + a);
+      f = (Tgeo * lam) * dphi;
+      fH = H * f;
+    }
     if (a == 1) F[1] = F[1] + f;
     else F[0] = F[0] + f;
-    F[2] = F[2] + H * f;
+    F[2] = F[2] + fH;
   }
-  const D4 kc = load_d4(props, nc, c, 9, wrt_c), kj = load_d4(props, nc, j, 9, !wrt_c);
-  const D4 ks = kc + kj;
-  const D4 kt = ks.v > 0.0 ? 2.0 * kc * kj / ks : cst(0.0);
+  const NC kc = prop<NC>(props, nc, c, 9);
+  const NJ kj = prop<NJ>(props, nc, j, 9);
+  const D4 ks = dual(kc + kj);
+  const D4 kt = ks.v > 0.0 ? (2.0 * kc * kj) / ks : cst(0.0);
   F[2] = F[2] + al * kt * (Tc - Tj);
 }
 
@@ -397,8 +456,8 @@ __global__ void __launch_bounds__(kThreads) k_thermal_rows(
     const double Tgeo = kUnit * kh * al;
     const double zj = cell_depth(P, g, j);
     D4 Fc[3], Fj[3];
-    face_flux(P, props, nc, c, j, u, Tgeo, al, zc, zj, true, Fc);
-    face_flux(P, props, nc, c, j, u, Tgeo, al, zc, zj, false, Fj);
+    face_flux<true>(props, nc, c, j, u, Tgeo, al, zc, zj, Fc);
+    face_flux<false>(props, nc, c, j, u, Tgeo, al, zc, zj, Fj);
 #pragma unroll
     for (int e = 0; e < 3; e++) {
       rc[e] = rc[e] + Fc[e].v;
