@@ -98,7 +98,18 @@ typedef struct {
  * that the complex step carries through. */
 static cplx rk_z(cplx A, cplx B) {
   cplx c1 = A - B - B * B, c0 = -A * B;
-  cplx z = 1.0 + fabs(re(c1)) + fabs(re(c0));
+  /* Starting point.  Above the largest root f is increasing and convex, so
+   * Newton's method from above converges to it -- unless f's local minimum
+   * (the larger stationary point z_m) lies above zero.  Then the only real
+   * root lies left of the local maximum, where f is increasing and concave,
+   * and Newton's method from z = 0 (f(0) = -AB < 0) climbs to it. */
+  double z0 = 1.0 + fabs(re(c1)) + fabs(re(c0));
+  const double disc = 1.0 - 3.0 * re(c1);
+  if (disc > 0.0) {
+    const double zm = (1.0 + sqrt(disc)) / 3.0;
+    if (((zm - 1.0) * zm + re(c1)) * zm + re(c0) > 0.0) z0 = 0.0;
+  }
+  cplx z = z0;
   for (int it = 0; it < 200; it++) {
     cplx f = ((z - 1.0) * z + c1) * z + c0;
     cplx fp = (3.0 * z - 2.0) * z + c1;

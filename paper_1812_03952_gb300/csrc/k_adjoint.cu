@@ -80,22 +80,51 @@ __global__ void __launch_bounds__(kThreads) k_spmv_t(MatView<double> A, const in
   }
 }
 
-__global__ void k_transpose_values(int b, int64_t nnzb, const int64_t *src_canon, const int64_t *map_src,
-                                   const double *ell_src, const double *tval_src, int64_t nc,
-                                   const int64_t *map_dst, double *ell_dst, double *tval_dst) {
+// Cell part of A^T: the block in slot s of cell i is the transpose of the
+// block in the opposite slot of cell j = i + off[s] (the slots are geometric,
+// so that block is always in A's ELL part).  One thread per (slot, cell):
+// for a fixed element the reads and the writes are both unit-stride in i.
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_transpose_ell(Geom g, const uint8_t *__restrict__ emask_dst,
+                                                            const double *__restrict__ ell_src,
+                                                            double *__restrict__ ell_dst) {
+  pdl_enter();
+  constexpr int BB = B * B;
+  const int64_t nc = g.nc;
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (i >= nc) return;
+  const int s = blockIdx.y;
+  double *dst = ell_dst + (int64_t)s * BB * nc + i;
+  if ((emask_dst[i] >> s) & 1u) {
+    const double *src = ell_src + (int64_t)(kSlots - 1 - s) * BB * nc + (i + g.off[s]);
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) dst[(int64_t)(r * B + c) * nc] = src[(int64_t)(c * B + r) * nc];
+  } else {
+#pragma unroll
+    for (int e = 0; e < BB; e++) dst[(int64_t)e * nc] = 0.0;
+  }
+}
+
+// Tail part of A^T: entry t of the tail is canonical block tq[t]; its source
+// is canonical block src_canon[tq[t]] of A, wherever A keeps it.
+__global__ void __launch_bounds__(kThreads) k_transpose_tail(int b, int64_t ntail, const int64_t *__restrict__ tq,
+                                                             const int64_t *__restrict__ src_canon,
+                                                             const int64_t *__restrict__ map_src,
+                                                             const double *__restrict__ ell_src,
+                                                             const double *__restrict__ tval_src, int64_t nc,
+                                                             double *__restrict__ tval_dst) {
   pdl_enter();
   const int bb = b * b;
   const int64_t idx = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  if (idx >= nnzb * bb) return;
-  const int64_t q = idx / bb;
+  if (idx >= ntail * bb) return;
+  const int64_t t = idx / bb;
   const int e = (int)(idx % bb), r = e / b, c = e % b;
-  const int64_t ls = map_src[src_canon[q]], ld = map_dst[q];
+  const int64_t ls = map_src[src_canon[tq[t]]];
   const int es = c * b + r;  // transposed element
-  double v;
-  if (ls < kSlots * nc) v = ell_src[((ls / nc) * bb + es) * nc + ls % nc];
-  else v = tval_src[(ls - kSlots * nc) * bb + es];
-  if (ld < kSlots * nc) ell_dst[((ld / nc) * bb + e) * nc + ld % nc] = v;
-  else tval_dst[(ld - kSlots * nc) * bb + e] = v;
+  tval_dst[idx] = ls < kSlots * nc ? ell_src[((ls / nc) * bb + es) * nc + ls % nc]
+                                   : tval_src[(ls - kSlots * nc) * bb + es];
 }
 
 template <int B>
@@ -172,12 +201,18 @@ void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double a
   TRS_LAUNCHED();
 }
 
-void launch_transpose_values(int bb, int64_t nnzb, const int64_t *src_canon, const int64_t *map_src,
-                             const double *ell_src, const double *tval_src, int64_t nc, const int64_t *map_dst,
-                             double *ell_dst, double *tval_dst, int b, cudaStream_t s) {
-  if (!nnzb) return;
-  launch_pdl(k_transpose_values, grid_of(nnzb * bb), kThreads, 0, s, b, nnzb, src_canon, map_src, ell_src, tval_src, nc,
-                                                             map_dst, ell_dst, tval_dst);
+void launch_transpose_values(const trs_bsr &A, trs_bsr &AT, cudaStream_t s) {
+  const int64_t nc = AT.g.nc;
+  if (nc) {
+    TRS_DISPATCH_B(A.b, launch_pdl(k_transpose_ell<B>, dim3(grid_of(nc), kSlots), dim3(kThreads), 0, s, AT.g,
+                                   (const uint8_t *)AT.emask.p, (const double *)A.ell.p, AT.ell.p));
+  }
+  if (AT.ntail) {
+    const int bb = A.b * A.b;
+    launch_pdl(k_transpose_tail, grid_of(AT.ntail * bb), kThreads, 0, s, A.b, AT.ntail, (const int64_t *)AT.ttail.p,
+               (const int64_t *)AT.tsrc.p, (const int64_t *)A.map.p, (const double *)A.ell.p,
+               (const double *)A.tval.p, A.g.nc, AT.tval.p);
+  }
   TRS_LAUNCHED();
 }
 

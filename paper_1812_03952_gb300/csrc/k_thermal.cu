@@ -177,11 +177,21 @@ __device__ D4 table(const double *tab, int n, int c, const D4 &s) {
 }
 
 // Largest real root of Z^3 - Z^2 + (A - B - B^2) Z - A B = 0 (Redlich-Kwong,
-// Sec. "Compressibility Factor of Real Gas"): Newton's method on the values
-// from above the largest root, then dZ = -(f_A dA + f_B dB) / f_Z.
+// Sec. "Compressibility Factor of Real Gas"): Newton's method on the values,
+// then dZ = -(f_A dA + f_B dB) / f_Z.  Newton starts above the largest root,
+// where f rises and is convex, unless f's local minimum (the larger
+// stationary point) is above zero: the only real root is then left of the
+// local maximum, where f rises and is concave, and Newton starts at z = 0
+// (f(0) = -AB < 0).  The test is evaluated without contraction.
 __device__ double rk_z(double a, double b) {
   const double c1 = a - b - b * b, c0 = -a * b;
   double z = 1.0 + fabs(c1) + fabs(c0);
+  const double disc = 1.0 - 3.0 * c1;
+  if (disc > 0.0) {
+    const double zm = __ddiv_rn(__dadd_rn(1.0, sqrt(disc)), 3.0);
+    const double fm = __dadd_rn(__dmul_rn(__dadd_rn(__dmul_rn(__dadd_rn(zm, -1.0), zm), c1), zm), c0);
+    if (fm > 0.0) z = 0.0;
+  }
   for (int it = 0; it < 200; it++) {
     const double f = ((z - 1.0) * z + c1) * z + c0;
     const double fp = (3.0 * z - 2.0) * z + c1;

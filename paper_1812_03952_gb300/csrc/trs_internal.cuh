@@ -225,6 +225,7 @@ struct trs_bsr {
   // for a matrix made by trs_bsr_transpose: canonical index in the source of
   // each canonical block (refresh with trs_bsr_transpose_values)
   trs::DBuf<int64_t> tsrc;
+  trs::DBuf<int64_t> ttail;   // canonical index of each tail entry, in tail order
   // tail entries grouped by column (for the transposed product)
   trs::DBuf<int64_t> tc_ptr, tc_src;
   trs::DBuf<int32_t> tc_row;

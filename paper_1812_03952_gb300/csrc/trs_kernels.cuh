@@ -290,9 +290,8 @@ void launch_decouple_mixed(int b, const MatView<double> &A, const int64_t *tdiag
 // ------------------------------------------------------------- k_adjoint
 void launch_spmv_t(int b, const trs_bsr &A, const double *x, double *y, double alpha, double beta,
                    cudaStream_t s);
-void launch_transpose_values(int bb, int64_t nnzb, const int64_t *src_canon, const int64_t *map_src,
-                             const double *ell_src, const double *tval_src, int64_t nc,
-                             const int64_t *map_dst, double *ell_dst, double *tval_dst, int b, cudaStream_t s);
+// AT's values from A's; AT made by trs_bsr_transpose (tsrc and ttail set)
+void launch_transpose_values(const trs_bsr &A, trs_bsr &AT, cudaStream_t s);
 void launch_outer_product(int b, const trs_bsr &A, const double *lambda, const double *x, double *dA,
                           cudaStream_t s);
 void launch_chain_theta(int b, const trs_bsr &A, const double *perm, int perm_is_log, double kvkh,

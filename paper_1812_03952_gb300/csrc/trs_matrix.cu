@@ -405,8 +405,18 @@ trs_status trs_bsr_transpose(const trs_bsr *A, void *stream, trs_bsr **out) {
     build_layout(T.get(), n, A->b, rp.data(), col.data(), A->structured ? grid : nullptr, s);
     T->tsrc.alloc(src.size());
     T->tsrc.upload(src.data(), nnzb, s);
-    launch_transpose_values(A->b * A->b, nnzb, T->tsrc.p, A->map.p, A->ell.p, A->tval.p, A->g.nc, T->map.p,
-                            T->ell.p, T->tval.p, A->b, s);
+    // the tail entries of T in tail order (build_layout fills the tail in
+    // canonical order with the blocks that have no geometric slot)
+    std::vector<int64_t> tq;
+    tq.reserve(std::max<int64_t>(T->ntail, 1));
+    const int64_t tnc = T->g.nc;
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t q = rp[i]; q < rp[i + 1]; q++)
+        if (!(i < tnc && col[q] < tnc && ell_slot(T->g, i, col[q]) >= 0)) tq.push_back(q);
+    TRS_REQUIRE((int64_t)tq.size() == T->ntail, TRS_ERR_INVALID, "tail count of the transpose");
+    T->ttail.alloc(std::max<int64_t>(T->ntail, 1));
+    T->ttail.upload(tq.data(), T->ntail, s);
+    launch_transpose_values(*A, *T, s);
     TRS_CUDA(cudaStreamSynchronize(s));
     *out = T.release();
   });
@@ -415,10 +425,10 @@ trs_status trs_bsr_transpose(const trs_bsr *A, void *stream, trs_bsr **out) {
 trs_status trs_bsr_transpose_values(const trs_bsr *A, trs_bsr *AT, void *stream) {
   return guarded([&] {
     TRS_REQUIRE(A && AT, TRS_ERR_INVALID, "NULL argument");
-    TRS_REQUIRE(AT->tsrc.p && AT->n == A->n && AT->b == A->b && AT->nnzb == A->nnzb && AT->g.nc == A->g.nc,
+    TRS_REQUIRE(AT->tsrc.p && AT->ttail.p && AT->n == A->n && AT->b == A->b && AT->nnzb == A->nnzb &&
+                    AT->g.nc == A->g.nc && AT->g.nx == A->g.nx && AT->g.ny == A->g.ny,
                 TRS_ERR_INVALID, "AT was not made by trs_bsr_transpose of a matrix with A's pattern");
-    launch_transpose_values(A->b * A->b, A->nnzb, AT->tsrc.p, A->map.p, A->ell.p, A->tval.p, A->g.nc, AT->map.p,
-                            AT->ell.p, AT->tval.p, A->b, (cudaStream_t)stream);
+    launch_transpose_values(*A, *AT, (cudaStream_t)stream);
   });
 }
 

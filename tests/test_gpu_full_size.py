@@ -149,3 +149,28 @@ def test_full_size_error_vs_oracle_solution(trs, oracle, full):
           f"FP64 at 1e-6 {e64:.3e} ({r64.stats['iters']} its), FP32 CPR at 1e-6 {e32:.3e} "
           f"({r32.stats['iters']} its)")
     assert e32 <= 10.0 * e64
+
+
+def test_full_size_physics_jacobian_sampled_rows(trs, oracle, synth, full):
+    """The physics Jacobian at the benchmark size (the thermal model on the
+    128x128x64 grid and wells, steam chambers around the injectors): the GPU
+    values against the oracle's complex-step Jacobian on 2,000 seeded cell rows
+    plus every well row, 1e-12 of each scalar row's largest entry, and the
+    residual on the same rows; then the benchmark's physics step (block ILU(1),
+    FGMRES(60)) meets rtol on the true residual."""
+    from test_gpu_thermal import _compare
+    sysm, ds, A, Ao = full
+    state = synth.thermal_state(sysm, synth.SEED_BASE + 77)
+    ts = trs.ThermalSystem(sysm, state, synth.SWT, synth.SLT)
+    R = ts.assemble()
+    th = oracle.Thermal(sysm, state, synth.SWT, synth.SLT)
+    rows = np.sort(np.random.default_rng(3).choice(sysm.n_cells, 2000, replace=False))
+    # the perforated cells too (their rows carry the well columns)
+    rows = np.union1d(rows, np.unique(sysm.perf_cell))
+    Jo = th.jacobian(rows=rows, pattern=Ao)
+    Ro = th.residual(rows=rows)
+    well_rows = np.arange(sysm.n_cells, sysm.n_rows)
+    _compare(ts.A.values(), R.cpu().numpy(), Jo, Ro, rows=np.concatenate([rows, well_rows]))
+    M = trs.CPR(ts.A, precision="fp32", ilu_fill=1)
+    d, res = trs.fgmres_solve(ts.A, M, R, rtol=1e-6, restart=60)
+    assert res.status == trs.TRS_OK and res.stats["true_relres"] <= 1e-6

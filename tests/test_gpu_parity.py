@@ -89,14 +89,46 @@ def test_spmv_parity(trs, oracle, synth, case, grid):
         assert np.all(err <= 16 * 2.2e-16 * bound + 1e-300)
 
 
-def test_transpose_matrix_exact(trs, oracle, synth):
-    s = _sys(synth, 8, 6, 4, 4, seed=11, n_pairs=2)
+@pytest.mark.parametrize("case", CASES, ids=_case_id)
+def test_transpose_matrix_exact(trs, oracle, synth, case):
+    """A^T (cell slots from the opposite slot of the neighbour, well blocks
+    from the tail) is A's blocks transposed, bit for bit; refreshed in place
+    after A's values change, it is the new A's transpose."""
+    s = _sys(synth, **case)
     ds = _gpu_system(trs, s)
     AT = ds.A.transpose()
     ATo = oracle.transpose(oracle.assemble(s))
     rp, col = AT.pattern()
     np.testing.assert_array_equal(rp, ATo.rp)
     np.testing.assert_array_equal(col, ATo.col)
+    np.testing.assert_array_equal(AT.values(), ATo.val)
+    s2 = _sys(synth, **dict(case, seed=case["seed"] + 50))
+    ds2 = trs.DeviceSystem(s2)
+    ds.A.assemble(ds2.k, ds2.M, ds2.acc, ds2.wi, ds2.lam, s2.kvkh, s2.c_t, False)
+    ds.A.transpose(into=AT)
+    np.testing.assert_array_equal(AT.values(), oracle.transpose(oracle.assemble(s2)).val)
+
+
+def test_transpose_unstructured_exact(trs, oracle):
+    """A matrix with no grid (a structurally symmetric random pattern, values
+    unsymmetric): every block goes through the tail path."""
+    rng = np.random.default_rng(12)
+    n, b = 300, 3
+    pairs = {(i, i) for i in range(n)}
+    for i in range(n):
+        for j in rng.choice(n, 3, replace=False):
+            pairs |= {(i, int(j)), (int(j), i)}
+    rows = [np.array(sorted(j for (r, j) in pairs if r == i)) for i in range(n)]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.standard_normal((rp[-1], b, b))
+    A = trs.Matrix.from_bsr(rp, col, val, b)
+    AT = A.transpose()
+    ATo = oracle.transpose(oracle.BSR(n, b, rp, col, val))
+    trp, tcol = AT.pattern()
+    np.testing.assert_array_equal(trp, ATo.rp)
+    np.testing.assert_array_equal(tcol, ATo.col)
     np.testing.assert_array_equal(AT.values(), ATo.val)
 
 

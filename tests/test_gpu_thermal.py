@@ -40,19 +40,32 @@ def trs():
     return T
 
 
-def _make(synth, case, all_gas=False):
+# (p kPa, T C) of compressed water where the Redlich-Kwong cubic has one real
+# root below a positive local minimum (Newton's method from above the roots
+# cycles there)
+COMPRESSED = ((1915.35, 12.43), (3000.0, 64.0), (3000.0, 69.0), (3800.0, 88.0), (4700.0, 129.0),
+              (5800.0, 148.0))
+
+
+def _make(synth, case, mode="chamber"):
     c = dict(case)
     gravity = c.pop("gravity", 9.80665)
     seed = c.pop("seed")
     nx, ny, nz = c.pop("nx"), c.pop("ny"), c.pop("nz")
     s = synth.small_system(nx, ny, nz, 4, seed=seed, **c)
     t = synth.thermal_state(s, seed + 100, gravity=gravity)
-    if all_gas:
-        u = t.u.reshape(-1, 4)
+    u = t.u.reshape(-1, 4)
+    if mode == "all_gas":
         u[:s.n_cells, 1] = 0.52
         u[:s.n_cells, 2] = 0.21
         u[:s.n_cells, 3] = 195.0
         t.gas[:] = 1
+    elif mode == "compressed":
+        pt = np.array(COMPRESSED)[np.arange(s.n_cells) % len(COMPRESSED)]
+        u[:s.n_cells, 0] = pt[:, 0]
+        u[:s.n_cells, 2] = 0.0
+        u[:s.n_cells, 3] = pt[:, 1]
+        t.gas[:s.n_cells] = 0
     return s, t
 
 
@@ -68,7 +81,11 @@ def _compare(J, R, Jo, Ro, rows=None):
     scale = np.zeros((Jo.n, b))
     np.maximum.at(scale, rr, np.abs(Jv).max(axis=2))
     err = np.abs(Jg - Jv).max(axis=2) / np.maximum(scale[rr], 1e-300)
-    assert err.max() <= 1e-12, float(err.max())
+    if err.max() > 1e-12:
+        k, e = np.unravel_index(np.argmax(err), err.shape)
+        blk = np.flatnonzero(sel)[k]
+        raise AssertionError(f"relative error {err.max():.3e} in block row {rr[k]}, column {Jo.col[blk]}, "
+                             f"scalar row {e}: GPU {Jg[k][e].tolist()} oracle {Jv[k][e].tolist()}")
     keep = np.arange(Jo.n) if rows is None else np.asarray(rows)
     Rr, Ror = R.reshape(-1, b)[keep], Ro.reshape(-1, b)[keep]
     for e in range(b):
@@ -76,10 +93,10 @@ def _compare(J, R, Jo, Ro, rows=None):
         assert np.abs(Rr[:, e] - Ror[:, e]).max() <= 1e-12 * mag, (e, float(np.abs(Rr[:, e] - Ror[:, e]).max() / mag))
 
 
-@pytest.mark.parametrize("all_gas", [False, True], ids=["chamber", "all_gas"])
+@pytest.mark.parametrize("mode", ["chamber", "all_gas", "compressed"])
 @pytest.mark.parametrize("case", CASES, ids=_cid)
-def test_thermal_jacobian_matches_oracle(trs, oracle, synth, case, all_gas):
-    s, t = _make(synth, case, all_gas)
+def test_thermal_jacobian_matches_oracle(trs, oracle, synth, case, mode):
+    s, t = _make(synth, case, mode)
     th = oracle.Thermal(s, t, synth.SWT, synth.SLT)
     Jo, Ro = th.jacobian(), th.residual()
     ts = trs.ThermalSystem(s, t, synth.SWT, synth.SLT)

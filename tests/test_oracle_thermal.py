@@ -186,6 +186,33 @@ def test_redlich_kwong(oracle, thermal):
         assert abs(z - max(r.real for r in roots if abs(r.imag) < 1e-9)) <= 1e-12
     # near-ideal at low pressure: Z -> 1
     assert abs(oracle.rk_z(1e-6, 1e-7) - 1.0) < 1e-6
+    # the model's whole (p, T) range, cold compressed water included, where
+    # the cubic has one real (liquid-like) root below a positive local
+    # minimum: Z is a root, and no real root lies above it
+    P = thermal()[1].params
+    TcK = P["tc_w"] + 273.15
+    for p in (200.0, 500.0, 1000.0, 1915.35, 2000.0, 5000.0, 10000.0, 20000.0):
+        for T in (5.0, 12.43, 25.0, 50.0, 100.0, 150.0, 200.0, 250.0, 300.0, 350.0):
+            TK = T + 273.15
+            A = 0.427480 * (p / P["pc_w"]) * (TcK / TK) ** 2.5
+            B = 0.086640 * (p / P["pc_w"]) * (TcK / TK)
+            c1, c0 = A - B - B * B, -A * B
+            z = oracle.rk_z(A, B)
+            assert abs(((z - 1.0) * z + c1) * z + c0) <= 1e-15 * max(1.0, abs(c1), abs(c0)), (p, T)
+            real = [r.real for r in np.roots([1.0, -1.0, c1, c0]) if abs(r.imag) <= 1e-7]
+            assert z >= max(real) - 1e-9, (p, T, z, real)
+    # states where Newton's method started above every root cycles near the
+    # local minimum instead of reaching the liquid-like root
+    for p, T in ((3000.0, 64.0), (3000.0, 69.0), (3800.0, 88.0), (4700.0, 129.0), (5800.0, 148.0)):
+        TK = T + 273.15
+        A = 0.427480 * (p / P["pc_w"]) * (TcK / TK) ** 2.5
+        B = 0.086640 * (p / P["pc_w"]) * (TcK / TK)
+        z = oracle.rk_z(A, B)
+        real = [r.real for r in np.roots([1.0, -1.0, A - B - B * B, -A * B]) if abs(r.imag) <= 1e-7]
+        assert len(real) == 1 and abs(z - real[0]) <= 1e-12 * max(1.0, abs(z)), (p, T, z, real)
+    # the single-real-root case met at 1915 kPa and 12.4 C
+    A, B = 0.2868008466275823, 0.01704208436092397
+    assert abs(oracle.rk_z(A, B) - 0.0195254201115644) <= 1e-13
     # saturated steam at 200 C: Z about 0.91 (steam tables: v = 0.1272 m^3/kg)
     s, t, th = thermal()
     rho_g = th.props([1554.9, 0.5, 0.3, 200.0])["rho_g"]
