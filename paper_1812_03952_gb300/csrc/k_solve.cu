@@ -1159,6 +1159,146 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_dots(const double *__re
   last_block_finish_kb(partial, counter, K, out);
 }
 
+// ------------------------------------------- bulk-copy staged Gram-Schmidt
+// The basis tile of a block (kTE consecutive elements of each of the K
+// vectors, and of w) is brought into shared memory by one-dimensional bulk
+// copies (cp.async.bulk, completed on an mbarrier), double-buffered, so that
+// the next tile is in flight while the FP64 pipe works on this one.  Every
+// wait is bounded: past kMbarSpin polls the block marks its sums NaN (the
+// solve then stops with TRS_ERR_NAN), waits (bounded) for its copies still
+// in flight and finishes.  Needs N even (16-byte aligned vector rows).
+constexpr int kTE = kThreads;   // elements per tile, one per thread
+constexpr int kMbarSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (int it = 0; it < kMbarSpin; it++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// UPD = false: out[k] = <V_k, w> (k < K), out[K] = <w, w>.
+// UPD = true:  w -= sum_k h_k V_k, then out[k] = <V_k, w> with the new w.
+template <int KM, bool UPD>
+__global__ void __launch_bounds__(kThreads, 1) k_cgs_staged(const double *__restrict__ V, int64_t N, int K,
+                                                            const double *__restrict__ h, double *__restrict__ w,
+                                                            double *partial, unsigned int *counter, double *out) {
+  extern __shared__ __align__(128) double tile[];   // [2][KM + 1][kTE]: K vectors, then w
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ double sh[KM];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_enter();
+  if (UPD)
+    for (int k = tid; k < K; k += kThreads) sh[k] = h[k];
+  __syncthreads();
+  const int64_t ntiles = (N + kTE - 1) / kTE;
+  // thread 0: the copies of tile t into buffer b
+  auto issue = [&](int64_t t, int b) {
+    const int64_t e0 = t * kTE;
+    const uint32_t bytes = (uint32_t)min((int64_t)kTE, N - e0) * 8u;
+    double *dst = tile + (size_t)b * (KM + 1) * kTE;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[b], bytes * (uint32_t)(K + 1));
+    for (int u = 0; u < K; u++) bulk_g2s(dst + (size_t)u * kTE, V + (int64_t)u * N + e0, bytes, &bar[b]);
+    bulk_g2s(dst + (size_t)KM * kTE, w + e0, bytes, &bar[b]);
+  };
+  double acc[KM] = {};
+  double ww = 0.0;
+  // bit b: the phase parity of bar[b]; a copy into buffer b not yet waited for
+  uint32_t parity = 0u, pending = 0u;
+  bool failed = false;
+  int64_t t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  if (t < ntiles) pending |= 1u;
+  for (int b = 0; t < ntiles; t += gridDim.x, b ^= 1) {
+    const int64_t tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) issue(tn, b ^ 1);
+    if (tn < ntiles) pending |= 1u << (b ^ 1);
+    const bool ok = mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u << b;
+    pending &= ~(1u << b);
+    const int64_t i = t * kTE + tid;
+    if (i < N) {
+      const double *tv = tile + (size_t)b * (KM + 1) * kTE + tid;
+      const double wi = tv[(size_t)KM * kTE];
+      if (!UPD) {
+        ww = fma(wi, wi, ww);
+#pragma unroll
+        for (int g = 0; g < KM; g += 4) {
+          if (g < K) {
+#pragma unroll
+            for (int u = g; u < g + 4; u++)
+              if (u < K) acc[u] = fma(tv[(size_t)u * kTE], wi, acc[u]);
+          }
+        }
+      } else {
+        double tt = wi;
+#pragma unroll
+        for (int g = 0; g < KM; g += 4) {
+          if (g < K) {
+#pragma unroll
+            for (int u = g; u < g + 4; u++)
+              if (u < K) tt = fma(-sh[u], tv[(size_t)u * kTE], tt);
+          }
+        }
+        w[i] = tt;
+#pragma unroll
+        for (int g = 0; g < KM; g += 4) {
+          if (g < K) {
+#pragma unroll
+            for (int u = g; u < g + 4; u++)
+              if (u < K) acc[u] = fma(tv[(size_t)u * kTE], tt, acc[u]);
+          }
+        }
+      }
+    }
+    __syncthreads();   // buffer b is read before it is refilled
+  }
+  if (failed) {
+    // copies still in flight land before the block leaves (bounded)
+    for (int b = 0; b < 2; b++)
+      if ((pending >> b) & 1u) mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
+#pragma unroll
+    for (int u = 0; u < KM; u++) acc[u] = __longlong_as_double(0x7ff8000000000000ll);
+    ww = __longlong_as_double(0x7ff8000000000000ll);
+  }
+  block_partial_kb<KM>(acc, K, partial, UPD ? nullptr : &ww);
+  last_block_finish_kb(partial, counter, UPD ? K : K + 1, out);
+}
+
 // Arnoldi column j of H (row-major, m columns): h1 + h2, norm; Givens.
 // status[0] = |g_{j+1}| / ||b||, status[1] = breakdown flag, hnorm[0] = h_{j+1,j}
 __global__ void k_givens(int j, int m, double *H, const double *h1, const double *h2, const double *hn2,
@@ -1628,6 +1768,40 @@ unsigned resident_grid(void (*kernel)(KArgs...), unsigned cap) {
   return std::min(cap, g);
 }
 
+// Blocks of a staged Gram-Schmidt kernel resident per GB300 SM times the SM
+// count (its shared-memory opt-in set on first use), capped at cap.
+template <class... KArgs>
+unsigned staged_grid(void (*kernel)(KArgs...), size_t smem, unsigned cap) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void *, int>, unsigned>> cache;
+  int dev = 0;
+  TRS_CUDA(cudaGetDevice(&dev));
+  const void *key = reinterpret_cast<const void *>(kernel);
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto &e : cache)
+    if (e.first.first == key && e.first.second == dev) return std::min(cap, e.second);
+  TRS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  TRS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+  TRS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned g = (unsigned)std::max(1, per_sm * sms);
+  cache.push_back({{key, dev}, g});
+  return std::min(cap, g);
+}
+
+// The staged kernels copy whole 16-byte units: N even, V and w 16-byte aligned.
+inline bool stageable(const double *V, int64_t N, const double *w) {
+  return N % 2 == 0 && ((uintptr_t)V & 15u) == 0 && ((uintptr_t)w & 15u) == 0;
+}
+
+template <int KM, bool UPD>
+void launch_staged(const double *V, int64_t N, int K, const double *h, double *w, const RedScratch &red,
+                   double *out, cudaStream_t s) {
+  const size_t smem = (size_t)2 * (KM + 1) * kTE * sizeof(double);
+  launch_pdl(k_cgs_staged<KM, UPD>, staged_grid(k_cgs_staged<KM, UPD>, smem, (unsigned)red.grid), kThreads, smem,
+             s, V, N, K, h, w, red.partial, red.counter, out);
+}
+
 void launch_multidot(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
   launch_pdl(k_multidot<32>, resident_grid(k_multidot<32>, (unsigned)red.grid), kThreads, 0, s, V, N, K, w,
@@ -1642,7 +1816,12 @@ void launch_cgs_update(const double *V, int64_t N, int K, const double *h, doubl
 void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
   const unsigned cap = (unsigned)red.grid;
-  if (K + 1 <= 8)
+  if (stageable(V, N, w) && K + 1 <= 32) {
+    double *wm = const_cast<double *>(w);   // read only (UPD = false)
+    if (K + 1 <= 8) launch_staged<8, false>(V, N, K, nullptr, wm, red, out, s);
+    else if (K + 1 <= 16) launch_staged<16, false>(V, N, K, nullptr, wm, red, out, s);
+    else launch_staged<32, false>(V, N, K, nullptr, wm, red, out, s);
+  } else if (K + 1 <= 8)
     launch_pdl(k_cgs_dots<8>, resident_grid(k_cgs_dots<8>, cap), kThreads, 0, s, V, N, K, w, red.partial,
                red.counter, out);
   else if (K + 1 <= 16)
@@ -1657,7 +1836,11 @@ void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const R
 void launch_cgs_update_dots(const double *V, int64_t N, int K, const double *h, double *w, const RedScratch &red,
                             double *out, cudaStream_t s) {
   const unsigned cap = (unsigned)red.grid;
-  if (K <= 8)
+  if (stageable(V, N, w) && K <= 32) {
+    if (K <= 8) launch_staged<8, true>(V, N, K, h, w, red, out, s);
+    else if (K <= 16) launch_staged<16, true>(V, N, K, h, w, red, out, s);
+    else launch_staged<32, true>(V, N, K, h, w, red, out, s);
+  } else if (K <= 8)
     launch_pdl(k_cgs_update_dots<8>, resident_grid(k_cgs_update_dots<8>, cap), kThreads, 0, s, V, N, K, h, w,
                red.partial, red.counter, out);
   else if (K <= 16)

@@ -11,12 +11,14 @@
 //
 // Derivatives are carried by forward-mode dual numbers (value and the four
 // partial derivatives with respect to one cell's unknowns), so the Jacobian is
-// the exact derivative of the residual this file computes.  Three kernels:
+// the exact derivative of the residual this file computes.  Four kernels:
 //   k_thermal_cells: per cell, the properties with their derivatives (kept
 //     for the neighbours), the accumulation terms and the gas constraint;
-//   k_thermal_rows:  per cell row, the six face fluxes (derivatives with
-//     respect to the cell and to the neighbour, each from a dual-number pass)
-//     and the perforations, written into the row's ELL blocks and tail;
+//   k_thermal_faces: per face, once, the flux with its derivatives with
+//     respect to both cells (a dual-number pass each), kept for the rows, and
+//     the two off-diagonal blocks it gives;
+//   k_thermal_rows:  per cell row, the six faces' terms and the
+//     perforations, into the residual, the diagonal block and the tail;
 //   k_thermal_wells: per well, the well equation.
 #include <type_traits>
 
@@ -103,8 +105,9 @@ __device__ __forceinline__ D4 operator*(double b, const D4 &a) { return a * b; }
 __device__ __forceinline__ D4 operator/(const D4 &a, double b) {
   D4 r;
   r.v = a.v / b;
+  const double ib = 1.0 / b;
 #pragma unroll
-  for (int k = 0; k < kNV; k++) r.d[k] = a.d[k] / b;
+  for (int k = 0; k < kNV; k++) r.d[k] = a.d[k] * ib;
   return r;
 }
 __device__ __forceinline__ D4 operator/(double a, const D4 &b) {
@@ -129,11 +132,12 @@ __device__ __forceinline__ D4 dlog(const D4 &a) {
   for (int k = 0; k < kNV; k++) r.d[k] = a.d[k] / a.v;
   return r;
 }
-// a^e for a constant exponent
-__device__ __forceinline__ D4 dpow(const D4 &a, double e) {
+// a^(5/2) = a^2 sqrt(a), d/da = (5/2) a sqrt(a) (a > 0)
+__device__ __forceinline__ D4 dpow52(const D4 &a) {
   D4 r;
-  r.v = pow(a.v, e);
-  const double s = e * r.v / a.v;
+  const double q = sqrt(a.v);
+  r.v = a.v * a.v * q;
+  const double s = 2.5 * a.v * q;
 #pragma unroll
   for (int k = 0; k < kNV; k++) r.d[k] = s * a.d[k];
   return r;
@@ -144,35 +148,33 @@ __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ double val(const D4 &x) { return x.v; }
 __device__ __forceinline__ double dexp(double a) { return exp(a); }
 __device__ __forceinline__ double dlog(double a) { return log(a); }
-__device__ __forceinline__ double dpow(double a, double e) { return pow(a, e); }
+__device__ __forceinline__ double dpow52(double a) { return a * a * sqrt(a); }
 // the promotion of a value to a dual number with zero derivatives
 __device__ __forceinline__ D4 dual(double a) { return cst(a); }
 __device__ __forceinline__ D4 dual(const D4 &a) { return a; }
 
 // ------------------------------------------------------------- properties
 // piecewise-linear interpolation of column c of an n x 3 table on its closed
-// interval, constant beyond the ends (the end segments' slopes at the ends)
-__device__ double table(const double *tab, int n, int c, double s) {
+// interval, constant beyond the ends (the end segments' slopes at the ends);
+// slope[2 i + c - 1] is the slope of column c on segment i (set on the host)
+__device__ double table(const double *tab, const double *slope, int n, int c, double s) {
   if (s < tab[0]) return tab[c];
   if (s > tab[(n - 1) * 3]) return tab[(n - 1) * 3 + c];
   int i = 0;
   while (i + 1 < n - 1 && s >= tab[(i + 1) * 3]) i++;
-  const double x0 = tab[i * 3], x1 = tab[(i + 1) * 3], y0 = tab[i * 3 + c], y1 = tab[(i + 1) * 3 + c];
-  const double slope = (y1 - y0) / (x1 - x0);
-  return y0 + slope * (s - x0);
+  return tab[i * 3 + c] + slope[2 * i + c - 1] * (s - tab[i * 3]);
 }
 
-__device__ D4 table(const double *tab, int n, int c, const D4 &s) {
+__device__ D4 table(const double *tab, const double *slope, int n, int c, const D4 &s) {
   if (s.v < tab[0]) return cst(tab[c]);
   if (s.v > tab[(n - 1) * 3]) return cst(tab[(n - 1) * 3 + c]);
   int i = 0;
   while (i + 1 < n - 1 && s.v >= tab[(i + 1) * 3]) i++;
-  const double x0 = tab[i * 3], x1 = tab[(i + 1) * 3], y0 = tab[i * 3 + c], y1 = tab[(i + 1) * 3 + c];
-  const double slope = (y1 - y0) / (x1 - x0);
+  const double sl = slope[2 * i + c - 1];
   D4 r;
-  r.v = y0 + slope * (s.v - x0);
+  r.v = tab[i * 3 + c] + sl * (s.v - tab[i * 3]);
 #pragma unroll
-  for (int k = 0; k < kNV; k++) r.d[k] = slope * s.d[k];
+  for (int k = 0; k < kNV; k++) r.d[k] = sl * s.d[k];
   return r;
 }
 
@@ -207,11 +209,11 @@ __device__ D4 rk_z(const D4 &A, const D4 &B) {
   const double c1 = a - b - b * b;
   const double z = rk_z(a, b);
   const double fz = (3.0 * z - 2.0) * z + c1;
-  const double fa = z - b, fb = -z - 2.0 * b * z - a;
+  const double fa = z - b, fb = -z - 2.0 * b * z - a, ifz = 1.0 / fz;
   D4 r;
   r.v = z;
 #pragma unroll
-  for (int k = 0; k < kNV; k++) r.d[k] = -(fa * A.d[k] + fb * B.d[k]) / fz;
+  for (int k = 0; k < kNV; k++) r.d[k] = -(fa * A.d[k] + fb * B.d[k]) * ifz;
   return r;
 }
 
@@ -232,8 +234,9 @@ __device__ void cell_props(const trs_thermal_params &P, const ThermalTables &tb,
   o.rho[1] = P.rho_o_ref * dexp(P.cp_o * dp - P.ct1_o * dT - 0.5 * P.ct2_o * dT * dT + P.cpt_o * dp * dT);
   {
     const double TcK = P.tc_w + 273.15;
-    const N A = 0.427480 * (p / P.pc_w) * dpow(TcK / TK, 2.5);
-    const N B = 0.086640 * (p / P.pc_w) * (TcK / TK);
+    const N pr = p * (1.0 / P.pc_w), tr = TcK / TK;
+    const N A = 0.427480 * pr * dpow52(tr);
+    const N B = 0.086640 * pr * tr;
     const N Z = rk_z(A, B);
     o.rho[2] = p / (Z * P.R_gas * TK);
   }
@@ -241,9 +244,9 @@ __device__ void cell_props(const trs_thermal_params &P, const ThermalTables &tb,
   mu[0] = P.avisc_w * dexp(P.bvisc_w / TK);
   mu[1] = P.avisc_o * dexp(P.bvisc_o / TK);
   mu[2] = P.mug_a + P.mug_b * T;
-  const N krw = table(tb.swt, tb.nswt, 1, Sw), krow = table(tb.swt, tb.nswt, 2, Sw);
+  const N krw = table(tb.swt, tb.swt_slope, tb.nswt, 1, Sw), krow = table(tb.swt, tb.swt_slope, tb.nswt, 2, Sw);
   const N Sl = 1.0 - Sg;
-  const N krg = table(tb.slt, tb.nslt, 1, Sl), krog = table(tb.slt, tb.nslt, 2, Sl);
+  const N krg = table(tb.slt, tb.slt_slope, tb.nslt, 1, Sl), krog = table(tb.slt, tb.slt_slope, tb.nslt, 2, Sl);
   const double krocw = tb.swt[2];
   N kro = krocw * ((krow / krocw + krw) * (krog / krocw + krg) - krw - krg);
   if (val(kro) < 0.0) kro = kro * 0.0;
@@ -396,7 +399,7 @@ __device__ __forceinline__ double prop<double>(const double *base, int64_t nc, i
 // cell's quantities enter as plain values.
 template <bool WC>
 __device__ void face_flux(const double *props, int64_t nc, int64_t c, int64_t j, const double *u, double Tgeo,
-                          double al, double zc, double zj, D4 (&F)[3]) {
+                          double al, double zc, double zj, D4 (&F)[3], bool *tie = nullptr) {
   using NC = typename std::conditional<WC, D4, double>::type;
   using NJ = typename std::conditional<WC, double, D4>::type;
   const NC pc = unknown<NC>(u[c * kNV], 0), Swc = unknown<NC>(u[c * kNV + 1], 1),
@@ -413,6 +416,7 @@ __device__ void face_flux(const double *props, int64_t nc, int64_t c, int64_t j,
     const D4 ssum = dual(Sc[a] + Sj[a]);
     const D4 gbar = ssum.v > 0.0 ? (Sc[a] * gc + Sj[a] * gj) / ssum : 0.5 * (gc + gj);
     const D4 dphi = (pc - pj) - gbar * (zc - zj);
+    if (tie && dphi.v == 0.0) *tie = true;
     D4 f, fH;
     if (dphi.v >= 0.0) {   // c upstream
       const NC lam = prop<NC>(props, nc, c, a), H = prop<NC>(props, nc, c, 3 + a);
@@ -434,14 +438,74 @@ __device__ void face_flux(const double *props, int64_t nc, int64_t c, int64_t j,
   F[2] = F[2] + al * kt * (Tc - Tj);
 }
 
-// Per cell row: the six faces and the perforations, added to the
+// Geometric factors of the face between c and j along axis (0 x, 1 y, 2 z):
+// T_geo = c_u k_h A / L with the harmonic mean of the permeabilities (vertical
+// ones times kv/kh), and A / L for conduction.
+__device__ __forceinline__ double face_tgeo(const trs_thermal_params &P, const double *perm, int64_t c, int64_t j,
+                                           int axis, double &al) {
+  al = axis == 0 ? P.dy * P.dz / P.dx : (axis == 1 ? P.dx * P.dz / P.dy : P.dx * P.dy / P.dz);
+  const double ki = perm[c], kj = perm[j];
+  double kh = (ki + kj > 0.0) ? 2.0 * ki * kj / (ki + kj) : 0.0;
+  if (axis == 2) kh = kh * P.kvkh;
+  return kUnit * kh * al;
+}
+
+// Face terms kept for the row kernel, per cell c and positive axis (the face
+// to c + e_x, c + e_y, c + e_z), structure of arrays: the flux F out of c (3),
+// dF/du_c (12), dF/du_j (12), and 1.0 when a phase potential difference is
+// exactly zero (then each side takes itself as upstream and the two rows'
+// fluxes are not negatives of each other).
+constexpr int kFaceDoubles = 28;
+
+// Per face, once: the flux out of c and its derivatives with respect to both
+// cells.  Row j sees the flux -F, so the off-diagonal blocks of both rows are
+// written here: row c's column j is dF/du_j, row j's column c is -dF/du_c.
+// Thread (c, axis): blockIdx.y is the axis.
+__global__ void __launch_bounds__(kThreads) k_thermal_faces(Geom g, trs_thermal_params P,
+                                                            const uint8_t *__restrict__ emask,
+                                                            const double *__restrict__ perm,
+                                                            const double *__restrict__ u, const double *props,
+                                                            double *__restrict__ faces, double *ell) {
+  pdl_enter();
+  constexpr int BB = kNV * kNV;
+  const int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (c >= g.nc) return;
+  const int axis = blockIdx.y;
+  const int s = 4 + axis;                 // slots 4, 5, 6: x+, y+, z+
+  if (!((emask[c] >> s) & 1u)) return;
+  const int so = kSlots - 1 - s;          // the same face seen from j
+  const int64_t nc = g.nc, j = c + g.off[s];
+  double al;
+  const double Tgeo = face_tgeo(P, perm, c, j, axis, al);
+  D4 Fc[3], Fj[3];
+  bool tie = false;
+  face_flux<true>(props, nc, c, j, u, Tgeo, al, cell_depth(P, g, c), cell_depth(P, g, j), Fc, &tie);
+  face_flux<false>(props, nc, c, j, u, Tgeo, al, cell_depth(P, g, c), cell_depth(P, g, j), Fj);
+  double *fb = faces + (int64_t)axis * kFaceDoubles * nc + c;
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    fb[(int64_t)e * nc] = Fc[e].v;
+#pragma unroll
+    for (int k = 0; k < kNV; k++) {
+      fb[(int64_t)(3 + e * kNV + k) * nc] = Fc[e].d[k];
+      fb[(int64_t)(15 + e * kNV + k) * nc] = Fj[e].d[k];
+      ell[((int64_t)s * BB + e * kNV + k) * nc + c] = Fj[e].d[k];
+      ell[((int64_t)so * BB + e * kNV + k) * nc + j] = -Fc[e].d[k];
+    }
+  }
+  fb[(int64_t)27 * nc] = tie ? 1.0 : 0.0;
+#pragma unroll
+  for (int k = 0; k < kNV; k++) {
+    ell[((int64_t)s * BB + 3 * kNV + k) * nc + c] = 0.0;
+    ell[((int64_t)so * BB + 3 * kNV + k) * nc + j] = 0.0;
+  }
+}
+
+// Per cell row: the six faces' terms (kept by k_thermal_faces), added to the
 // accumulation part k_thermal_cells left in the residual and the diagonal
-// block; off-diagonal blocks and the well-column tail blocks are written.
-__global__ void __launch_bounds__(kThreads) k_thermal_rows(
-    Geom g, trs_thermal_params P, const uint8_t *__restrict__ emask, const double *__restrict__ perm,
-    const double *__restrict__ u, const double *props, const int64_t *__restrict__ cperf_ptr,
-    const int64_t *__restrict__ cperf_idx, const int64_t *__restrict__ perf_cw, const int32_t *__restrict__ perf_well,
-    const double *__restrict__ wi, const int32_t *__restrict__ well_type, double *ell, double *tval, double *R) {
+// block.
+__global__ void __launch_bounds__(kThreads) k_thermal_rows(Geom g, const uint8_t *__restrict__ emask,
+                                                           const double *__restrict__ faces, double *ell, double *R) {
   pdl_enter();
   constexpr int BB = kNV * kNV;
   const int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -453,35 +517,58 @@ __global__ void __launch_bounds__(kThreads) k_thermal_rows(
 #pragma unroll
   for (int e = 0; e < kNV; e++) rc[e] = R[c * kNV + e];
   const unsigned m = emask[c];
-  const double zc = cell_depth(P, g, c);
   for (int d = 0; d < 6; d++) {
     const int s = d < 3 ? d : d + 1;
     if (!((m >> s) & 1u)) continue;
     const int64_t j = c + g.off[s];
-    const int axis = (d == 2 || d == 3) ? 0 : ((d == 1 || d == 4) ? 1 : 2);
-    const double al = axis == 0 ? P.dy * P.dz / P.dx : (axis == 1 ? P.dx * P.dz / P.dy : P.dx * P.dy / P.dz);
-    const double ki = perm[c], kj = perm[j];
-    double kh = (ki + kj > 0.0) ? 2.0 * ki * kj / (ki + kj) : 0.0;
-    if (axis == 2) kh = kh * P.kvkh;
-    const double Tgeo = kUnit * kh * al;
-    const double zj = cell_depth(P, g, j);
-    D4 Fc[3], Fj[3];
-    face_flux<true>(props, nc, c, j, u, Tgeo, al, zc, zj, Fc);
-    face_flux<false>(props, nc, c, j, u, Tgeo, al, zc, zj, Fj);
+    if (d >= 3) {
+      // c's own face: F out of c and dF/du_c
+      const double *fb = faces + (int64_t)(d - 3) * kFaceDoubles * nc + c;
+#pragma unroll
+      for (int e = 0; e < 3; e++) {
+        rc[e] = rc[e] + fb[(int64_t)e * nc];
+#pragma unroll
+        for (int k = 0; k < kNV; k++) dg[e * kNV + k] = dg[e * kNV + k] + fb[(int64_t)(3 + e * kNV + k) * nc];
+      }
+      continue;
+    }
+    // the face kept by j (d = 0, 1, 2: z-, y-, x-, axis 2 - d): the flux out of
+    // c is -F and its derivative with respect to c is -dF/du_j; a face with a
+    // tie is left to k_thermal_ties
+    const double *fb = faces + (int64_t)(2 - d) * kFaceDoubles * nc + j;
+    if (fb[(int64_t)27 * nc] != 0.0) continue;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
-      rc[e] = rc[e] + Fc[e].v;
+      rc[e] = rc[e] - fb[(int64_t)e * nc];
 #pragma unroll
-      for (int k = 0; k < kNV; k++) {
-        dg[e * kNV + k] = dg[e * kNV + k] + Fc[e].d[k];
-        ell[((int64_t)s * BB + e * kNV + k) * nc + c] = Fj[e].d[k];
-      }
+      for (int k = 0; k < kNV; k++) dg[e * kNV + k] = dg[e * kNV + k] - fb[(int64_t)(15 + e * kNV + k) * nc];
     }
-#pragma unroll
-    for (int k = 0; k < kNV; k++) ell[((int64_t)s * BB + 3 * kNV + k) * nc + c] = 0.0;
   }
-  // perforations: Q > 0 flows into the cell
-  if (cperf_ptr[c] < cperf_ptr[c + 1]) {
+#pragma unroll
+  for (int e = 0; e < BB; e++) ell[((int64_t)kSelf * BB + e) * nc + c] = dg[e];
+#pragma unroll
+  for (int e = 0; e < kNV; e++) R[c * kNV + e] = rc[e];
+}
+
+// Per perforated cell: the perforations' terms, Q > 0 flowing into the cell,
+// added to the residual and the diagonal block; the well-column tail blocks
+// are written.
+__global__ void __launch_bounds__(kThreads) k_thermal_perfs(
+    Geom g, trs_thermal_params P, const double *__restrict__ u, const double *props,
+    const int64_t *__restrict__ cperf_ptr, const int64_t *__restrict__ cperf_idx, const int64_t *__restrict__ perf_cw,
+    const int32_t *__restrict__ perf_well, const double *__restrict__ wi, const int32_t *__restrict__ well_type,
+    double *ell, double *tval, double *R) {
+  pdl_enter();
+  constexpr int BB = kNV * kNV;
+  const int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (c >= g.nc || cperf_ptr[c] == cperf_ptr[c + 1]) return;
+  const int64_t nc = g.nc;
+  double dg[BB], rc[kNV];
+#pragma unroll
+  for (int e = 0; e < BB; e++) dg[e] = ell[((int64_t)kSelf * BB + e) * nc + c];
+#pragma unroll
+  for (int e = 0; e < kNV; e++) rc[e] = R[c * kNV + e];
+  {
     const double pcv = u[c * kNV];
     const int64_t wrow0 = g.nc;
     for (int64_t t = cperf_ptr[c]; t < cperf_ptr[c + 1]; t++) {
@@ -524,6 +611,43 @@ __global__ void __launch_bounds__(kThreads) k_thermal_rows(
   for (int e = 0; e < BB; e++) ell[((int64_t)kSelf * BB + e) * nc + c] = dg[e];
 #pragma unroll
   for (int e = 0; e < kNV; e++) R[c * kNV + e] = rc[e];
+}
+
+// The faces with a tie seen from the cell that does not keep them (its z-,
+// y- or x- face): that side takes itself as upstream, so its flux and
+// derivatives come from its own pair of one-sided passes, added to what
+// k_thermal_rows left in the residual and the diagonal block.
+__global__ void __launch_bounds__(kThreads) k_thermal_ties(Geom g, trs_thermal_params P,
+                                                           const uint8_t *__restrict__ emask,
+                                                           const double *__restrict__ perm,
+                                                           const double *__restrict__ u, const double *props,
+                                                           const double *__restrict__ faces, double *ell, double *R) {
+  pdl_enter();
+  constexpr int BB = kNV * kNV;
+  const int64_t c = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (c >= g.nc) return;
+  const int64_t nc = g.nc;
+  const unsigned m = emask[c];
+  for (int d = 0; d < 3; d++) {
+    if (!((m >> d) & 1u)) continue;
+    const int64_t j = c + g.off[d];
+    const int axis = 2 - d;
+    if (faces[((int64_t)axis * kFaceDoubles + 27) * nc + j] == 0.0) continue;
+    double al;
+    const double Tgeo = face_tgeo(P, perm, c, j, axis, al);
+    D4 Fc[3], Fj[3];
+    face_flux<true>(props, nc, c, j, u, Tgeo, al, cell_depth(P, g, c), cell_depth(P, g, j), Fc);
+    face_flux<false>(props, nc, c, j, u, Tgeo, al, cell_depth(P, g, c), cell_depth(P, g, j), Fj);
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      R[c * kNV + e] += Fc[e].v;
+#pragma unroll
+      for (int k = 0; k < kNV; k++) {
+        ell[((int64_t)kSelf * BB + e * kNV + k) * nc + c] += Fc[e].d[k];
+        ell[((int64_t)d * BB + e * kNV + k) * nc + c] = Fj[e].d[k];
+      }
+    }
+  }
 }
 
 // Per well: injectors sum_m WI_u (p_b - p_m) - q_target; producers
@@ -584,15 +708,27 @@ void launch_thermal(trs_bsr *A, const trs_thermal_params &P, const ThermalTables
                     const double *u, const double *u_old, const uint8_t *gas, const double *wi,
                     const int32_t *well_type, const double *well_target, double *R, cudaStream_t s) {
   const int64_t nc = A->g.nc;
-  if ((int64_t)A->thermal_props.n < (int64_t)kPropDoubles * nc) A->thermal_props.alloc((size_t)kPropDoubles * nc);
+  const int64_t scratch = (int64_t)(kPropDoubles + 3 * kFaceDoubles) * nc;
+  if ((int64_t)A->thermal_props.n < scratch) A->thermal_props.alloc((size_t)scratch);
+  double *faces = A->thermal_props.p + (int64_t)kPropDoubles * nc;
   if (nc) {
     launch_pdl(k_thermal_cells, grid_of(nc), kThreads, 0, s, A->g, P, tb, u, u_old, gas, A->thermal_props.p,
                A->ell.p, R);
     TRS_LAUNCHED();
-    launch_pdl(k_thermal_rows, grid_of(nc), kThreads, 0, s, A->g, P, (const uint8_t *)A->emask.p,
-               perm, u, (const double *)A->thermal_props.p, (const int64_t *)A->cperf_ptr.p,
-               (const int64_t *)A->cperf_idx.p, (const int64_t *)A->perf_cw.p, (const int32_t *)A->perf_well.p, wi,
-               well_type, A->ell.p, A->tval.p, R);
+    launch_pdl(k_thermal_faces, dim3(grid_of(nc), 3), dim3(kThreads), 0, s, A->g, P, (const uint8_t *)A->emask.p,
+               perm, u, (const double *)A->thermal_props.p, faces, A->ell.p);
+    TRS_LAUNCHED();
+    launch_pdl(k_thermal_rows, grid_of(nc), kThreads, 0, s, A->g, (const uint8_t *)A->emask.p, (const double *)faces,
+               A->ell.p, R);
+    TRS_LAUNCHED();
+    if (A->n_perf) {
+      launch_pdl(k_thermal_perfs, grid_of(nc), kThreads, 0, s, A->g, P, u, (const double *)A->thermal_props.p,
+                 (const int64_t *)A->cperf_ptr.p, (const int64_t *)A->cperf_idx.p, (const int64_t *)A->perf_cw.p,
+                 (const int32_t *)A->perf_well.p, wi, well_type, A->ell.p, A->tval.p, R);
+      TRS_LAUNCHED();
+    }
+    launch_pdl(k_thermal_ties, grid_of(nc), kThreads, 0, s, A->g, P, (const uint8_t *)A->emask.p, perm, u,
+               (const double *)A->thermal_props.p, (const double *)faces, A->ell.p, R);
     TRS_LAUNCHED();
   }
   if (A->n_wells) {
@@ -629,6 +765,12 @@ extern "C" trs_status trs_thermal_assemble(trs_bsr *A, const trs_thermal_params 
     tb.nslt = nslt;
     for (int r = 0; r < 3 * nswt; r++) tb.swt[r] = swt[r];
     for (int r = 0; r < 3 * nslt; r++) tb.slt[r] = slt[r];
+    for (int i = 0; i + 1 < nswt; i++)
+      for (int c = 1; c <= 2; c++)
+        tb.swt_slope[2 * i + c - 1] = (swt[3 * (i + 1) + c] - swt[3 * i + c]) / (swt[3 * (i + 1)] - swt[3 * i]);
+    for (int i = 0; i + 1 < nslt; i++)
+      for (int c = 1; c <= 2; c++)
+        tb.slt_slope[2 * i + c - 1] = (slt[3 * (i + 1) + c] - slt[3 * i + c]) / (slt[3 * (i + 1)] - slt[3 * i]);
     for (int r = 1; r < nswt; r++)
       TRS_REQUIRE(swt[3 * r] > swt[3 * (r - 1)], TRS_ERR_INVALID, "table saturations must increase");
     for (int r = 1; r < nslt; r++)

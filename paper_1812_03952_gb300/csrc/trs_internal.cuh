@@ -171,6 +171,9 @@ struct ThermalTables {
   int nswt, nslt;
   double swt[3 * kThermalTableMax];   // S_w, k_rw, k_row
   double slt[3 * kThermalTableMax];   // S_l, k_rg, k_rog
+  // per segment i, the slopes (y_{i+1} - y_i) / (x_{i+1} - x_i) of columns 1, 2
+  double swt_slope[2 * kThermalTableMax];
+  double slt_slope[2 * kThermalTableMax];
 };
 
 struct Geom {

@@ -60,6 +60,12 @@ def _make(synth, case, mode="chamber"):
         u[:s.n_cells, 2] = 0.21
         u[:s.n_cells, 3] = 195.0
         t.gas[:] = 1
+    elif mode == "uniform":
+        # every cell in the first cell's state: each horizontal face (each face
+        # without gravity) has zero potential differences, so each side takes
+        # itself as upstream
+        u[:s.n_cells] = u[0]
+        t.gas[:s.n_cells] = t.gas[0]
     elif mode == "compressed":
         pt = np.array(COMPRESSED)[np.arange(s.n_cells) % len(COMPRESSED)]
         u[:s.n_cells, 0] = pt[:, 0]
@@ -93,7 +99,7 @@ def _compare(J, R, Jo, Ro, rows=None):
         assert np.abs(Rr[:, e] - Ror[:, e]).max() <= 1e-12 * mag, (e, float(np.abs(Rr[:, e] - Ror[:, e]).max() / mag))
 
 
-@pytest.mark.parametrize("mode", ["chamber", "all_gas", "compressed"])
+@pytest.mark.parametrize("mode", ["chamber", "all_gas", "compressed", "uniform"])
 @pytest.mark.parametrize("case", CASES, ids=_cid)
 def test_thermal_jacobian_matches_oracle(trs, oracle, synth, case, mode):
     s, t = _make(synth, case, mode)
