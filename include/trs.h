@@ -465,6 +465,17 @@ uint64_t trs_kernel_launches(void);
  * (host pointers, may be NULL).  Process-wide; not for concurrent solves. */
 trs_status trs_profile_spmv(int32_t enable, double *total_ms, int64_t *launches);
 
+/* Testing the bounded waits.  The Gram-Schmidt kernels of FGMRES stage their
+ * basis tiles through bulk copies completed on mbarriers, and every wait for
+ * a tile gives up after a fixed number of polls: the kernel then makes its
+ * sums NaN, waits (bounded) for its copies still in flight and returns, and
+ * the solve ends with TRS_ERR_NAN.  With extra_bytes > 0 each stage expects
+ * that many bytes more than its copies deliver, so every wait runs out (about
+ * a second per launch) and that path can be tested; 0 restores normal
+ * operation.  Process-wide; extra_bytes must be 0..65536 and a multiple of
+ * 16, else TRS_ERR_INVALID. */
+trs_status trs_test_stall_staged_copies(int32_t extra_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,6 +4,7 @@
 // All reductions are deterministic: a fixed grid, warp shuffles in a fixed
 // pattern, per-block partial sums, and the last block to finish summing the
 // partials in block order.
+#include <atomic>
 #include <mutex>
 
 #include "trs_api_common.cuh"
@@ -652,12 +653,14 @@ __global__ void __launch_bounds__(kThreads) k_resid_p(MatView<T> At, const T *__
     const int64_t nc = At.g.nc;
     T acc = unit ? y[i * B] : T(0);
     const unsigned m = At.emask[i] & (unit ? ~(1u << kSelf) : ~0u);
+    // all slots' loads at once; an absent slot reads row i and adds zero terms
 #pragma unroll
     for (int s = 0; s < kSlots; s++) {
-      if (!((m >> s) & 1u)) continue;
-      const int64_t j = i + At.g.off[s];
+      const bool on = (m >> s) & 1u;
+      const int64_t j = on ? i + At.g.off[s] : i;
 #pragma unroll
-      for (int c = 0; c < B; c++) acc = fma(atp[((int64_t)s * B + c) * nc + i], y[j * B + c], acc);
+      for (int c = 0; c < B; c++)
+        acc = fma(on ? atp[((int64_t)s * B + c) * nc + i] : T(0), y[j * B + c], acc);
     }
     if (m & kTailBit)
     for (int64_t t = At.tptr[i]; t < At.tptr[i + 1]; t++) {
@@ -780,14 +783,23 @@ __device__ __forceinline__ T scalar_rowdot_fn(const ScalarOp<T> &op, int64_t i, 
   T acc = T(0);
   if (op.is_ell) {
     if (i < op.g.nc) {
+      // every slot's loads are issued at once, an absent slot reading row i
+      // and contributing a zero term, so a row costs one memory round trip
       const unsigned m = op.emask[i];
+      T a[kSlots], x[kSlots];
 #pragma unroll
-      for (int s = 0; s < kSlots; s++)
-        if ((m >> s) & 1u) acc = fma(op.ell[(int64_t)s * op.g.nc + i], xv(i + op.g.off[s]), acc);
+      for (int s = 0; s < kSlots; s++) {
+        const bool on = (m >> s) & 1u;
+        a[s] = on ? op.ell[(int64_t)s * op.g.nc + i] : T(0);
+        x[s] = xv(on ? i + op.g.off[s] : i);
+      }
+#pragma unroll
+      for (int s = 0; s < kSlots; s++) acc = fma(a[s], x[s], acc);
       if (!(m & kTailBit)) return acc;
     }
     for (int64_t t = op.tptr[i]; t < op.tptr[i + 1]; t++) acc = fma(op.tval[t], xv((int64_t)op.tcol[t]), acc);
   } else {
+#pragma unroll 4
     for (int64_t p = op.rp[i]; p < op.rp[i + 1]; p++) acc = fma(op.val[p], xv((int64_t)op.col[p]), acc);
   }
   return acc;
@@ -1168,7 +1180,8 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update_dots(const double *__re
 // solve then stops with TRS_ERR_NAN), waits (bounded) for its copies still
 // in flight and finishes.  Needs N even (16-byte aligned vector rows).
 constexpr int kTE = kThreads;   // elements per tile, one per thread
-constexpr int kMbarSpin = 1 << 22;
+constexpr int kMbarSpin = 1 << 20;      // polls of a tile's barrier
+constexpr int kMbarDrain = 1 << 16;     // polls for copies still in flight after a failure
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -1195,8 +1208,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0u;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (int it = 0; it < kMbarSpin; it++)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int polls) {
+  for (int it = 0; it < polls; it++)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1206,7 +1219,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 template <int KM, bool UPD>
 __global__ void __launch_bounds__(kThreads, 1) k_cgs_staged(const double *__restrict__ V, int64_t N, int K,
                                                             const double *__restrict__ h, double *__restrict__ w,
-                                                            double *partial, unsigned int *counter, double *out) {
+                                                            double *partial, unsigned int *counter, double *out,
+                                                            uint32_t tx_extra) {
   extern __shared__ __align__(128) double tile[];   // [2][KM + 1][kTE]: K vectors, then w
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ double sh[KM];
@@ -1227,7 +1241,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgs_staged(const double *__rest
     const uint32_t bytes = (uint32_t)min((int64_t)kTE, N - e0) * 8u;
     double *dst = tile + (size_t)b * (KM + 1) * kTE;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&bar[b], bytes * (uint32_t)(K + 1));
+    mbar_expect_tx(&bar[b], bytes * (uint32_t)(K + 1) + tx_extra);
     for (int u = 0; u < K; u++) bulk_g2s(dst + (size_t)u * kTE, V + (int64_t)u * N + e0, bytes, &bar[b]);
     bulk_g2s(dst + (size_t)KM * kTE, w + e0, bytes, &bar[b]);
   };
@@ -1243,7 +1257,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgs_staged(const double *__rest
     const int64_t tn = t + gridDim.x;
     if (tid == 0 && tn < ntiles) issue(tn, b ^ 1);
     if (tn < ntiles) pending |= 1u << (b ^ 1);
-    const bool ok = mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
+    const bool ok = mbar_wait_bounded(&bar[b], (parity >> b) & 1u, kMbarSpin);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -1290,7 +1304,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgs_staged(const double *__rest
   if (failed) {
     // copies still in flight land before the block leaves (bounded)
     for (int b = 0; b < 2; b++)
-      if ((pending >> b) & 1u) mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
+      if ((pending >> b) & 1u) mbar_wait_bounded(&bar[b], (parity >> b) & 1u, kMbarDrain);
 #pragma unroll
     for (int u = 0; u < KM; u++) acc[u] = __longlong_as_double(0x7ff8000000000000ll);
     ww = __longlong_as_double(0x7ff8000000000000ll);
@@ -1794,12 +1808,15 @@ inline bool stageable(const double *V, int64_t N, const double *w) {
   return N % 2 == 0 && ((uintptr_t)V & 15u) == 0 && ((uintptr_t)w & 15u) == 0;
 }
 
+// bytes each stage expects beyond its copies (trs_test_stall_staged_copies)
+std::atomic<uint32_t> g_stage_stall{0u};
+
 template <int KM, bool UPD>
 void launch_staged(const double *V, int64_t N, int K, const double *h, double *w, const RedScratch &red,
                    double *out, cudaStream_t s) {
   const size_t smem = (size_t)2 * (KM + 1) * kTE * sizeof(double);
   launch_pdl(k_cgs_staged<KM, UPD>, staged_grid(k_cgs_staged<KM, UPD>, smem, (unsigned)red.grid), kThreads, smem,
-             s, V, N, K, h, w, red.partial, red.counter, out);
+             s, V, N, K, h, w, red.partial, red.counter, out, g_stage_stall.load(std::memory_order_relaxed));
 }
 
 void launch_multidot(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
@@ -2034,5 +2051,14 @@ extern "C" trs_status trs_residual_norm_noalloc(const trs_bsr *A, const double *
     TRS_LAUNCHED();
     TRS_CUDA(cudaMemcpyAsync(norm, out + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     TRS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+extern "C" trs_status trs_test_stall_staged_copies(int32_t extra_bytes) {
+  using namespace trs;
+  return guarded([&] {
+    TRS_REQUIRE(extra_bytes >= 0 && extra_bytes <= 65536 && extra_bytes % 16 == 0, TRS_ERR_INVALID,
+                "extra_bytes must be 0..65536 and a multiple of 16");
+    g_stage_stall.store((uint32_t)extra_bytes, std::memory_order_relaxed);
   });
 }

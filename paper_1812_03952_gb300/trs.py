@@ -47,6 +47,7 @@ EXPORTS = (
     "trs_cpr_destroy", "trs_solve_default_opts", "trs_fgmres_solve", "trs_fgmres_solve_host",
     "trs_bicgstab_solve", "trs_bicgstab_solve_host", "trs_solve_adjoint", "trs_outer_product", "trs_chain_theta", "trs_last_error", "trs_version",
     "trs_kernel_launches", "trs_residual_norm_noalloc", "trs_profile_spmv", "trs_thermal_assemble",
+    "trs_test_stall_staged_copies",
 )
 
 
@@ -169,6 +170,7 @@ def load(path: str = LIB_PATH):
         "trs_profile_spmv": (i32, [i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "trs_thermal_assemble": (i32, [vp, C.POINTER(ThermalParams), vp, i32, vp, i32, vp, vp, vp, vp, vp, vp,
                                        vp, vp, vp]),
+        "trs_test_stall_staged_copies": (i32, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -188,6 +190,12 @@ def profile_spmv(enable: bool):
     ms, n = C.c_double(0.0), C.c_int64(0)
     _check(load().trs_profile_spmv(int(enable), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def test_stall_staged_copies(extra_bytes: int):
+    """Testing only: the staged Gram-Schmidt waits expect extra_bytes more
+    than their copies deliver, so they run out (0 restores normal operation)."""
+    _check(load().trs_test_stall_staged_copies(int(extra_bytes)))
 
 
 def _check(code, allow=()):
