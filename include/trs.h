@@ -188,6 +188,10 @@ typedef struct {
  *   the cells of a structured grid (cell c = x + nx*(y + ny*z)) whose
  *   couplings are the 7-point neighbours; other blocks (wells) go to a
  *   general tail.  NULL: every row is stored in the general form.
+ *   The kernels are built for the grid form: in the general form every row
+ *   takes the paths meant for the few long well rows (a warp or a block per
+ *   row), which are correct but slow (on a 1M-cell 7-point system about 11x
+ *   for the SpMV and 46x for a CPR-FGMRES solve).
  * Errors: TRS_ERR_INVALID (checked on the host before any upload),
  *   TRS_ERR_UNSUPPORTED, TRS_ERR_OOM, TRS_ERR_CUDA.  Inputs stay caller-owned. */
 trs_status trs_bsr_create(int64_t n_block_rows, int32_t b, const int64_t *row_ptr,
