@@ -1833,11 +1833,13 @@ void launch_cgs_update(const double *V, int64_t N, int K, const double *h, doubl
 void launch_cgs_dots(const double *V, int64_t N, int K, const double *w, const RedScratch &red, double *out,
                      cudaStream_t s) {
   const unsigned cap = (unsigned)red.grid;
-  if (stageable(V, N, w) && K + 1 <= 32) {
+  // staged up to 16 vectors; at 32 one 135 KB block per SM keeps too few
+  // tiles in flight for a pass of one FMA per element (measured slower than
+  // the register kernel there)
+  if (stageable(V, N, w) && K + 1 <= 16) {
     double *wm = const_cast<double *>(w);   // read only (UPD = false)
     if (K + 1 <= 8) launch_staged<8, false>(V, N, K, nullptr, wm, red, out, s);
-    else if (K + 1 <= 16) launch_staged<16, false>(V, N, K, nullptr, wm, red, out, s);
-    else launch_staged<32, false>(V, N, K, nullptr, wm, red, out, s);
+    else launch_staged<16, false>(V, N, K, nullptr, wm, red, out, s);
   } else if (K + 1 <= 8)
     launch_pdl(k_cgs_dots<8>, resident_grid(k_cgs_dots<8>, cap), kThreads, 0, s, V, N, K, w, red.partial,
                red.counter, out);
