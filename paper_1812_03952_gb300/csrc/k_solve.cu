@@ -1022,6 +1022,8 @@ __global__ void __launch_bounds__(kThreads) k_cgs_update(const double *__restric
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
     double v = w[i];
+    // unrolled so that several basis loads are in flight ahead of the FMA chain
+#pragma unroll 8
     for (int k = 0; k < K; k++) v = fma(-sh[k], V[(int64_t)k * N + i], v);
     w[i] = v;
     acc[0] = fma(v, v, acc[0]);
@@ -1360,6 +1362,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(const TZ *__restrict__ Z, 
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
     double v = x[i];
+#pragma unroll 8
     for (int k = 0; k < K; k++) v = fma(sy[k], to_d(Z[(int64_t)k * N + i]), v);
     x[i] = v;
   }
