@@ -1096,10 +1096,10 @@ __global__ void __launch_bounds__(kThreads) k_multidot(const double *__restrict_
       const double wi = w[i];
       if (last) ww = fma(wi, wi, ww);
 #pragma unroll
-      for (int g = 0; g < KC; g += 4) {
+      for (int g = 0; g < KC; g += 8) {
         if (g < Kc) {
 #pragma unroll
-          for (int u = g; u < g + 4; u++)
+          for (int u = g; u < g + 8; u++)
             if (u < Kc) acc[u] = fma(Vc[(int64_t)u * N + i], wi, acc[u]);
         }
       }
@@ -1120,13 +1120,14 @@ __global__ void __launch_bounds__(kThreads) k_cgs_dots(const double *__restrict_
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
     const double wi = w[i];
     ww = fma(wi, wi, ww);
-    // groups of four: K is the same for every thread, so a group past K is
-    // branched over rather than issued with its lanes masked off
+    // groups of eight: K is the same for every thread, so a group past K is
+    // branched over rather than issued with its lanes masked off, and the
+    // eight loads of a group are in flight together
 #pragma unroll
-    for (int g = 0; g < KM; g += 4) {
+    for (int g = 0; g < KM; g += 8) {
       if (g < K) {
 #pragma unroll
-        for (int u = g; u < g + 4; u++)
+        for (int u = g; u < g + 8; u++)
           if (u < K) acc[u] = fma(V[(int64_t)u * N + i], wi, acc[u]);
       }
     }
